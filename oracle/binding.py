@@ -1,0 +1,318 @@
+"""ctypes binding of the FP64 CPU oracle (test infrastructure only).
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline / reference
+arm import this module.  It converts the neutral parameter dictionaries of
+paper_2503_16955_gb300.workloads into the oracle's own C structures and calls
+liboracle.so; it shares no code with the product's binding.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GEOMETRY = {"flat": 0, "cyl": 1}
+MDF = {"gaussian": 0, "lorentzian": 1, "pseudo_voigt": 2, "vmf": 3, "wl": 4, "swl": 5, "uniform": 6}
+IRC = {"darwin": 0, "darwin_prins": 1, "pseudo_voigt": 2, "gaussian": 3, "lorentzian": 4, "box": 5}
+SRC = {"mono": 0, "gauss": 1, "lorentz": 2, "inv_e": 3, "uniform": 4}
+OUTCOME = {0: "miss", 1: "absorbed", 2: "exit_front", 3: "exit_back", 4: "exit_side",
+           5: "capped", 6: "stuck"}
+MDF_M = 4096
+MDF_T = 256
+MAX_COMP = 16
+
+D3 = C.c_double * 3
+
+
+class Spec(C.Structure):
+    _fields_ = [
+        ("d_spacing_A", C.c_double), ("thickness_mm", C.c_double),
+        ("geometry", C.c_int32), ("mdf", C.c_int32),
+        ("radius_mm", C.c_double),
+        ("centre", D3), ("normal", D3), ("axis", D3),
+        ("centre_axial_mm", C.c_double),
+        ("size_disp_mm", C.c_double), ("size_nondisp_mm", C.c_double),
+        ("mdf_fwhm_rad", C.c_double), ("mdf_eta", C.c_double),
+        ("irc", C.c_int32), ("max_reflections", C.c_int32),
+        ("irc_fwhm_rad", C.c_double), ("irc_lorentz_fwhm_rad", C.c_double),
+        ("irc_shift_rad", C.c_double), ("prins_g", C.c_double),
+        ("absorption_length_mm", C.c_double), ("absorption_ref_keV", C.c_double),
+        ("absorption_power", C.c_double),
+        ("refl_K_per_mm2", C.c_double), ("refl_darwin_fwhm_rad", C.c_double),
+        ("refl_ref_keV", C.c_double),
+        ("max_collisions", C.c_int64),
+        ("det_centre", D3), ("det_u", D3), ("det_v", D3),
+        ("det_nx", C.c_int32), ("det_ny", C.c_int32),
+        ("pixel_mm", C.c_double),
+    ]
+
+
+class Component(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("e0_keV", C.c_double),
+                ("width_keV", C.c_double), ("lo_keV", C.c_double), ("hi_keV", C.c_double),
+                ("weight", C.c_double)]
+
+
+class Source(C.Structure):
+    _fields_ = [("n_comp", C.c_int32), ("pad", C.c_int32), ("comp", Component * MAX_COMP),
+                ("origin", D3), ("axis", D3), ("cone_half_angle_rad", C.c_double),
+                ("spot_fwhm_mm", C.c_double * 2)]
+
+
+class Tally(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("emitted", "miss", "absorbed", "exit_front", "exit_back",
+                                          "exit_side", "capped", "stuck", "no_bragg", "det_hits")] + \
+               [("refl_hist", C.c_uint64 * 16), ("collisions", C.c_uint64)]
+
+    def as_dict(self):
+        d = {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "refl_hist"}
+        d["refl_hist"] = [int(x) for x in self.refl_hist]
+        return d
+
+
+RECORD_DTYPE = np.dtype([
+    ("ray_id", np.uint64), ("outcome", np.int32), ("nrefl", np.int32), ("ncoll", np.int64),
+    ("energy_keV", np.float64), ("pos", np.float64, 3), ("dir", np.float64, 3),
+    ("u_mm", np.float64), ("v_mm", np.float64), ("ix", np.int32), ("iy", np.int32),
+    ("det_hit", np.int32), ("no_bragg", np.int32)])
+
+
+class RayConsts(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("E_keV", "lambda_A", "sin_aB", "alpha_B", "mu0", "Q",
+                                          "mubar", "p_abs")] + [("no_bragg", C.c_int32),
+                                                                ("pad", C.c_int32)]
+
+
+class MdfTable(C.Structure):
+    _fields_ = [("body", C.c_double * MDF_M), ("tail", C.c_double * (MDF_T + 1)), ("qmax", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        dp, u32p, i64p = C.POINTER(C.c_double), C.POINTER(C.c_uint32), C.POINTER(C.c_int64)
+        sig = {
+            "orc_philox4x32_10": (None, [u32p, u32p, u32p]),
+            "orc_pv_width": (None, [C.c_double, C.c_double, dp, dp]),
+            "orc_irc": (C.c_double, [C.POINTER(Spec), C.c_double]),
+            "orc_irc_max": (C.c_double, [C.POINTER(Spec)]),
+            "orc_darwin_prins_area": (C.c_double, [C.c_double]),
+            "orc_mdf_W": (C.c_double, [C.POINTER(Spec), C.c_double]),
+            "orc_mdf_qmax": (C.c_double, [C.POINTER(Spec)]),
+            "orc_mdf_norm": (C.c_double, [C.POINTER(Spec)]),
+            "orc_mdf_cdf": (C.c_double, [C.POINTER(Spec), C.c_double]),
+            "orc_mdf_ccdf": (C.c_double, [C.POINTER(Spec), C.c_double]),
+            "orc_mdf_quantile_exact": (C.c_double, [C.POINTER(Spec), C.c_double, C.c_int, C.c_double]),
+            "orc_mdf_build_table": (C.c_int, [C.POINTER(Spec), C.POINTER(MdfTable)]),
+            "orc_mdf_table_lookup": (C.c_double, [C.POINTER(MdfTable), C.c_uint32]),
+            "orc_ray_constants": (C.c_int, [C.POINTER(Spec), C.c_double, C.POINTER(RayConsts)]),
+            "orc_trace": (C.c_int, [C.POINTER(Spec), C.POINTER(Source), C.c_uint64, C.c_uint64,
+                                    C.c_uint64, C.c_int, i64p, C.POINTER(Tally), C.c_void_p]),
+            "orc_walk_injected": (C.c_int, [C.POINTER(Spec), C.c_double, dp, dp, u32p, C.c_int64,
+                                            C.c_void_p]),
+            "orc_sample_crystallites": (C.c_int64, [C.POINTER(Spec), C.c_double, C.c_double,
+                                                    C.c_int64, C.c_uint64, dp, dp]),
+            "orc_reflection_rate": (C.c_double, [C.POINTER(Spec), C.c_double, C.c_double]),
+            "orc_last_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _err():
+    return lib().orc_last_error().decode()
+
+
+def make_spec(d):
+    """Neutral dict -> oracle Spec."""
+    s = Spec()
+    s.d_spacing_A = d["d_spacing_A"]
+    s.thickness_mm = d["thickness_mm"]
+    s.geometry = GEOMETRY[d["geometry"]]
+    s.mdf = MDF[d["mdf"]]
+    s.radius_mm = d.get("radius_mm", 0.0)
+    s.centre = D3(*d["centre_mm"])
+    s.normal = D3(*d["normal"])
+    s.axis = D3(*d["axis"])
+    s.centre_axial_mm = d.get("centre_axial_mm", 0.0)
+    s.size_disp_mm = d["size_disp_mm"]
+    s.size_nondisp_mm = d["size_nondisp_mm"]
+    s.mdf_fwhm_rad = d["mdf_fwhm_rad"]
+    s.mdf_eta = d.get("mdf_eta", 0.0)
+    s.irc = IRC[d["irc"]]
+    s.max_reflections = d["max_reflections"]
+    s.irc_fwhm_rad = d["irc_fwhm_rad"]
+    s.irc_lorentz_fwhm_rad = d.get("irc_lorentz_fwhm_rad", 0.0)
+    s.irc_shift_rad = d.get("irc_shift_rad", 0.0)
+    s.prins_g = d.get("prins_g", 0.0)
+    s.absorption_length_mm = d["absorption_length_mm"]
+    s.absorption_ref_keV = d.get("absorption_ref_keV", 8.0)
+    s.absorption_power = d.get("absorption_power", 0.0)
+    s.refl_K_per_mm2 = d.get("refl_K_per_mm2", -1.0)
+    s.refl_darwin_fwhm_rad = d.get("refl_darwin_fwhm_rad", d["irc_fwhm_rad"])
+    s.refl_ref_keV = d.get("refl_ref_keV", 8.0)
+    s.max_collisions = d.get("max_collisions", 1_000_000)
+    s.det_centre = D3(*d["det_centre_mm"])
+    s.det_u = D3(*d["det_u"])
+    s.det_v = D3(*d["det_v"])
+    s.det_nx = d["det_nx"]
+    s.det_ny = d["det_ny"]
+    s.pixel_mm = d["pixel_mm"]
+    return s
+
+
+def make_source(d):
+    s = Source()
+    comps = d["components"]
+    if not 1 <= len(comps) <= MAX_COMP:
+        raise ValueError("1..16 spectral components")
+    s.n_comp = len(comps)
+    for i, c in enumerate(comps):
+        s.comp[i].kind = SRC[c["kind"]]
+        s.comp[i].e0_keV = c.get("e0_keV", 0.0)
+        s.comp[i].width_keV = c.get("width_keV", 0.0)
+        s.comp[i].lo_keV = c.get("lo_keV", 0.0)
+        s.comp[i].hi_keV = c.get("hi_keV", 0.0)
+        s.comp[i].weight = c.get("weight", 1.0)
+    s.origin = D3(*d["origin_mm"])
+    s.axis = D3(*d["axis"])
+    s.cone_half_angle_rad = d["cone_half_angle_rad"]
+    sf = d.get("spot_fwhm_mm", (0.0, 0.0))
+    s.spot_fwhm_mm = (C.c_double * 2)(*sf)
+    return s
+
+
+def philox(counter, key):
+    ctr = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in counter])
+    k = (C.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    out = (C.c_uint32 * 4)()
+    lib().orc_philox4x32_10(ctr, k, out)
+    return [int(x) for x in out]
+
+
+def pv_width(fg, fl):
+    F, eta = C.c_double(), C.c_double()
+    lib().orc_pv_width(fg, fl, C.byref(F), C.byref(eta))
+    return F.value, eta.value
+
+
+def irc(spec_dict, x):
+    s = make_spec(spec_dict)
+    return np.array([lib().orc_irc(C.byref(s), float(v)) for v in np.atleast_1d(x)])
+
+
+def irc_max(spec_dict):
+    s = make_spec(spec_dict)
+    return lib().orc_irc_max(C.byref(s))
+
+
+def darwin_prins_area(g):
+    return lib().orc_darwin_prins_area(g)
+
+
+def mdf_W(spec_dict, q):
+    s = make_spec(spec_dict)
+    return np.array([lib().orc_mdf_W(C.byref(s), float(v)) for v in np.atleast_1d(q)])
+
+
+def mdf_norm(spec_dict):
+    s = make_spec(spec_dict)
+    return lib().orc_mdf_norm(C.byref(s))
+
+
+def mdf_qmax(spec_dict):
+    s = make_spec(spec_dict)
+    return lib().orc_mdf_qmax(C.byref(s))
+
+
+def mdf_cdf(spec_dict, q):
+    s = make_spec(spec_dict)
+    return lib().orc_mdf_cdf(C.byref(s), q)
+
+
+def mdf_ccdf(spec_dict, q):
+    s = make_spec(spec_dict)
+    return lib().orc_mdf_ccdf(C.byref(s), q)
+
+
+def mdf_quantile_exact(spec_dict, u=0.0, comp=None):
+    s = make_spec(spec_dict)
+    if comp is not None:
+        return lib().orc_mdf_quantile_exact(C.byref(s), 0.0, 1, comp)
+    return lib().orc_mdf_quantile_exact(C.byref(s), u, 0, 0.0)
+
+
+def mdf_table(spec_dict):
+    s = make_spec(spec_dict)
+    t = MdfTable()
+    if lib().orc_mdf_build_table(C.byref(s), C.byref(t)) != 0:
+        raise RuntimeError(_err())
+    return t
+
+
+def mdf_table_lookup(table, words):
+    return np.array([lib().orc_mdf_table_lookup(C.byref(table), int(w)) for w in np.atleast_1d(words)])
+
+
+def ray_constants(spec_dict, E):
+    s = make_spec(spec_dict)
+    c = RayConsts()
+    lib().orc_ray_constants(C.byref(s), E, C.byref(c))
+    return {n: getattr(c, n) for n, _ in RayConsts._fields_ if n != "pad"}
+
+
+def trace(spec_dict, source_dict, n_rays, seed, ray_offset=0, n_threads=0, records=False):
+    """Trace n_rays; returns (int64 image [ny, nx], tally dict, records or None)."""
+    s = make_spec(spec_dict)
+    src = make_source(source_dict)
+    img = np.zeros((spec_dict["det_ny"], spec_dict["det_nx"]), dtype=np.int64)
+    tal = Tally()
+    rec = np.zeros(n_rays, dtype=RECORD_DTYPE) if records else None
+    rc = lib().orc_trace(C.byref(s), C.byref(src), n_rays, seed, ray_offset, n_threads,
+                         img.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(tal),
+                         rec.ctypes.data if records else None)
+    if rc != 0:
+        raise RuntimeError(_err())
+    return img, tal.as_dict(), rec
+
+
+def walk_injected(spec_dict, E, pos, direction, words):
+    s = make_spec(spec_dict)
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32))
+    rec = np.zeros(1, dtype=RECORD_DTYPE)
+    p = D3(*pos)
+    d = D3(*direction)
+    rc = lib().orc_walk_injected(C.byref(s), E, p, d, w.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                 len(w), rec.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(_err())
+    return rec[0]
+
+
+def sample_crystallites(spec_dict, E, alpha, n, seed):
+    s = make_spec(spec_dict)
+    dl = np.zeros(n)
+    ps = np.zeros(n)
+    got = lib().orc_sample_crystallites(C.byref(s), E, alpha, n, seed,
+                                        dl.ctypes.data_as(C.POINTER(C.c_double)),
+                                        ps.ctypes.data_as(C.POINTER(C.c_double)))
+    return dl[:got], ps[:got]
+
+
+def reflection_rate(spec_dict, E, alpha):
+    s = make_spec(spec_dict)
+    return lib().orc_reflection_rate(C.byref(s), E, alpha)
+
+
+def n_threads_default():
+    return os.cpu_count() or 1

@@ -1,0 +1,169 @@
+/*
+ * heart_oracle.h -- plain FP64 CPU oracle of the mosaic-crystal ray path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product (the package, its CUDA
+ * kernels, its C-ABI library) includes, links or calls this code.  Only the
+ * tests, __graft_entry__.smoke() and bench.py's cpu_baseline / reference arm
+ * load liboracle.so.  The oracle shares no header, helper, table generator or
+ * constant with the GPU path; the two agree only through the written
+ * specification of the sampling model (Section 2 of the paper, restated in the
+ * header comment of oracle.c).
+ *
+ * Every routine is the slow, obviously-correct form: positions in the global
+ * frame, libm transcendental functions, adaptive Simpson quadrature, no
+ * blocking or reordering beyond the paper's algorithm.
+ *
+ * Parity status per function (pins live in tests/test_oracle_*.py):
+ *   orc_philox4x32_10        pinned (PyTorch's Philox engine on matched key/counter)
+ *   orc_pv_width             pinned (54.3 and 110.8 urad printed in Sec. 4.2)
+ *   orc_irc                  pinned (unit area; Darwin 8/3 integral; DP -> Darwin as g -> 0)
+ *   orc_mdf_*                pinned (closed-form quantiles of vMF, WL, SWL, uniform; sphere norms)
+ *   orc_trace                pinned (Beer-Lambert, reflection rate vs quadrature of Eq. ReflXsection,
+ *                                    von Hamos focus 2R cot(aB), conservation, thread invariance,
+ *                                    hand-traced injected-uniform walks)
+ *   orc_reflection_rate      pinned (small-Gamma limit Eq. SimpleZachXsection for vMF)
+ *   orc_sample_crystallites  pinned (accepted Delta ~ IRC; psi ~ W(theta(psi)), Appendix Method II)
+ *   absolute reflectivity / detector image shapes against experiment: parity unpinned
+ *   (the paper's measured spectra are not available).
+ */
+#ifndef HEART_ORACLE_H
+#define HEART_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* geometry, mosaic distribution (MDF), intrinsic rocking curve (IRC) and
+ * spectral-component codes: the numbering is part of the written interface
+ * convention shared with the product by specification only. */
+enum { ORC_FLAT = 0, ORC_CYL = 1 };
+enum { ORC_MDF_GAUSSIAN = 0, ORC_MDF_LORENTZIAN = 1, ORC_MDF_PSEUDO_VOIGT = 2,
+       ORC_MDF_VMF = 3, ORC_MDF_WL = 4, ORC_MDF_SWL = 5, ORC_MDF_UNIFORM = 6 };
+enum { ORC_IRC_DARWIN = 0, ORC_IRC_DARWIN_PRINS = 1, ORC_IRC_PSEUDO_VOIGT = 2,
+       ORC_IRC_GAUSSIAN = 3, ORC_IRC_LORENTZIAN = 4, ORC_IRC_BOX = 5 };
+enum { ORC_SRC_MONO = 0, ORC_SRC_GAUSS = 1, ORC_SRC_LORENTZ = 2, ORC_SRC_INV_E = 3,
+       ORC_SRC_UNIFORM = 4 };
+enum { ORC_MISS = 0, ORC_ABSORBED = 1, ORC_EXIT_FRONT = 2, ORC_EXIT_BACK = 3,
+       ORC_EXIT_SIDE = 4, ORC_CAPPED = 5, ORC_STUCK = 6 };
+
+#define ORC_MDF_M 4096        /* body quantile knots, uniform in u          */
+#define ORC_MDF_T 256         /* tail intervals, uniform in -log2(1-u)      */
+#define ORC_MAX_COMP 16
+
+typedef struct {
+    double d_spacing_A;       /* d_H of Eq. BraggLaw, Angstrom */
+    double thickness_mm;
+    int32_t geometry;         /* ORC_FLAT / ORC_CYL */
+    int32_t mdf;
+    double radius_mm;         /* cylinder: radius of the reflecting (inner) face */
+    double centre[3];         /* flat: centre of front face; cyl: point on the axis */
+    double normal[3];         /* flat: front-face normal N; cyl: direction axis -> crystal centre */
+    double axis[3];           /* flat: dispersive in-plane direction; cyl: cylinder axis */
+    double centre_axial_mm;   /* cyl: axial coordinate of the crystal centre */
+    double size_disp_mm;      /* flat: extent along axis; cyl: axial length */
+    double size_nondisp_mm;   /* flat: extent along N x axis; cyl: arc length on r = R */
+    double mdf_fwhm_rad;      /* Gamma */
+    double mdf_eta;           /* pseudo-Voigt Lorentzian fraction */
+    int32_t irc;
+    int32_t max_reflections;
+    double irc_fwhm_rad;      /* Darwin / DP: Darwin (g=0) FWHM; G, L, box: FWHM; pV: Gaussian FWHM */
+    double irc_lorentz_fwhm_rad;  /* pV: Lorentzian FWHM */
+    double irc_shift_rad;     /* Delta_M */
+    double prins_g;           /* Darwin-Prins absorption parameter */
+    double absorption_length_mm, absorption_ref_keV, absorption_power;
+    double refl_K_per_mm2;    /* |r_e F_H / V| in mm^-2; < 0: derive from the Darwin width */
+    double refl_darwin_fwhm_rad, refl_ref_keV;
+    int64_t max_collisions;   /* per-ray cap on tentative collisions (STUCK) */
+    double det_centre[3], det_u[3], det_v[3];
+    int32_t det_nx, det_ny;
+    double pixel_mm;
+} orc_spec;
+
+typedef struct { int32_t kind; int32_t pad; double e0_keV, width_keV, lo_keV, hi_keV, weight; } orc_component;
+
+typedef struct {
+    int32_t n_comp; int32_t pad;
+    orc_component comp[ORC_MAX_COMP];
+    double origin[3], axis[3];
+    double cone_half_angle_rad;
+    double spot_fwhm_mm[2];
+} orc_source;
+
+typedef struct {
+    uint64_t emitted, miss, absorbed, exit_front, exit_back, exit_side, capped, stuck,
+             no_bragg, det_hits, refl_hist[16], collisions;
+} orc_tally;
+
+/* one record per traced ray (tests only) */
+typedef struct {
+    uint64_t ray_id;
+    int32_t outcome, nrefl;
+    int64_t ncoll;
+    double energy_keV;
+    double pos[3];            /* exit point, absorption point, or entry-less origin */
+    double dir[3];            /* final direction */
+    double u_mm, v_mm;        /* detector-plane coordinates (NaN if no plane hit) */
+    int32_t ix, iy;           /* pixel (-1 if outside) */
+    int32_t det_hit, no_bragg;
+} orc_record;
+
+typedef struct {
+    double body[ORC_MDF_M];       /* q = 1 - cos(theta) at u = i / M            */
+    double tail[ORC_MDF_T + 1];   /* q at u = 1 - 2^-tau_j, tau_j = 12 + 21 j/T */
+    double qmax;
+} orc_mdf_table;
+
+typedef struct {
+    double E_keV, lambda_A, sin_aB, alpha_B, mu0, Q, mubar, p_abs;
+    int32_t no_bragg, pad;
+} orc_ray_consts;
+
+/* Philox4x32-10 (Salmon et al., SC'11) */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* pseudo-Voigt total width and eta (Sec. 2.2.1) */
+void orc_pv_width(double fg, double fl, double *fwhm, double *eta);
+
+/* IRC, unit area, argument = Delta - Delta_M (rad) */
+double orc_irc(const orc_spec *s, double x);
+double orc_irc_max(const orc_spec *s);
+double orc_darwin_prins_area(double g);       /* integral of R(y) dy */
+
+/* MDF: un-normalised W as a function of q = 1 - cos(theta) */
+double orc_mdf_W(const orc_spec *s, double q);
+double orc_mdf_qmax(const orc_spec *s);
+double orc_mdf_norm(const orc_spec *s);        /* integral of W dq over [0, qmax] */
+double orc_mdf_cdf(const orc_spec *s, double q);      /* F(q) */
+double orc_mdf_ccdf(const orc_spec *s, double q);     /* 1 - F(q), computed directly */
+double orc_mdf_quantile_exact(const orc_spec *s, double u, int tail_complement, double comp);
+int    orc_mdf_build_table(const orc_spec *s, orc_mdf_table *t);
+double orc_mdf_table_lookup(const orc_mdf_table *t, uint32_t w);
+
+/* per-ray constants (Eq. BraggLaw, Q of Sec. 2.2.3, majorant) */
+int orc_ray_constants(const orc_spec *s, double E_keV, orc_ray_consts *c);
+
+/* full path: source -> entry -> walk -> detector -> image (int64, += ) */
+int orc_trace(const orc_spec *s, const orc_source *src, uint64_t n_rays, uint64_t seed,
+              uint64_t ray_offset, int n_threads, int64_t *image, orc_tally *tally,
+              orc_record *records);
+
+/* the walk of one ray from a given entry state, fed with explicit 32-bit words
+ * (4 per tentative collision) instead of Philox; for hand-traced tests */
+int orc_walk_injected(const orc_spec *s, double E_keV, const double pos[3], const double dir[3],
+                      const uint32_t *words, int64_t n_words, orc_record *rec);
+
+/* accepted crystallites at a fixed ray direction and surface normal:
+ * returns Delta (= alpha~ - alpha_B - Delta_M) and psi of n accepted draws */
+int64_t orc_sample_crystallites(const orc_spec *s, double E_keV, double alpha_rad, int64_t n,
+                                uint64_t seed, double *delta_out, double *psi_out);
+
+/* reflection rate r(alpha) (per mm of path) by 2-D quadrature of Eq. ReflXsection */
+double orc_reflection_rate(const orc_spec *s, double E_keV, double alpha_rad);
+
+const char *orc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
