@@ -1,0 +1,239 @@
+/*
+ * heart.h -- C ABI of the GB300 mosaic-crystal ray tracer.
+ *
+ * The library traces X-ray photons through a mosaic-crystal spectrometer as
+ * described in Gawne et al., "HEART: A New X-Ray Tracing Code for Mosaic
+ * Crystal Spectrometers" (arXiv 2503.16955): rays are sampled from a source
+ * (Sec. 2.1), intersected with a flat or cylindrical (von Hamos) crystal
+ * (Sec. 2.2), walked through the crystal depth with absorption and
+ * mosaic-crystallite reflections (Sec. 2.2.3-2.2.4, Appendix A), and the rays
+ * leaving the crystal are binned into integer detector pixels (Sec. 2.3).
+ * Every step runs in CUDA kernels on the current device.
+ *
+ * Conventions
+ *   Units: mm, keV, rad.  Vectors are 3 doubles in one global frame.
+ *   Ownership: descriptors are host memory read during the call and not kept.
+ *     Spectrometer tables live in device memory owned by the handle until
+ *     heart_spectrometer_destroy.  Images passed to heart_trace are
+ *     caller-owned device memory; the library adds counts (+=) and never
+ *     clears them.  Server job images are owned by the server until
+ *     heart_release.
+ *   Errors: every call returns a heart_status; nothing throws across the ABI.
+ *     heart_last_error() returns a thread-local message for the last failure
+ *     in the calling thread.  Invalid descriptors, null or misaligned
+ *     pointers return HEART_EINVAL before any launch.
+ *   Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls on one spectrometer handle must not overlap in time
+ *     (they share its tally scratch buffer): use one stream per handle or
+ *     synchronise between calls.
+ *   Determinism: each ray owns a Philox4x32-10 stream keyed by the seed and
+ *     addressed by its ray id (ray_offset + i), so images and tallies do not
+ *     depend on launch shape, chunking or concurrent jobs.
+ */
+#ifndef HEART_H
+#define HEART_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HEART_OK = 0,
+    HEART_EINVAL = 1,     /* bad argument or descriptor                      */
+    HEART_ENOMEM = 2,     /* device or host allocation failed / over the cap */
+    HEART_ECUDA = 3,      /* a CUDA runtime call failed                      */
+    HEART_EBUSY = 4,      /* heart_poll: job not finished yet                */
+    HEART_ETIMEOUT = 5,   /* heart_poll: timeout elapsed                     */
+    HEART_ELIMIT = 6,     /* at least one ray hit the per-ray collision cap  */
+    HEART_ENOTFOUND = 7   /* unknown job id                                  */
+} heart_status;
+
+typedef enum { HEART_FLAT = 0, HEART_CYL_VON_HAMOS = 1 } heart_geometry;
+
+/* mosaic distribution functions W(theta) (Sec. 2.2.2) */
+typedef enum {
+    HEART_MDF_GAUSSIAN = 0,          /* Eq. (Gaussian) in theta               */
+    HEART_MDF_LORENTZIAN = 1,        /* Eq. (Lorentz) in theta                */
+    HEART_MDF_PSEUDO_VOIGT = 2,      /* eta L + (1 - eta) G, shared FWHM      */
+    HEART_MDF_VMF = 3,               /* Eq. (MF), von Mises-Fisher            */
+    HEART_MDF_WRAPPED_LORENTZIAN = 4,/* Eq. (WL)                              */
+    HEART_MDF_SPHERICAL_WRAPPED_LORENTZIAN = 5, /* Eq. (SWL)                  */
+    HEART_MDF_UNIFORM = 6            /* constant for theta <= Gamma / 2       */
+} heart_mdf;
+
+/* intrinsic rocking curves, unit area (Sec. 2.2.1) */
+typedef enum {
+    HEART_IRC_DARWIN = 0,            /* Darwin curve, FWHM = (3/sqrt 2) delta */
+    HEART_IRC_DARWIN_PRINS = 1,      /* Darwin-Prins with absorption g        */
+    HEART_IRC_PSEUDO_VOIGT = 2,      /* pseudo-Voigt from Gaussian/Lorentz FWHM */
+    HEART_IRC_GAUSSIAN = 3,
+    HEART_IRC_LORENTZIAN = 4,
+    HEART_IRC_BOX = 5
+} heart_irc;
+
+typedef enum { HEART_FP64 = 0, HEART_FP32 = 1 } heart_precision;
+typedef enum { HEART_COUNT_I32 = 0, HEART_COUNT_I64 = 1 } heart_count_type;
+
+/* spectral component kinds (Sec. 2.1: an intensity profile used as a PDF) */
+typedef enum {
+    HEART_SRC_MONO = 0,      /* delta at e0                               */
+    HEART_SRC_GAUSS = 1,     /* Gaussian, sigma = width                   */
+    HEART_SRC_LORENTZ = 2,   /* Lorentzian, FWHM = width, truncated E > 0 */
+    HEART_SRC_INV_E = 3,     /* 1/E on [lo, hi]                           */
+    HEART_SRC_UNIFORM = 4    /* uniform on [lo, hi]                       */
+} heart_source_kind;
+
+/* ray outcomes (Sec. 2.2.4) */
+typedef enum {
+    HEART_MISS = 0, HEART_ABSORBED = 1, HEART_EXIT_FRONT = 2, HEART_EXIT_BACK = 3,
+    HEART_EXIT_SIDE = 4, HEART_CAPPED = 5, HEART_STUCK = 6
+} heart_outcome;
+
+typedef struct heart_spectrometer heart_spectrometer;
+typedef struct heart_server heart_server;
+
+/*
+ * Crystal and detector (Sec. 2.2 crystal classes, Sec. 2.3 detector).
+ * Flat: the crystal occupies the slab -thickness <= (x - centre).N <= 0,
+ *   |(x - centre).e_d| <= size_disp/2, |(x - centre).(N x e_d)| <= size_nondisp/2,
+ *   with N = normal and e_d = axis projected perpendicular to N.
+ * Cylindrical (von Hamos): the shell R <= r <= R + thickness around the line
+ *   through `centre` along `axis`; axial coordinate within
+ *   centre_axial +- size_disp/2; azimuth within +- size_nondisp/(2R) of the
+ *   direction `normal` (projected perpendicular to the axis).  The inner face
+ *   r = R reflects; the local normal points toward the axis.
+ * Detector: plane through det_centre spanned by det_u, det_v (orthonormalised);
+ *   pixel (ix, iy) = floor(u/pixel + nx/2), floor(v/pixel + ny/2); either face.
+ */
+typedef struct {
+    double d_spacing_A;             /* lattice spacing d_H, Eq. (BraggLaw)     */
+    double thickness_mm;
+    int32_t geometry;               /* heart_geometry */
+    int32_t mdf;                    /* heart_mdf */
+    double radius_mm;               /* cylinder radius (inner face)            */
+    double centre_mm[3];
+    double normal[3];
+    double axis[3];
+    double centre_axial_mm;         /* cylinder only */
+    double size_disp_mm, size_nondisp_mm;
+    double mdf_fwhm_rad;            /* Gamma */
+    double mdf_eta;                 /* pseudo-Voigt MDF Lorentzian fraction */
+    int32_t irc;                    /* heart_irc */
+    int32_t max_reflections;        /* the (n+1)-th reflection ends the ray as CAPPED */
+    double irc_fwhm_rad;            /* Darwin/DP: Darwin FWHM; G/L/box: FWHM; pV: Gaussian FWHM */
+    double irc_lorentz_fwhm_rad;    /* pV: Lorentzian FWHM */
+    double irc_shift_rad;           /* Delta_M, peak position of the IRC */
+    double prins_g;                 /* Darwin-Prins absorption parameter */
+    double absorption_length_mm;    /* 1/mu0 at absorption_ref_keV */
+    double absorption_ref_keV;
+    double absorption_power;        /* l_abs(E) = l_ref (E / E_ref)^power */
+    double refl_K_per_mm2;          /* K = |r_e F_H / V|; < 0: derive from refl_darwin_fwhm_rad */
+    double refl_darwin_fwhm_rad;    /* Darwin FWHM at refl_ref_keV (used when K < 0) */
+    double refl_ref_keV;
+    int64_t max_collisions;         /* per-ray cap on tentative collisions (STUCK) */
+    double det_centre_mm[3], det_u[3], det_v[3];
+    int32_t det_nx, det_ny;
+    double pixel_mm;
+    int32_t count_type;             /* heart_count_type of images traced with this handle */
+    int32_t reserved;
+} heart_spectrometer_desc;
+
+typedef struct {
+    int32_t kind;                   /* heart_source_kind */
+    int32_t reserved;
+    double e0_keV, width_keV, lo_keV, hi_keV;
+    double weight;                  /* relative photon share of this component */
+} heart_spectral_component;
+
+/* Point or Gaussian-spot source emitting uniformly in solid angle inside a cone. */
+typedef struct {
+    const heart_spectral_component *components;   /* host array, 1..16 entries */
+    int32_t n_components;
+    int32_t reserved;
+    double origin_mm[3];
+    double axis[3];                 /* cone axis */
+    double cone_half_angle_rad;
+    double spot_fwhm_mm[2];         /* 2-D Gaussian spot perpendicular to the axis */
+} heart_source_desc;
+
+typedef struct {
+    uint64_t emitted, miss, absorbed, exit_front, exit_back, exit_side, capped, stuck;
+    uint64_t no_bragg, det_hits;
+    uint64_t refl_hist[16];         /* rays that entered, by reflections (15 = 15 or more) */
+    uint64_t collisions;            /* tentative collisions (null-collision walk steps inside) */
+} heart_tally;
+
+/* per-ray record (tests and debugging) */
+typedef struct {
+    uint64_t ray_id;
+    int32_t outcome, nrefl;
+    int64_t ncoll;
+    double energy_keV;
+    double pos[3];                  /* exit or absorption point; source origin for MISS */
+    double dir[3];
+    double u_mm, v_mm;              /* detector-plane coordinates, NaN if the plane is not hit */
+    int32_t ix, iy;                 /* pixel, -1 outside */
+    int32_t det_hit, no_bragg;
+} heart_ray_record;
+
+/* Create a spectrometer: validates the descriptor, builds the mosaic
+ * inverse-CDF table and IRC constants on the current device.  Returns
+ * HEART_EINVAL for an invalid descriptor, HEART_ENOMEM / HEART_ECUDA on
+ * device failures. */
+heart_status heart_spectrometer_create(const heart_spectrometer_desc *desc, heart_spectrometer **out);
+heart_status heart_spectrometer_destroy(heart_spectrometer *spec);
+
+/* Trace rays ray_offset .. ray_offset + n_rays - 1 (Sec. 2.2.4: n_rays counts
+ * emitted rays, misses included) and add their detector hits to d_image
+ * (device, det_ny x det_nx row-major, int32 or int64 per the descriptor,
+ * aligned to its element size).  precision selects the plain FP64 kernel or
+ * the FP32 persistent kernel.  If `out` is non-NULL the call synchronises
+ * `stream` and fills the tallies; returns HEART_ELIMIT (after filling) if a
+ * ray hit the collision cap. */
+heart_status heart_trace(heart_spectrometer *spec, const heart_source_desc *src, uint64_t n_rays,
+                         uint64_t seed, uint64_t ray_offset, void *d_image,
+                         heart_precision precision, void *stream, heart_tally *out);
+
+/* As heart_trace, with host memory: h_image (host, += ) is copied to the
+ * device, traced and copied back inside the call.  Synchronous. */
+heart_status heart_trace_host(heart_spectrometer *spec, const heart_source_desc *src,
+                              uint64_t n_rays, uint64_t seed, uint64_t ray_offset, void *h_image,
+                              heart_precision precision, heart_tally *out);
+
+/* As heart_trace, and also writes one heart_ray_record per ray to d_records
+ * (device, n_rays entries).  d_image may be NULL.  Synchronous. */
+heart_status heart_trace_records(heart_spectrometer *spec, const heart_source_desc *src,
+                                 uint64_t n_rays, uint64_t seed, uint64_t ray_offset,
+                                 void *d_image, heart_precision precision, void *d_records,
+                                 void *stream, heart_tally *out);
+
+/* Many spectrometers of uneven ray counts in one persistent FP32 launch
+ * (work items = (job, ray range) claimed by blocks).  specs[i], srcs[i],
+ * n_rays[i], seeds[i], d_images[i] describe job i; out (may be NULL) receives
+ * n_jobs tallies after a stream synchronisation. */
+heart_status heart_trace_batch(heart_spectrometer *const *specs, const heart_source_desc *const *srcs,
+                               const uint64_t *n_rays, const uint64_t *seeds, void *const *d_images,
+                               int32_t n_jobs, void *stream, heart_tally *out);
+
+/* Request loop: jobs are admitted while their images fit under mem_cap_bytes,
+ * batched into persistent launches as they arrive, and polled for results. */
+heart_status heart_server_create(size_t mem_cap_bytes, heart_server **out);
+heart_status heart_server_destroy(heart_server *server);
+heart_status heart_submit(heart_server *server, heart_spectrometer *spec, const heart_source_desc *src,
+                          uint64_t n_rays, uint64_t seed, heart_precision precision, uint64_t *job_id);
+/* HEART_OK when done (tallies and a device image pointer valid until
+ * heart_release), HEART_ETIMEOUT if not done within timeout_ms (0 = do not
+ * wait, returns HEART_EBUSY), HEART_ENOTFOUND for an unknown id. */
+heart_status heart_poll(heart_server *server, uint64_t job_id, int32_t timeout_ms, heart_tally *out,
+                        const void **d_image_out);
+heart_status heart_release(heart_server *server, uint64_t job_id);
+
+const char *heart_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

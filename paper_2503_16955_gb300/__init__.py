@@ -1,0 +1,348 @@
+"""GB300-native mosaic-crystal X-ray ray tracer (the per-ray transport of HEART,
+arXiv 2503.16955) -- thin Python binding of the C-ABI library libheart.so.
+
+The binding only marshals arguments: every step of the ray path runs in the
+library's CUDA kernels.  PyTorch provides device memory and streams.  If the
+library is missing the calls raise; there is no CPU fallback.
+
+Functions carry the C names of include/heart.h:
+    heart_spectrometer_create(desc) -> Spectrometer
+    heart_trace(spec, source, n_rays, seed, ray_offset, d_image, precision, stream) -> tally
+    heart_trace_host(spec, source, n_rays, seed, ray_offset, h_image, precision) -> tally
+    heart_trace_records(spec, source, n_rays, seed, ray_offset, precision, d_image=None) -> (records, tally)
+    heart_trace_batch(specs, sources, n_rays, seeds, d_images, stream) -> [tally]
+    heart_server_create / heart_submit / heart_poll / heart_release / heart_server_destroy
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libheart.so")
+
+GEOMETRY = {"flat": 0, "cyl": 1}
+MDF = {"gaussian": 0, "lorentzian": 1, "pseudo_voigt": 2, "vmf": 3, "wl": 4, "swl": 5, "uniform": 6}
+IRC = {"darwin": 0, "darwin_prins": 1, "pseudo_voigt": 2, "gaussian": 3, "lorentzian": 4, "box": 5}
+SRC = {"mono": 0, "gauss": 1, "lorentz": 2, "inv_e": 3, "uniform": 4}
+PRECISION = {"fp64": 0, "fp32": 1}
+COUNT = {"i32": 0, "i64": 1}
+STATUS = {0: "HEART_OK", 1: "HEART_EINVAL", 2: "HEART_ENOMEM", 3: "HEART_ECUDA", 4: "HEART_EBUSY",
+          5: "HEART_ETIMEOUT", 6: "HEART_ELIMIT", 7: "HEART_ENOTFOUND"}
+OUTCOME = {0: "miss", 1: "absorbed", 2: "exit_front", 3: "exit_back", 4: "exit_side",
+           5: "capped", 6: "stuck"}
+
+D3 = C.c_double * 3
+
+
+class heart_spectrometer_desc(C.Structure):
+    _fields_ = [
+        ("d_spacing_A", C.c_double), ("thickness_mm", C.c_double),
+        ("geometry", C.c_int32), ("mdf", C.c_int32), ("radius_mm", C.c_double),
+        ("centre_mm", D3), ("normal", D3), ("axis", D3), ("centre_axial_mm", C.c_double),
+        ("size_disp_mm", C.c_double), ("size_nondisp_mm", C.c_double),
+        ("mdf_fwhm_rad", C.c_double), ("mdf_eta", C.c_double),
+        ("irc", C.c_int32), ("max_reflections", C.c_int32),
+        ("irc_fwhm_rad", C.c_double), ("irc_lorentz_fwhm_rad", C.c_double),
+        ("irc_shift_rad", C.c_double), ("prins_g", C.c_double),
+        ("absorption_length_mm", C.c_double), ("absorption_ref_keV", C.c_double),
+        ("absorption_power", C.c_double),
+        ("refl_K_per_mm2", C.c_double), ("refl_darwin_fwhm_rad", C.c_double), ("refl_ref_keV", C.c_double),
+        ("max_collisions", C.c_int64),
+        ("det_centre_mm", D3), ("det_u", D3), ("det_v", D3),
+        ("det_nx", C.c_int32), ("det_ny", C.c_int32), ("pixel_mm", C.c_double),
+        ("count_type", C.c_int32), ("reserved", C.c_int32),
+    ]
+
+
+class heart_spectral_component(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("e0_keV", C.c_double),
+                ("width_keV", C.c_double), ("lo_keV", C.c_double), ("hi_keV", C.c_double),
+                ("weight", C.c_double)]
+
+
+class heart_source_desc(C.Structure):
+    _fields_ = [("components", C.POINTER(heart_spectral_component)), ("n_components", C.c_int32),
+                ("reserved", C.c_int32), ("origin_mm", D3), ("axis", D3),
+                ("cone_half_angle_rad", C.c_double), ("spot_fwhm_mm", C.c_double * 2)]
+
+
+class heart_tally(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("emitted", "miss", "absorbed", "exit_front", "exit_back",
+                                          "exit_side", "capped", "stuck", "no_bragg", "det_hits")] + \
+               [("refl_hist", C.c_uint64 * 16), ("collisions", C.c_uint64)]
+
+    def as_dict(self):
+        d = {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "refl_hist"}
+        d["refl_hist"] = [int(x) for x in self.refl_hist]
+        return d
+
+
+RECORD_DTYPE = np.dtype([
+    ("ray_id", np.uint64), ("outcome", np.int32), ("nrefl", np.int32), ("ncoll", np.int64),
+    ("energy_keV", np.float64), ("pos", np.float64, 3), ("dir", np.float64, 3),
+    ("u_mm", np.float64), ("v_mm", np.float64), ("ix", np.int32), ("iy", np.int32),
+    ("det_hit", np.int32), ("no_bragg", np.int32)])
+assert RECORD_DTYPE.itemsize == 112
+
+EXPORTS = ["heart_spectrometer_create", "heart_spectrometer_destroy", "heart_trace", "heart_trace_host",
+           "heart_trace_records", "heart_trace_batch", "heart_server_create", "heart_server_destroy",
+           "heart_submit", "heart_poll", "heart_release", "heart_last_error"]
+
+
+class HeartError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def library(path=None):
+    """Load libheart.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libheart.so is not built (%s); run __graft_entry__.build()" % p)
+    L = C.CDLL(p)
+    vp, u64, i32 = C.c_void_p, C.c_uint64, C.c_int32
+    L.heart_spectrometer_create.argtypes = [C.POINTER(heart_spectrometer_desc), C.POINTER(vp)]
+    L.heart_spectrometer_destroy.argtypes = [vp]
+    L.heart_trace.argtypes = [vp, C.POINTER(heart_source_desc), u64, u64, u64, vp, i32, vp,
+                              C.POINTER(heart_tally)]
+    L.heart_trace_host.argtypes = [vp, C.POINTER(heart_source_desc), u64, u64, u64, vp, i32,
+                                   C.POINTER(heart_tally)]
+    L.heart_trace_records.argtypes = [vp, C.POINTER(heart_source_desc), u64, u64, u64, vp, i32, vp, vp,
+                                      C.POINTER(heart_tally)]
+    L.heart_trace_batch.argtypes = [C.POINTER(vp), C.POINTER(C.POINTER(heart_source_desc)),
+                                    C.POINTER(u64), C.POINTER(u64), C.POINTER(vp), i32, vp,
+                                    C.POINTER(heart_tally)]
+    L.heart_server_create.argtypes = [C.c_size_t, C.POINTER(vp)]
+    L.heart_server_destroy.argtypes = [vp]
+    L.heart_submit.argtypes = [vp, vp, C.POINTER(heart_source_desc), u64, u64, i32, C.POINTER(u64)]
+    L.heart_poll.argtypes = [vp, u64, i32, C.POINTER(heart_tally), C.POINTER(vp)]
+    L.heart_release.argtypes = [vp, u64]
+    L.heart_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        if name != "heart_last_error":
+            getattr(L, name).restype = C.c_int
+    if path is None:
+        _lib = L
+    return L
+
+
+def _check(status, allow=(0,)):
+    if status not in allow:
+        raise HeartError(status, library().heart_last_error().decode())
+    return status
+
+
+def make_desc(d):
+    """Neutral parameter dict (see workloads.py) -> heart_spectrometer_desc."""
+    s = heart_spectrometer_desc()
+    s.d_spacing_A = d["d_spacing_A"]
+    s.thickness_mm = d["thickness_mm"]
+    s.geometry = GEOMETRY[d["geometry"]]
+    s.mdf = MDF[d["mdf"]]
+    s.radius_mm = d.get("radius_mm", 0.0)
+    s.centre_mm = D3(*d["centre_mm"])
+    s.normal = D3(*d["normal"])
+    s.axis = D3(*d["axis"])
+    s.centre_axial_mm = d.get("centre_axial_mm", 0.0)
+    s.size_disp_mm = d["size_disp_mm"]
+    s.size_nondisp_mm = d["size_nondisp_mm"]
+    s.mdf_fwhm_rad = d["mdf_fwhm_rad"]
+    s.mdf_eta = d.get("mdf_eta", 0.0)
+    s.irc = IRC[d["irc"]]
+    s.max_reflections = d["max_reflections"]
+    s.irc_fwhm_rad = d["irc_fwhm_rad"]
+    s.irc_lorentz_fwhm_rad = d.get("irc_lorentz_fwhm_rad", 0.0)
+    s.irc_shift_rad = d.get("irc_shift_rad", 0.0)
+    s.prins_g = d.get("prins_g", 0.0)
+    s.absorption_length_mm = d["absorption_length_mm"]
+    s.absorption_ref_keV = d.get("absorption_ref_keV", 8.0)
+    s.absorption_power = d.get("absorption_power", 0.0)
+    s.refl_K_per_mm2 = d.get("refl_K_per_mm2", -1.0)
+    s.refl_darwin_fwhm_rad = d.get("refl_darwin_fwhm_rad", d["irc_fwhm_rad"])
+    s.refl_ref_keV = d.get("refl_ref_keV", 8.0)
+    s.max_collisions = d.get("max_collisions", 1_000_000)
+    s.det_centre_mm = D3(*d["det_centre_mm"])
+    s.det_u = D3(*d["det_u"])
+    s.det_v = D3(*d["det_v"])
+    s.det_nx = d["det_nx"]
+    s.det_ny = d["det_ny"]
+    s.pixel_mm = d["pixel_mm"]
+    s.count_type = COUNT[d.get("count_type", "i32")]
+    return s
+
+
+def make_source(d):
+    """Neutral source dict -> heart_source_desc (keeps its component array alive)."""
+    comps = d["components"]
+    arr = (heart_spectral_component * len(comps))()
+    for i, c in enumerate(comps):
+        arr[i].kind = SRC[c["kind"]]
+        arr[i].e0_keV = c.get("e0_keV", 0.0)
+        arr[i].width_keV = c.get("width_keV", 0.0)
+        arr[i].lo_keV = c.get("lo_keV", 0.0)
+        arr[i].hi_keV = c.get("hi_keV", 0.0)
+        arr[i].weight = c.get("weight", 1.0)
+    s = heart_source_desc()
+    s.components = arr
+    s.n_components = len(comps)
+    s.origin_mm = D3(*d["origin_mm"])
+    s.axis = D3(*d["axis"])
+    s.cone_half_angle_rad = d["cone_half_angle_rad"]
+    s.spot_fwhm_mm = (C.c_double * 2)(*d.get("spot_fwhm_mm", (0.0, 0.0)))
+    s._keep = arr
+    return s
+
+
+class Spectrometer:
+    """Owns a heart_spectrometer handle (device tables)."""
+
+    def __init__(self, desc_dict):
+        self.desc = dict(desc_dict)
+        self._c = make_desc(desc_dict)
+        h = C.c_void_p()
+        _check(library().heart_spectrometer_create(C.byref(self._c), C.byref(h)))
+        self.handle = h
+        self.shape = (desc_dict["det_ny"], desc_dict["det_nx"])
+        self.count_dtype = "int64" if desc_dict.get("count_type", "i32") == "i64" else "int32"
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            library().heart_spectrometer_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def heart_spectrometer_create(desc_dict):
+    return Spectrometer(desc_dict)
+
+
+def heart_spectrometer_destroy(spec):
+    spec.close()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def heart_trace(spec, source, n_rays, seed, ray_offset, d_image, precision="fp32", stream=None,
+                want_tally=True):
+    """Trace on the device; d_image is a CUDA tensor (+= counts)."""
+    src = make_source(source)
+    t = heart_tally()
+    st = library().heart_trace(spec.handle, C.byref(src), int(n_rays), int(seed), int(ray_offset),
+                               C.c_void_p(d_image.data_ptr()), PRECISION[precision],
+                               C.c_void_p(_stream_ptr(stream)), C.byref(t) if want_tally else None)
+    _check(st, allow=(0, 6))
+    return t.as_dict() if want_tally else None
+
+
+def heart_trace_host(spec, source, n_rays, seed, ray_offset, h_image, precision="fp32"):
+    """Host-memory variant: h_image (numpy, C-contiguous, += counts)."""
+    src = make_source(source)
+    t = heart_tally()
+    assert h_image.flags["C_CONTIGUOUS"]
+    st = library().heart_trace_host(spec.handle, C.byref(src), int(n_rays), int(seed), int(ray_offset),
+                                    C.c_void_p(h_image.ctypes.data), PRECISION[precision], C.byref(t))
+    _check(st, allow=(0, 6))
+    return t.as_dict()
+
+
+def heart_trace_records(spec, source, n_rays, seed, ray_offset=0, precision="fp64", d_image=None, stream=None):
+    """Per-ray records (numpy structured array) and tallies."""
+    import torch
+    src = make_source(source)
+    t = heart_tally()
+    rec = torch.empty(int(n_rays) * RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    st = library().heart_trace_records(spec.handle, C.byref(src), int(n_rays), int(seed), int(ray_offset),
+                                       C.c_void_p(d_image.data_ptr()) if d_image is not None else None,
+                                       PRECISION[precision], C.c_void_p(rec.data_ptr()),
+                                       C.c_void_p(_stream_ptr(stream)), C.byref(t))
+    _check(st, allow=(0, 6))
+    out = np.frombuffer(rec.cpu().numpy().tobytes(), dtype=RECORD_DTYPE)
+    return out, t.as_dict()
+
+
+def heart_trace_batch(specs, sources, n_rays, seeds, d_images, stream=None):
+    """Many spectrometers in one persistent FP32 launch."""
+    n = len(specs)
+    srcs = [make_source(s) for s in sources]
+    hs = (C.c_void_p * n)(*[s.handle.value for s in specs])
+    sp = (C.POINTER(heart_source_desc) * n)(*[C.pointer(s) for s in srcs])
+    nr = (C.c_uint64 * n)(*[int(x) for x in n_rays])
+    sd = (C.c_uint64 * n)(*[int(x) for x in seeds])
+    im = (C.c_void_p * n)(*[d.data_ptr() for d in d_images])
+    tl = (heart_tally * n)()
+    st = library().heart_trace_batch(hs, sp, nr, sd, im, n, C.c_void_p(_stream_ptr(stream)), tl)
+    _check(st, allow=(0, 6))
+    return [tl[i].as_dict() for i in range(n)]
+
+
+class Server:
+    def __init__(self, mem_cap_bytes):
+        h = C.c_void_p()
+        _check(library().heart_server_create(int(mem_cap_bytes), C.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, spec, source, n_rays, seed, precision="fp32"):
+        src = make_source(source)
+        jid = C.c_uint64()
+        _check(library().heart_submit(self.handle, spec.handle, C.byref(src), int(n_rays), int(seed),
+                                      PRECISION[precision], C.byref(jid)))
+        self._keep[jid.value] = spec
+        return jid.value
+
+    def poll(self, job_id, timeout_ms=0):
+        """(status_name, tally or None, device image pointer or None)."""
+        t = heart_tally()
+        img = C.c_void_p()
+        st = library().heart_poll(self.handle, int(job_id), int(timeout_ms), C.byref(t), C.byref(img))
+        if st in (4, 5):
+            return STATUS[st], None, None
+        _check(st, allow=(0, 6))
+        return STATUS[st], t.as_dict(), img.value
+
+    def release(self, job_id):
+        _check(library().heart_release(self.handle, int(job_id)))
+        self._keep.pop(job_id, None)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(library().heart_server_destroy(self.handle))
+        self.handle = None
+
+
+def heart_server_create(mem_cap_bytes):
+    return Server(mem_cap_bytes)
+
+
+def heart_submit(server, spec, source, n_rays, seed, precision="fp32"):
+    return server.submit(spec, source, n_rays, seed, precision)
+
+
+def heart_poll(server, job_id, timeout_ms=0):
+    return server.poll(job_id, timeout_ms)
+
+
+def heart_release(server, job_id):
+    return server.release(job_id)
+
+
+def heart_server_destroy(server):
+    server.close()

@@ -1,0 +1,314 @@
+// heart_api.cu -- the C ABI entry points and the plain FP64 kernel.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "heart.h"
+#include "heart_fp64.cuh"
+#include "heart_internal.h"
+#include "heart_lib.h"
+
+namespace heart {
+
+thread_local std::string g_last_error;
+
+heart_status fail(heart_status st, const char *msg) {
+    g_last_error = msg;
+    return st;
+}
+
+heart_status cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return HEART_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// plain FP64 kernel: one ray per thread, grid-stride, mosaic table in smem
+// ---------------------------------------------------------------------------
+template <typename CountT>
+__device__ __forceinline__ void add_pixel(CountT *img, size_t idx);
+template <>
+__device__ __forceinline__ void add_pixel<int32_t>(int32_t *img, size_t idx) { atomicAdd((int *)img + idx, 1); }
+template <>
+__device__ __forceinline__ void add_pixel<int64_t>(int64_t *img, size_t idx) {
+    atomicAdd((unsigned long long *)img + idx, 1ull);
+}
+
+template <typename CountT>
+__global__ void __launch_bounds__(256) k_trace_fp64(const SpecParams S, const SourceParams P, uint64_t n,
+                                                    uint32_t k0, uint32_t k1, uint64_t offset, CountT *img,
+                                                    unsigned long long *tally, heart_ray_record *rec) {
+    extern __shared__ double s_tab[];
+    __shared__ unsigned long long s_t[kTallyN];
+    for (int i = threadIdx.x; i < kMdfKnots; i += blockDim.x) s_tab[i] = S.mdf64[i];
+    for (int i = threadIdx.x; i < kTallyN; i += blockDim.x) s_t[i] = 0ull;
+    __syncthreads();
+    unsigned long long my_emit = 0, my_coll = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        RayOut64 r;
+        trace_ray64(S, P, k0, k1, offset + i, s_tab, r);
+        ++my_emit;
+        my_coll += (unsigned long long)r.ncoll;
+        atomicAdd(&s_t[r.outcome == HEART_MISS ? T_MISS : T_ABSORBED + (r.outcome - HEART_ABSORBED)], 1ull);
+        if (r.outcome != HEART_MISS) atomicAdd(&s_t[T_HIST0 + (r.nrefl < 15 ? r.nrefl : 15)], 1ull);
+        if (r.no_bragg) atomicAdd(&s_t[T_NO_BRAGG], 1ull);
+        if (r.det_hit) {
+            add_pixel<CountT>(img, (size_t)r.iy * (size_t)S.nx + (size_t)r.ix);
+            atomicAdd(&s_t[T_DET_HITS], 1ull);
+        }
+        if (rec) {
+            heart_ray_record &o = rec[i];
+            o.ray_id = offset + i;
+            o.outcome = r.outcome;
+            o.nrefl = r.nrefl;
+            o.ncoll = r.ncoll;
+            o.energy_keV = r.E;
+            for (int j = 0; j < 3; ++j) { o.pos[j] = r.pos[j]; o.dir[j] = r.dir[j]; }
+            o.u_mm = r.u;
+            o.v_mm = r.v;
+            o.ix = r.ix;
+            o.iy = r.iy;
+            o.det_hit = r.det_hit;
+            o.no_bragg = r.no_bragg;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        my_emit += __shfl_down_sync(0xffffffffu, my_emit, off);
+        my_coll += __shfl_down_sync(0xffffffffu, my_coll, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&s_t[T_EMITTED], my_emit);
+        atomicAdd(&s_t[T_COLLISIONS], my_coll);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTallyN; i += blockDim.x)
+        if (s_t[i]) atomicAdd(&tally[i], s_t[i]);
+}
+
+static int g_num_sms = 0;
+int num_sms() {
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+heart_status launch_fp64(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
+                         void *img, unsigned long long *tally, heart_ray_record *rec, cudaStream_t st) {
+    if (n == 0) return HEART_OK;
+    const int threads = 256;
+    const size_t smem = (size_t)kMdfKnots * sizeof(double);
+    uint64_t want = (n + threads - 1) / threads;
+    uint64_t cap = (uint64_t)num_sms() * 6;
+    const int blocks = (int)(want < cap ? want : cap);
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    if (S.count_type == HEART_COUNT_I64) {
+        static bool attr = false;
+        if (!attr) { cudaFuncSetAttribute(k_trace_fp64<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
+        k_trace_fp64<int64_t><<<blocks, threads, smem, st>>>(S, P, n, k0, k1, offset, (int64_t *)img, tally, rec);
+    } else {
+        static bool attr = false;
+        if (!attr) { cudaFuncSetAttribute(k_trace_fp64<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
+        k_trace_fp64<int32_t><<<blocks, threads, smem, st>>>(S, P, n, k0, k1, offset, (int32_t *)img, tally, rec);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "FP64 kernel launch");
+    return HEART_OK;
+}
+
+}  // namespace heart
+
+using namespace heart;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" const char *heart_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" heart_status heart_spectrometer_create(const heart_spectrometer_desc *desc, heart_spectrometer **out) {
+    if (!out) return fail(HEART_EINVAL, "null output pointer");
+    *out = nullptr;
+    std::vector<double> tab(kMdfKnots);
+    SpecParams p;
+    char err[256] = {0};
+    heart_status st = build_spec_params(desc, &p, tab.data(), err, (int)sizeof err);
+    if (st != HEART_OK) return fail(st, err);
+    std::vector<float> tab32(kMdfKnots);
+    for (int i = 0; i < kMdfKnots; ++i) tab32[i] = (float)tab[i];
+    heart_spectrometer *h = new (std::nothrow) heart_spectrometer();
+    if (!h) return fail(HEART_ENOMEM, "host allocation failed");
+    cudaError_t e;
+    if ((e = cudaGetDevice(&h->device)) != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
+    // [FP64 table][FP32 table, padded to 8 bytes][scratch words]
+    size_t bytes = kMdfKnots * sizeof(double) + (kMdfKnots + (kMdfKnots & 1)) * sizeof(float) +
+                   kScratchWords * sizeof(unsigned long long);
+    if ((e = cudaMalloc(&h->d_block, bytes)) != cudaSuccess) { delete h; return cuda_fail(e, "cudaMalloc tables"); }
+    h->d_tab64 = (double *)h->d_block;
+    h->d_tab32 = (float *)(h->d_tab64 + kMdfKnots);
+    h->d_scratch = (unsigned long long *)(h->d_tab32 + kMdfKnots + (kMdfKnots & 1));
+    if ((e = cudaMemcpy(h->d_tab64, tab.data(), kMdfKnots * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(h->d_tab32, tab32.data(), kMdfKnots * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        cudaFree(h->d_block);
+        delete h;
+        return cuda_fail(e, "cudaMemcpy tables");
+    }
+    if ((e = cudaMallocHost(&h->h_scratch, kScratchWords * sizeof(unsigned long long))) != cudaSuccess) {
+        cudaFree(h->d_block);
+        delete h;
+        return cuda_fail(e, "cudaMallocHost");
+    }
+    p.mdf64 = h->d_tab64;
+    p.mdf32 = h->d_tab32;
+    h->p = p;
+    h->desc = *desc;
+    *out = h;
+    return HEART_OK;
+}
+
+extern "C" heart_status heart_spectrometer_destroy(heart_spectrometer *h) {
+    if (!h) return fail(HEART_EINVAL, "null spectrometer");
+    cudaFree(h->d_block);
+    cudaFreeHost(h->h_scratch);
+    if (h->d_image_host_path) cudaFree(h->d_image_host_path);
+    delete h;
+    return HEART_OK;
+}
+
+static void fill_tally(const unsigned long long *t, heart_tally *out) {
+    std::memcpy(out, t, sizeof(heart_tally));
+}
+
+// common body of heart_trace / heart_trace_records
+static heart_status trace_impl(heart_spectrometer *h, const heart_source_desc *src, uint64_t n_rays, uint64_t seed,
+                               uint64_t ray_offset, void *d_image, heart_precision prec, void *d_records,
+                               void *stream, heart_tally *out, bool sync) {
+    if (!h) return fail(HEART_EINVAL, "null spectrometer");
+    if (prec != HEART_FP64 && prec != HEART_FP32) return fail(HEART_EINVAL, "unknown precision");
+    size_t elt = h->p.count_type == HEART_COUNT_I64 ? 8 : 4;
+    if (!d_image && !d_records) return fail(HEART_EINVAL, "null image");
+    if (d_image && ((uintptr_t)d_image % elt) != 0) return fail(HEART_EINVAL, "image pointer misaligned");
+    if (d_records && ((uintptr_t)d_records % 8) != 0) return fail(HEART_EINVAL, "records pointer misaligned");
+    if (ray_offset + n_rays < ray_offset) return fail(HEART_EINVAL, "ray range overflows 64 bits");
+    SourceParams P;
+    char err[256] = {0};
+    heart_status st = build_source_params(src, &P, err, (int)sizeof err);
+    if (st != HEART_OK) return fail(st, err);
+    cudaStream_t cs = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(h->d_scratch, 0, kScratchWords * sizeof(unsigned long long), cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    void *img = d_image;
+    if (!img) {
+        // records only: count into the handle's own scratch image
+        size_t bytes = (size_t)h->p.nx * h->p.ny * elt;
+        if (!h->d_image_host_path || h->host_image_bytes < bytes) {
+            if (h->d_image_host_path) cudaFree(h->d_image_host_path);
+            h->d_image_host_path = nullptr;
+            if ((e = cudaMalloc(&h->d_image_host_path, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc image");
+            h->host_image_bytes = bytes;
+        }
+        img = h->d_image_host_path;
+    }
+    if (prec == HEART_FP64 || d_records) {
+        st = launch_fp64(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, (heart_ray_record *)d_records, cs);
+    } else {
+        st = launch_fp32(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, cs);
+    }
+    if (st != HEART_OK) return st;
+    if (out || sync) {
+        if ((e = cudaMemcpyAsync(h->h_scratch, h->d_scratch, kTallyN * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
+            return cuda_fail(e, "tally copy");
+        if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return cuda_fail(e, "trace");
+        if (out) fill_tally(h->h_scratch, out);
+        if (h->h_scratch[T_STUCK] > 0) return fail(HEART_ELIMIT, "a ray reached the collision cap");
+    }
+    return HEART_OK;
+}
+
+extern "C" heart_status heart_trace(heart_spectrometer *h, const heart_source_desc *src, uint64_t n_rays, uint64_t seed,
+                                    uint64_t ray_offset, void *d_image, heart_precision precision, void *stream,
+                                    heart_tally *out) {
+    if (!d_image) return fail(HEART_EINVAL, "null image");
+    return trace_impl(h, src, n_rays, seed, ray_offset, d_image, precision, nullptr, stream, out, false);
+}
+
+extern "C" heart_status heart_trace_records(heart_spectrometer *h, const heart_source_desc *src, uint64_t n_rays,
+                                            uint64_t seed, uint64_t ray_offset, void *d_image,
+                                            heart_precision precision, void *d_records, void *stream,
+                                            heart_tally *out) {
+    if (!d_records) return fail(HEART_EINVAL, "null records");
+    if (precision == HEART_FP32) {
+        // records come from the FP32 kernel's record variant
+        if (!h) return fail(HEART_EINVAL, "null spectrometer");
+        SourceParams P;
+        char err[256] = {0};
+        heart_status st = build_source_params(src, &P, err, (int)sizeof err);
+        if (st != HEART_OK) return fail(st, err);
+        if (((uintptr_t)d_records % 8) != 0) return fail(HEART_EINVAL, "records pointer misaligned");
+        cudaStream_t cs = (cudaStream_t)stream;
+        cudaError_t e = cudaMemsetAsync(h->d_scratch, 0, kScratchWords * sizeof(unsigned long long), cs);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        void *img = d_image;
+        size_t elt = h->p.count_type == HEART_COUNT_I64 ? 8 : 4;
+        if (!img) {
+            size_t bytes = (size_t)h->p.nx * h->p.ny * elt;
+            if (!h->d_image_host_path || h->host_image_bytes < bytes) {
+                if (h->d_image_host_path) cudaFree(h->d_image_host_path);
+                h->d_image_host_path = nullptr;
+                if ((e = cudaMalloc(&h->d_image_host_path, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc image");
+                h->host_image_bytes = bytes;
+            }
+            img = h->d_image_host_path;
+        }
+        st = launch_fp32_records(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch,
+                                 (heart_ray_record *)d_records, cs);
+        if (st != HEART_OK) return st;
+        if ((e = cudaMemcpyAsync(h->h_scratch, h->d_scratch, kTallyN * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
+            return cuda_fail(e, "tally copy");
+        if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return cuda_fail(e, "trace");
+        if (out) fill_tally(h->h_scratch, out);
+        if (h->h_scratch[T_STUCK] > 0) return fail(HEART_ELIMIT, "a ray reached the collision cap");
+        return HEART_OK;
+    }
+    return trace_impl(h, src, n_rays, seed, ray_offset, d_image, precision, d_records, stream, out, true);
+}
+
+extern "C" heart_status heart_trace_host(heart_spectrometer *h, const heart_source_desc *src, uint64_t n_rays,
+                                         uint64_t seed, uint64_t ray_offset, void *h_image, heart_precision precision,
+                                         heart_tally *out) {
+    if (!h) return fail(HEART_EINVAL, "null spectrometer");
+    if (!h_image) return fail(HEART_EINVAL, "null host image");
+    size_t elt = h->p.count_type == HEART_COUNT_I64 ? 8 : 4;
+    size_t bytes = (size_t)h->p.nx * h->p.ny * elt;
+    cudaError_t e;
+    if (!h->d_image_host_path || h->host_image_bytes < bytes) {
+        if (h->d_image_host_path) cudaFree(h->d_image_host_path);
+        h->d_image_host_path = nullptr;
+        if ((e = cudaMalloc(&h->d_image_host_path, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc image");
+        h->host_image_bytes = bytes;
+    }
+    cudaStream_t cs = 0;
+    if ((e = cudaMemcpyAsync(h->d_image_host_path, h_image, bytes, cudaMemcpyHostToDevice, cs)) != cudaSuccess)
+        return cuda_fail(e, "image upload");
+    heart_status st = trace_impl(h, src, n_rays, seed, ray_offset, h->d_image_host_path, precision, nullptr, cs,
+                                 nullptr, false);
+    if (st != HEART_OK) return st;
+    if ((e = cudaMemcpyAsync(h->h_scratch, h->d_scratch, kTallyN * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
+        return cuda_fail(e, "tally copy");
+    if ((e = cudaMemcpyAsync(h_image, h->d_image_host_path, bytes, cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
+        return cuda_fail(e, "image download");
+    if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return cuda_fail(e, "trace");
+    if (out) fill_tally(h->h_scratch, out);
+    if (h->h_scratch[T_STUCK] > 0) return fail(HEART_ELIMIT, "a ray reached the collision cap");
+    return HEART_OK;
+}

@@ -1,0 +1,320 @@
+// heart_fp64.cuh -- device functions of the plain FP64 ray path: one ray per
+// thread, every quantity in double precision, positions in the global frame.
+// This is the reference-precision GPU path that replays the CPU oracle's
+// random streams ray by ray (same Philox words, same decisions).
+#pragma once
+#include <stdint.h>
+
+#include "heart_internal.h"
+
+namespace heart {
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1, uint32_t out[4]) {
+    // Salmon et al. (SC'11) Philox4x32 with 10 rounds: two 32x32->64
+    // multiplies per round, Weyl-sequence key schedule.
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+__device__ __forceinline__ double u01_64(uint32_t w) {
+    return ((double)w + 0.5) * 2.3283064365386962890625e-10;   // (w + 1/2) 2^-32
+}
+
+__device__ __forceinline__ double dot3d(const double *a, const double *b) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+struct RayOut64 {
+    int outcome, nrefl, ix, iy, det_hit, no_bragg;
+    long long ncoll;
+    double E, pos[3], dir[3], u, v;
+};
+
+// mosaic quantile q = 1 - cos(theta) from one 32-bit word (table in smem)
+__device__ __forceinline__ double mdf_q64(const double *tab, uint32_t w) {
+    const uint32_t i = w >> 20;
+    if (i < (uint32_t)(kMdfM - 1)) {
+        const double f = ((double)(w & 0xFFFFFu) + 0.5) * (1.0 / 1048576.0);
+        const double a = tab[i], b = tab[i + 1];
+        return a + f * (b - a);
+    }
+    const double m = (double)(0xFFFFFFFFu - w) + 0.5;
+    const double y = (32.0 - log2(m) - 12.0) * (kMdfT / 21.0);
+    int j = (int)floor(y);
+    j = j < 0 ? 0 : (j > kMdfT - 1 ? kMdfT - 1 : j);
+    const double f = y - j;
+    const double a = tab[kMdfM + j], b = tab[kMdfM + j + 1];
+    return a + f * (b - a);
+}
+
+__device__ __forceinline__ double dp_reflectivity64(double y, double g) {
+    const double ar = y * y - g * g - 1.0, ai = 2.0 * y * g;
+    const double r = hypot(ar, ai);
+    double zr, zi;
+    if (ar >= 0) { zr = sqrt(0.5 * (r + ar)); zi = (zr > 0) ? 0.5 * ai / zr : 0.0; }
+    else { zi = copysign(sqrt(0.5 * (r - ar)), ai); zr = 0.5 * ai / zi; }
+    const double m1 = hypot(y - zr, g - zi), m2 = hypot(y + zr, g + zi);
+    const double m = m1 > m2 ? m1 : m2;
+    return 1.0 / (m * m);
+}
+
+// unit-area rocking curve at x = Delta - Delta_M
+__device__ __forceinline__ double irc64(const SpecParams &S, double x) {
+    switch (S.irc) {
+    case HEART_IRC_DARWIN: {
+        const double y = fabs(x) / S.irc_delta;
+        if (y <= 1.0) return 1.0 / S.irc_norm;
+        const double d = y + sqrt(y * y - 1.0);
+        return 1.0 / (d * d * S.irc_norm);
+    }
+    case HEART_IRC_DARWIN_PRINS: return dp_reflectivity64(x / S.irc_delta, S.irc_g) / S.irc_norm;
+    case HEART_IRC_PSEUDO_VOIGT: {
+        const double F = S.irc_fwhm;
+        const double L = F / (2.0 * 3.14159265358979323846) / (0.25 * F * F + x * x);
+        const double c = 2.772588722239781 / (F * F);            // 4 ln 2 / F^2
+        const double G = sqrt(c / 3.14159265358979323846) * exp(-c * x * x);
+        return S.irc_eta * L + (1.0 - S.irc_eta) * G;
+    }
+    case HEART_IRC_GAUSSIAN: {
+        const double c = 2.772588722239781 / (S.irc_fwhm * S.irc_fwhm);
+        return sqrt(c / 3.14159265358979323846) * exp(-c * x * x);
+    }
+    case HEART_IRC_LORENTZIAN:
+        return S.irc_fwhm / (2.0 * 3.14159265358979323846) / (0.25 * S.irc_fwhm * S.irc_fwhm + x * x);
+    default:
+        return fabs(x) <= 0.5 * S.irc_fwhm ? 1.0 / S.irc_fwhm : 0.0;
+    }
+}
+
+// entry point on the front face; true on a hit
+__device__ __forceinline__ bool entry64(const SpecParams &S, const double o[3], const double k[3], double p[3]) {
+    const double rel[3] = {o[0] - S.c[0], o[1] - S.c[1], o[2] - S.c[2]};
+    if (S.geometry == HEART_FLAT) {
+        const double h0 = dot3d(rel, S.N), kN = dot3d(k, S.N);
+        if (!(kN < 0) || !(h0 > 0)) return false;
+        const double t = h0 / (-kN);
+        for (int i = 0; i < 3; ++i) p[i] = o[i] + t * k[i];
+        const double r2[3] = {p[0] - S.c[0], p[1] - S.c[1], p[2] - S.c[2]};
+        return fabs(dot3d(r2, S.ed)) <= S.half_d && fabs(dot3d(r2, S.en)) <= S.half_n;
+    }
+    const double X = dot3d(rel, S.cc), Y = dot3d(rel, S.ww);
+    const double kX = dot3d(k, S.cc), kY = dot3d(k, S.ww);
+    const double c = X * X + Y * Y - S.radius * S.radius;
+    if (!(c < 0)) return false;
+    const double a = kX * kX + kY * kY;
+    if (!(a > 0)) return false;
+    const double b = X * kX + Y * kY;
+    const double sq = sqrt(b * b - a * c);
+    const double t = (b > 0) ? -c / (b + sq) : (-b + sq) / a;
+    for (int i = 0; i < 3; ++i) p[i] = o[i] + t * k[i];
+    const double r2[3] = {p[0] - S.c[0], p[1] - S.c[1], p[2] - S.c[2]};
+    const double z = dot3d(r2, S.ax), Xp = dot3d(r2, S.cc), Yp = dot3d(r2, S.ww);
+    return fabs(z - S.zc) <= S.half_d && fabs(Yp) * S.cphi <= Xp * S.sphi;
+}
+
+// distance from p (inside) along k to the first boundary crossing, and the face
+__device__ __forceinline__ double exit_distance64(const SpecParams &S, const double p[3], const double k[3],
+                                                  int *face) {
+    const double rel[3] = {p[0] - S.c[0], p[1] - S.c[1], p[2] - S.c[2]};
+    double best = 1e300;
+    int f = HEART_EXIT_SIDE;
+    auto cand = [&](double v, int fc) {
+        v = v < 0 ? 0 : v;
+        if (v < best) { best = v; f = fc; }
+    };
+    if (S.geometry == HEART_FLAT) {
+        const double h = dot3d(rel, S.N), a = dot3d(rel, S.ed), b = dot3d(rel, S.en);
+        const double kh = dot3d(k, S.N), ka = dot3d(k, S.ed), kb = dot3d(k, S.en);
+        if (kh > 0) cand((0.0 - h) / kh, HEART_EXIT_FRONT);
+        if (kh < 0) cand((-S.thickness - h) / kh, HEART_EXIT_BACK);
+        if (ka > 0) cand((S.half_d - a) / ka, HEART_EXIT_SIDE);
+        if (ka < 0) cand((-S.half_d - a) / ka, HEART_EXIT_SIDE);
+        if (kb > 0) cand((S.half_n - b) / kb, HEART_EXIT_SIDE);
+        if (kb < 0) cand((-S.half_n - b) / kb, HEART_EXIT_SIDE);
+    } else {
+        const double z = dot3d(rel, S.ax), X = dot3d(rel, S.cc), Y = dot3d(rel, S.ww);
+        const double kz = dot3d(k, S.ax), kX = dot3d(k, S.cc), kY = dot3d(k, S.ww);
+        const double R = S.radius, Ro = S.radius + S.thickness;
+        const double a = kX * kX + kY * kY, b = X * kX + Y * kY;
+        if (a > 0) {
+            const double ci = X * X + Y * Y - R * R;
+            if (b < 0) {
+                const double disc = b * b - a * ci;
+                if (disc >= 0) cand(ci / (-b + sqrt(disc)), HEART_EXIT_FRONT);
+            }
+            const double co = X * X + Y * Y - Ro * Ro;
+            double disc = b * b - a * co;
+            disc = disc < 0 ? 0 : disc;
+            const double sq = sqrt(disc);
+            cand((b > 0) ? -co / (b + sq) : (-b + sq) / a, HEART_EXIT_BACK);
+        }
+        if (kz > 0) cand((S.zc + S.half_d - z) / kz, HEART_EXIT_SIDE);
+        if (kz < 0) cand((S.zc - S.half_d - z) / kz, HEART_EXIT_SIDE);
+        const double gp = -X * S.sphi + Y * S.cphi, rp = -kX * S.sphi + kY * S.cphi;
+        if (rp > 0) cand(-gp / rp, HEART_EXIT_SIDE);
+        const double gm = -X * S.sphi - Y * S.cphi, rm = -kX * S.sphi - kY * S.cphi;
+        if (rm > 0) cand(-gm / rm, HEART_EXIT_SIDE);
+    }
+    *face = f;
+    return best;
+}
+
+__device__ __forceinline__ void local_frame64(const SpecParams &S, const double p[3], double N[3], double t1[3],
+                                              double t2[3]) {
+    if (S.geometry == HEART_FLAT) {
+        for (int i = 0; i < 3; ++i) { N[i] = S.N[i]; t1[i] = S.ed[i]; t2[i] = S.en[i]; }
+        return;
+    }
+    const double rel[3] = {p[0] - S.c[0], p[1] - S.c[1], p[2] - S.c[2]};
+    const double X = dot3d(rel, S.cc), Y = dot3d(rel, S.ww);
+    const double inv = 1.0 / sqrt(X * X + Y * Y);
+    for (int i = 0; i < 3; ++i) { N[i] = -(X * S.cc[i] + Y * S.ww[i]) * inv; t1[i] = S.ax[i]; }
+    t2[0] = N[1] * t1[2] - N[2] * t1[1];
+    t2[1] = N[2] * t1[0] - N[0] * t1[2];
+    t2[2] = N[0] * t1[1] - N[1] * t1[0];
+}
+
+__device__ __forceinline__ void detector64(const SpecParams &S, const double x[3], const double k[3], RayOut64 &r) {
+    const double den = dot3d(k, S.nd);
+    if (den == 0) return;
+    const double rel[3] = {S.D0[0] - x[0], S.D0[1] - x[1], S.D0[2] - x[2]};
+    const double t = dot3d(rel, S.nd) / den;
+    if (!(t > 0)) return;
+    const double P[3] = {x[0] + t * k[0] - S.D0[0], x[1] + t * k[1] - S.D0[1], x[2] + t * k[2] - S.D0[2]};
+    r.u = dot3d(P, S.eu);
+    r.v = dot3d(P, S.ev);
+    const double fx = r.u / S.pix + 0.5 * S.nx, fy = r.v / S.pix + 0.5 * S.ny;
+    if (fx >= 0 && fx < S.nx && fy >= 0 && fy < S.ny) {
+        r.ix = (int)floor(fx);
+        r.iy = (int)floor(fy);
+        r.det_hit = 1;
+    }
+}
+
+// one ray, source to detector
+__device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, uint32_t k0, uint32_t k1,
+                            uint64_t ray, const double *tab, RayOut64 &r) {
+    constexpr double kTwoPi = 6.283185307179586476925;
+    const uint32_t rl = (uint32_t)ray, rh = (uint32_t)(ray >> 32);
+    uint32_t a[4], b[4];
+    philox4x32_10(rl, rh, 0u, 0u, k0, k1, a);
+    philox4x32_10(rl, rh, 1u, 0u, k0, k1, b);
+    r.outcome = HEART_MISS; r.nrefl = 0; r.ncoll = 0; r.ix = -1; r.iy = -1; r.det_hit = 0; r.no_bragg = 0;
+    r.u = __longlong_as_double(0x7ff8000000000000LL);
+    r.v = r.u;
+
+    // energy (Sec. 2.1): component by cumulative weight, then its parameter
+    const double uc = u01_64(a[0]);
+    int c = P.n_comp - 1;
+    for (int i = 0; i < P.n_comp; ++i)
+        if (uc < P.cumw[i]) { c = i; break; }
+    const double up = u01_64(a[1]);
+    double E;
+    switch (P.kind[c]) {
+    case HEART_SRC_MONO: E = P.e0[c]; break;
+    case HEART_SRC_GAUSS:
+        E = P.e0[c] + P.width[c] * (sqrt(-2.0 * log(u01_64(b[2]))) * cos(kTwoPi * u01_64(b[3])));
+        break;
+    case HEART_SRC_LORENTZ: {
+        const double uu = P.lorentz_F0[c] + up * (1.0 - P.lorentz_F0[c]);
+        E = P.e0[c] + 0.5 * P.width[c] * tan(3.14159265358979323846 * (uu - 0.5));
+        break;
+    }
+    case HEART_SRC_INV_E: E = P.lo[c] * pow(P.hi[c] / P.lo[c], up); break;
+    default: E = P.lo[c] + (P.hi[c] - P.lo[c]) * up; break;
+    }
+    r.E = E;
+    // direction uniform in solid angle inside the cone
+    const double w = u01_64(a[2]) * P.one_minus_cos_max;
+    const double cphi = 1.0 - w, sphi = sqrt(w * (2.0 - w));
+    const double beta = kTwoPi * u01_64(a[3]);
+    const double cb = cos(beta), sb = sin(beta);
+    double k[3], o[3];
+    for (int i = 0; i < 3; ++i) k[i] = cphi * P.ax[i] + sphi * (cb * P.b1[i] + sb * P.b2[i]);
+    // Gaussian spot
+    const double rr = sqrt(-2.0 * log(u01_64(b[0])));
+    const double ang = kTwoPi * u01_64(b[1]);
+    const double z1 = rr * cos(ang), z2 = rr * sin(ang);
+    for (int i = 0; i < 3; ++i) o[i] = P.origin[i] + P.sig1 * z1 * P.b1[i] + P.sig2 * z2 * P.b2[i];
+
+    double x[3];
+    const bool hit = (E > 0 && isfinite(E)) && entry64(S, o, k, x);
+    if (!hit) {
+        for (int i = 0; i < 3; ++i) { r.pos[i] = o[i]; r.dir[i] = k[i]; }
+        return;
+    }
+    // per-ray constants: Bragg angle (Eq. BraggLaw), mu0, Q, majorant
+    const double lam_A = 12.398419843320026 / E;
+    const double sB = lam_A / (2.0 * S.d_A);
+    const double mu0 = 1.0 / (S.labs * pow(E / S.labs_ref, S.labs_pow));
+    double aB = 0.0, Q = 0.0;
+    if (!(sB < 1.0)) {
+        r.no_bragg = 1;
+    } else {
+        aB = asin(sB);
+        const double lam = lam_A * 1e-7;
+        Q = S.K * S.K * lam * lam * lam / (2.0 * sB * sqrt(1.0 - sB * sB));
+    }
+    const double mubar = mu0 + Q * S.irc_max;
+    const double pa = mu0 / mubar;
+
+    // null-collision walk (Sec. 2.2.4)
+    int outcome = HEART_STUCK, nrefl = 0;
+    long long ncoll = 0;
+    uint32_t call = 2;
+    for (;;) {
+        if (ncoll >= S.max_coll) { outcome = HEART_STUCK; break; }
+        uint32_t wd[4];
+        philox4x32_10(rl, rh, call++, 0u, k0, k1, wd);
+        const double l = -log(u01_64(wd[0])) / mubar;
+        int face;
+        const double se = exit_distance64(S, x, k, &face);
+        if (l > se) {
+            for (int i = 0; i < 3; ++i) x[i] += se * k[i];
+            outcome = face;
+            break;
+        }
+        for (int i = 0; i < 3; ++i) x[i] += l * k[i];
+        ++ncoll;
+        const double u1 = u01_64(wd[1]);
+        if (u1 < pa) { outcome = HEART_ABSORBED; break; }
+        const double v = (u1 - pa) / (1.0 - pa);
+        double N[3], t1[3], t2[3];
+        local_frame64(S, x, N, t1, t2);
+        const double q = mdf_q64(tab, wd[2]);
+        const double ct = 1.0 - q, st = sqrt(q * (2.0 - q));
+        double sx, cx;
+        sincospi(2.0 * u01_64(wd[3]), &sx, &cx);
+        double n[3];
+        for (int i = 0; i < 3; ++i) n[i] = ct * N[i] + st * (cx * t1[i] + sx * t2[i]);
+        const double kn = dot3d(k, n);
+        double sa = fabs(kn);
+        sa = sa > 1.0 ? 1.0 : sa;
+        const double delta = asin(sa) - aB - S.irc_shift;
+        const double c2 = 1.0 - 2.0 * sa * sa;                // cos(2 a~)
+        const double G = 0.5 * (1.0 + c2 * c2);               // Eq. (G_unpol)
+        if (v < irc64(S, delta) * G / S.irc_max) {
+            ++nrefl;
+            if (nrefl > S.max_refl) { outcome = HEART_CAPPED; break; }
+            for (int i = 0; i < 3; ++i) k[i] -= 2.0 * kn * n[i];
+            const double inv = 1.0 / sqrt(dot3d(k, k));
+            for (int i = 0; i < 3; ++i) k[i] *= inv;
+        }
+    }
+    r.outcome = outcome;
+    r.nrefl = nrefl;
+    r.ncoll = ncoll;
+    for (int i = 0; i < 3; ++i) { r.pos[i] = x[i]; r.dir[i] = k[i]; }
+    if (outcome == HEART_EXIT_FRONT || outcome == HEART_EXIT_BACK || outcome == HEART_EXIT_SIDE)
+        detector64(S, x, k, r);
+}
+
+}  // namespace heart

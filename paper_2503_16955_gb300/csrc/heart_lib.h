@@ -1,0 +1,41 @@
+// heart_lib.h -- library-internal declarations (handles, launchers).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "heart.h"
+#include "heart_internal.h"
+
+namespace heart {
+// device scratch words per handle: tallies, then work counters of the
+// persistent kernels
+constexpr int kScratchWords = 64;
+constexpr int kCounterWord = 32;     // first work-counter word
+
+extern thread_local std::string g_last_error;
+heart_status fail(heart_status st, const char *msg);
+heart_status cuda_fail(cudaError_t e, const char *what);
+int num_sms();
+
+heart_status launch_fp64(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
+                         void *img, unsigned long long *tally, heart_ray_record *rec, cudaStream_t st);
+heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
+                         void *img, unsigned long long *scratch, cudaStream_t st);
+heart_status launch_fp32_records(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed,
+                                 uint64_t offset, void *img, unsigned long long *scratch, heart_ray_record *rec,
+                                 cudaStream_t st);
+}  // namespace heart
+
+struct heart_spectrometer {
+    heart::SpecParams p;
+    heart_spectrometer_desc desc;
+    int device = 0;
+    void *d_block = nullptr;              // tables + scratch, one allocation
+    double *d_tab64 = nullptr;
+    float *d_tab32 = nullptr;
+    unsigned long long *d_scratch = nullptr;
+    unsigned long long *h_scratch = nullptr;   // pinned tally copy
+    void *d_image_host_path = nullptr;    // image buffer of heart_trace_host
+    size_t host_image_bytes = 0;
+};

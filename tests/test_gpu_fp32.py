@@ -1,0 +1,137 @@
+"""FP32 persistent kernel against the FP64 kernel on the same Philox streams,
+and against an independent-stream oracle image.
+
+Tolerances (fixed before measuring):
+  * outcome flips (outcome or reflection count differs) <= 1e-4 of rays;
+  * for rays with the same outcome, detector hit positions within 1 um;
+  * line centroid and FWHM of the dispersive profile within 0.1 % of FP64;
+  * two-sample chi-square of the FP32 image against an oracle image traced
+    with another seed: p > 0.01.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import binding as ob
+from paper_2503_16955_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2503_16955_gb300 as H
+    return H
+
+
+def _pair(H, spec, src, n, seed, offset=0):
+    s = H.heart_spectrometer_create(spec)
+    r64, t64 = H.heart_trace_records(s, src, n, seed, offset, precision="fp64")
+    r32, t32 = H.heart_trace_records(s, src, n, seed, offset, precision="fp32")
+    s.close()
+    return r64, t64, r32, t32
+
+
+def _profile_stats(u):
+    """centroid and FWHM of a 1-D hit profile (histogram at 1/4 of its rms)"""
+    c = float(np.mean(u))
+    h, e = np.histogram(u, bins=200, range=(c - 4 * u.std(), c + 4 * u.std()))
+    m = h.max()
+    above = np.flatnonzero(h >= 0.5 * m)
+    fw = e[above[-1] + 1] - e[above[0]]
+    return c, fw
+
+
+@pytest.mark.parametrize("name,n", [("flat_hopg_mono", 200_000), ("von_hamos_hapg", 200_000)])
+def test_fp32_same_stream_against_fp64(H, name, n):
+    w = getattr(W, name)()
+    r64, t64, r32, t32 = _pair(H, w["spec"], w["source"], n, w["seed"])
+    assert np.array_equal(r64["ray_id"], r32["ray_id"])
+    flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"])
+    assert flip.mean() <= 1e-4, (int(flip.sum()), n)
+    same = ~flip & (r64["det_hit"] == 1) & (r32["det_hit"] == 1)
+    assert same.sum() > 100
+    du = np.abs(r64["u_mm"][same] - r32["u_mm"][same])
+    dv = np.abs(r64["v_mm"][same] - r32["v_mm"][same])
+    assert du.max() <= 1e-3 and dv.max() <= 1e-3, (du.max(), dv.max())
+    # centroid and FWHM of the dispersive profile (detector u), 0.1 %
+    u64 = r64["u_mm"][r64["det_hit"] == 1]
+    u32 = r32["u_mm"][r32["det_hit"] == 1]
+    c64, f64 = _profile_stats(u64)
+    c32, f32 = _profile_stats(u32)
+    px = w["spec"]["pixel_mm"]
+    assert abs(c32 - c64) <= 1e-3 * max(abs(c64), 0.5 * w["spec"]["det_nx"] * px)
+    assert abs(f32 - f64) <= 1e-3 * f64 + 1e-9
+    # tallies of the same streams agree up to the flipped rays
+    for k in ("emitted", "miss"):
+        assert t32[k] == t64[k]
+    assert abs(t32["det_hits"] - t64["det_hits"]) <= int(flip.sum())
+    assert abs(t32["collisions"] - t64["collisions"]) <= 1e-4 * t64["collisions"] + 100 * flip.sum()
+
+
+def _two_sample_chi2(a, b, min_count=5):
+    """pooled two-sample chi-square on 1-D histograms a, b"""
+    A, B = a.sum(), b.sum()
+    pa, pb, ca, cb = [], [], 0, 0
+    for x, y in zip(a, b):
+        ca += x
+        cb += y
+        if ca + cb >= 2 * min_count:
+            pa.append(ca)
+            pb.append(cb)
+            ca = cb = 0
+    if ca + cb > 0 and pa:
+        pa[-1] += ca
+        pb[-1] += cb
+    pa, pb = np.array(pa, float), np.array(pb, float)
+    k1, k2 = math.sqrt(B / A), math.sqrt(A / B)
+    chi2 = (((k1 * pa - k2 * pb) ** 2) / (pa + pb)).sum()
+    return stats.chi2.sf(chi2, len(pa) - 1), len(pa)
+
+
+@pytest.mark.parametrize("name,n_gpu,n_orc", [("flat_hopg_mono", 4_000_000, 1_000_000),
+                                              ("von_hamos_hapg", 4_000_000, 1_000_000)])
+def test_fp32_image_matches_independent_oracle(H, name, n_gpu, n_orc):
+    import torch
+    w = getattr(W, name)()
+    s = H.heart_spectrometer_create(w["spec"])
+    img = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    H.heart_trace(s, w["source"], n_gpu, 1002, 0, img, precision="fp32")
+    g = img.cpu().numpy().astype(np.int64)
+    s.close()
+    o, _, _ = ob.trace(w["spec"], w["source"], n_orc, 2002)
+    # dispersive (columns) and non-dispersive (rows) profiles
+    for axis in (0, 1):
+        p, nb = _two_sample_chi2(g.sum(axis=axis), o.sum(axis=axis))
+        assert nb >= 10 and p > 0.01, (axis, p, nb)
+    # hit fraction
+    pg, po = g.sum() / n_gpu, o.sum() / n_orc
+    sd = math.sqrt(po * (1 - po) / n_orc + pg * (1 - pg) / n_gpu)
+    assert abs(pg - po) <= 4.5 * sd
+
+
+def test_fp32_int64_image_and_chunking_invariance(H):
+    import torch
+    w = W.von_hamos_hapg()
+    spec = dict(w["spec"])
+    spec["count_type"] = "i64"
+    s = H.heart_spectrometer_create(spec)
+    a = torch.zeros(s.shape, dtype=torch.int64, device="cuda")
+    ta = H.heart_trace(s, w["source"], 1_000_000, 5, 0, a, precision="fp32")
+    b = torch.zeros(s.shape, dtype=torch.int64, device="cuda")
+    tb1 = H.heart_trace(s, w["source"], 400_000, 5, 0, b, precision="fp32")
+    tb2 = H.heart_trace(s, w["source"], 600_000, 5, 400_000, b, precision="fp32")
+    s.close()
+    # counter-based streams: the image does not depend on how rays are chunked
+    assert torch.equal(a, b)
+    assert ta["det_hits"] == tb1["det_hits"] + tb2["det_hits"] == int(a.sum())
+    assert ta["emitted"] == 1_000_000
+    assert ta["emitted"] == (ta["miss"] + ta["absorbed"] + ta["exit_front"] + ta["exit_back"] +
+                             ta["exit_side"] + ta["capped"] + ta["stuck"])
