@@ -230,6 +230,11 @@ heart_status heart_submit(heart_server *server, heart_spectrometer *spec, const 
 heart_status heart_poll(heart_server *server, uint64_t job_id, int32_t timeout_ms, heart_tally *out,
                         const void **d_image_out);
 heart_status heart_release(heart_server *server, uint64_t job_id);
+/* Copy a finished job's image (det_ny x det_nx, the handle's count type) into
+ * dst: host memory if dst_is_host != 0, else device memory.  Synchronous. */
+heart_status heart_fetch_image(heart_server *server, uint64_t job_id, void *dst, int32_t dst_is_host);
+/* Seconds from heart_submit to completion, measured by the server (finished jobs). */
+heart_status heart_job_latency(heart_server *server, uint64_t job_id, double *seconds);
 
 const char *heart_last_error(void);
 

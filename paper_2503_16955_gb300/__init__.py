@@ -87,7 +87,8 @@ assert RECORD_DTYPE.itemsize == 112
 
 EXPORTS = ["heart_spectrometer_create", "heart_spectrometer_destroy", "heart_trace", "heart_trace_host",
            "heart_trace_records", "heart_trace_batch", "heart_server_create", "heart_server_destroy",
-           "heart_submit", "heart_poll", "heart_release", "heart_last_error"]
+           "heart_submit", "heart_poll", "heart_release", "heart_fetch_image", "heart_job_latency",
+           "heart_last_error"]
 
 
 class HeartError(RuntimeError):
@@ -125,6 +126,8 @@ def library(path=None):
     L.heart_submit.argtypes = [vp, vp, C.POINTER(heart_source_desc), u64, u64, i32, C.POINTER(u64)]
     L.heart_poll.argtypes = [vp, u64, i32, C.POINTER(heart_tally), C.POINTER(vp)]
     L.heart_release.argtypes = [vp, u64]
+    L.heart_job_latency.argtypes = [vp, u64, C.POINTER(C.c_double)]
+    L.heart_fetch_image.argtypes = [vp, u64, vp, i32]
     L.heart_last_error.restype = C.c_char_p
     for name in EXPORTS:
         if name != "heart_last_error":
@@ -317,6 +320,21 @@ class Server:
             return STATUS[st], None, None
         _check(st, allow=(0, 6))
         return STATUS[st], t.as_dict(), img.value
+
+    def fetch(self, job_id, out):
+        """copy the finished job's image into `out` (CUDA tensor or numpy array)"""
+        if hasattr(out, "data_ptr"):
+            ptr, host = out.data_ptr(), int(not out.is_cuda)
+        else:
+            ptr, host = out.ctypes.data, 1
+        _check(library().heart_fetch_image(self.handle, int(job_id), C.c_void_p(ptr), host))
+        return out
+
+    def latency(self, job_id):
+        """server-measured seconds from submit to completion"""
+        v = C.c_double()
+        _check(library().heart_job_latency(self.handle, int(job_id), C.byref(v)))
+        return v.value
 
     def release(self, job_id):
         _check(library().heart_release(self.handle, int(job_id)))

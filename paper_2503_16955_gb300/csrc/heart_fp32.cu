@@ -1,28 +1,37 @@
-// heart_fp32.cu -- the FP32 persistent ray-transport kernel.
+// heart_fp32.cu -- the FP32 persistent ray-transport kernel (single and batched).
 //
-// Precision plan (Sec. 2.2.3-2.2.4 of the paper fix what is computed; this
-// file fixes how):
-//  * per ray and per straight segment (entry, after each reflection) the
-//    direction k, the segment start x0 and sin(aB + Delta_M) are held in FP64,
-//    and the Bragg anchor A = |k.N(x0)| - sin(aB + Delta_M) is formed in FP64;
-//  * per tentative collision everything is FP32, and only *small* quantities
-//    are formed: the candidate offset D = k.n - k.N (size ~ theta), the
-//    along-segment change of k.N on a cylinder, and the rocking-curve argument
-//    Delta = asin(s) - asin(sB) = asin((s - sB)(s + sB) / (s cB + sB cs)) with
-//    s - sB = A + sign * (D + dkappa); no large number is ever subtracted in FP32;
-//  * the path length along a segment is a Kahan-compensated FP32 sum.
-// Decisions that compare a uniform with a per-ray threshold (absorption,
-// spectral component) compare the raw 32-bit Philox word with an integer
-// threshold, so they agree with the FP64 path exactly.
+// What is computed is fixed by the paper (Sec. 2.1 source, Sec. 2.2 crystal,
+// Sec. 2.2.3-2.2.4 walk, Appendix A orientation sampling, Sec. 2.3 detector);
+// the sampling model is the null-collision walk of the FP64 path.  This file
+// fixes how it runs on an FP32 machine:
 //
-// Work distribution: a persistent grid; each warp owns a shared-memory buffer
-// of spawned rays (source sampled, crystal entry found, misses already tallied).
-// All 32 lanes spawn together (full SIMT efficiency) when the buffer runs low;
-// lanes whose ray ended pop a new ray from the buffer once at least
-// `refill` lanes are idle, so the expensive spawn never runs divergently.
+// Precision.  The Bragg decision needs |Delta| = |asin|k.n| - (aB + Delta_M)|
+// to ~1e-8 rad while |k.n| ~ 0.2.  No FP64 is used; instead every quantity
+// that the decision depends on is carried as a *small* FP32 number relative to
+// an FP64 constant computed once per launch on the host:
+//   * sin(aB + Delta_M) = sB0[c] + ds, with sB0[c] fixed per spectral
+//     component and ds formed from the small energy offset of the ray;
+//   * the anchor A = |k.N| - sin(aB + Delta_M) at the start of each straight
+//     segment: at entry from the small offset of k from the cone axis, after a
+//     reflection from the closed form A' = -A + 2e - 2q (sB + e);
+//   * per tentative collision the candidate offset D = k.n - k.N ~ theta and,
+//     on a cylinder, the along-segment change of k.N from the path length;
+//   * Delta = asin((s - sB)(s + sB) / (s cB + sB cs)) with s - sB = e small.
+// Positions are FP32 in the crystal frame; the path along a segment is a
+// Kahan-compensated sum.  Decisions comparing a uniform with a per-ray
+// threshold compare the raw 32-bit Philox word with an integer threshold.
+//
+// Work distribution.  A persistent grid claims work items (job, ray range)
+// from a global counter; a block stages its job's parameters and mosaic
+// table in shared memory.  Each warp keeps a shared-memory buffer of spawned
+// rays (source sampled, crystal entry found, misses tallied): all 32 lanes
+// spawn together when it runs low, and idle lanes pop from it once at least
+// `refill` of them are idle, so spawning never runs divergently.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "heart_fp64.cuh"
 #include "heart_lib.h"
@@ -33,55 +42,69 @@ constexpr int kWarpsPerBlock = 4;
 constexpr int kBlockThreads = kWarpsPerBlock * 32;
 constexpr int kBuf = 64;                 // spawned rays buffered per warp
 
-// Per-launch parameters in the crystal-local frame.
+TuneConfig g_tune;                        // launch shape picked by the autotuner
+
+// Per-job parameters in the crystal-local frame.
 // flat: axes (e_d, e_n, N), origin at the front-face centre; crystal
 //       |p0| <= half_d, |p1| <= half_n, -t <= p2 <= 0.
 // cylinder: axes (axis, c, axis x c), origin on the axis; crystal
 //       |p0 - zc| <= half_d, R <= hypot(p1, p2) <= R + t, |p2| cphi <= p1 sphi.
 struct Launch32 {
     // source, local frame
-    double o[3], ax[3], b1[3], b2[3];
+    float o[3], ax[3], b1[3], b2[3];
     float omc, sig1, sig2;
+    float a_n;                            // flat: axis . N; cylinder: axis . cylinder axis
     int32_t n_comp;
     uint32_t comp_thr[kMaxComp];          // component i if word < comp_thr[i]
     int32_t kind[kMaxComp];
-    double e0[kMaxComp];
-    float width[kMaxComp], lo[kMaxComp], hi[kMaxComp], lF0[kMaxComp];
+    float e_ref[kMaxComp];                // reference energy of each component
+    float width[kMaxComp], half_ln[kMaxComp], lF0[kMaxComp];
+    float sB0[kMaxComp];                  // sin(aB(e_ref) + Delta_M)
+    float A0[kMaxComp];                   // |k.N| - sB0 for k on the cone axis
+    float sB_raw[kMaxComp], cB_raw[kMaxComp];   // sin / cos aB(e_ref) without the shift
     // crystal
     float half_d, half_n, thick, R, zc, sphi, cphi;
-    double R64, zc64, cos_shift;
-    float sin_shift;
-    // rocking curve (argument x = Delta - Delta_M)
-    float irc_fwhm, irc_eta, irc_delta, irc_inv_norm, irc_g, inv_irc_max, irc_c, irc_gnorm;
+    float cos_shift, sin_shift, c_a;
+    // rocking curve (argument x = Delta - Delta_M), relative to its maximum
+    float irc_fwhm, irc_eta, irc_delta, irc_g, irc_c, irc_gnorm;
     // physics
-    double sB_scale;                      // hc / (2 d)   [keV]
     float labs, labs_ref, labs_pow, K2, irc_max;
     int32_t max_refl;
     int64_t max_coll;
     // detector, local frame
-    double D0[3];
-    float eu[3], ev[3], nd[3], inv_pix, hnx, hny;
+    float D0[3], eu[3], ev[3], nd[3], inv_pix, hnx, hny;
     int32_t nx, ny, count64;
     // run
     uint64_t n, offset;
     uint32_t k0, k1;
     int32_t refill;                       // pop when at least this many lanes are idle
+    int32_t geometry, irc_kind;
     const float *tab;
+    void *img;                            // this job's image (int32 or int64)
+    unsigned long long *tally;            // this job's kTallyN tally words
+    heart_ray_record *rec;                // per-ray records or nullptr
     double fc[3], fa[3][3];               // local -> global frame (records only)
 };
 
-struct WarpBuf {                          // spawned rays waiting for a lane (SoA)
-    double x[3][kBuf], k[3][kBuf], sB[kBuf];
-    uint32_t rl[kBuf], rh[kBuf];
-    float inv_mu[kBuf], pa[kBuf], E[kBuf];
-    uint32_t pa_thr[kBuf];
-    int32_t nb[kBuf];                     // no-Bragg flag
+// a spawned ray waiting for a lane (SoA per warp)
+struct WarpBuf {
+    float x[3][kBuf], k[3][kBuf];
+    float A[kBuf], sB[kBuf], inv_mu[kBuf], pa[kBuf], E[kBuf];
+    uint32_t rl[kBuf], rh[kBuf], pa_thr[kBuf];
+    int32_t nb[kBuf];
     int count;
 };
 
 __device__ __forceinline__ float u01_32(uint32_t w) {
     // (w + 1/2) 2^-32 rounded to FP32: relative error <= 2^-24 against the FP64 uniform
     return __fmaf_rn(__uint2float_rn(w), 2.3283064365386963e-10f, 1.16415321826934814e-10f);
+}
+
+// cos / sin (2 pi u) from the SFU on the centred argument 2 pi (u - 1/2)
+__device__ __forceinline__ void sincos_2pi(float u, float *s, float *c) {
+    __sincosf(6.28318530717958648f * (u - 0.5f), s, c);
+    *s = -*s;
+    *c = -*c;
 }
 
 __device__ __forceinline__ float mdf_q32(const float *tab, uint32_t w) {
@@ -101,10 +124,11 @@ __device__ __forceinline__ float mdf_q32(const float *tab, uint32_t w) {
 }
 
 // unit-area rocking curve divided by its maximum, at x = Delta - Delta_M
-template <int IRC>
+template <int IRC_T>
 __device__ __forceinline__ float irc_rel32(const Launch32 &L, float x) {
+    const int IRC = IRC_T >= 0 ? IRC_T : L.irc_kind;
     if (IRC == HEART_IRC_DARWIN) {
-        const float y = fabsf(x) * L.irc_delta;            // irc_delta holds 1/delta here
+        const float y = fabsf(x) * L.irc_delta;            // irc_delta holds 1/delta
         if (y <= 1.0f) return 1.0f;
         const float d = y + sqrtf(__fmaf_rn(y, y, -1.0f));
         return __frcp_rn(d * d);
@@ -119,7 +143,6 @@ __device__ __forceinline__ float irc_rel32(const Launch32 &L, float x) {
         const float m = fmaxf(m1, m2);
         return __frcp_rn(m * m) * L.irc_gnorm;              // irc_gnorm = 1 / max R
     } else if (IRC == HEART_IRC_PSEUDO_VOIGT) {
-        // (eta L + (1 - eta) G) / max, with L and G unit-area at FWHM F
         const float hf = 0.5f * L.irc_fwhm;
         const float lor = __fdividef(hf * hf, __fmaf_rn(x, x, hf * hf));   // L(x)/L(0)
         const float gau = __expf(-L.irc_c * x * x);                        // G(x)/G(0)
@@ -140,8 +163,10 @@ __device__ __forceinline__ float irc_rel32(const Launch32 &L, float x) {
 // is rejected exactly as the full evaluation would reject it.
 //   Darwin: R <= 1 / y^2 for |y| >= 1.  Darwin-Prins: R = 1/m^2 with m the
 //   larger root modulus, m >= |eta| >= |y|.  Lorentzian: (F/2)^2 / x^2.
-template <int IRC>
+//   pseudo-Voigt: the weighted Lorentzian tail plus the Gaussian at a.
+template <int IRC_T>
 __device__ __forceinline__ float irc_bound32(const Launch32 &L, float a) {
+    const int IRC = IRC_T >= 0 ? IRC_T : L.irc_kind;
     if (IRC == HEART_IRC_DARWIN) {
         const float y = a * L.irc_delta;
         return y <= 1.0f ? 1.0f : __frcp_rn(y * y);
@@ -153,124 +178,150 @@ __device__ __forceinline__ float irc_bound32(const Launch32 &L, float a) {
         return a <= hf ? 1.0f : __fdividef(hf * hf, a * a);
     } else if (IRC == HEART_IRC_BOX) {
         return a <= 0.5f * L.irc_fwhm ? 1.0f : 0.0f;
+    } else if (IRC == HEART_IRC_PSEUDO_VOIGT) {
+        const float hf = 0.5f * L.irc_fwhm;
+        if (a <= hf) return 1.0f;
+        return __fmaf_rn(L.irc_eta, __fdividef(hf * hf, a * a), L.irc_g * __expf(-L.irc_c * a * a)) * L.irc_gnorm;
     } else {
-        return 1.0f;                  // Gaussian and pseudo-Voigt: evaluated directly (one exp)
+        return 1.0f;                  // Gaussian: evaluated directly (one exp)
     }
 }
 
-// lane state of one ray being walked
+// lane state of one ray being walked (all FP32)
 struct Lane {
-    double x0[3], k[3], sB;               // FP64 segment anchors
-    float kf[3];                          // k in FP32
-    float A, sgn, sBf, cB;                // Bragg anchor, sign of k.N, sin / cos of aB + Delta_M
+    float x0[3], k[3];                    // segment start and direction, crystal frame
+    float A, sgn, sB, cB;                 // Bragg anchor, sign of k.N, sin / cos of aB + Delta_M
     float s_exit, Lsum, Lcomp;            // exit distance, Kahan sum of the path
     float inv_mu, pa, inv_1mpa, E;
     uint32_t pa_thr, rl, rh, call;
     int32_t face, nrefl, ncoll, no_bragg;
-    // cylinder along-segment constants
-    float cb1, cb2, cga, ck0, ctau0;
+    // cylinder: depth below the inner face at x0 and along-segment constants of k.N
+    float rho0, cb1, cb2, cga, ck0, ctau0;
 };
 
 // ---------------------------------------------------------------------------
-// spawn: source sample + entry intersection (Sec. 2.1, Sec. 2.2) in the local
-// frame; FP64 only where the Bragg decision needs it
+// spawn: source sample + entry (Sec. 2.1, Sec. 2.2) in the crystal frame
 // ---------------------------------------------------------------------------
-template <int GEOM>
-__device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, double x[3], double k[3], double &sB,
-                                      float &inv_mu, float &pa, uint32_t &pa_thr, float &E32, int &nb) {
+template <int GEOM_T>
+__device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3], float k[3], float &A,
+                                      float &sB, float &inv_mu, float &pa, uint32_t &pa_thr, float &E32, int &nb) {
+    const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
     const uint32_t rl = (uint32_t)ray, rh = (uint32_t)(ray >> 32);
     uint32_t a[4], b[4];
     philox4x32_10(rl, rh, 0u, 0u, L.k0, L.k1, a);
     philox4x32_10(rl, rh, 1u, 0u, L.k0, L.k1, b);
-    // direction: uniform in solid angle in the cone
-    const float w = u01_32(a[2]) * L.omc;
+    // direction, uniform in solid angle in the cone; dn = k.n_ref - axis.n_ref
+    const float w = u01_32(a[2]) * L.omc;                 // 1 - cos(phi)
     const float sphi = sqrtf(w * (2.0f - w));
-    float sb, cb;
-    sincospif(2.0f * u01_32(a[3]), &sb, &cb);
-    const double cphi = 1.0 - (double)w, p1 = (double)(sphi * cb), p2 = (double)(sphi * sb);
-    for (int i = 0; i < 3; ++i) k[i] = cphi * L.ax[i] + p1 * L.b1[i] + p2 * L.b2[i];
-    double o[3] = {L.o[0], L.o[1], L.o[2]};
+    float sbeta, cbeta;
+    sincospif(2.0f * u01_32(a[3]), &sbeta, &cbeta);
+    const float p1 = sphi * cbeta, p2 = sphi * sbeta;
+    for (int i = 0; i < 3; ++i) k[i] = __fmaf_rn(p2, L.b2[i], __fmaf_rn(p1, L.b1[i], __fmaf_rn(-w, L.ax[i], L.ax[i])));
+    const int ni = GEOM == HEART_FLAT ? 2 : 0;            // N (flat) or the cylinder axis
+    const float dn = __fmaf_rn(p2, L.b2[ni], __fmaf_rn(p1, L.b1[ni], -w * L.ax[ni]));
+    float o[3] = {L.o[0], L.o[1], L.o[2]};
     if (L.sig1 > 0.0f || L.sig2 > 0.0f) {
         const float r = sqrtf(-2.0f * __logf(u01_32(b[0])));
         float s, co;
-        __sincosf(6.28318530717958648f * (u01_32(b[1]) - 0.5f), &s, &co);
-        const double z1 = -(double)(L.sig1 * r * co), z2 = -(double)(L.sig2 * r * s);
-        for (int i = 0; i < 3; ++i) o[i] += z1 * L.b1[i] + z2 * L.b2[i];
+        sincos_2pi(u01_32(b[1]), &s, &co);
+        const float z1 = L.sig1 * r * co, z2 = L.sig2 * r * s;
+        for (int i = 0; i < 3; ++i) o[i] = __fmaf_rn(z2, L.b2[i], __fmaf_rn(z1, L.b1[i], o[i]));
     }
-    for (int i = 0; i < 3; ++i) x[i] = o[i];       // a miss reports its origin
-    // entry on the front face
+    for (int i = 0; i < 3; ++i) x[i] = o[i];              // a miss reports its origin
+    float dA;                                             // |k.N| at entry minus the cone-axis value
     if (GEOM == HEART_FLAT) {
-        if (!(k[2] < 0.0) || !(o[2] > 0.0)) return false;
-        const double t = o[2] / (-k[2]);
-        x[0] = o[0] + t * k[0];
-        x[1] = o[1] + t * k[1];
-        x[2] = 0.0;                                  // on the front face
-        if (fabs(x[0]) > (double)L.half_d || fabs(x[1]) > (double)L.half_n) return false;
+        if (!(k[2] < 0.0f) || !(o[2] > 0.0f)) return false;
+        const float t = o[2] / (-k[2]);
+        const float ex = __fmaf_rn(t, k[0], o[0]), ey = __fmaf_rn(t, k[1], o[1]);
+        if (fabsf(ex) > L.half_d || fabsf(ey) > L.half_n) return false;
+        x[0] = ex; x[1] = ey; x[2] = 0.0f;
+        dA = -dn;                                         // |k_h| = |a_h| - dn for k_h < 0
     } else {
-        const double c0 = o[1] * o[1] + o[2] * o[2] - L.R64 * L.R64;
-        if (!(c0 < 0.0)) return false;
-        const double aa = k[1] * k[1] + k[2] * k[2];
-        if (!(aa > 0.0)) return false;
-        const double bb = o[1] * k[1] + o[2] * k[2];
-        const double sq = sqrt(bb * bb - aa * c0);
-        const double t = (bb > 0.0) ? -c0 / (bb + sq) : (-bb + sq) / aa;
-        double xe[3];
-        for (int i = 0; i < 3; ++i) xe[i] = o[i] + t * k[i];
-        if (fabs(xe[0] - L.zc64) > (double)L.half_d) return false;
-        if (fabs(xe[2]) * (double)L.cphi > xe[1] * (double)L.sphi) return false;
+        const float aa = __fmaf_rn(k[1], k[1], k[2] * k[2]);
+        if (!(aa > 0.0f)) return false;
+        const float ro2 = __fmaf_rn(o[1], o[1], o[2] * o[2]);
+        const float c0 = ro2 - L.R * L.R;
+        if (!(c0 < 0.0f)) return false;
+        const float bo = __fmaf_rn(o[1], k[1], o[2] * k[2]);
+        const float sq = sqrtf(__fmaf_rn(bo, bo, -aa * c0));
+        const float t = (bo > 0.0f) ? -c0 / (bo + sq) : (sq - bo) / aa;
+        float xe[3];
+        for (int i = 0; i < 3; ++i) xe[i] = __fmaf_rn(t, k[i], o[i]);
+        if (fabsf(xe[0] - L.zc) > L.half_d) return false;
+        if (fabsf(xe[2]) * L.cphi > xe[1] * L.sphi) return false;
         for (int i = 0; i < 3; ++i) x[i] = xe[i];
+        // |k.N| at r = R: sqrt((1 - kz^2)(1 - eps_o)), eps_o = (ro^2 - bo^2/aa) / R^2,
+        // minus the sine of the cone axis to the cylinder axis, as small terms
+        const float eps_o = (ro2 - bo * bo / aa) / (L.R * L.R);
+        const float kabs = sqrtf(aa * (1.0f - eps_o));
+        const float num = -dn * (2.0f * L.a_n + dn) - aa * eps_o;   // |k.N|^2 - c_a^2
+        dA = num / (kabs + L.c_a);
     }
-    // energy (only rays that entered need it)
+    // energy (only rays that entered need it), as a small offset from the
+    // component's reference energy so that sin(aB) keeps ~1e-9 accuracy
     int c = L.n_comp - 1;
     for (int i = 0; i < L.n_comp - 1; ++i)
         if (a[0] < L.comp_thr[i]) { c = i; break; }
     const float up = u01_32(a[1]);
-    double E;
+    float E, ds;                                          // ds = sin(aB(E)) - sin(aB(e_ref))
+    const float e0 = L.e_ref[c], s0 = L.sB_raw[c];
     switch (L.kind[c]) {
-    case HEART_SRC_MONO: E = L.e0[c]; break;
-    case HEART_SRC_GAUSS: {
-        float s, co;
-        __sincosf(6.28318530717958648f * (u01_32(b[3]) - 0.5f), &s, &co);
-        E = L.e0[c] - (double)(L.width[c] * sqrtf(-2.0f * __logf(u01_32(b[2]))) * co);
+    case HEART_SRC_MONO: E = e0; ds = 0.0f; break;
+    case HEART_SRC_INV_E: {
+        const float g = (up - 0.5f) * L.half_ln[c];       // E = e_ref exp(g)
+        E = e0 * __expf(g);
+        ds = s0 * expm1f(-g);
         break;
     }
-    case HEART_SRC_LORENTZ: {
-        const float uu = __fmaf_rn(up, 1.0f - L.lF0[c], L.lF0[c]);
-        E = L.e0[c] + (double)(0.5f * L.width[c] * tanf(3.14159265f * (uu - 0.5f)));
+    default: {
+        float dE;
+        if (L.kind[c] == HEART_SRC_GAUSS) {
+            float s, co;
+            sincos_2pi(u01_32(b[3]), &s, &co);
+            dE = L.width[c] * sqrtf(-2.0f * __logf(u01_32(b[2]))) * co;
+        } else if (L.kind[c] == HEART_SRC_LORENTZ) {
+            const float uu = __fmaf_rn(up, 1.0f - L.lF0[c], L.lF0[c]);
+            dE = 0.5f * L.width[c] * tanf(3.14159265f * (uu - 0.5f));
+        } else {
+            dE = L.width[c] * (up - 0.5f);                // uniform: width holds hi - lo
+        }
+        E = e0 + dE;
+        const float r = dE / e0;
+        ds = -s0 * r / (1.0f + r);
         break;
     }
-    case HEART_SRC_INV_E: E = (double)(L.lo[c] * exp2f(up * log2f(L.hi[c] / L.lo[c]))); break;
-    default: E = (double)L.lo[c] + (double)(L.hi[c] - L.lo[c]) * (double)up; break;
     }
-    E32 = (float)E;
-    if (!(E > 0.0) || !isfinite(E)) return false;
-    // per-ray constants: sin(aB + Delta_M) in FP64 (Eq. BraggLaw), the rest FP32
-    const double sB0 = L.sB_scale / E;
-    nb = !(sB0 < 1.0);
+    E32 = E;
+    if (!(E > 0.0f) || !isfinite(E)) return false;
+    const float sraw = s0 + ds;
+    nb = !(sraw < 1.0f);
     float Q = 0.0f;
     if (!nb) {
-        const float cb0 = sqrtf(fmaxf(0.0f, 1.0f - (float)(sB0 * sB0)));
-        sB = sB0 * L.cos_shift + (double)(cb0 * L.sin_shift);
-        const float lam = (float)(12.398419843320026e-7 / E);        // mm
-        Q = L.K2 * lam * lam * lam / (2.0f * (float)sB0 * cb0);
+        // shift by Delta_M: sin(aB + dM) - sin(aB0 + dM) from small terms
+        const float craw = sqrtf(fmaxf(0.0f, __fmaf_rn(-sraw, sraw, 1.0f)));
+        const float dc = -ds * (sraw + s0) / (craw + L.cB_raw[c]);
+        const float dsp = __fmaf_rn(ds, L.cos_shift, dc * L.sin_shift);
+        sB = L.sB0[c] + dsp;
+        A = L.A0[c] + dA - dsp;
+        const float lam = 12.398419843320026e-7f / E;     // mm
+        Q = L.K2 * lam * lam * lam / (2.0f * sraw * craw);
     } else {
-        sB = 2.0;
+        sB = 2.0f;
+        A = 0.0f;
     }
-    const float mu0 = 1.0f / (L.labs * powf(E32 / L.labs_ref, L.labs_pow));
+    const float mu0 = 1.0f / (L.labs * __powf(E / L.labs_ref, L.labs_pow));
     const float mubar = __fmaf_rn(Q, L.irc_max, mu0);
     inv_mu = 1.0f / mubar;
     pa = nb ? 1.0f : mu0 / mubar;
     // absorb iff (w + 1/2) 2^-32 < pa  <=>  w < ceil(pa 2^32 - 1/2)
-    const double thr = ceil((double)pa * 4294967296.0 - 0.5);
-    pa_thr = thr >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)thr;
-    if (nb) pa_thr = 0xFFFFFFFFu;
+    pa_thr = nb ? 0xFFFFFFFFu : __float2uint_ru(fminf(pa * 4294967296.0f, 4294967040.0f));
     return true;
 }
 
-// start a straight segment at x0 along k (entry or after a reflection)
-template <int GEOM>
+// start a straight segment at x0 along k; s.A, s.sgn, s.sB and (cylinder) s.rho0 are set
+template <int GEOM_T>
 __device__ __forceinline__ void segment(const Launch32 &L, Lane &s) {
-    for (int i = 0; i < 3; ++i) s.kf[i] = (float)s.k[i];
+    const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
     s.Lsum = 0.0f;
     s.Lcomp = 0.0f;
     float best = 3.0e38f;
@@ -279,11 +330,9 @@ __device__ __forceinline__ void segment(const Launch32 &L, Lane &s) {
         v = fmaxf(v, 0.0f);
         if (v < best) { best = v; face = f; }
     };
-    double kappa;
     if (GEOM == HEART_FLAT) {
-        kappa = s.k[2];
-        const float h = (float)s.x0[2], a = (float)s.x0[0], b = (float)s.x0[1];
-        const float kh = s.kf[2], ka = s.kf[0], kb = s.kf[1];
+        const float h = s.x0[2], a = s.x0[0], b = s.x0[1];
+        const float kh = s.k[2], ka = s.k[0], kb = s.k[1];
         if (kh > 0) cand(-h / kh, HEART_EXIT_FRONT);
         if (kh < 0) cand((-L.thick - h) / kh, HEART_EXIT_BACK);
         if (ka > 0) cand((L.half_d - a) / ka, HEART_EXIT_SIDE);
@@ -291,80 +340,70 @@ __device__ __forceinline__ void segment(const Launch32 &L, Lane &s) {
         if (kb > 0) cand((L.half_n - b) / kb, HEART_EXIT_SIDE);
         if (kb < 0) cand((-L.half_n - b) / kb, HEART_EXIT_SIDE);
     } else {
-        const double X = s.x0[1], Y = s.x0[2];
-        const double r0 = sqrt(X * X + Y * Y);
-        const double b0 = X * s.k[1] + Y * s.k[2];
-        kappa = -b0 / r0;
-        const float rho = (float)(r0 - L.R64);               // depth below the inner face
-        const float aa = s.kf[1] * s.kf[1] + s.kf[2] * s.kf[2];
-        const float bb = (float)b0, R = L.R, t = L.thick;
-        const float ci = rho * (2.0f * R + rho);                // r^2 - R^2
-        const float co = (rho - t) * (2.0f * R + rho + t);      // r^2 - (R + t)^2
+        const float R = L.R, t = L.thick, rho = s.rho0;
+        const float r0 = R + rho;
+        const float X = s.x0[1], Y = s.x0[2];
+        const float kappa = s.sgn * (s.sB + s.A);           // k.N at x0
+        const float aa = __fmaf_rn(s.k[1], s.k[1], s.k[2] * s.k[2]);
+        const float bb = -kappa * r0;                        // (X, Y) . (kX, kY)
+        const float ci = rho * (2.0f * R + rho);             // r^2 - R^2
+        const float co = (rho - t) * (2.0f * R + rho + t);   // r^2 - (R + t)^2
         if (aa > 0.0f) {
             if (bb < 0.0f) {
-                const float disc = bb * bb - aa * ci;
-                if (disc >= 0.0f) cand(ci / (-bb + sqrtf(disc)), HEART_EXIT_FRONT);
+                const float disc = __fmaf_rn(bb, bb, -aa * ci);
+                if (disc >= 0.0f) cand(ci / (sqrtf(disc) - bb), HEART_EXIT_FRONT);
             }
-            const float sq = sqrtf(fmaxf(bb * bb - aa * co, 0.0f));
-            cand(bb > 0.0f ? -co / (bb + sq) : (-bb + sq) / aa, HEART_EXIT_BACK);
+            const float sq = sqrtf(fmaxf(__fmaf_rn(bb, bb, -aa * co), 0.0f));
+            cand(bb > 0.0f ? -co / (bb + sq) : (sq - bb) / aa, HEART_EXIT_BACK);
         }
-        const float z = (float)(s.x0[0] - L.zc64), kz = s.kf[0];
+        const float z = s.x0[0] - L.zc, kz = s.k[0];
         if (kz > 0) cand((L.half_d - z) / kz, HEART_EXIT_SIDE);
         if (kz < 0) cand((-L.half_d - z) / kz, HEART_EXIT_SIDE);
-        const float Xf = (float)X, Yf = (float)Y;
-        const float gp = -Xf * L.sphi + Yf * L.cphi, rp = -s.kf[1] * L.sphi + s.kf[2] * L.cphi;
+        const float gp = -X * L.sphi + Y * L.cphi, rp = -s.k[1] * L.sphi + s.k[2] * L.cphi;
         if (rp > 0) cand(-gp / rp, HEART_EXIT_SIDE);
-        const float gm = -Xf * L.sphi - Yf * L.cphi, rm = -s.kf[1] * L.sphi - s.kf[2] * L.cphi;
+        const float gm = -X * L.sphi - Y * L.cphi, rm = -s.k[1] * L.sphi - s.k[2] * L.cphi;
         if (rm > 0) cand(-gm / rm, HEART_EXIT_SIDE);
         // k.N along the segment: r(l)^2 = r0^2 (1 + l (cb1 + l cb2))
-        const float inv_r0 = (float)(1.0 / r0);
-        s.cb1 = 2.0f * bb * inv_r0 * inv_r0;
-        s.cb2 = aa * inv_r0 * inv_r0;
-        s.cga = aa * inv_r0;
-        s.ck0 = (float)kappa;
-        s.ctau0 = (float)((X * s.k[2] - Y * s.k[1]) / r0);    // k . t2 at x0 (t2 = N x axis)
+        const float ir0 = 1.0f / r0;
+        s.cb1 = 2.0f * bb * ir0 * ir0;
+        s.cb2 = aa * ir0 * ir0;
+        s.cga = aa * ir0;
+        s.ck0 = kappa;
+        s.ctau0 = (X * s.k[2] - Y * s.k[1]) * ir0;          // k . t2 at x0 (t2 = N x axis)
     }
     s.s_exit = best;
     s.face = face;
-    s.sgn = kappa < 0.0 ? -1.0f : 1.0f;
-    s.A = (float)(fabs(kappa) - s.sB);
 }
 
-__device__ __forceinline__ void to_global(const Launch32 &L, const double *p, double *g, bool point) {
+__device__ __forceinline__ void to_global(const Launch32 &L, const float *p, double *g, bool point) {
     for (int i = 0; i < 3; ++i)
-        g[i] = (point ? L.fc[i] : 0.0) + p[0] * L.fa[0][i] + p[1] * L.fa[1][i] + p[2] * L.fa[2][i];
+        g[i] = (point ? L.fc[i] : 0.0) + (double)p[0] * L.fa[0][i] + (double)p[1] * L.fa[1][i] +
+               (double)p[2] * L.fa[2][i];
 }
 
-template <typename T>
-__device__ __forceinline__ void add_image(const Launch32 &L, void *img, int ix, int iy) {
-    const size_t idx = (size_t)iy * (size_t)L.nx + (size_t)ix;
-    if (L.count64) atomicAdd((unsigned long long *)img + idx, 1ull);
-    else atomicAdd((int *)img + idx, 1);
-}
-
-// tally slots in shared memory (32-bit, flushed as 64-bit)
+// tally slots in shared memory (32-bit per chunk, flushed as 64-bit)
 struct BlockTally {
     unsigned int t[kTallyN];
+    unsigned long long coll, emit, miss;
 };
 
 // finish a ray: detector projection + binning + tallies (+ record)
-template <int GEOM, bool REC>
-__device__ __forceinline__ void finish(const Launch32 &L, Lane &s, int outcome, void *img, BlockTally &bt,
-                                       heart_ray_record *rec) {
+template <bool REC>
+__device__ __forceinline__ void finish(const Launch32 &L, Lane &s, int outcome, BlockTally &bt) {
     int ix = -1, iy = -1, hit = 0;
     float u = __int_as_float(0x7fc00000), v = u;
-    double xe[3];
-    const float len = (outcome == HEART_EXIT_FRONT || outcome == HEART_EXIT_BACK || outcome == HEART_EXIT_SIDE)
-                          ? s.s_exit : s.Lsum;
-    for (int i = 0; i < 3; ++i) xe[i] = s.x0[i] + (double)len * s.k[i];
-    if (outcome == HEART_EXIT_FRONT || outcome == HEART_EXIT_BACK || outcome == HEART_EXIT_SIDE) {
-        const float rel[3] = {(float)(L.D0[0] - xe[0]), (float)(L.D0[1] - xe[1]), (float)(L.D0[2] - xe[2])};
-        const float den = s.kf[0] * L.nd[0] + s.kf[1] * L.nd[1] + s.kf[2] * L.nd[2];
+    const bool out = outcome == HEART_EXIT_FRONT || outcome == HEART_EXIT_BACK || outcome == HEART_EXIT_SIDE;
+    const float len = out ? s.s_exit : s.Lsum;
+    float xe[3];
+    for (int i = 0; i < 3; ++i) xe[i] = __fmaf_rn(len, s.k[i], s.x0[i]);
+    if (out) {
+        const float rel[3] = {L.D0[0] - xe[0], L.D0[1] - xe[1], L.D0[2] - xe[2]};
+        const float den = s.k[0] * L.nd[0] + s.k[1] * L.nd[1] + s.k[2] * L.nd[2];
         if (den != 0.0f) {
             const float t = (rel[0] * L.nd[0] + rel[1] * L.nd[1] + rel[2] * L.nd[2]) / den;
             if (t > 0.0f) {
-                const float P[3] = {__fmaf_rn(t, s.kf[0], -rel[0]), __fmaf_rn(t, s.kf[1], -rel[1]),
-                                    __fmaf_rn(t, s.kf[2], -rel[2])};
+                const float P[3] = {__fmaf_rn(t, s.k[0], -rel[0]), __fmaf_rn(t, s.k[1], -rel[1]),
+                                    __fmaf_rn(t, s.k[2], -rel[2])};
                 u = P[0] * L.eu[0] + P[1] * L.eu[1] + P[2] * L.eu[2];
                 v = P[0] * L.ev[0] + P[1] * L.ev[1] + P[2] * L.ev[2];
                 const float fx = __fmaf_rn(u, L.inv_pix, L.hnx), fy = __fmaf_rn(v, L.inv_pix, L.hny);
@@ -372,7 +411,9 @@ __device__ __forceinline__ void finish(const Launch32 &L, Lane &s, int outcome, 
                     ix = min((int)fx, L.nx - 1);
                     iy = min((int)fy, L.ny - 1);
                     hit = 1;
-                    add_image<int>(L, img, ix, iy);
+                    const size_t idx = (size_t)iy * (size_t)L.nx + (size_t)ix;
+                    if (L.count64) atomicAdd((unsigned long long *)L.img + idx, 1ull);
+                    else atomicAdd((int *)L.img + idx, 1);
                     atomicAdd(&bt.t[T_DET_HITS], 1u);
                 }
             }
@@ -383,7 +424,7 @@ __device__ __forceinline__ void finish(const Launch32 &L, Lane &s, int outcome, 
     if (s.no_bragg) atomicAdd(&bt.t[T_NO_BRAGG], 1u);
     if (REC) {
         const uint64_t ray = ((uint64_t)s.rh << 32) | s.rl;
-        heart_ray_record &o = rec[ray - L.offset];
+        heart_ray_record &o = L.rec[ray - L.offset];
         o.ray_id = ray;
         o.outcome = outcome;
         o.nrefl = s.nrefl;
@@ -401,8 +442,9 @@ __device__ __forceinline__ void finish(const Launch32 &L, Lane &s, int outcome, 
 }
 
 // one tentative collision; returns an outcome code, or -1 while the ray lives
-template <int GEOM, int IRC>
+template <int GEOM_T, int IRC>
 __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab) {
+    const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
     if (s.ncoll >= L.max_coll) return HEART_STUCK;
     uint32_t w[4];
     philox4x32_10(s.rl, s.rh, s.call++, 0u, L.k0, L.k1, w);
@@ -419,194 +461,254 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
     const float q = mdf_q32(tab, w[2]);
     const float st = sqrtf(q * (2.0f - q));
     float sx, cx;
-    __sincosf(6.28318530717958648f * (u01_32(w[3]) - 0.5f), &sx, &cx);
-    sx = -sx;
-    cx = -cx;
-    float D, dk = 0.0f, rinv = 1.0f;
+    sincos_2pi(u01_32(w[3]), &sx, &cx);
+    float D, dk = 0.0f, eps = 0.0f, rho = 1.0f;
     if (GEOM == HEART_FLAT) {
-        D = __fmaf_rn(st, __fmaf_rn(s.kf[0], cx, s.kf[1] * sx), -q * s.kf[2]);
+        D = __fmaf_rn(st, __fmaf_rn(s.k[0], cx, s.k[1] * sx), -q * s.k[2]);
     } else {
         // k.N and k.t2 at the collision point from the along-segment length
         const float Lp = s.Lsum;
-        const float eps = Lp * __fmaf_rn(Lp, s.cb2, s.cb1);
-        const float rho = sqrtf(1.0f + eps);
-        rinv = 1.0f / rho;
+        eps = Lp * __fmaf_rn(Lp, s.cb2, s.cb1);
+        rho = sqrtf(1.0f + eps);
+        const float rinv = 1.0f / rho;
         dk = (s.ck0 * (-eps / (1.0f + rho)) - Lp * s.cga) * rinv;
         const float tau = s.ctau0 * rinv;
-        D = __fmaf_rn(st, __fmaf_rn(s.kf[0], cx, tau * sx), -q * (s.ck0 + dk));
+        D = __fmaf_rn(st, __fmaf_rn(s.k[0], cx, tau * sx), -q * (s.ck0 + dk));
     }
-    const float e = __fmaf_rn(s.sgn, D + dk, s.A);            // |k.n| - sin(aB + Delta_M)
+    const float Ac = __fmaf_rn(s.sgn, dk, s.A);               // anchor at the collision point
+    const float e = __fmaf_rn(s.sgn, D, Ac);                  // |k.n| - sin(aB + Delta_M)
     if (v >= irc_bound32<IRC>(L, fabsf(e))) return -1;        // rejected whatever Delta is
-    float sa = s.sBf + e;
+    float sa = s.sB + e;
     float delta;
     if (sa > 0.0f) {
         sa = fminf(sa, 1.0f);
         const float cs = sqrtf(fmaxf(0.0f, 1.0f - sa * sa));
-        delta = asinf(fminf(1.0f, e * (2.0f * s.sBf + e) / __fmaf_rn(sa, s.cB, s.sBf * cs)));
+        delta = asinf(fmaxf(-1.0f, fminf(1.0f, e * (2.0f * s.sB + e) / __fmaf_rn(sa, s.cB, s.sB * cs))));
     } else {
         sa = fminf(-sa, 1.0f);                                 // the normal flipped side
-        delta = asinf(sa) - asinf(s.sBf);
+        delta = asinf(sa) - asinf(s.sB);
     }
     const float c2 = __fmaf_rn(-2.0f * sa, sa, 1.0f);
     const float G = 0.5f * __fmaf_rn(c2, c2, 1.0f);
     if (v < irc_rel32<IRC>(L, delta) * G) {
         ++s.nrefl;
         if (s.nrefl > L.max_refl) return HEART_CAPPED;
-        // reflection k <- k - 2 (k.n) n in FP64 (Sec. 2.2.4)
-        double n[3];
-        const double ct = 1.0 - (double)q;
+        // reflection k <- k - 2 (k.n) n (Sec. 2.2.4)
+        const float ct = 1.0f - q;
+        float n[3];
         if (GEOM == HEART_FLAT) {
-            n[0] = (double)(st * cx);
-            n[1] = (double)(st * sx);
-            n[2] = ct;
+            n[0] = st * cx; n[1] = st * sx; n[2] = ct;
         } else {
-            const double Lp = (double)s.Lsum;
-            const double X = s.x0[1] + Lp * s.k[1], Y = s.x0[2] + Lp * s.k[2];
-            const double ir = 1.0 / sqrt(X * X + Y * Y);
-            const double sxs = (double)(st * sx);
-            n[0] = (double)(st * cx);
+            const float X = __fmaf_rn(s.Lsum, s.k[1], s.x0[1]), Y = __fmaf_rn(s.Lsum, s.k[2], s.x0[2]);
+            const float drho = (L.R + s.rho0) * eps / (1.0f + rho);   // r - r0 at the collision
+            const float ir = 1.0f / (L.R + s.rho0 + drho);
+            const float sxs = st * sx;
+            n[0] = st * cx;
             n[1] = (-ct * X - sxs * Y) * ir;
             n[2] = (-ct * Y + sxs * X) * ir;
+            s.rho0 += drho;                                        // depth of the new segment start
         }
-        const double kn = (s.sgn < 0.0f ? -1.0 : 1.0) * (s.sB + (double)e);
-        double kk = 0.0;
+        const float kn = s.sgn * (s.sB + e);
+        float kk = 0.0f;
         for (int i = 0; i < 3; ++i) {
-            s.x0[i] += (double)s.Lsum * s.k[i];
-            s.k[i] -= 2.0 * kn * n[i];
-            kk += s.k[i] * s.k[i];
+            s.x0[i] = __fmaf_rn(s.Lsum, s.k[i], s.x0[i]);
+            s.k[i] = __fmaf_rn(-2.0f * kn, n[i], s.k[i]);
+            kk = __fmaf_rn(s.k[i], s.k[i], kk);
         }
-        const double sc = 1.5 - 0.5 * kk;                       // one Newton step of 1/sqrt(kk)
+        const float sc = rsqrtf(kk);
         for (int i = 0; i < 3; ++i) s.k[i] *= sc;
-        segment<GEOM>(L, s);
+        // new anchor from small terms: k'.N = sgn * T, T = Ac - sB - 2e + 2q (sB + e)
+        const float T = Ac - s.sB - 2.0f * e + 2.0f * q * (s.sB + e);
+        if (T < 0.0f) {
+            s.A = -Ac + 2.0f * e - 2.0f * q * (s.sB + e);
+            s.sgn = -s.sgn;
+        } else {
+            s.A = T - s.sB;
+        }
+        segment<GEOM_T>(L, s);
     }
     return -1;
 }
 
+// Work plan: chunks of (job, ray range) claimed by blocks from a global counter.
+struct WorkPlan {
+    const Launch32 *jobs;                 // device job table, or nullptr for the single job
+    const unsigned long long *chunk_begin;// first chunk index of each job (n_jobs + 1 entries)
+    int32_t n_jobs;
+    uint32_t chunk_rays;
+    unsigned long long n_chunks;
+    unsigned long long *counter;          // zero before the launch
+};
+
 template <int GEOM, int IRC, bool REC>
-__global__ void __launch_bounds__(kBlockThreads, 5) k_trace_fp32(const Launch32 L, void *img,
-                                                              unsigned long long *scratch, heart_ray_record *rec) {
+__global__ void __launch_bounds__(kBlockThreads, 6) k_trace_fp32(const Launch32 single, const WorkPlan W) {
+    __shared__ Launch32 sL;
     __shared__ float s_tab[kMdfKnots];
     __shared__ WarpBuf s_buf[kWarpsPerBlock];
     __shared__ BlockTally bt;
-    for (int i = threadIdx.x; i < kMdfKnots; i += blockDim.x) s_tab[i] = L.tab[i];
-    for (int i = threadIdx.x; i < kTallyN; i += blockDim.x) bt.t[i] = 0u;
+    __shared__ unsigned long long s_next, s_end, s_chunk;
+    __shared__ int s_job;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    WarpBuf &B = s_buf[wid];
-    if (lane == 0) B.count = 0;
-    __syncthreads();
-    unsigned long long *counter = scratch + kCounterWord;
     const unsigned lt_mask = (1u << lane) - 1u;
-
-    Lane s;
-    bool alive = false;
-    bool more = true;                  // global rays may remain
-    unsigned long long my_coll = 0, my_emit = 0, my_miss = 0;
+    WarpBuf &B = s_buf[wid];
+    const Launch32 &L = sL;
+    int cur_job = -1;
     for (;;) {
-        const unsigned idle = __ballot_sync(0xffffffffu, !alive);
-        const int n_idle = __popc(idle);
-        if (n_idle == 32 && !more && B.count == 0) break;
-        if (n_idle >= L.refill || (n_idle > 0 && !more) || n_idle == 32) {
-            // make sure the buffer can serve every idle lane
-            while (more && B.count < n_idle) {
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(counter, 32ull);
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (base >= L.n) { more = false; break; }
-                const uint64_t id = base + lane;
-                double x[3], k[3], sB = 0.0;
-                float inv_mu = 0.f, pa = 0.f, E32 = 0.f;
-                uint32_t pa_thr = 0;
-                int nb = 0;
-                bool hit = false;
-                if (id < L.n) {
-                    ++my_emit;
-                    hit = spawn<GEOM>(L, L.offset + id, x, k, sB, inv_mu, pa, pa_thr, E32, nb);
-                    if (!hit) {
-                        ++my_miss;
-                        if (REC) {
-                            heart_ray_record &o = rec[id];
-                            o.ray_id = L.offset + id;
-                            o.outcome = HEART_MISS;
-                            o.nrefl = 0; o.ncoll = 0; o.energy_keV = E32;
-                            to_global(L, x, o.pos, true);
-                            to_global(L, k, o.dir, false);
-                            o.u_mm = __longlong_as_double(0x7ff8000000000000LL); o.v_mm = o.u_mm;
-                            o.ix = -1; o.iy = -1; o.det_hit = 0; o.no_bragg = 0;
+        if (threadIdx.x == 0) {
+            const unsigned long long c = atomicAdd(W.counter, 1ull);
+            s_chunk = c;
+            if (c < W.n_chunks) {
+                int j = 0;
+                unsigned long long first = c * (unsigned long long)W.chunk_rays, nj = single.n;
+                if (W.jobs) {
+                    int lo = 0, hi = W.n_jobs;           // largest j with chunk_begin[j] <= c
+                    while (hi - lo > 1) { const int m = (lo + hi) >> 1; if (W.chunk_begin[m] <= c) lo = m; else hi = m; }
+                    j = lo;
+                    first = (c - W.chunk_begin[j]) * (unsigned long long)W.chunk_rays;
+                    nj = W.jobs[j].n;
+                }
+                s_job = j;
+                s_next = first;
+                s_end = min(first + (unsigned long long)W.chunk_rays, nj);
+            }
+        }
+        __syncthreads();
+        if (s_chunk >= W.n_chunks) break;
+        const int j = s_job;
+        if (j != cur_job) {
+            // this block's job changed: load its parameters, then its mosaic table
+            const uint32_t *src = (const uint32_t *)(W.jobs ? &W.jobs[j] : &single);
+            uint32_t *dst = (uint32_t *)&sL;
+            for (int i = threadIdx.x; i < (int)(sizeof(Launch32) / 4); i += blockDim.x) dst[i] = src[i];
+            __syncthreads();
+            for (int i = threadIdx.x; i < kMdfKnots; i += blockDim.x) s_tab[i] = sL.tab[i];
+            cur_job = j;
+        }
+        for (int i = threadIdx.x; i < kTallyN; i += blockDim.x) bt.t[i] = 0u;
+        if (threadIdx.x == 0) { bt.coll = 0ull; bt.emit = 0ull; bt.miss = 0ull; }
+        if (lane == 0) B.count = 0;
+        __syncthreads();
+
+        Lane s;
+        bool alive = false;
+        bool more = true;
+        unsigned long long my_coll = 0, my_emit = 0, my_miss = 0;
+        for (;;) {
+            const unsigned idle = __ballot_sync(0xffffffffu, !alive);
+            const int n_idle = __popc(idle);
+            if (n_idle == 32 && !more && B.count == 0) break;
+            if (n_idle >= L.refill || (n_idle > 0 && !more) || n_idle == 32) {
+                while (more && B.count < n_idle) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(&s_next, 32ull);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    const unsigned long long end = s_end;
+                    if (base >= end) { more = false; break; }
+                    const unsigned long long id = base + lane;
+                    float x[3], k[3], A = 0.f, sB = 0.f, inv_mu = 0.f, pa = 0.f, E32 = 0.f;
+                    uint32_t pa_thr = 0;
+                    int nb = 0;
+                    bool hit = false;
+                    if (id < end) {
+                        ++my_emit;
+                        hit = spawn<GEOM>(L, L.offset + id, x, k, A, sB, inv_mu, pa, pa_thr, E32, nb);
+                        if (!hit) {
+                            ++my_miss;
+                            if (REC) {
+                                heart_ray_record &o = L.rec[id];
+                                o.ray_id = L.offset + id;
+                                o.outcome = HEART_MISS;
+                                o.nrefl = 0; o.ncoll = 0; o.energy_keV = E32;
+                                to_global(L, x, o.pos, true);
+                                to_global(L, k, o.dir, false);
+                                o.u_mm = __longlong_as_double(0x7ff8000000000000LL); o.v_mm = o.u_mm;
+                                o.ix = -1; o.iy = -1; o.det_hit = 0; o.no_bragg = 0;
+                            }
                         }
                     }
+                    const unsigned hm = __ballot_sync(0xffffffffu, hit);
+                    if (hit) {
+                        const int slot = B.count + __popc(hm & lt_mask);
+                        for (int i = 0; i < 3; ++i) { B.x[i][slot] = x[i]; B.k[i][slot] = k[i]; }
+                        const uint64_t ray = L.offset + id;
+                        B.A[slot] = A;
+                        B.sB[slot] = sB;
+                        B.rl[slot] = (uint32_t)ray;
+                        B.rh[slot] = (uint32_t)(ray >> 32);
+                        B.inv_mu[slot] = inv_mu;
+                        B.pa[slot] = pa;
+                        B.pa_thr[slot] = pa_thr;
+                        B.E[slot] = E32;
+                        B.nb[slot] = nb;
+                    }
+                    __syncwarp();
+                    if (lane == 0) B.count += __popc(hm);
+                    __syncwarp();
+                    if (base + 32 >= end) more = false;
                 }
-                const unsigned hm = __ballot_sync(0xffffffffu, hit);
-                if (hit) {
-                    const int slot = B.count + __popc(hm & lt_mask);
-                    for (int i = 0; i < 3; ++i) { B.x[i][slot] = x[i]; B.k[i][slot] = k[i]; }
-                    B.sB[slot] = sB;
-                    const uint64_t ray = L.offset + id;
-                    B.rl[slot] = (uint32_t)ray;
-                    B.rh[slot] = (uint32_t)(ray >> 32);
-                    B.inv_mu[slot] = inv_mu;
-                    B.pa[slot] = pa;
-                    B.pa_thr[slot] = pa_thr;
-                    B.E[slot] = E32;
-                    B.nb[slot] = nb;
+                const int avail = B.count;
+                const int rank = __popc(idle & lt_mask);
+                if (!alive && rank < avail) {
+                    const int slot = avail - 1 - rank;
+                    for (int i = 0; i < 3; ++i) { s.x0[i] = B.x[i][slot]; s.k[i] = B.k[i][slot]; }
+                    s.A = B.A[slot];
+                    s.sB = B.sB[slot];
+                    s.rl = B.rl[slot];
+                    s.rh = B.rh[slot];
+                    s.inv_mu = B.inv_mu[slot];
+                    s.pa = B.pa[slot];
+                    s.pa_thr = B.pa_thr[slot];
+                    s.E = B.E[slot];
+                    s.no_bragg = B.nb[slot];
+                    s.inv_1mpa = s.pa < 1.0f ? 1.0f / (1.0f - s.pa) : 0.0f;
+                    s.cB = sqrtf(fmaxf(0.0f, __fmaf_rn(-s.sB, s.sB, 1.0f)));
+                    s.sgn = -1.0f;                           // entering: k.N < 0
+                    s.rho0 = 0.0f;                           // on the front face
+                    s.call = 2u;
+                    s.nrefl = 0;
+                    s.ncoll = 0;
+                    segment<GEOM>(L, s);
+                    alive = true;
                 }
                 __syncwarp();
-                if (lane == 0) B.count += __popc(hm);
+                if (lane == 0) B.count = avail - min(avail, n_idle);
                 __syncwarp();
-                if (base + 32 >= L.n) more = false;
             }
-            // idle lanes pop, highest slots first
-            const int avail = B.count;
-            const int rank = __popc(idle & lt_mask);
-            if (!alive && rank < avail) {
-                const int slot = avail - 1 - rank;
-                for (int i = 0; i < 3; ++i) { s.x0[i] = B.x[i][slot]; s.k[i] = B.k[i][slot]; }
-                s.sB = B.sB[slot];
-                s.rl = B.rl[slot];
-                s.rh = B.rh[slot];
-                s.inv_mu = B.inv_mu[slot];
-                s.pa = B.pa[slot];
-                s.pa_thr = B.pa_thr[slot];
-                s.E = B.E[slot];
-                s.no_bragg = B.nb[slot];
-                s.inv_1mpa = s.pa < 1.0f ? 1.0f / (1.0f - s.pa) : 0.0f;
-                s.sBf = (float)s.sB;
-                s.cB = sqrtf(fmaxf(0.0f, 1.0f - s.sBf * s.sBf));
-                s.call = 2u;
-                s.nrefl = 0;
-                s.ncoll = 0;
-                segment<GEOM>(L, s);
-                alive = true;
-            }
-            __syncwarp();
-            if (lane == 0) B.count = avail - min(avail, n_idle);
-            __syncwarp();
-        }
-        if (alive) {
-            const int oc = step<GEOM, IRC>(L, s, s_tab);
-            if (oc >= 0) {
-                my_coll += (unsigned long long)s.ncoll;
-                finish<GEOM, REC>(L, s, oc, img, bt, rec);
-                alive = false;
+            if (alive) {
+                const int oc = step<GEOM, IRC>(L, s, s_tab);
+                if (oc >= 0) {
+                    my_coll += (unsigned long long)s.ncoll;
+                    finish<REC>(L, s, oc, bt);
+                    alive = false;
+                }
             }
         }
+        for (int off = 16; off > 0; off >>= 1) {
+            my_coll += __shfl_down_sync(0xffffffffu, my_coll, off);
+            my_emit += __shfl_down_sync(0xffffffffu, my_emit, off);
+            my_miss += __shfl_down_sync(0xffffffffu, my_miss, off);
+        }
+        if (lane == 0) {
+            atomicAdd(&bt.coll, my_coll);
+            atomicAdd(&bt.emit, my_emit);
+            atomicAdd(&bt.miss, my_miss);
+        }
+        __syncthreads();
+        // flush this chunk's tallies to the job
+        unsigned long long *T = sL.tally;
+        for (int i = threadIdx.x; i < kTallyN; i += blockDim.x) {
+            unsigned long long v = bt.t[i];
+            if (i == T_COLLISIONS) v = bt.coll;
+            if (i == T_EMITTED) v = bt.emit;
+            if (i == T_MISS) v = bt.miss;
+            if (v) atomicAdd(&T[i], v);
+        }
+        __syncthreads();
     }
-    for (int off = 16; off > 0; off >>= 1) {
-        my_coll += __shfl_down_sync(0xffffffffu, my_coll, off);
-        my_emit += __shfl_down_sync(0xffffffffu, my_emit, off);
-        my_miss += __shfl_down_sync(0xffffffffu, my_miss, off);
-    }
-    __syncthreads();
-    if (lane == 0) {
-        atomicAdd(&scratch[T_COLLISIONS], my_coll);
-        atomicAdd(&scratch[T_EMITTED], my_emit);
-        atomicAdd(&scratch[T_MISS], my_miss);
-    }
-    for (int i = threadIdx.x; i < kTallyN; i += blockDim.x)
-        if (bt.t[i] && i != T_EMITTED && i != T_MISS && i != T_COLLISIONS) atomicAdd(&scratch[i], (unsigned long long)bt.t[i]);
 }
 
 // ---------------------------------------------------------------------------
-// host side: local-frame parameters and launch
+// host side: crystal-frame parameters, small-quantity anchors and launch
 // ---------------------------------------------------------------------------
 namespace {
 void to_local(const SpecParams &S, const double *v, double *out, bool point) {
@@ -624,41 +726,70 @@ void to_local(const SpecParams &S, const double *v, double *out, bool point) {
 void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
                    Launch32 &L) {
     std::memset(&L, 0, sizeof L);
-    to_local(S, P.origin, L.o, true);
-    to_local(S, P.ax, L.ax, false);
-    to_local(S, P.b1, L.b1, false);
-    to_local(S, P.b2, L.b2, false);
+    double o[3], ax[3], b1[3], b2[3];
+    to_local(S, P.origin, o, true);
+    to_local(S, P.ax, ax, false);
+    to_local(S, P.b1, b1, false);
+    to_local(S, P.b2, b2, false);
+    for (int i = 0; i < 3; ++i) {
+        L.o[i] = (float)o[i];
+        L.ax[i] = (float)ax[i];
+        L.b1[i] = (float)b1[i];
+        L.b2[i] = (float)b2[i];
+    }
     L.omc = (float)P.one_minus_cos_max;
     L.sig1 = (float)P.sig1;
     L.sig2 = (float)P.sig2;
+    // the reference direction's normal component: flat N (local z), cylinder axis (local x)
+    const double a_n = S.geometry == HEART_FLAT ? ax[2] : ax[0];
+    L.a_n = (float)a_n;
+    const double axis_sine = std::sqrt(std::fmax(0.0, 1.0 - a_n * a_n));   // cylinder: |k.N| of the axis ray
+    L.c_a = (float)axis_sine;
+    const double cs = std::cos(S.irc_shift), sn = std::sin(S.irc_shift);
+    L.cos_shift = (float)cs;
+    L.sin_shift = (float)sn;
     L.n_comp = P.n_comp;
     for (int i = 0; i < P.n_comp; ++i) {
         // first word w with (w + 1/2) 2^-32 >= cumw
         const double thr = std::ceil(P.cumw[i] * 4294967296.0 - 0.5);
         L.comp_thr[i] = thr >= 4294967295.0 ? 0xFFFFFFFFu : (thr <= 0 ? 0u : (uint32_t)thr);
         L.kind[i] = P.kind[i];
-        L.e0[i] = P.e0[i];
-        L.width[i] = (float)P.width[i];
-        L.lo[i] = (float)P.lo[i];
-        L.hi[i] = (float)P.hi[i];
+        double e_ref = P.e0[i];
+        switch (P.kind[i]) {
+        case HEART_SRC_INV_E:
+            e_ref = std::sqrt(P.lo[i] * P.hi[i]);
+            L.half_ln[i] = (float)std::log(P.hi[i] / P.lo[i]);
+            break;
+        case HEART_SRC_UNIFORM:
+            e_ref = 0.5 * (P.lo[i] + P.hi[i]);
+            L.width[i] = (float)(P.hi[i] - P.lo[i]);
+            break;
+        default:
+            L.width[i] = (float)P.width[i];
+        }
+        L.e_ref[i] = (float)e_ref;
         L.lF0[i] = (float)P.lorentz_F0[i];
+        const double s0 = 12.398419843320026 / (2.0 * S.d_A * e_ref);
+        L.sB_raw[i] = (float)s0;
+        const double c0 = s0 < 1.0 ? std::sqrt(1.0 - s0 * s0) : 0.0;
+        L.cB_raw[i] = (float)c0;
+        const double sBs = s0 < 1.0 ? s0 * cs + c0 * sn : s0;      // sin(aB + Delta_M)
+        L.sB0[i] = (float)sBs;
+        // anchor of the cone-axis ray: |a_n| (flat) or the axis sine (cylinder), minus sB
+        const double kref = S.geometry == HEART_FLAT ? std::fabs(a_n) : axis_sine;
+        L.A0[i] = (float)(kref - sBs);
     }
     L.half_d = (float)S.half_d;
     L.half_n = (float)S.half_n;
     L.thick = (float)S.thickness;
     L.R = (float)S.radius;
-    L.R64 = S.radius;
     L.zc = (float)S.zc;
-    L.zc64 = S.zc;
     L.sphi = (float)S.sphi;
     L.cphi = (float)S.cphi;
-    L.cos_shift = std::cos(S.irc_shift);
-    L.sin_shift = (float)std::sin(S.irc_shift);
     // rocking curve, relative to its maximum
     L.irc_fwhm = (float)S.irc_fwhm;
     L.irc_eta = (float)S.irc_eta;
     L.irc_g = (float)S.irc_g;
-    L.inv_irc_max = (float)(1.0 / S.irc_max);
     L.irc_c = (float)(4.0 * 0.69314718055994530942 / (S.irc_fwhm * S.irc_fwhm));
     switch (S.irc) {
     case HEART_IRC_DARWIN: L.irc_delta = (float)(1.0 / S.irc_delta); break;
@@ -667,17 +798,15 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
         L.irc_gnorm = (float)(1.0 / (S.irc_max * S.irc_norm));   // 1 / max R(y)
         break;
     case HEART_IRC_PSEUDO_VOIGT: {
-        const double F = S.irc_fwhm, eta = S.irc_eta;
-        const double L0 = 2.0 / (3.14159265358979323846 * F), G0 = std::sqrt(4.0 * 0.69314718055994530942 / 3.14159265358979323846) / F;
-        // (eta L0 l(x) + (1-eta) G0 g(x)) / max  with l, g the shapes relative to their peaks
-        L.irc_eta = (float)(eta * L0);
+        const double F = S.irc_fwhm, eta = S.irc_eta, pi = 3.14159265358979323846;
+        const double L0 = 2.0 / (pi * F), G0 = std::sqrt(4.0 * 0.69314718055994530942 / pi) / F;
+        L.irc_eta = (float)(eta * L0);            // weights of the peak-relative shapes
         L.irc_g = (float)((1.0 - eta) * G0);
         L.irc_gnorm = (float)(1.0 / S.irc_max);
         break;
     }
     default: break;
     }
-    L.sB_scale = 12.398419843320026 / (2.0 * S.d_A);
     L.labs = (float)S.labs;
     L.labs_ref = (float)S.labs_ref;
     L.labs_pow = (float)S.labs_pow;
@@ -685,12 +814,17 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
     L.irc_max = (float)S.irc_max;
     L.max_refl = S.max_refl;
     L.max_coll = S.max_coll;
-    to_local(S, S.D0, L.D0, true);
-    double eu[3], ev[3], nd[3];
+    double D0[3], eu[3], ev[3], nd[3];
+    to_local(S, S.D0, D0, true);
     to_local(S, S.eu, eu, false);
     to_local(S, S.ev, ev, false);
     to_local(S, S.nd, nd, false);
-    for (int i = 0; i < 3; ++i) { L.eu[i] = (float)eu[i]; L.ev[i] = (float)ev[i]; L.nd[i] = (float)nd[i]; }
+    for (int i = 0; i < 3; ++i) {
+        L.D0[i] = (float)D0[i];
+        L.eu[i] = (float)eu[i];
+        L.ev[i] = (float)ev[i];
+        L.nd[i] = (float)nd[i];
+    }
     L.inv_pix = (float)(1.0 / S.pix);
     L.hnx = 0.5f * (float)S.nx;
     L.hny = 0.5f * (float)S.ny;
@@ -701,7 +835,9 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
     L.offset = offset;
     L.k0 = (uint32_t)seed;
     L.k1 = (uint32_t)(seed >> 32);
-    L.refill = 8;
+    L.refill = g_tune.refill;
+    L.geometry = S.geometry;
+    L.irc_kind = S.irc;
     L.tab = S.mdf32;
     const double *a0 = S.geometry == HEART_FLAT ? S.ed : S.ax;
     const double *a1 = S.geometry == HEART_FLAT ? S.en : S.cc;
@@ -710,67 +846,165 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
 }
 
 template <int GEOM, int IRC, bool REC>
-static void launch_t(const Launch32 &L, void *img, unsigned long long *scratch, heart_ray_record *rec,
-                     cudaStream_t st, int blocks) {
-    k_trace_fp32<GEOM, IRC, REC><<<blocks, kBlockThreads, 0, st>>>(L, img, scratch, rec);
+static void launch_t(const Launch32 &L, const WorkPlan &W, cudaStream_t st, int blocks) {
+    k_trace_fp32<GEOM, IRC, REC><<<blocks, kBlockThreads, 0, st>>>(L, W);
+}
+
+static int resident_blocks() {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_fp32<-1, -1, false>, kBlockThreads, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    return per_sm * num_sms();
 }
 
 template <bool REC>
-static heart_status dispatch(const SpecParams &S, const Launch32 &L, void *img, unsigned long long *scratch,
-                             heart_ray_record *rec, cudaStream_t st) {
-    int per_sm = 0;
-    // resident blocks per SM for this kernel shape
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_fp32<HEART_FLAT, HEART_IRC_DARWIN, REC>,
-                                                  kBlockThreads, 0);
-    if (per_sm < 1) per_sm = 1;
-    uint64_t need = (L.n + 31) / 32 / kWarpsPerBlock + 1;
-    uint64_t cap = (uint64_t)num_sms() * (uint64_t)per_sm;
-    const int blocks = (int)(need < cap ? need : cap);
+static heart_status dispatch(const Launch32 &L, const WorkPlan &W, cudaStream_t st, bool generic) {
+    const uint64_t cap = (uint64_t)resident_blocks();
+    const int blocks = (int)(W.n_chunks < cap ? W.n_chunks : cap);
+    if (blocks <= 0) return HEART_OK;
+    if (generic) {
+        launch_t<-1, -1, REC>(L, W, st, blocks);
+    } else {
 #define HEART_IRC_CASES(G)                                                                    \
-    switch (S.irc) {                                                                          \
-    case HEART_IRC_DARWIN: launch_t<G, HEART_IRC_DARWIN, REC>(L, img, scratch, rec, st, blocks); break; \
-    case HEART_IRC_DARWIN_PRINS: launch_t<G, HEART_IRC_DARWIN_PRINS, REC>(L, img, scratch, rec, st, blocks); break; \
-    case HEART_IRC_PSEUDO_VOIGT: launch_t<G, HEART_IRC_PSEUDO_VOIGT, REC>(L, img, scratch, rec, st, blocks); break; \
-    case HEART_IRC_GAUSSIAN: launch_t<G, HEART_IRC_GAUSSIAN, REC>(L, img, scratch, rec, st, blocks); break; \
-    case HEART_IRC_LORENTZIAN: launch_t<G, HEART_IRC_LORENTZIAN, REC>(L, img, scratch, rec, st, blocks); break; \
-    default: launch_t<G, HEART_IRC_BOX, REC>(L, img, scratch, rec, st, blocks); break;      \
+    switch (L.irc_kind) {                                                                     \
+    case HEART_IRC_DARWIN: launch_t<G, HEART_IRC_DARWIN, REC>(L, W, st, blocks); break;      \
+    case HEART_IRC_DARWIN_PRINS: launch_t<G, HEART_IRC_DARWIN_PRINS, REC>(L, W, st, blocks); break; \
+    case HEART_IRC_PSEUDO_VOIGT: launch_t<G, HEART_IRC_PSEUDO_VOIGT, REC>(L, W, st, blocks); break; \
+    case HEART_IRC_GAUSSIAN: launch_t<G, HEART_IRC_GAUSSIAN, REC>(L, W, st, blocks); break;  \
+    case HEART_IRC_LORENTZIAN: launch_t<G, HEART_IRC_LORENTZIAN, REC>(L, W, st, blocks); break; \
+    default: launch_t<G, HEART_IRC_BOX, REC>(L, W, st, blocks); break;                        \
     }
-    if (S.geometry == HEART_FLAT) { HEART_IRC_CASES(HEART_FLAT) } else { HEART_IRC_CASES(HEART_CYL_VON_HAMOS) }
+        if (L.geometry == HEART_FLAT) { HEART_IRC_CASES(HEART_FLAT) } else { HEART_IRC_CASES(HEART_CYL_VON_HAMOS) }
 #undef HEART_IRC_CASES
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "FP32 kernel launch");
     return HEART_OK;
 }
 
-heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
-                         void *img, unsigned long long *scratch, cudaStream_t st) {
+static heart_status launch_single(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed,
+                                  uint64_t offset, void *img, unsigned long long *scratch, heart_ray_record *rec,
+                                  cudaStream_t st) {
     if (n == 0) return HEART_OK;
     Launch32 L;
     make_launch32(S, P, n, seed, offset, L);
-    return dispatch<false>(S, L, img, scratch, nullptr, st);
+    L.img = img;
+    L.tally = scratch;
+    L.rec = rec;
+    WorkPlan W;
+    std::memset(&W, 0, sizeof W);
+    W.n_jobs = 1;
+    W.chunk_rays = g_tune.chunk_rays;
+    W.n_chunks = (n + W.chunk_rays - 1) / W.chunk_rays;
+    W.counter = scratch + kCounterWord;
+    return rec ? dispatch<true>(L, W, st, false) : dispatch<false>(L, W, st, false);
+}
+
+heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
+                         void *img, unsigned long long *scratch, cudaStream_t st) {
+    return launch_single(S, P, n, seed, offset, img, scratch, nullptr, st);
 }
 
 heart_status launch_fp32_records(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed,
                                  uint64_t offset, void *img, unsigned long long *scratch, heart_ray_record *rec,
                                  cudaStream_t st) {
-    if (n == 0) return HEART_OK;
-    Launch32 L;
-    make_launch32(S, P, n, seed, offset, L);
-    return dispatch<true>(S, L, img, scratch, rec, st);
+    return launch_single(S, P, n, seed, offset, img, scratch, rec, st);
+}
+
+// Device block of a batched launch:
+// [Launch32 x n][chunk_begin x (n + 1)][tallies x n x kTallyN][counter]
+size_t batch_bytes(int n) {
+    size_t a = (size_t)n * sizeof(Launch32);
+    a = (a + 15) & ~(size_t)15;
+    a += (size_t)(n + 1) * 8;
+    a = (a + 15) & ~(size_t)15;
+    a += (size_t)n * kTallyN * 8 + 16;
+    return a;
+}
+
+heart_status launch_batch(const SpecParams *const *S, const SourceParams *P, const uint64_t *n_rays,
+                          const uint64_t *seeds, const uint64_t *offsets, void *const *imgs, int n, void *dev,
+                          std::vector<unsigned char> &host, cudaStream_t st, unsigned long long **tallies_dev,
+                          unsigned long long *const *tally_ptrs) {
+    const size_t total = batch_bytes(n);
+    host.assign(total, 0);
+    Launch32 *jobs = (Launch32 *)host.data();
+    const size_t off_cb = ((size_t)n * sizeof(Launch32) + 15) & ~(size_t)15;
+    const size_t off_t = (off_cb + (size_t)(n + 1) * 8 + 15) & ~(size_t)15;
+    const size_t off_c = off_t + (size_t)n * kTallyN * 8;
+    unsigned long long *cb = (unsigned long long *)(host.data() + off_cb);
+    unsigned char *d = (unsigned char *)dev;
+    const uint32_t chunk = g_tune.chunk_rays;
+    unsigned long long nch = 0;
+    for (int i = 0; i < n; ++i) {
+        make_launch32(*S[i], P[i], n_rays[i], seeds[i], offsets ? offsets[i] : 0, jobs[i]);
+        jobs[i].img = imgs[i];
+        jobs[i].tally = tally_ptrs ? tally_ptrs[i] : (unsigned long long *)(d + off_t) + (size_t)i * kTallyN;
+        jobs[i].rec = nullptr;
+        cb[i] = nch;
+        nch += (n_rays[i] + chunk - 1) / chunk;
+    }
+    cb[n] = nch;
+    *tallies_dev = (unsigned long long *)(d + off_t);
+    // the host block is pageable: the copy is staged before this call returns
+    cudaError_t e = cudaMemcpyAsync(dev, host.data(), total, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch upload");
+    if (nch == 0) return HEART_OK;
+    WorkPlan W;
+    std::memset(&W, 0, sizeof W);
+    W.jobs = (const Launch32 *)d;
+    W.chunk_begin = (const unsigned long long *)(d + off_cb);
+    W.n_jobs = n;
+    W.chunk_rays = chunk;
+    W.n_chunks = nch;
+    W.counter = (unsigned long long *)(d + off_c);
+    Launch32 dummy;
+    std::memset(&dummy, 0, sizeof dummy);
+    return dispatch<false>(dummy, W, st, true);
 }
 
 }  // namespace heart
 
-extern "C" heart_status heart_trace_batch(heart_spectrometer *const *, const heart_source_desc *const *,
-                                          const uint64_t *, const uint64_t *, void *const *, int32_t, void *,
-                                          heart_tally *) {
-    return heart::fail(HEART_EINVAL, "batched path not built");
+extern "C" heart_status heart_trace_batch(heart_spectrometer *const *specs, const heart_source_desc *const *srcs,
+                                          const uint64_t *n_rays, const uint64_t *seeds, void *const *d_images,
+                                          int32_t n_jobs, void *stream, heart_tally *out) {
+    using namespace heart;
+    if (n_jobs == 0) return HEART_OK;
+    if (n_jobs < 0 || !specs || !srcs || !n_rays || !seeds || !d_images) return fail(HEART_EINVAL, "null batch array");
+    std::vector<SourceParams> P((size_t)n_jobs);
+    std::vector<const SpecParams *> S((size_t)n_jobs);
+    char err[256] = {0};
+    for (int i = 0; i < n_jobs; ++i) {
+        if (!specs[i]) return fail(HEART_EINVAL, "null spectrometer in batch");
+        const size_t elt = specs[i]->p.count_type == HEART_COUNT_I64 ? 8 : 4;
+        if (!d_images[i] || ((uintptr_t)d_images[i] % elt) != 0) return fail(HEART_EINVAL, "null or misaligned image in batch");
+        heart_status st = build_source_params(srcs[i], &P[i], err, (int)sizeof err);
+        if (st != HEART_OK) return fail(st, err);
+        S[i] = &specs[i]->p;
+    }
+    cudaStream_t cs = (cudaStream_t)stream;
+    void *dev = nullptr;
+    const size_t bytes = batch_bytes(n_jobs);
+    cudaError_t e = cudaMallocAsync(&dev, bytes, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync batch");
+    std::vector<unsigned char> host;
+    unsigned long long *tall = nullptr;
+    heart_status st = launch_batch(S.data(), P.data(), n_rays, seeds, nullptr, d_images, n_jobs, dev, host, cs, &tall,
+                                   nullptr);
+    if (st == HEART_OK && out) {
+        std::vector<unsigned long long> h((size_t)n_jobs * kTallyN);
+        e = cudaMemcpyAsync(h.data(), tall, h.size() * 8, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) st = cuda_fail(e, "batch tallies");
+        bool stuck = false;
+        for (int i = 0; st == HEART_OK && i < n_jobs; ++i) {
+            std::memcpy(&out[i], &h[(size_t)i * kTallyN], sizeof(heart_tally));
+            stuck |= out[i].stuck > 0;
+        }
+        if (st == HEART_OK && stuck) st = fail(HEART_ELIMIT, "a ray reached the collision cap");
+    }
+    cudaFreeAsync(dev, cs);
+    return st;
 }
-extern "C" heart_status heart_server_create(size_t, heart_server **) { return heart::fail(HEART_EINVAL, "server not built"); }
-extern "C" heart_status heart_server_destroy(heart_server *) { return heart::fail(HEART_EINVAL, "server not built"); }
-extern "C" heart_status heart_submit(heart_server *, heart_spectrometer *, const heart_source_desc *, uint64_t, uint64_t,
-                                     heart_precision, uint64_t *) { return heart::fail(HEART_EINVAL, "server not built"); }
-extern "C" heart_status heart_poll(heart_server *, uint64_t, int32_t, heart_tally *, const void **) {
-    return heart::fail(HEART_EINVAL, "server not built");
-}
-extern "C" heart_status heart_release(heart_server *, uint64_t) { return heart::fail(HEART_EINVAL, "server not built"); }

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "heart.h"
 #include "heart_internal.h"
@@ -12,6 +13,12 @@ namespace heart {
 // persistent kernels
 constexpr int kScratchWords = 64;
 constexpr int kCounterWord = 32;     // first work-counter word
+
+struct TuneConfig {
+    int refill = 8;                    // pop new rays when this many lanes of a warp are idle
+    uint32_t chunk_rays = 1u << 16;    // rays per work item claimed by a block
+};
+extern TuneConfig g_tune;
 
 extern thread_local std::string g_last_error;
 heart_status fail(heart_status st, const char *msg);
@@ -25,6 +32,11 @@ heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n,
 heart_status launch_fp32_records(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed,
                                  uint64_t offset, void *img, unsigned long long *scratch, heart_ray_record *rec,
                                  cudaStream_t st);
+size_t batch_bytes(int n);
+heart_status launch_batch(const SpecParams *const *S, const SourceParams *P, const uint64_t *n_rays,
+                          const uint64_t *seeds, const uint64_t *offsets, void *const *imgs, int n, void *dev,
+                          std::vector<unsigned char> &host, cudaStream_t st, unsigned long long **tallies_dev,
+                          unsigned long long *const *tally_ptrs);
 }  // namespace heart
 
 struct heart_spectrometer {
