@@ -218,6 +218,32 @@ heart_status heart_trace_batch(heart_spectrometer *const *specs, const heart_sou
                                const uint64_t *n_rays, const uint64_t *seeds, void *const *d_images,
                                int32_t n_jobs, void *stream, heart_tally *out);
 
+/* Maximum number of jobs of heart_trace_batch_static. */
+#define HEART_STATIC_MAX_JOBS 64
+
+/* heart_trace_batch for callers that cannot allocate device memory during the
+ * call (this entry point has no counterpart in the paper; it exists for
+ * deployment).  Examples: an application that gives all free device memory
+ * to its own pool at start-up, or a control loop that must not risk an
+ * allocation failure or the synchronisation an allocation can cause.
+ * heart_trace_batch allocates a small per-call work area (job table, work
+ * counter, tallies); this variant uses a fixed work area in a device array
+ * that the library declares at file scope, sized for HEART_STATIC_MAX_JOBS
+ * jobs, and allocates nothing on the device.  The caller still passes the
+ * spectrometers (created beforehand), sources and device images, exactly as
+ * for heart_trace_batch, and gets the same images and tallies.
+ *   - n_jobs > HEART_STATIC_MAX_JOBS returns HEART_EINVAL with a message.
+ *   - Every GPU that loads the library holds the array until the process exits.
+ *   - All calls share the array; each call rewrites it (tallies and the work
+ *     counter start at zero), so calls that overlap on the GPU race: serialise
+ *     them on one stream.  Host staging is serialised by a lock.
+ *   - The first call on each device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ * If `out` is non-NULL the call synchronises `stream` and fills n_jobs tallies. */
+heart_status heart_trace_batch_static(heart_spectrometer *const *specs, const heart_source_desc *const *srcs,
+                                      const uint64_t *n_rays, const uint64_t *seeds, void *const *d_images,
+                                      int32_t n_jobs, void *stream, heart_tally *out);
+
 /* Request loop: jobs are admitted while their images fit under mem_cap_bytes,
  * batched into persistent launches as they arrive, and polled for results. */
 heart_status heart_server_create(size_t mem_cap_bytes, heart_server **out);

@@ -86,7 +86,7 @@ RECORD_DTYPE = np.dtype([
 assert RECORD_DTYPE.itemsize == 112
 
 EXPORTS = ["heart_spectrometer_create", "heart_spectrometer_destroy", "heart_trace", "heart_trace_host",
-           "heart_trace_records", "heart_trace_batch", "heart_server_create", "heart_server_destroy",
+           "heart_trace_records", "heart_trace_batch", "heart_trace_batch_static", "heart_server_create", "heart_server_destroy",
            "heart_submit", "heart_poll", "heart_release", "heart_fetch_image", "heart_job_latency",
            "heart_last_error"]
 
@@ -121,6 +121,7 @@ def library(path=None):
     L.heart_trace_batch.argtypes = [C.POINTER(vp), C.POINTER(C.POINTER(heart_source_desc)),
                                     C.POINTER(u64), C.POINTER(u64), C.POINTER(vp), i32, vp,
                                     C.POINTER(heart_tally)]
+    L.heart_trace_batch_static.argtypes = L.heart_trace_batch.argtypes
     L.heart_server_create.argtypes = [C.c_size_t, C.POINTER(vp)]
     L.heart_server_destroy.argtypes = [vp]
     L.heart_submit.argtypes = [vp, vp, C.POINTER(heart_source_desc), u64, u64, i32, C.POINTER(u64)]
@@ -292,6 +293,27 @@ def heart_trace_batch(specs, sources, n_rays, seeds, d_images, stream=None):
     im = (C.c_void_p * n)(*[d.data_ptr() for d in d_images])
     tl = (heart_tally * n)()
     st = library().heart_trace_batch(hs, sp, nr, sd, im, n, C.c_void_p(_stream_ptr(stream)), tl)
+    _check(st, allow=(0, 6))
+    return [tl[i].as_dict() for i in range(n)]
+
+
+STATIC_MAX_JOBS = 64
+
+
+def heart_trace_batch_static(specs, sources, n_rays, seeds, d_images, stream=None):
+    """As heart_trace_batch, on the library's fixed device work area: the call
+    allocates no device memory (for callers that cannot allocate while they
+    run).  At most STATIC_MAX_JOBS jobs; calls share the work area, so
+    serialise them."""
+    n = len(specs)
+    srcs = [make_source(s) for s in sources]
+    hs = (C.c_void_p * n)(*[s.handle.value for s in specs])
+    sp = (C.POINTER(heart_source_desc) * n)(*[C.pointer(s) for s in srcs])
+    nr = (C.c_uint64 * n)(*[int(x) for x in n_rays])
+    sd = (C.c_uint64 * n)(*[int(x) for x in seeds])
+    im = (C.c_void_p * n)(*[d.data_ptr() for d in d_images])
+    tl = (heart_tally * max(n, 1))()
+    st = library().heart_trace_batch_static(hs, sp, nr, sd, im, n, C.c_void_p(_stream_ptr(stream)), tl)
     _check(st, allow=(0, 6))
     return [tl[i].as_dict() for i in range(n)]
 

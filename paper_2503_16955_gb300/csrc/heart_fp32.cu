@@ -31,6 +31,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "heart_fp64.cuh"
@@ -1007,4 +1008,119 @@ extern "C" heart_status heart_trace_batch(heart_spectrometer *const *specs, cons
     }
     cudaFreeAsync(dev, cs);
     return st;
+}
+
+// ---------------------------------------------------------------------------
+// Batched trace without any allocation.
+//
+// Some callers cannot allocate device memory while they run: an application
+// that hands all free device memory to its own pool at start-up, or a
+// control loop that must never risk an allocation failure or the implicit
+// synchronisation an allocation can cause.  heart_trace_batch needs a small
+// per-call work area (job table, work counter, tallies) and allocates it on
+// the stream; this variant runs the same batched kernel on a work area that
+// lives in a fixed, file-scope device array instead, so a call allocates
+// nothing on the device.  The array holds at most kStaticMaxJobs jobs, every
+// GPU that loads the library keeps it until the process exits, and all calls
+// share it: each call rewrites it completely (work counter and tallies start
+// at zero), and calls that overlap on the GPU race on it.
+// ---------------------------------------------------------------------------
+namespace heart {
+namespace {
+
+constexpr int kStaticMaxJobs = HEART_STATIC_MAX_JOBS;
+constexpr size_t kStaticJobsBytes = ((size_t)kStaticMaxJobs * sizeof(Launch32) + 15) & ~(size_t)15;
+constexpr size_t kStaticChunkBytes = (((size_t)kStaticMaxJobs + 1) * 8 + 15) & ~(size_t)15;
+constexpr size_t kStaticTallyBytes = (size_t)kStaticMaxJobs * kTallyN * 8;
+constexpr size_t kStaticBytes = kStaticJobsBytes + kStaticChunkBytes + kStaticTallyBytes + 16;
+
+static __device__ __align__(256) unsigned char g_static_work[kStaticBytes];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;                                 // serialises the host staging below
+void *g_static_dev[kStaticMaxDevices] = {nullptr};      // device address of g_static_work, per device
+unsigned char g_static_host[kStaticBytes];              // host image of the work area
+SourceParams g_static_src[kStaticMaxJobs];
+
+}  // namespace
+}  // namespace heart
+
+extern "C" heart_status heart_trace_batch_static(heart_spectrometer *const *specs,
+                                                 const heart_source_desc *const *srcs, const uint64_t *n_rays,
+                                                 const uint64_t *seeds, void *const *d_images, int32_t n_jobs,
+                                                 void *stream, heart_tally *out) {
+    using namespace heart;
+    if (n_jobs == 0) return HEART_OK;
+    if (n_jobs < 0) return fail(HEART_EINVAL, "negative job count");
+    if (n_jobs > kStaticMaxJobs)
+        return fail(HEART_EINVAL, "heart_trace_batch_static: more jobs than HEART_STATIC_MAX_JOBS (64)");
+    if (!specs || !srcs || !n_rays || !seeds || !d_images) return fail(HEART_EINVAL, "null batch array");
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kStaticMaxDevices) return fail(HEART_EINVAL, "device ordinal out of range");
+    if (!g_static_dev[dev]) {
+        // once per device, with that device current: the array's device address
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_static_work);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+        g_static_dev[dev] = ptr;
+    }
+    unsigned char *d = (unsigned char *)g_static_dev[dev];
+    char err[256] = {0};
+    for (int i = 0; i < n_jobs; ++i) {
+        if (!specs[i]) return fail(HEART_EINVAL, "null spectrometer in batch");
+        const size_t elt = specs[i]->p.count_type == HEART_COUNT_I64 ? 8 : 4;
+        if (!d_images[i] || ((uintptr_t)d_images[i] % elt) != 0) return fail(HEART_EINVAL, "null or misaligned image in batch");
+        heart_status st = build_source_params(srcs[i], &g_static_src[i], err, (int)sizeof err);
+        if (st != HEART_OK) return fail(st, err);
+    }
+    // host image of the work area: job table, chunk table, zero tallies and counter
+    std::memset(g_static_host, 0, kStaticBytes);
+    Launch32 *jobs = (Launch32 *)g_static_host;
+    unsigned long long *cb = (unsigned long long *)(g_static_host + kStaticJobsBytes);
+    unsigned long long *d_tallies = (unsigned long long *)(d + kStaticJobsBytes + kStaticChunkBytes);
+    const uint32_t chunk = g_tune.chunk_rays;
+    unsigned long long nch = 0;
+    for (int i = 0; i < n_jobs; ++i) {
+        make_launch32(specs[i]->p, g_static_src[i], n_rays[i], seeds[i], 0, jobs[i]);
+        jobs[i].img = d_images[i];
+        jobs[i].tally = d_tallies + (size_t)i * kTallyN;
+        jobs[i].rec = nullptr;
+        cb[i] = nch;
+        nch += (n_rays[i] + chunk - 1) / chunk;
+    }
+    cb[n_jobs] = nch;
+    cudaStream_t cs = (cudaStream_t)stream;
+    // pageable source: staged before the call returns, so the buffer can be reused
+    e = cudaMemcpyAsync(d, g_static_host, kStaticBytes, cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "work area upload");
+    if (nch > 0) {
+        WorkPlan W;
+        std::memset(&W, 0, sizeof W);
+        W.jobs = (const Launch32 *)d;
+        W.chunk_begin = (const unsigned long long *)(d + kStaticJobsBytes);
+        W.n_jobs = n_jobs;
+        W.chunk_rays = chunk;
+        W.n_chunks = nch;
+        W.counter = (unsigned long long *)(d + kStaticJobsBytes + kStaticChunkBytes + kStaticTallyBytes);
+        Launch32 dummy;
+        std::memset(&dummy, 0, sizeof dummy);
+        heart_status st = dispatch<false>(dummy, W, cs, true);
+        if (st != HEART_OK) return st;
+    }
+    if (out) {
+        unsigned long long *h = (unsigned long long *)(g_static_host + kStaticJobsBytes + kStaticChunkBytes);
+        e = cudaMemcpyAsync(h, d_tallies, (size_t)n_jobs * kTallyN * 8, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) return cuda_fail(e, "tally read-back");
+        bool stuck = false;
+        for (int i = 0; i < n_jobs; ++i) {
+            std::memcpy(&out[i], h + (size_t)i * kTallyN, sizeof(heart_tally));
+            stuck |= out[i].stuck > 0;
+        }
+        if (stuck) return fail(HEART_ELIMIT, "a ray reached the collision cap");
+    }
+    return HEART_OK;
 }
