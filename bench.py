@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--rays", type=float, default=1e8)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--serving-jobs", type=int, default=1000)
+    p.add_argument("--no-extra", action="store_true", help="skip batched / serving / FP64 measurements")
     return p.parse_args()
 
 
@@ -119,6 +121,102 @@ def cpu_baseline(workload, seconds, threads=0):
             "collisions_per_ray": tal["collisions"] / max(1, n2)}
 
 
+def batched_measurement(H, W, torch, stream):
+    """64 spectrometers of uneven ray counts in one persistent launch."""
+    jobs = W.batched_64()
+    specs = [H.heart_spectrometer_create(j["spec"]) for j in jobs]
+    imgs = [torch.zeros(s.shape, dtype=torch.int32, device="cuda") for s in specs]
+    args = ([j["source"] for j in jobs], [j["n_rays"] for j in jobs], [j["seed"] for j in jobs])
+    small = [max(1, n // 100) for n in args[1]]
+    H.heart_trace_batch(specs, args[0], small, args[2], imgs, stream=stream)      # warm
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tl = H.heart_trace_batch(specs, args[0], args[1], args[2], imgs, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    total = sum(args[1])
+    for s in specs:
+        s.close()
+    return {"jobs": len(jobs), "rays": total, "seconds": sec, "rays_per_s": total / sec,
+            "collisions_per_ray": sum(t["collisions"] for t in tl) / total,
+            "note": "one heart_trace_batch launch (includes tally read-back)"}
+
+
+def serving_measurement(H, W, n_jobs, rate):
+    """Poisson stream of trace jobs through the request loop; latencies are
+    measured by the server from submit to completion."""
+    import threading as th
+    pool = W.batched_64(seed=4, ray_range=(1e4, 1e8))
+    specs = [H.heart_spectrometer_create(j["spec"]) for j in pool]
+    stream = W.serving_stream(n_jobs=n_jobs, rate_per_s=rate)
+    srv = H.heart_server_create(40 << 30)
+    ids = []
+    lat = []
+    done = th.Event()
+
+    def reaper():
+        i = 0
+        while i < len(stream):
+            while i >= len(ids):
+                time.sleep(0.0005)
+            st, t, _ = srv.poll(ids[i], timeout_ms=600_000)
+            lat.append(srv.latency(ids[i]))
+            srv.release(ids[i])
+            i += 1
+        done.set()
+
+    r = th.Thread(target=reaper, daemon=True)
+    r.start()
+    t0 = time.perf_counter()
+    rays = 0
+    for k, job in enumerate(stream):
+        delay = job["arrival_s"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        j = k % len(specs)
+        ids.append(srv.submit(specs[j], pool[j]["source"], job["n_rays"], job["seed"]))
+        rays += job["n_rays"]
+    done.wait()
+    wall = time.perf_counter() - t0
+    srv.close()
+    for s in specs:
+        s.close()
+    lat_ms = sorted(1e3 * x for x in lat)
+    q = lambda p: lat_ms[min(len(lat_ms) - 1, int(p * len(lat_ms)))]
+    offered = rays / stream[-1]["arrival_s"]
+    return {"jobs": n_jobs, "rate_per_s": rate, "p50_ms": q(0.50), "p99_ms": q(0.99), "max_ms": lat_ms[-1],
+            "rays_per_s": rays / wall, "offered_rays_per_s": offered,
+            "note": "spectrometers drawn from a pool of 64 (seed 4); rays log-uniform 1e4-1e8"}
+
+
+def fp64_measurement(H, W, torch, stream):
+    """Plain FP64 single-configuration path on the flat HOPG workload (2e5 rays)."""
+    w = W.flat_hopg_mono()
+    s = H.heart_spectrometer_create(w["spec"])
+    img = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    H.heart_trace(s, w["source"], w["n_rays"], w["seed"], 0, img, precision="fp64", stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for i in range(reps):
+        H.heart_trace(s, w["source"], w["n_rays"], w["seed"], (i + 1) * w["n_rays"], img, precision="fp64",
+                      stream=stream, want_tally=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64 = reps * w["n_rays"] / (e0.elapsed_time(e1) / 1e3)
+    n32 = 100 * w["n_rays"]
+    H.heart_trace(s, w["source"], n32, w["seed"], 0, img, precision="fp32", stream=stream, want_tally=False)
+    e0.record(stream)
+    H.heart_trace(s, w["source"], n32, w["seed"], n32, img, precision="fp32", stream=stream, want_tally=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp32 = n32 / (e0.elapsed_time(e1) / 1e3)
+    s.close()
+    return {"workload": w["name"], "fp64_rays_per_s": fp64, "fp32_rays_per_s": fp32, "fp32_speedup": fp32 / fp64}
+
+
 def run_reference(args):
     import torch.distributed as dist  # noqa: F401
     rank = int(os.environ.get("RANK", "0"))
@@ -182,6 +280,7 @@ def main():
         if world > 1:
             dist.barrier()
 
+    tune = H.heart_autotune(spec, w["source"], probe_rays=min(n, 1 << 24), stream=stream)
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
             H.heart_trace(spec, w["source"], n, w["seed"], offset(1000 + i), img, precision="fp32",
@@ -236,6 +335,11 @@ def main():
     clocks = clk.summary()
     cpu = cpu_baseline(w, args.cpu_seconds) if rank == 0 and world == 1 else None
     spec.close()
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        extra["batched"] = batched_measurement(H, W, torch, stream)
+        extra["fp64_plain"] = fp64_measurement(H, W, torch, stream)
+        extra["serving"] = serving_measurement(H, W, args.serving_jobs, 200.0)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -243,6 +347,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w["name"], "rays_per_step": n, "precision": "fp32",
                        "detector": "%dx%d int32" % (w["spec"]["det_ny"], w["spec"]["det_nx"]),
+                       "launch": tune,
                        "collisions_per_ray": coll_per_ray, "det_hits_per_ray": det_frac,
                        "detector_hits_per_s": value * det_frac,
                        "l2": "inputs are per-ray counters (no input data); the 4 MB image stays in L2"},
@@ -257,6 +362,7 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            **extra,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -78,6 +78,11 @@ class heart_tally(C.Structure):
         return d
 
 
+class heart_tune(C.Structure):
+    _fields_ = [("blocks_per_sm", C.c_int32), ("refill_lanes", C.c_int32), ("max_chunk_rays", C.c_uint32),
+                ("reserved", C.c_int32), ("rays_per_s", C.c_double)]
+
+
 RECORD_DTYPE = np.dtype([
     ("ray_id", np.uint64), ("outcome", np.int32), ("nrefl", np.int32), ("ncoll", np.int64),
     ("energy_keV", np.float64), ("pos", np.float64, 3), ("dir", np.float64, 3),
@@ -86,7 +91,7 @@ RECORD_DTYPE = np.dtype([
 assert RECORD_DTYPE.itemsize == 112
 
 EXPORTS = ["heart_spectrometer_create", "heart_spectrometer_destroy", "heart_trace", "heart_trace_host",
-           "heart_trace_records", "heart_trace_batch", "heart_trace_batch_static", "heart_server_create", "heart_server_destroy",
+           "heart_trace_records", "heart_trace_batch", "heart_trace_batch_static", "heart_autotune", "heart_server_create", "heart_server_destroy",
            "heart_submit", "heart_poll", "heart_release", "heart_fetch_image", "heart_job_latency",
            "heart_last_error"]
 
@@ -122,6 +127,7 @@ def library(path=None):
                                     C.POINTER(u64), C.POINTER(u64), C.POINTER(vp), i32, vp,
                                     C.POINTER(heart_tally)]
     L.heart_trace_batch_static.argtypes = L.heart_trace_batch.argtypes
+    L.heart_autotune.argtypes = [vp, C.POINTER(heart_source_desc), u64, vp, C.POINTER(heart_tune)]
     L.heart_server_create.argtypes = [C.c_size_t, C.POINTER(vp)]
     L.heart_server_destroy.argtypes = [vp]
     L.heart_submit.argtypes = [vp, vp, C.POINTER(heart_source_desc), u64, u64, i32, C.POINTER(u64)]
@@ -298,6 +304,17 @@ def heart_trace_batch(specs, sources, n_rays, seeds, d_images, stream=None):
 
 
 STATIC_MAX_JOBS = 64
+
+
+def heart_autotune(spec, source, probe_rays=1 << 24, stream=None):
+    """Pick the FP32 launch shape (blocks per SM, refill threshold) by timing
+    probes; the choice applies to every later FP32 launch of the process."""
+    src = make_source(source)
+    t = heart_tune()
+    _check(library().heart_autotune(spec.handle, C.byref(src), int(probe_rays),
+                                    C.c_void_p(_stream_ptr(stream)), C.byref(t)))
+    return {"blocks_per_sm": t.blocks_per_sm, "refill_lanes": t.refill_lanes,
+            "max_chunk_rays": t.max_chunk_rays, "probe_rays_per_s": t.rays_per_s}
 
 
 def heart_trace_batch_static(specs, sources, n_rays, seeds, d_images, stream=None):

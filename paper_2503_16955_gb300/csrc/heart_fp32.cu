@@ -78,6 +78,7 @@ struct Launch32 {
     // run
     uint64_t n, offset;
     uint32_t k0, k1;
+    uint32_t rk0[10], rk1[10];            // Philox round keys of (k0, k1)
     int32_t refill;                       // pop when at least this many lanes are idle
     int32_t geometry, irc_kind;
     const float *tab;
@@ -95,6 +96,25 @@ struct WarpBuf {
     int32_t nb[kBuf];
     int count;
 };
+
+// Philox4x32-10 with the round keys read from the launch parameters (the
+// Weyl key schedule is the same for every ray of a job)
+template <bool RK>
+__device__ __forceinline__ void philox_l(const Launch32 &L, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                         uint32_t out[4]) {
+    if (!RK) {
+        philox4x32_10(c0, c1, c2, c3, L.k0, L.k1, out);
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ L.rk0[r], n2 = hi0 ^ c3 ^ L.rk1[r];
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
 
 __device__ __forceinline__ float u01_32(uint32_t w) {
     // (w + 1/2) 2^-32 rounded to FP32: relative error <= 2^-24 against the FP64 uniform
@@ -166,7 +186,7 @@ __device__ __forceinline__ float irc_rel32(const Launch32 &L, float x) {
 //   larger root modulus, m >= |eta| >= |y|.  Lorentzian: (F/2)^2 / x^2.
 //   pseudo-Voigt: the weighted Lorentzian tail plus the Gaussian at a.
 template <int IRC_T>
-__device__ __forceinline__ float irc_bound32(const Launch32 &L, float a) {
+__device__ __forceinline__ float irc_bound32_raw(const Launch32 &L, float a) {
     const int IRC = IRC_T >= 0 ? IRC_T : L.irc_kind;
     if (IRC == HEART_IRC_DARWIN) {
         const float y = a * L.irc_delta;
@@ -186,6 +206,13 @@ __device__ __forceinline__ float irc_bound32(const Launch32 &L, float a) {
     } else {
         return 1.0f;                  // Gaussian: evaluated directly (one exp)
     }
+}
+
+// the bound with a relative margin of 1e-5 that covers the approximate
+// reciprocal and exponential used to form it
+template <int IRC_T>
+__device__ __forceinline__ float irc_bound32(const Launch32 &L, float a) {
+    return irc_bound32_raw<IRC_T>(L, a) * 1.00001f;
 }
 
 // lane state of one ray being walked (all FP32)
@@ -209,8 +236,8 @@ __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
     const uint32_t rl = (uint32_t)ray, rh = (uint32_t)(ray >> 32);
     uint32_t a[4], b[4];
-    philox4x32_10(rl, rh, 0u, 0u, L.k0, L.k1, a);
-    philox4x32_10(rl, rh, 1u, 0u, L.k0, L.k1, b);
+    philox_l<(GEOM_T >= 0)>(L, rl, rh, 0u, 0u, a);
+    philox_l<(GEOM_T >= 0)>(L, rl, rh, 1u, 0u, b);
     // direction, uniform in solid angle in the cone; dn = k.n_ref - axis.n_ref
     const float w = u01_32(a[2]) * L.omc;                 // 1 - cos(phi)
     const float sphi = sqrtf(w * (2.0f - w));
@@ -448,7 +475,7 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
     if (s.ncoll >= L.max_coll) return HEART_STUCK;
     uint32_t w[4];
-    philox4x32_10(s.rl, s.rh, s.call++, 0u, L.k0, L.k1, w);
+    philox_l<(GEOM_T >= 0)>(L, s.rl, s.rh, s.call++, 0u, w);
     const float l = -__logf(u01_32(w[0])) * s.inv_mu;
     // Kahan-compensated path length along the segment
     const float y = l - s.Lcomp;
@@ -541,8 +568,12 @@ struct WorkPlan {
     unsigned long long *counter;          // zero before the launch
 };
 
-template <int GEOM, int IRC, bool REC>
-__global__ void __launch_bounds__(kBlockThreads, 6) k_trace_fp32(const Launch32 single, const WorkPlan W) {
+// GEOM >= 0: single-job kernel, parameters read from the launch's constant
+// bank; GEOM < 0: the generic batched kernel, the block's job staged in smem
+template <int GEOM, int IRC, bool REC, int OCC>
+__global__ void __launch_bounds__(kBlockThreads, OCC)
+    k_trace_fp32(const __grid_constant__ Launch32 single, const __grid_constant__ WorkPlan W) {
+    constexpr bool BATCH = GEOM < 0;
     __shared__ Launch32 sL;
     __shared__ float s_tab[kMdfKnots];
     __shared__ WarpBuf s_buf[kWarpsPerBlock];
@@ -552,7 +583,7 @@ __global__ void __launch_bounds__(kBlockThreads, 6) k_trace_fp32(const Launch32 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     WarpBuf &B = s_buf[wid];
-    const Launch32 &L = sL;
+    const Launch32 &L = BATCH ? sL : single;
     int cur_job = -1;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -578,11 +609,13 @@ __global__ void __launch_bounds__(kBlockThreads, 6) k_trace_fp32(const Launch32 
         const int j = s_job;
         if (j != cur_job) {
             // this block's job changed: load its parameters, then its mosaic table
-            const uint32_t *src = (const uint32_t *)(W.jobs ? &W.jobs[j] : &single);
-            uint32_t *dst = (uint32_t *)&sL;
-            for (int i = threadIdx.x; i < (int)(sizeof(Launch32) / 4); i += blockDim.x) dst[i] = src[i];
-            __syncthreads();
-            for (int i = threadIdx.x; i < kMdfKnots; i += blockDim.x) s_tab[i] = sL.tab[i];
+            if (BATCH) {
+                const uint32_t *src = (const uint32_t *)&W.jobs[j];
+                uint32_t *dst = (uint32_t *)&sL;
+                for (int i = threadIdx.x; i < (int)(sizeof(Launch32) / 4); i += blockDim.x) dst[i] = src[i];
+                __syncthreads();
+            }
+            for (int i = threadIdx.x; i < kMdfKnots; i += blockDim.x) s_tab[i] = L.tab[i];
             cur_job = j;
         }
         for (int i = threadIdx.x; i < kTallyN; i += blockDim.x) bt.t[i] = 0u;
@@ -676,7 +709,8 @@ __global__ void __launch_bounds__(kBlockThreads, 6) k_trace_fp32(const Launch32 
                 __syncwarp();
             }
             if (alive) {
-                const int oc = step<GEOM, IRC>(L, s, s_tab);
+                int oc = step<GEOM, IRC>(L, s, s_tab);
+                if (oc < 0) oc = step<GEOM, IRC>(L, s, s_tab);    // two collisions per refill check
                 if (oc >= 0) {
                     my_coll += (unsigned long long)s.ncoll;
                     finish<REC>(L, s, oc, bt);
@@ -696,7 +730,7 @@ __global__ void __launch_bounds__(kBlockThreads, 6) k_trace_fp32(const Launch32 
         }
         __syncthreads();
         // flush this chunk's tallies to the job
-        unsigned long long *T = sL.tally;
+        unsigned long long *T = L.tally;
         for (int i = threadIdx.x; i < kTallyN; i += blockDim.x) {
             unsigned long long v = bt.t[i];
             if (i == T_COLLISIONS) v = bt.coll;
@@ -836,6 +870,13 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
     L.offset = offset;
     L.k0 = (uint32_t)seed;
     L.k1 = (uint32_t)(seed >> 32);
+    uint32_t a = L.k0, b = L.k1;
+    for (int r = 0; r < 10; ++r) {
+        L.rk0[r] = a;
+        L.rk1[r] = b;
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
     L.refill = g_tune.refill;
     L.geometry = S.geometry;
     L.irc_kind = S.irc;
@@ -846,36 +887,65 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
     for (int i = 0; i < 3; ++i) { L.fc[i] = S.c[i]; L.fa[0][i] = a0[i]; L.fa[1][i] = a1[i]; L.fa[2][i] = a2[i]; }
 }
 
-template <int GEOM, int IRC, bool REC>
-static void launch_t(const Launch32 &L, const WorkPlan &W, cudaStream_t st, int blocks) {
-    k_trace_fp32<GEOM, IRC, REC><<<blocks, kBlockThreads, 0, st>>>(L, W);
-}
-
-static int resident_blocks() {
+template <int GEOM, int IRC, bool REC, int OCC>
+static void launch_occ(const Launch32 &L, const WorkPlan &W, cudaStream_t st, uint64_t n_chunks) {
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_fp32<-1, -1, false>, kBlockThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_fp32<GEOM, IRC, REC, OCC>, kBlockThreads, 0);
         if (per_sm < 1) per_sm = 1;
     }
-    return per_sm * num_sms();
+    const uint64_t cap = (uint64_t)per_sm * (uint64_t)num_sms();
+    const int blocks = (int)(n_chunks < cap ? n_chunks : cap);
+    if (blocks > 0) k_trace_fp32<GEOM, IRC, REC, OCC><<<blocks, kBlockThreads, 0, st>>>(L, W);
+}
+
+template <int GEOM, int IRC, bool REC>
+static void launch_t(const Launch32 &L, const WorkPlan &W, cudaStream_t st) {
+    // records are a test path: one occupancy variant
+    if constexpr (!REC) {
+        if (g_tune.blocks_per_sm >= 8) {
+            launch_occ<GEOM, IRC, REC, 8>(L, W, st, W.n_chunks);
+            return;
+        }
+    }
+    launch_occ<GEOM, IRC, REC, 6>(L, W, st, W.n_chunks);
+}
+
+// resident blocks of the launch shape in use (for chunk sizing)
+static int resident_blocks() {
+    static int per_sm[2] = {0, 0};
+    const int v = g_tune.blocks_per_sm >= 8 ? 1 : 0;
+    if (per_sm[v] == 0) {
+        if (v) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[v], k_trace_fp32<-1, -1, false, 8>, kBlockThreads, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[v], k_trace_fp32<-1, -1, false, 6>, kBlockThreads, 0);
+        if (per_sm[v] < 1) per_sm[v] = 1;
+    }
+    return per_sm[v] * num_sms();
+}
+
+// rays per work item: about eight items per resident block, a power of two
+// between 2^12 and the tuned maximum, so the last wave of items is short
+static uint32_t chunk_for(uint64_t total_rays) {
+    const uint64_t target = total_rays / ((uint64_t)resident_blocks() * 8ull);
+    uint32_t c = 4096u;
+    while ((uint64_t)c * 2 <= target && c * 2 <= g_tune.chunk_rays) c *= 2;
+    return c;
 }
 
 template <bool REC>
 static heart_status dispatch(const Launch32 &L, const WorkPlan &W, cudaStream_t st, bool generic) {
-    const uint64_t cap = (uint64_t)resident_blocks();
-    const int blocks = (int)(W.n_chunks < cap ? W.n_chunks : cap);
-    if (blocks <= 0) return HEART_OK;
+    if (W.n_chunks == 0) return HEART_OK;
     if (generic) {
-        launch_t<-1, -1, REC>(L, W, st, blocks);
+        launch_t<-1, -1, REC>(L, W, st);
     } else {
 #define HEART_IRC_CASES(G)                                                                    \
     switch (L.irc_kind) {                                                                     \
-    case HEART_IRC_DARWIN: launch_t<G, HEART_IRC_DARWIN, REC>(L, W, st, blocks); break;      \
-    case HEART_IRC_DARWIN_PRINS: launch_t<G, HEART_IRC_DARWIN_PRINS, REC>(L, W, st, blocks); break; \
-    case HEART_IRC_PSEUDO_VOIGT: launch_t<G, HEART_IRC_PSEUDO_VOIGT, REC>(L, W, st, blocks); break; \
-    case HEART_IRC_GAUSSIAN: launch_t<G, HEART_IRC_GAUSSIAN, REC>(L, W, st, blocks); break;  \
-    case HEART_IRC_LORENTZIAN: launch_t<G, HEART_IRC_LORENTZIAN, REC>(L, W, st, blocks); break; \
-    default: launch_t<G, HEART_IRC_BOX, REC>(L, W, st, blocks); break;                        \
+    case HEART_IRC_DARWIN: launch_t<G, HEART_IRC_DARWIN, REC>(L, W, st); break;              \
+    case HEART_IRC_DARWIN_PRINS: launch_t<G, HEART_IRC_DARWIN_PRINS, REC>(L, W, st); break;  \
+    case HEART_IRC_PSEUDO_VOIGT: launch_t<G, HEART_IRC_PSEUDO_VOIGT, REC>(L, W, st); break;  \
+    case HEART_IRC_GAUSSIAN: launch_t<G, HEART_IRC_GAUSSIAN, REC>(L, W, st); break;          \
+    case HEART_IRC_LORENTZIAN: launch_t<G, HEART_IRC_LORENTZIAN, REC>(L, W, st); break;      \
+    default: launch_t<G, HEART_IRC_BOX, REC>(L, W, st); break;                                \
     }
         if (L.geometry == HEART_FLAT) { HEART_IRC_CASES(HEART_FLAT) } else { HEART_IRC_CASES(HEART_CYL_VON_HAMOS) }
 #undef HEART_IRC_CASES
@@ -897,7 +967,7 @@ static heart_status launch_single(const SpecParams &S, const SourceParams &P, ui
     WorkPlan W;
     std::memset(&W, 0, sizeof W);
     W.n_jobs = 1;
-    W.chunk_rays = g_tune.chunk_rays;
+    W.chunk_rays = chunk_for(n);
     W.n_chunks = (n + W.chunk_rays - 1) / W.chunk_rays;
     W.counter = scratch + kCounterWord;
     return rec ? dispatch<true>(L, W, st, false) : dispatch<false>(L, W, st, false);
@@ -937,7 +1007,9 @@ heart_status launch_batch(const SpecParams *const *S, const SourceParams *P, con
     const size_t off_c = off_t + (size_t)n * kTallyN * 8;
     unsigned long long *cb = (unsigned long long *)(host.data() + off_cb);
     unsigned char *d = (unsigned char *)dev;
-    const uint32_t chunk = g_tune.chunk_rays;
+    uint64_t all_rays = 0;
+    for (int i = 0; i < n; ++i) all_rays += n_rays[i];
+    const uint32_t chunk = chunk_for(all_rays);
     unsigned long long nch = 0;
     for (int i = 0; i < n; ++i) {
         make_launch32(*S[i], P[i], n_rays[i], seeds[i], offsets ? offsets[i] : 0, jobs[i]);
@@ -1008,6 +1080,68 @@ extern "C" heart_status heart_trace_batch(heart_spectrometer *const *specs, cons
     }
     cudaFreeAsync(dev, cs);
     return st;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: time candidate launch shapes on a probe and keep the fastest
+// ---------------------------------------------------------------------------
+extern "C" heart_status heart_autotune(heart_spectrometer *h, const heart_source_desc *src, uint64_t probe_rays,
+                                       void *stream, heart_tune *out) {
+    using namespace heart;
+    if (!h) return fail(HEART_EINVAL, "null spectrometer");
+    if (probe_rays < 4096) return fail(HEART_EINVAL, "probe needs at least 4096 rays");
+    SourceParams P;
+    char err[256] = {0};
+    heart_status st = build_source_params(src, &P, err, (int)sizeof err);
+    if (st != HEART_OK) return fail(st, err);
+    cudaStream_t cs = (cudaStream_t)stream;
+    const size_t elt = h->p.count_type == HEART_COUNT_I64 ? 8 : 4;
+    const size_t bytes = (size_t)h->p.nx * h->p.ny * elt;
+    cudaError_t e;
+    if (!h->d_image_host_path || h->host_image_bytes < bytes) {
+        if (h->d_image_host_path) cudaFree(h->d_image_host_path);
+        h->d_image_host_path = nullptr;
+        if ((e = cudaMalloc(&h->d_image_host_path, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc image");
+        h->host_image_bytes = bytes;
+    }
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    const int occs[2] = {6, 8};
+    const int refills[3] = {4, 8, 16};
+    TuneConfig best = g_tune;
+    double best_rate = -1.0;
+    const TuneConfig saved = g_tune;
+    for (int oi = 0; oi < 2; ++oi) {
+        for (int ri = 0; ri < 3; ++ri) {
+            g_tune.blocks_per_sm = occs[oi];
+            g_tune.refill = refills[ri];
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2; ++rep) {       // first repetition warms up
+                cudaMemsetAsync(h->d_scratch, 0, kScratchWords * sizeof(unsigned long long), cs);
+                cudaEventRecord(t0, cs);
+                st = launch_fp32(h->p, P, probe_rays, 0x5eed + rep, 0, h->d_image_host_path, h->d_scratch, cs);
+                cudaEventRecord(t1, cs);
+                if (st != HEART_OK) break;
+                if ((e = cudaEventSynchronize(t1)) != cudaSuccess) { st = cuda_fail(e, "autotune probe"); break; }
+                cudaEventElapsedTime(&ms, t0, t1);
+            }
+            if (st != HEART_OK) { g_tune = saved; cudaEventDestroy(t0); cudaEventDestroy(t1); return st; }
+            const double rate = (double)probe_rays / (ms * 1e-3);
+            if (rate > best_rate) { best_rate = rate; best = g_tune; }
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    g_tune = best;
+    if (out) {
+        out->blocks_per_sm = best.blocks_per_sm;
+        out->refill_lanes = best.refill;
+        out->max_chunk_rays = best.chunk_rays;
+        out->reserved = 0;
+        out->rays_per_s = best_rate;
+    }
+    return HEART_OK;
 }
 
 // ---------------------------------------------------------------------------
