@@ -33,6 +33,22 @@ INSTR_PER_RAY = 240            # two Philox blocks, source, entry, per-ray const
 SM_COUNT = 152
 LANES_PER_SM_CLK = 128         # 4 SM sub-partitions x 32 lanes, one warp-instruction issue each per clock
 SM_MAX_MHZ = 2070.0
+# DRAM bytes (read + write) of one k_trace_fp32 launch, from the ncu capture in
+# profiles/k_trace_fp32_von_hamos.md; valid only for the kernel sources hashed there
+TRAFFIC_BYTES = 592_640
+TRAFFIC_SOURCES = ("paper_2503_16955_gb300/csrc/heart_fp32.cu", "paper_2503_16955_gb300/csrc/heart_fp64.cuh",
+                   "paper_2503_16955_gb300/csrc/heart_internal.h")
+TRAFFIC_SOURCE_HASH = "40def836f1114ea0"
+
+
+def measured_traffic():
+    """per-launch DRAM traffic, or None if the kernel changed since the capture"""
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return TRAFFIC_BYTES if h.hexdigest()[:16] == TRAFFIC_SOURCE_HASH else None
 
 
 def parse():
@@ -352,7 +368,9 @@ def main():
                        "detector_hits_per_s": value * det_frac,
                        "l2": "inputs are per-ray counters (no input data); the 4 MB image stays in L2"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-instr/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": measured_traffic(),
+                         "traffic_note": "ncu dram__bytes_read+write of one launch (2e7-ray capture); table "
+                                         "staging per block, does not grow with rays",
                          "kernel": "k_trace_fp32 (persistent, one launch per step)",
                          "peak_basis": "152 SMs x 128 lanes x 2070 MHz (max SM clock); algorithmic "
                                        "%d instr/collision + %d instr/ray" % (INSTR_PER_COLLISION, INSTR_PER_RAY)},

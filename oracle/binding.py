@@ -84,6 +84,23 @@ class RayConsts(C.Structure):
                                                                 ("pad", C.c_int32)]
 
 
+class QE(C.Structure):
+    _fields_ = [("n", C.c_int32), ("pad", C.c_int32), ("keV", C.c_double * 32), ("qe", C.c_double * 32)]
+
+
+def make_qe(table):
+    """[(keV, qe), ...] -> QE (None / empty: QE = 1)"""
+    q = QE()
+    table = list(table or [])
+    if len(table) > 32:
+        raise ValueError("at most 32 QE knots")
+    q.n = len(table)
+    for i, (e, v) in enumerate(table):
+        q.keV[i] = e
+        q.qe[i] = v
+    return q
+
+
 class MdfTable(C.Structure):
     _fields_ = [("body", C.c_double * MDF_M), ("tail", C.c_double * (MDF_T + 1)), ("qmax", C.c_double)]
 
@@ -114,6 +131,10 @@ def lib():
             "orc_ray_constants": (C.c_int, [C.POINTER(Spec), C.c_double, C.POINTER(RayConsts)]),
             "orc_trace": (C.c_int, [C.POINTER(Spec), C.POINTER(Source), C.c_uint64, C.c_uint64,
                                     C.c_uint64, C.c_int, i64p, C.POINTER(Tally), C.c_void_p]),
+            "orc_trace_energy": (C.c_int, [C.POINTER(Spec), C.POINTER(Source), C.c_uint64, C.c_uint64,
+                                           C.c_uint64, C.c_int, i64p, i64p, C.POINTER(QE), C.POINTER(Tally),
+                                           C.c_void_p]),
+            "orc_qe_eval": (C.c_double, [C.POINTER(QE), C.c_double]),
             "orc_walk_injected": (C.c_int, [C.POINTER(Spec), C.c_double, dp, dp, u32p, C.c_int64,
                                             C.c_void_p]),
             "orc_sample_crystallites": (C.c_int64, [C.POINTER(Spec), C.c_double, C.c_double,
@@ -284,6 +305,30 @@ def trace(spec_dict, source_dict, n_rays, seed, ray_offset=0, n_threads=0, recor
     if rc != 0:
         raise RuntimeError(_err())
     return img, tal.as_dict(), rec
+
+
+def trace_energy(spec_dict, source_dict, n_rays, seed, qe=None, ray_offset=0, n_threads=0, records=False):
+    """(count image, energy image in 1e-6 keV, tally, records)"""
+    s = make_spec(spec_dict)
+    src = make_source(source_dict)
+    shape = (spec_dict["det_ny"], spec_dict["det_nx"])
+    img = np.zeros(shape, dtype=np.int64)
+    eimg = np.zeros(shape, dtype=np.int64)
+    q = make_qe(qe)
+    tal = Tally()
+    rec = np.zeros(n_rays, dtype=RECORD_DTYPE) if records else None
+    rc = lib().orc_trace_energy(C.byref(s), C.byref(src), n_rays, seed, ray_offset, n_threads,
+                                img.ctypes.data_as(C.POINTER(C.c_int64)),
+                                eimg.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(q), C.byref(tal),
+                                rec.ctypes.data if records else None)
+    if rc != 0:
+        raise RuntimeError(_err())
+    return img, eimg, tal.as_dict(), rec
+
+
+def qe_eval(table, E):
+    q = make_qe(table)
+    return lib().orc_qe_eval(C.byref(q), E)
 
 
 def walk_injected(spec_dict, E, pos, direction, words):

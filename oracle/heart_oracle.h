@@ -148,6 +148,19 @@ int orc_trace(const orc_spec *s, const orc_source *src, uint64_t n_rays, uint64_
               uint64_t ray_offset, int n_threads, int64_t *image, orc_tally *tally,
               orc_record *records);
 
+/* detector quantum efficiency, linear in energy between the knots and
+ * constant beyond them (Sec. 3: energies multiplied by their QE before the
+ * keV image is binned); n = 0 means QE = 1 */
+#define ORC_MAX_QE 32
+typedef struct { int32_t n, pad; double keV[ORC_MAX_QE], qe[ORC_MAX_QE]; } orc_qe;
+double orc_qe_eval(const orc_qe *q, double E_keV);
+
+/* as orc_trace, and adds round(E * QE(E) * 1e6) (units of 1e-6 keV) of each
+ * detected photon to energy_image (Sec. 2.3: the summed-keV image) */
+int orc_trace_energy(const orc_spec *s, const orc_source *src, uint64_t n_rays, uint64_t seed,
+                     uint64_t ray_offset, int n_threads, int64_t *image, int64_t *energy_image,
+                     const orc_qe *qe, orc_tally *tally, orc_record *records);
+
 /* the walk of one ray from a given entry state, fed with explicit 32-bit words
  * (4 per tentative collision) instead of Philox; for hand-traced tests */
 int orc_walk_injected(const orc_spec *s, double E_keV, const double pos[3], const double dir[3],

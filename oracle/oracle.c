@@ -837,6 +837,8 @@ typedef struct {
     uint64_t begin, end, offset;
     uint32_t key[2];
     int64_t *image;          /* private per thread */
+    int64_t *eimage;         /* private per thread, or NULL */
+    const orc_qe *qe;
     orc_tally tally;
     orc_record *records;
 } job;
@@ -884,6 +886,8 @@ static void trace_one(job *J, uint64_t i) {
         if (rec.det_hit) {
             J->tally.det_hits++;
             J->image[(int64_t)rec.iy * s->det_nx + rec.ix] += 1;
+            if (J->eimage)
+                J->eimage[(int64_t)rec.iy * s->det_nx + rec.ix] += (int64_t)llround(E * orc_qe_eval(J->qe, E) * 1e6);
         }
     }
     if (J->records) J->records[i] = rec;
@@ -895,10 +899,28 @@ static void *thread_main(void *arg) {
     return NULL;
 }
 
+double orc_qe_eval(const orc_qe *q, double E) {
+    if (!q || q->n <= 0) return 1.0;
+    if (E <= q->keV[0]) return q->qe[0];
+    for (int i = 1; i < q->n; ++i)
+        if (E <= q->keV[i]) {
+            double f = (E - q->keV[i - 1]) / (q->keV[i] - q->keV[i - 1]);
+            return q->qe[i - 1] + f * (q->qe[i] - q->qe[i - 1]);
+        }
+    return q->qe[q->n - 1];
+}
+
 int orc_trace(const orc_spec *s, const orc_source *src, uint64_t n_rays, uint64_t seed,
               uint64_t ray_offset, int n_threads, int64_t *image, orc_tally *tally,
               orc_record *records) {
+    return orc_trace_energy(s, src, n_rays, seed, ray_offset, n_threads, image, NULL, NULL, tally, records);
+}
+
+int orc_trace_energy(const orc_spec *s, const orc_source *src, uint64_t n_rays, uint64_t seed,
+                     uint64_t ray_offset, int n_threads, int64_t *image, int64_t *energy_image,
+                     const orc_qe *qe, orc_tally *tally, orc_record *records) {
     if (!s || !src || !image || !tally) return fail("null argument");
+    if (qe && (qe->n < 0 || qe->n > ORC_MAX_QE)) return fail("bad QE table");
     if (src->n_comp < 1 || src->n_comp > ORC_MAX_COMP) return fail("bad component count");
     geom g;
     if (geom_init(&g, s)) return -1;
@@ -931,8 +953,10 @@ int orc_trace(const orc_spec *s, const orc_source *src, uint64_t n_rays, uint64_
         J->offset = ray_offset;
         J->key[0] = (uint32_t)seed; J->key[1] = (uint32_t)(seed >> 32);
         J->image = (t == 0) ? image : (int64_t *)calloc(npix, sizeof(int64_t));
+        J->eimage = (!energy_image) ? NULL : (t == 0) ? energy_image : (int64_t *)calloc(npix, sizeof(int64_t));
+        J->qe = qe;
         J->records = records;
-        if (!J->image) { n_threads = t; break; }
+        if (!J->image || (energy_image && !J->eimage)) { n_threads = t; break; }
     }
     int nt = n_threads;
     for (int t = 1; t < nt; ++t) pthread_create(&th[t], NULL, thread_main, &jobs[t]);
@@ -949,6 +973,10 @@ int orc_trace(const orc_spec *s, const orc_source *src, uint64_t n_rays, uint64_
         if (t > 0) {
             for (size_t p = 0; p < npix; ++p) image[p] += jobs[t].image[p];
             free(jobs[t].image);
+            if (energy_image) {
+                for (size_t p = 0; p < npix; ++p) energy_image[p] += jobs[t].eimage[p];
+                free(jobs[t].eimage);
+            }
         }
     }
     free(jobs); free(th); free(tab);

@@ -323,3 +323,36 @@ def test_source_sampling_distributions():
     spread = np.sort(np.linalg.svd(off, compute_uv=False) / math.sqrt(n))
     sig = np.array([0.4, 1.0]) / (2 * math.sqrt(2 * LN2))
     assert np.allclose(spread[1:], sig, rtol=0.01)
+
+
+# --------------------------------------------------------------------------
+# energy image and detector quantum efficiency (Sec. 2.3, Sec. 3)
+# --------------------------------------------------------------------------
+def test_qe_is_linear_interpolation_clamped_at_the_ends():
+    table = [(7.5, 0.9), (8.0, 0.8), (8.6, 0.5), (9.0, 0.55)]
+    xs, ys = zip(*table)
+    for E in np.linspace(7.0, 9.5, 51):
+        assert ob.qe_eval(table, E) == pytest.approx(np.interp(E, xs, ys), rel=1e-14, abs=1e-15)
+    assert ob.qe_eval([], 8.0) == 1.0
+
+
+def test_energy_image_sums_detected_photon_energies():
+    w = W.von_hamos_hapg()
+    qe = [(7.5, 0.9), (8.0, 0.8), (8.5, 0.5)]
+    img, eimg, tal, rec = ob.trace_energy(w["spec"], w["source"], 40_000, 5, qe=qe, records=True)
+    hit = rec["det_hit"] == 1
+    assert int(img.sum()) == tal["det_hits"] == int(hit.sum())
+    # per pixel: the sum of round(E * QE(E) * 1e6) over the rays binned there
+    want = np.zeros_like(eimg)
+    for r in rec[hit]:
+        want[r["iy"], r["ix"]] += int(round(r["energy_keV"] * ob.qe_eval(qe, r["energy_keV"]) * 1e6))
+    assert np.array_equal(eimg, want)
+    # the count image is the plain trace's image, unchanged by the energy accumulator
+    img2, _, _ = ob.trace(w["spec"], w["source"], 40_000, 5)
+    assert np.array_equal(img, img2)
+
+
+def test_mono_energy_image_is_count_times_energy():
+    w = W.flat_hopg_mono()
+    img, eimg, tal, _ = ob.trace_energy(w["spec"], w["source"], 100_000, 6)
+    assert np.array_equal(eimg, img * 8_000_000)
