@@ -57,7 +57,11 @@ class Component(C.Structure):
 class Source(C.Structure):
     _fields_ = [("n_comp", C.c_int32), ("pad", C.c_int32), ("comp", Component * MAX_COMP),
                 ("origin", D3), ("axis", D3), ("cone_half_angle_rad", C.c_double),
-                ("spot_fwhm_mm", C.c_double * 2)]
+                ("spot_fwhm_mm", C.c_double * 2), ("polarization", D3)]
+
+
+class Rays(C.Structure):
+    _fields_ = [(n, C.POINTER(C.c_double)) for n in ("ox", "oy", "oz", "kx", "ky", "kz", "E", "px", "py", "pz")]
 
 
 class Tally(C.Structure):
@@ -75,7 +79,7 @@ RECORD_DTYPE = np.dtype([
     ("ray_id", np.uint64), ("outcome", np.int32), ("nrefl", np.int32), ("ncoll", np.int64),
     ("energy_keV", np.float64), ("pos", np.float64, 3), ("dir", np.float64, 3),
     ("u_mm", np.float64), ("v_mm", np.float64), ("ix", np.int32), ("iy", np.int32),
-    ("det_hit", np.int32), ("no_bragg", np.int32)])
+    ("det_hit", np.int32), ("no_bragg", np.int32), ("pol", np.float64, 3)])
 
 
 class RayConsts(C.Structure):
@@ -135,8 +139,12 @@ def lib():
                                            C.c_uint64, C.c_int, i64p, i64p, C.POINTER(QE), C.POINTER(Tally),
                                            C.c_void_p]),
             "orc_qe_eval": (C.c_double, [C.POINTER(QE), C.c_double]),
-            "orc_walk_injected": (C.c_int, [C.POINTER(Spec), C.c_double, dp, dp, u32p, C.c_int64,
+            "orc_trace_rays": (C.c_int, [C.POINTER(Spec), C.POINTER(Rays), C.c_uint64, C.c_uint64, C.c_uint64,
+                                         C.c_int, i64p, i64p, C.POINTER(QE), C.POINTER(Tally), C.c_void_p]),
+            "orc_walk_injected": (C.c_int, [C.POINTER(Spec), C.c_double, dp, dp, dp, u32p, C.c_int64,
                                             C.c_void_p]),
+            "orc_walk_injected_n": (C.c_int, [C.POINTER(Spec), C.c_int64, dp, dp, dp, dp, u32p, C.c_int64,
+                                              C.c_void_p]),
             "orc_sample_crystallites": (C.c_int64, [C.POINTER(Spec), C.c_double, C.c_double,
                                                     C.c_int64, C.c_uint64, dp, dp]),
             "orc_reflection_rate": (C.c_double, [C.POINTER(Spec), C.c_double, C.c_double]),
@@ -210,6 +218,7 @@ def make_source(d):
     s.cone_half_angle_rad = d["cone_half_angle_rad"]
     sf = d.get("spot_fwhm_mm", (0.0, 0.0))
     s.spot_fwhm_mm = (C.c_double * 2)(*sf)
+    s.polarization = D3(*d.get("polarization", (0.0, 0.0, 0.0)))
     return s
 
 
@@ -331,17 +340,62 @@ def qe_eval(table, E):
     return lib().orc_qe_eval(C.byref(q), E)
 
 
-def walk_injected(spec_dict, E, pos, direction, words):
+def trace_rays(spec_dict, rays, seed, qe=None, ray_offset=0, n_threads=0, records=False):
+    """User-supplied rays: dict of float64 arrays ox, oy, oz, kx, ky, kz, E and
+    optionally px, py, pz.  Returns (image, energy image, tally, records)."""
+    s = make_spec(spec_dict)
+    n = len(rays["E"])
+    arrs = {k: np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for k, v in rays.items()}
+    R = Rays()
+    for k in ("ox", "oy", "oz", "kx", "ky", "kz", "E", "px", "py", "pz"):
+        if k in arrs:
+            setattr(R, k, arrs[k].ctypes.data_as(C.POINTER(C.c_double)))
+    shape = (spec_dict["det_ny"], spec_dict["det_nx"])
+    img = np.zeros(shape, dtype=np.int64)
+    eimg = np.zeros(shape, dtype=np.int64)
+    q = make_qe(qe)
+    tal = Tally()
+    rec = np.zeros(n, dtype=RECORD_DTYPE) if records else None
+    rc = lib().orc_trace_rays(C.byref(s), C.byref(R), n, seed, ray_offset, n_threads,
+                              img.ctypes.data_as(C.POINTER(C.c_int64)), eimg.ctypes.data_as(C.POINTER(C.c_int64)),
+                              C.byref(q), C.byref(tal), rec.ctypes.data if records else None)
+    if rc != 0:
+        raise RuntimeError(_err())
+    return img, eimg, tal.as_dict(), rec
+
+
+def walk_injected(spec_dict, E, pos, direction, words, pol=None):
     s = make_spec(spec_dict)
     w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32))
     rec = np.zeros(1, dtype=RECORD_DTYPE)
     p = D3(*pos)
     d = D3(*direction)
-    rc = lib().orc_walk_injected(C.byref(s), E, p, d, w.ctypes.data_as(C.POINTER(C.c_uint32)),
+    pp = D3(*pol) if pol is not None else None
+    rc = lib().orc_walk_injected(C.byref(s), E, p, d, pp, w.ctypes.data_as(C.POINTER(C.c_uint32)),
                                  len(w), rec.ctypes.data)
     if rc != 0:
         raise RuntimeError(_err())
     return rec[0]
+
+
+def walk_injected_n(spec_dict, E, pos, direction, words, pol=None):
+    """many injected walks with one mosaic table: E (n,), pos/direction/pol
+    (n, 3), words (n, m)"""
+    s = make_spec(spec_dict)
+    E = np.ascontiguousarray(np.asarray(E, dtype=np.float64))
+    n = len(E)
+    P = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(n, 3))
+    D = np.ascontiguousarray(np.asarray(direction, dtype=np.float64).reshape(n, 3))
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32).reshape(n, -1))
+    pp = None if pol is None else np.ascontiguousarray(np.asarray(pol, dtype=np.float64).reshape(n, 3))
+    rec = np.zeros(n, dtype=RECORD_DTYPE)
+    dp = C.POINTER(C.c_double)
+    rc = lib().orc_walk_injected_n(C.byref(s), n, E.ctypes.data_as(dp), P.ctypes.data_as(dp), D.ctypes.data_as(dp),
+                                   pp.ctypes.data_as(dp) if pp is not None else None,
+                                   w.ctypes.data_as(C.POINTER(C.c_uint32)), w.shape[1], rec.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(_err())
+    return rec
 
 
 def sample_crystallites(spec_dict, E, alpha, n, seed):

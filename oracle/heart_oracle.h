@@ -23,6 +23,11 @@
  *                                    hand-traced injected-uniform walks)
  *   orc_reflection_rate      pinned (small-Gamma limit Eq. SimpleZachXsection for vMF)
  *   orc_sample_crystallites  pinned (accepted Delta ~ IRC; psi ~ W(theta(psi)), Appendix Method II)
+ *   polarised walk (G_pol, p update) pinned (sigma: G = 1, pi: G = cos^2 2a on hand-traced rays; the
+ *                                    thresholds of two orthogonal p sum to twice the unpolarised one;
+ *                                    closed-form reflected p; p stays unit and perpendicular to k)
+ *   orc_trace_rays           pinned (rays repeating a zero-cone source reproduce orc_trace exactly)
+ *   orc_trace_energy         pinned (mono line: energy image = E x QE x counts; QE interpolation)
  *   absolute reflectivity / detector image shapes against experiment: parity unpinned
  *   (the paper's measured spectra are not available).
  */
@@ -88,7 +93,15 @@ typedef struct {
     double origin[3], axis[3];
     double cone_half_angle_rad;
     double spot_fwhm_mm[2];
+    double polarization[3];   /* linear polarisation p0 (projected perpendicular to
+                                 each ray); zero vector: unpolarised */
 } orc_source;
+
+/* user-supplied rays (Sec. 2.1: origins, energies, directions and optional
+ * polarisations given as arrays); px/py/pz may be NULL (unpolarised) */
+typedef struct {
+    const double *ox, *oy, *oz, *kx, *ky, *kz, *E, *px, *py, *pz;
+} orc_rays;
 
 typedef struct {
     uint64_t emitted, miss, absorbed, exit_front, exit_back, exit_side, capped, stuck,
@@ -106,6 +119,7 @@ typedef struct {
     double u_mm, v_mm;        /* detector-plane coordinates (NaN if no plane hit) */
     int32_t ix, iy;           /* pixel (-1 if outside) */
     int32_t det_hit, no_bragg;
+    double pol[3];            /* final polarisation (zero if unpolarised) */
 } orc_record;
 
 typedef struct {
@@ -161,10 +175,21 @@ int orc_trace_energy(const orc_spec *s, const orc_source *src, uint64_t n_rays, 
                      uint64_t ray_offset, int n_threads, int64_t *image, int64_t *energy_image,
                      const orc_qe *qe, orc_tally *tally, orc_record *records);
 
+/* as orc_trace_energy for user-supplied rays: ray i (id ray_offset + i) starts
+ * at its own origin, direction, energy and polarisation; the walk draws its
+ * Philox words from call 2 on, as for sampled rays */
+int orc_trace_rays(const orc_spec *s, const orc_rays *rays, uint64_t n_rays, uint64_t seed,
+                   uint64_t ray_offset, int n_threads, int64_t *image, int64_t *energy_image,
+                   const orc_qe *qe, orc_tally *tally, orc_record *records);
+
 /* the walk of one ray from a given entry state, fed with explicit 32-bit words
  * (4 per tentative collision) instead of Philox; for hand-traced tests */
 int orc_walk_injected(const orc_spec *s, double E_keV, const double pos[3], const double dir[3],
-                      const uint32_t *words, int64_t n_words, orc_record *rec);
+                      const double *pol, const uint32_t *words, int64_t n_words, orc_record *rec);
+/* n such walks sharing one mosaic table: ray i takes E[i], pos[3i..], dir[3i..],
+ * pol[3i..] (pol may be NULL: all unpolarised) and words[i * words_per_ray ..] */
+int orc_walk_injected_n(const orc_spec *s, int64_t n, const double *E_keV, const double *pos, const double *dir,
+                        const double *pol, const uint32_t *words, int64_t words_per_ray, orc_record *rec);
 
 /* accepted crystallites at a fixed ray direction and surface normal:
  * returns Delta (= alpha~ - alpha_B - Delta_M) and psi of n accepted draws */

@@ -715,8 +715,8 @@ static int next4(wsrc *ws, uint32_t w[4]) {
 }
 
 /* the depth walk of one ray from its entry point (Sec. 2.2.4) */
-static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[3], wsrc *ws,
-                 orc_record *rec) {
+static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[3], int pol, double p[3],
+                 wsrc *ws, orc_record *rec) {
     const orc_spec *s = g->s;
     int nrefl = 0;
     int64_t ncoll = 0;
@@ -751,14 +751,28 @@ static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[
         if (sa > 1.0) sa = 1.0;
         double at = asin(sa);                            /* incidence on the crystallite */
         double delta = at - rc->alpha_B - s->irc_shift_rad;
-        double c2 = cos(2.0 * at);
-        double G = 0.5 * (1.0 + c2 * c2);                /* Eq. (G_unpol) */
+        double ks[3];                                    /* reflected direction (reflection equation) */
+        for (int i = 0; i < 3; ++i) ks[i] = k[i] - 2.0 * kn * n[i];
+        double G;
+        if (pol) {
+            double pk = dot3(p, ks);
+            G = 1.0 - pk * pk;                           /* G = 1 - (p . k_s)^2, Eq. (G_pol) */
+        } else {
+            double c2 = cos(2.0 * at);
+            G = 0.5 * (1.0 + c2 * c2);                   /* Eq. (G_unpol) */
+        }
         double P = irc_eval(&g->irc, delta) * G / g->irc_max;
         if (v < P) {
             ++nrefl;
             if (nrefl > s->max_reflections) { outcome = ORC_CAPPED; break; }
-            for (int i = 0; i < 3; ++i) k[i] -= 2.0 * kn * n[i];   /* reflection equation */
+            memcpy(k, ks, sizeof ks);
             normalize3(k);
+            if (pol) {                                   /* p_s = (p - (p.k_s) k_s) / sqrt(1 - (p.k_s)^2) */
+                double pk = dot3(p, k);
+                double d = sqrt(1.0 - pk * pk);
+                for (int i = 0; i < 3; ++i) p[i] = (p[i] - pk * k[i]) / d;
+                normalize3(p);
+            }
         }
     }
     rec->outcome = outcome;
@@ -766,9 +780,20 @@ static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[
     rec->ncoll = ncoll;
     memcpy(rec->pos, x, 3 * sizeof(double));
     memcpy(rec->dir, k, 3 * sizeof(double));
+    for (int i = 0; i < 3; ++i) rec->pol[i] = pol ? p[i] : 0.0;
     rec->u_mm = NAN; rec->v_mm = NAN; rec->ix = -1; rec->iy = -1; rec->det_hit = 0;
     if (outcome == ORC_EXIT_FRONT || outcome == ORC_EXIT_BACK || outcome == ORC_EXIT_SIDE)
         detector(g, x, k, rec);
+}
+
+/* polarisation of a ray: p0 projected perpendicular to k, or none */
+static int project_pol(const double p0[3], const double k[3], double p[3]) {
+    double pk = dot3(p0, k);
+    for (int i = 0; i < 3; ++i) p[i] = p0[i] - pk * k[i];
+    double n = sqrt(dot3(p, p));
+    if (!(n > 1e-12)) { p[0] = p[1] = p[2] = 0.0; return 0; }
+    for (int i = 0; i < 3; ++i) p[i] /= n;
+    return 1;
 }
 
 /* ------------------------------------------------------------------ */
@@ -839,6 +864,7 @@ typedef struct {
     int64_t *image;          /* private per thread */
     int64_t *eimage;         /* private per thread, or NULL */
     const orc_qe *qe;
+    const orc_rays *rays;    /* user-supplied rays, or NULL (sampled source) */
     orc_tally tally;
     orc_record *records;
 } job;
@@ -850,11 +876,26 @@ static void trace_one(job *J, uint64_t i) {
     wsrc ws = {0};
     ws.key[0] = J->key[0]; ws.key[1] = J->key[1];
     ws.ray = ray; ws.call = 0;
-    uint32_t a[4], b[4];
-    next4(&ws, a);
-    next4(&ws, b);
-    double E, o[3], k[3], p[3];
-    sample_source(J->src, J->cumw, J->ax, J->b1, J->b2, a, b, &E, o, k);
+    double E, o[3], k[3], p[3], pv[3] = {0, 0, 0};
+    int pol = 0;
+    if (J->rays) {
+        const orc_rays *R = J->rays;
+        E = R->E[i];
+        o[0] = R->ox[i]; o[1] = R->oy[i]; o[2] = R->oz[i];
+        k[0] = R->kx[i]; k[1] = R->ky[i]; k[2] = R->kz[i];
+        if (normalize3(k)) E = NAN;                     /* a zero direction cannot enter */
+        if (R->px) {
+            double p0[3] = {R->px[i], R->py[i], R->pz[i]};
+            pol = project_pol(p0, k, pv);
+        }
+        ws.call = 2;                                    /* the walk's words, as for sampled rays */
+    } else {
+        uint32_t a[4], b[4];
+        next4(&ws, a);
+        next4(&ws, b);
+        sample_source(J->src, J->cumw, J->ax, J->b1, J->b2, a, b, &E, o, k);
+        pol = project_pol(J->src->polarization, k, pv);
+    }
     orc_record rec;
     memset(&rec, 0, sizeof rec);
     rec.ray_id = ray;
@@ -866,13 +907,14 @@ static void trace_one(job *J, uint64_t i) {
         rec.outcome = ORC_MISS;
         memcpy(rec.pos, o, sizeof rec.pos);
         memcpy(rec.dir, k, sizeof rec.dir);
+        for (int c = 0; c < 3; ++c) rec.pol[c] = pol ? pv[c] : 0.0;
         rec.u_mm = NAN; rec.v_mm = NAN; rec.ix = -1; rec.iy = -1;
     } else {
         orc_ray_consts rc;
         orc_ray_constants(s, E, &rc);
         if (rc.no_bragg) J->tally.no_bragg++;
         rec.no_bragg = rc.no_bragg;
-        walk(g, &rc, p, k, &ws, &rec);
+        walk(g, &rc, p, k, pol, pv, &ws, &rec);
         J->tally.collisions += (uint64_t)rec.ncoll;
         J->tally.refl_hist[rec.nrefl < 15 ? rec.nrefl : 15]++;
         switch (rec.outcome) {
@@ -916,12 +958,34 @@ int orc_trace(const orc_spec *s, const orc_source *src, uint64_t n_rays, uint64_
     return orc_trace_energy(s, src, n_rays, seed, ray_offset, n_threads, image, NULL, NULL, tally, records);
 }
 
+static int trace_driver(const orc_spec *s, const orc_source *src, const orc_rays *rays, uint64_t n_rays,
+                        uint64_t seed, uint64_t ray_offset, int n_threads, int64_t *image,
+                        int64_t *energy_image, const orc_qe *qe, orc_tally *tally, orc_record *records);
+
 int orc_trace_energy(const orc_spec *s, const orc_source *src, uint64_t n_rays, uint64_t seed,
                      uint64_t ray_offset, int n_threads, int64_t *image, int64_t *energy_image,
                      const orc_qe *qe, orc_tally *tally, orc_record *records) {
-    if (!s || !src || !image || !tally) return fail("null argument");
+    if (!src) return fail("null argument");
+    return trace_driver(s, src, NULL, n_rays, seed, ray_offset, n_threads, image, energy_image, qe, tally,
+                        records);
+}
+
+int orc_trace_rays(const orc_spec *s, const orc_rays *rays, uint64_t n_rays, uint64_t seed,
+                   uint64_t ray_offset, int n_threads, int64_t *image, int64_t *energy_image,
+                   const orc_qe *qe, orc_tally *tally, orc_record *records) {
+    if (!rays || !rays->ox || !rays->oy || !rays->oz || !rays->kx || !rays->ky || !rays->kz || !rays->E)
+        return fail("null ray array");
+    if (rays->px && (!rays->py || !rays->pz)) return fail("partial polarisation arrays");
+    return trace_driver(s, NULL, rays, n_rays, seed, ray_offset, n_threads, image, energy_image, qe, tally,
+                        records);
+}
+
+static int trace_driver(const orc_spec *s, const orc_source *src, const orc_rays *rays, uint64_t n_rays,
+                        uint64_t seed, uint64_t ray_offset, int n_threads, int64_t *image,
+                        int64_t *energy_image, const orc_qe *qe, orc_tally *tally, orc_record *records) {
+    if (!s || !image || !tally) return fail("null argument");
     if (qe && (qe->n < 0 || qe->n > ORC_MAX_QE)) return fail("bad QE table");
-    if (src->n_comp < 1 || src->n_comp > ORC_MAX_COMP) return fail("bad component count");
+    if (src && (src->n_comp < 1 || src->n_comp > ORC_MAX_COMP)) return fail("bad component count");
     geom g;
     if (geom_init(&g, s)) return -1;
     orc_mdf_table *tab = (orc_mdf_table *)malloc(sizeof(orc_mdf_table));
@@ -929,12 +993,15 @@ int orc_trace_energy(const orc_spec *s, const orc_source *src, uint64_t n_rays, 
     if (orc_mdf_build_table(s, tab)) { free(tab); return -1; }
     g.mdf = tab;
     double cumw[ORC_MAX_COMP], tot = 0.0;
-    for (int i = 0; i < src->n_comp; ++i) tot += src->comp[i].weight;
-    double run = 0.0;
-    for (int i = 0; i < src->n_comp; ++i) { run += src->comp[i].weight; cumw[i] = run / tot; }
-    double ax[3] = {src->axis[0], src->axis[1], src->axis[2]}, b1[3], b2[3];
-    if (normalize3(ax)) { free(tab); return fail("bad source axis"); }
-    source_basis(ax, b1, b2);
+    double ax[3] = {0, 0, 1}, b1[3] = {1, 0, 0}, b2[3] = {0, 1, 0};
+    if (src) {
+        for (int i = 0; i < src->n_comp; ++i) tot += src->comp[i].weight;
+        double run = 0.0;
+        for (int i = 0; i < src->n_comp; ++i) { run += src->comp[i].weight; cumw[i] = run / tot; }
+        memcpy(ax, src->axis, sizeof ax);
+        if (normalize3(ax)) { free(tab); return fail("bad source axis"); }
+        source_basis(ax, b1, b2);
+    }
 
     if (n_threads <= 0) n_threads = (int)sysconf(_SC_NPROCESSORS_ONLN);
     if (n_threads < 1) n_threads = 1;
@@ -955,6 +1022,7 @@ int orc_trace_energy(const orc_spec *s, const orc_source *src, uint64_t n_rays, 
         J->image = (t == 0) ? image : (int64_t *)calloc(npix, sizeof(int64_t));
         J->eimage = (!energy_image) ? NULL : (t == 0) ? energy_image : (int64_t *)calloc(npix, sizeof(int64_t));
         J->qe = qe;
+        J->rays = rays;
         J->records = records;
         if (!J->image || (energy_image && !J->eimage)) { n_threads = t; break; }
     }
@@ -983,25 +1051,37 @@ int orc_trace_energy(const orc_spec *s, const orc_source *src, uint64_t n_rays, 
     return 0;
 }
 
-int orc_walk_injected(const orc_spec *s, double E, const double pos[3], const double dir[3],
-                      const uint32_t *words, int64_t n_words, orc_record *rec) {
+int orc_walk_injected_n(const orc_spec *s, int64_t n, const double *E, const double *pos, const double *dir,
+                        const double *pol, const uint32_t *words, int64_t words_per_ray, orc_record *rec) {
     geom g;
     if (geom_init(&g, s)) return -1;
     orc_mdf_table *tab = (orc_mdf_table *)malloc(sizeof(orc_mdf_table));
     if (!tab) return fail("out of memory");
     if (orc_mdf_build_table(s, tab)) { free(tab); return -1; }
     g.mdf = tab;
-    orc_ray_consts rc;
-    orc_ray_constants(s, E, &rc);
-    wsrc ws = {0};
-    ws.words = words; ws.n = n_words; ws.pos = 0;
-    double x[3] = {pos[0], pos[1], pos[2]}, k[3] = {dir[0], dir[1], dir[2]};
-    memset(rec, 0, sizeof *rec);
-    rec->energy_keV = E;
-    rec->no_bragg = rc.no_bragg;
-    walk(&g, &rc, x, k, &ws, rec);
+    for (int64_t i = 0; i < n; ++i) {
+        orc_ray_consts rc;
+        orc_ray_constants(s, E[i], &rc);
+        wsrc ws = {0};
+        ws.words = words + i * words_per_ray; ws.n = words_per_ray; ws.pos = 0;
+        double x[3], k[3];
+        memcpy(x, pos + 3 * i, sizeof x);
+        memcpy(k, dir + 3 * i, sizeof k);
+        orc_record *r = rec + i;
+        memset(r, 0, sizeof *r);
+        r->energy_keV = E[i];
+        r->no_bragg = rc.no_bragg;
+        double pv[3] = {0, 0, 0};
+        int pl = pol ? project_pol(pol + 3 * i, k, pv) : 0;
+        walk(&g, &rc, x, k, pl, pv, &ws, r);
+    }
     free(tab);
     return 0;
+}
+
+int orc_walk_injected(const orc_spec *s, double E, const double pos[3], const double dir[3],
+                      const double *pol, const uint32_t *words, int64_t n_words, orc_record *rec) {
+    return orc_walk_injected_n(s, 1, &E, pos, dir, pol, words, n_words, rec);
 }
 
 /* ------------------------------------------------------------------ */
