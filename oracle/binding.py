@@ -15,7 +15,7 @@ from . import build as _build
 GEOMETRY = {"flat": 0, "cyl": 1}
 MDF = {"gaussian": 0, "lorentzian": 1, "pseudo_voigt": 2, "vmf": 3, "wl": 4, "swl": 5, "uniform": 6}
 IRC = {"darwin": 0, "darwin_prins": 1, "pseudo_voigt": 2, "gaussian": 3, "lorentzian": 4, "box": 5}
-SRC = {"mono": 0, "gauss": 1, "lorentz": 2, "inv_e": 3, "uniform": 4}
+SRC = {"mono": 0, "gauss": 1, "lorentz": 2, "inv_e": 3, "uniform": 4, "table": 5}
 OUTCOME = {0: "miss", 1: "absorbed", 2: "exit_front", 3: "exit_back", 4: "exit_side",
            5: "capped", 6: "stuck"}
 MDF_M = 4096
@@ -57,7 +57,9 @@ class Component(C.Structure):
 class Source(C.Structure):
     _fields_ = [("n_comp", C.c_int32), ("pad", C.c_int32), ("comp", Component * MAX_COMP),
                 ("origin", D3), ("axis", D3), ("cone_half_angle_rad", C.c_double),
-                ("spot_fwhm_mm", C.c_double * 2), ("polarization", D3)]
+                ("spot_fwhm_mm", C.c_double * 2), ("polarization", D3),
+                ("table_keV", C.POINTER(C.c_double)), ("table_pdf", C.POINTER(C.c_double)),
+                ("n_table", C.c_int32), ("pad2", C.c_int32)]
 
 
 class Rays(C.Structure):
@@ -219,6 +221,13 @@ def make_source(d):
     sf = d.get("spot_fwhm_mm", (0.0, 0.0))
     s.spot_fwhm_mm = (C.c_double * 2)(*sf)
     s.polarization = D3(*d.get("polarization", (0.0, 0.0, 0.0)))
+    if d.get("table") is not None:
+        keV = np.ascontiguousarray(np.asarray(d["table"][0], dtype=np.float64))
+        pdf = np.ascontiguousarray(np.asarray(d["table"][1], dtype=np.float64))
+        s.table_keV = keV.ctypes.data_as(C.POINTER(C.c_double))
+        s.table_pdf = pdf.ctypes.data_as(C.POINTER(C.c_double))
+        s.n_table = min(len(keV), len(pdf))
+        s._keep = (keV, pdf)
     return s
 
 

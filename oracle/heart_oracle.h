@@ -27,6 +27,8 @@
  *                                    thresholds of two orthogonal p sum to twice the unpolarised one;
  *                                    closed-form reflected p; p stays unit and perpendicular to k)
  *   orc_trace_rays           pinned (rays repeating a zero-cone source reproduce orc_trace exactly)
+ *   tabulated spectrum       pinned (KS against the piecewise-linear CDF written from the knots; a
+ *                                    two-knot table reproduces the uniform component bit for bit)
  *   orc_trace_energy         pinned (mono line: energy image = E x QE x counts; QE interpolation)
  *   absolute reflectivity / detector image shapes against experiment: parity unpinned
  *   (the paper's measured spectra are not available).
@@ -48,13 +50,14 @@ enum { ORC_MDF_GAUSSIAN = 0, ORC_MDF_LORENTZIAN = 1, ORC_MDF_PSEUDO_VOIGT = 2,
 enum { ORC_IRC_DARWIN = 0, ORC_IRC_DARWIN_PRINS = 1, ORC_IRC_PSEUDO_VOIGT = 2,
        ORC_IRC_GAUSSIAN = 3, ORC_IRC_LORENTZIAN = 4, ORC_IRC_BOX = 5 };
 enum { ORC_SRC_MONO = 0, ORC_SRC_GAUSS = 1, ORC_SRC_LORENTZ = 2, ORC_SRC_INV_E = 3,
-       ORC_SRC_UNIFORM = 4 };
+       ORC_SRC_UNIFORM = 4, ORC_SRC_TABLE = 5 };
 enum { ORC_MISS = 0, ORC_ABSORBED = 1, ORC_EXIT_FRONT = 2, ORC_EXIT_BACK = 3,
        ORC_EXIT_SIDE = 4, ORC_CAPPED = 5, ORC_STUCK = 6 };
 
 #define ORC_MDF_M 4096        /* body quantile knots, uniform in u          */
 #define ORC_MDF_T 256         /* tail intervals, uniform in -log2(1-u)      */
 #define ORC_MAX_COMP 16
+#define ORC_MAX_TABLE 8192    /* knots of a tabulated spectrum            */
 
 typedef struct {
     double d_spacing_A;       /* d_H of Eq. BraggLaw, Angstrom */
@@ -95,6 +98,11 @@ typedef struct {
     double spot_fwhm_mm[2];
     double polarization[3];   /* linear polarisation p0 (projected perpendicular to
                                  each ray); zero vector: unpolarised */
+    /* tabulated spectrum used by ORC_SRC_TABLE components: density values at
+     * ascending knots; the CDF is the trapezoid-rule integral at the knots,
+     * linear between them (a constant density within each interval) */
+    const double *table_keV, *table_pdf;
+    int32_t n_table, pad2;
 } orc_source;
 
 /* user-supplied rays (Sec. 2.1: origins, energies, directions and optional

@@ -810,8 +810,8 @@ static void source_basis(const double a[3], double b1[3], double b2[3]) {
     cross3(a, b1, b2);
 }
 
-static void sample_source(const orc_source *src, const double cumw[], const double ax[3],
-                          const double b1[3], const double b2[3], const uint32_t a[4],
+static void sample_source(const orc_source *src, const double cumw[], const double *tcdf,
+                          const double ax[3], const double b1[3], const double b2[3], const uint32_t a[4],
                           const uint32_t b[4], double *E, double o[3], double k[3]) {
     /* energy: component by cumulative weight, then its parameter */
     double uc = U(a[0]);
@@ -836,6 +836,13 @@ static void sample_source(const orc_source *src, const double cumw[], const doub
     }
     case ORC_SRC_INV_E: *E = cp->lo_keV * pow(cp->hi_keV / cp->lo_keV, up); break;
     case ORC_SRC_UNIFORM: *E = cp->lo_keV + (cp->hi_keV - cp->lo_keV) * up; break;
+    case ORC_SRC_TABLE: {                    /* inverse of the piecewise-linear CDF */
+        int i = 0;
+        while (!(up < tcdf[i + 1])) ++i;      /* the interval with C_i <= up < C_i+1 */
+        const double *x = src->table_keV;
+        *E = x[i] + (up - tcdf[i]) / (tcdf[i + 1] - tcdf[i]) * (x[i + 1] - x[i]);
+        break;
+    }
     default: *E = NAN;
     }
     /* direction: uniform in solid angle inside the cone */
@@ -858,6 +865,7 @@ typedef struct {
     const geom *g;
     const orc_source *src;
     const double *cumw;
+    const double *tcdf;      /* CDF of the tabulated spectrum at its knots, or NULL */
     double ax[3], b1[3], b2[3];
     uint64_t begin, end, offset;
     uint32_t key[2];
@@ -893,7 +901,7 @@ static void trace_one(job *J, uint64_t i) {
         uint32_t a[4], b[4];
         next4(&ws, a);
         next4(&ws, b);
-        sample_source(J->src, J->cumw, J->ax, J->b1, J->b2, a, b, &E, o, k);
+        sample_source(J->src, J->cumw, J->tcdf, J->ax, J->b1, J->b2, a, b, &E, o, k);
         pol = project_pol(J->src->polarization, k, pv);
     }
     orc_record rec;
@@ -962,6 +970,32 @@ static int trace_driver(const orc_spec *s, const orc_source *src, const orc_rays
                         uint64_t seed, uint64_t ray_offset, int n_threads, int64_t *image,
                         int64_t *energy_image, const orc_qe *qe, orc_tally *tally, orc_record *records);
 
+/* CDF of a tabulated spectrum at its knots: C_0 = 0, C_i+1 = C_i + (p_i + p_i+1)/2 (x_i+1 - x_i),
+ * divided by the total (the trapezoid rule; the CDF is linear between knots) */
+static int build_table_cdf(const orc_source *src, double **out) {
+    int n = src->n_table;
+    if (!src->table_keV || !src->table_pdf || n < 2 || n > ORC_MAX_TABLE) return fail("bad spectrum table");
+    for (int i = 0; i < n; ++i) {
+        if (!isfinite(src->table_keV[i]) || !isfinite(src->table_pdf[i]) || src->table_pdf[i] < 0.0)
+            return fail("bad spectrum table value");
+        if (i > 0 && !(src->table_keV[i] > src->table_keV[i - 1])) return fail("spectrum knots not ascending");
+    }
+    if (!(src->table_keV[0] > 0.0)) return fail("spectrum energies must be positive");
+    double *c = (double *)malloc((size_t)n * sizeof(double));
+    if (!c) return fail("out of memory");
+    double run = 0.0;
+    c[0] = 0.0;
+    for (int i = 0; i + 1 < n; ++i) {
+        run += 0.5 * (src->table_pdf[i] + src->table_pdf[i + 1]) * (src->table_keV[i + 1] - src->table_keV[i]);
+        c[i + 1] = run;
+    }
+    if (!(run > 0.0) || !isfinite(run)) { free(c); return fail("spectrum table has no mass"); }
+    for (int i = 1; i < n; ++i) c[i] /= run;
+    c[n - 1] = 1.0;
+    *out = c;
+    return 0;
+}
+
 int orc_trace_energy(const orc_spec *s, const orc_source *src, uint64_t n_rays, uint64_t seed,
                      uint64_t ray_offset, int n_threads, int64_t *image, int64_t *energy_image,
                      const orc_qe *qe, orc_tally *tally, orc_record *records) {
@@ -1002,6 +1036,12 @@ static int trace_driver(const orc_spec *s, const orc_source *src, const orc_rays
         if (normalize3(ax)) { free(tab); return fail("bad source axis"); }
         source_basis(ax, b1, b2);
     }
+    double *tcdf = NULL;
+    if (src) {
+        int uses = 0;
+        for (int i = 0; i < src->n_comp; ++i) uses |= src->comp[i].kind == ORC_SRC_TABLE;
+        if (uses && build_table_cdf(src, &tcdf)) { free(tab); return -1; }
+    }
 
     if (n_threads <= 0) n_threads = (int)sysconf(_SC_NPROCESSORS_ONLN);
     if (n_threads < 1) n_threads = 1;
@@ -1010,10 +1050,10 @@ static int trace_driver(const orc_spec *s, const orc_source *src, const orc_rays
     size_t npix = (size_t)s->det_nx * (size_t)s->det_ny;
     job *jobs = (job *)calloc((size_t)n_threads, sizeof(job));
     pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
-    if (!jobs || !th) { free(tab); free(jobs); free(th); return fail("out of memory"); }
+    if (!jobs || !th) { free(tab); free(tcdf); free(jobs); free(th); return fail("out of memory"); }
     for (int t = 0; t < n_threads; ++t) {
         job *J = &jobs[t];
-        J->g = &g; J->src = src; J->cumw = cumw;
+        J->g = &g; J->src = src; J->cumw = cumw; J->tcdf = tcdf;
         memcpy(J->ax, ax, sizeof ax); memcpy(J->b1, b1, sizeof b1); memcpy(J->b2, b2, sizeof b2);
         J->begin = n_rays * (uint64_t)t / (uint64_t)n_threads;
         J->end = n_rays * (uint64_t)(t + 1) / (uint64_t)n_threads;
@@ -1047,7 +1087,7 @@ static int trace_driver(const orc_spec *s, const orc_source *src, const orc_rays
             }
         }
     }
-    free(jobs); free(th); free(tab);
+    free(jobs); free(th); free(tab); free(tcdf);
     return 0;
 }
 

@@ -356,3 +356,58 @@ def test_mono_energy_image_is_count_times_energy():
     w = W.flat_hopg_mono()
     img, eimg, tal, _ = ob.trace_energy(w["spec"], w["source"], 100_000, 6)
     assert np.array_equal(eimg, img * 8_000_000)
+
+
+# --------------------------------------------------------------------------
+# tabulated spectrum (a density at knots; the CDF is linear between them)
+# --------------------------------------------------------------------------
+def _missing_source(comps, table=None):
+    s = flat(normal=[0.0, 0.0, -1.0])          # every ray misses: records keep E
+    src = dict(components=comps, origin_mm=[0.0, 0.0, 1.0], axis=[0.0, 0.0, 1.0],
+               cone_half_angle_rad=0.01, spot_fwhm_mm=(0.0, 0.0))
+    if table is not None:
+        src["table"] = table
+    return s, src
+
+
+def test_tabulated_spectrum_follows_its_piecewise_linear_cdf():
+    # an asymmetric table with a zero-density gap (7.9 - 8.0 keV) mixed with a line
+    keV = np.array([7.6, 7.7, 7.9, 8.0, 8.05, 8.3])
+    pdf = np.array([0.5, 2.0, 0.0, 0.0, 4.0, 1.0])
+    s, src = _missing_source([dict(kind="table", weight=0.7), dict(kind="mono", e0_keV=9.0, weight=0.3)],
+                             (keV, pdf))
+    n = 200_000
+    _, tal, rec = ob.trace(s, src, n, seed=41, records=True)
+    E = rec["energy_keV"]
+    tab = E[E < 8.5]
+    assert abs(len(tab) / n - 0.7) < 5 * math.sqrt(0.21 / n)
+    # CDF at the knots by hand (trapezoids), linear in between
+    mass = np.concatenate([[0.0], np.cumsum(0.5 * (pdf[1:] + pdf[:-1]) * np.diff(keV))])
+    cdf = lambda x: np.interp(x, keV, mass / mass[-1])
+    assert stats.kstest(tab, cdf).pvalue > 1e-3
+    assert not np.any((tab > 7.9) & (tab < 8.0))           # the empty interval is never drawn
+    assert tab.min() >= 7.6 and tab.max() <= 8.3
+    # the density within an interval is flat: fraction in [7.6, 7.65] vs [7.65, 7.7]
+    a = np.count_nonzero((tab >= 7.6) & (tab < 7.65))
+    b = np.count_nonzero((tab >= 7.65) & (tab < 7.7))
+    assert abs(a - b) < 5 * math.sqrt(a + b)
+
+
+def test_two_knot_table_reproduces_the_uniform_component():
+    s, su = _missing_source([dict(kind="uniform", lo_keV=7.3, hi_keV=8.9, weight=1.0)])
+    _, st = _missing_source([dict(kind="table", weight=1.0)], (np.array([7.3, 8.9]), np.array([2.5, 2.5])))
+    _, _, ru = ob.trace(s, su, 20_000, seed=42, records=True)
+    _, _, rt = ob.trace(s, st, 20_000, seed=42, records=True)
+    assert np.array_equal(ru["energy_keV"], rt["energy_keV"])
+
+
+def test_tabulated_spectrum_validation():
+    s, src = _missing_source([dict(kind="table", weight=1.0)])
+    for table in [None, (np.array([8.0]), np.array([1.0])), (np.array([8.0, 7.0]), np.array([1.0, 1.0])),
+                  (np.array([7.0, 8.0]), np.array([1.0, -1.0])), (np.array([7.0, 8.0]), np.array([0.0, 0.0])),
+                  (np.array([-1.0, 8.0]), np.array([1.0, 1.0]))]:
+        bad = dict(src)
+        if table is not None:
+            bad["table"] = table
+        with pytest.raises(RuntimeError):
+            ob.trace(s, bad, 10, seed=1)
