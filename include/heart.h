@@ -83,7 +83,8 @@ typedef enum {
     HEART_SRC_GAUSS = 1,     /* Gaussian, sigma = width                   */
     HEART_SRC_LORENTZ = 2,   /* Lorentzian, FWHM = width, truncated E > 0 */
     HEART_SRC_INV_E = 3,     /* 1/E on [lo, hi]                           */
-    HEART_SRC_UNIFORM = 4    /* uniform on [lo, hi]                       */
+    HEART_SRC_UNIFORM = 4,   /* uniform on [lo, hi]                       */
+    HEART_SRC_TABLE = 5      /* the source's tabulated spectrum (below)    */
 } heart_source_kind;
 
 /* ray outcomes (Sec. 2.2.4) */
@@ -157,7 +158,43 @@ typedef struct {
     double axis[3];                 /* cone axis */
     double cone_half_angle_rad;
     double spot_fwhm_mm[2];         /* 2-D Gaussian spot perpendicular to the axis */
+    double polarization[3];         /* linear polarisation p0, projected perpendicular to each
+                                       ray (Sec. 2.1); zero vector: unpolarised */
+    /* Tabulated spectrum (Sec. 2.1: a measured or modelled spectrum), drawn by
+     * components of kind HEART_SRC_TABLE: density values table_pdf[i] >= 0 at
+     * strictly ascending energies table_keV[i] > 0, 2 <= n_table <= 8192 (host
+     * arrays, copied during the call).  The CDF is the trapezoid rule at the
+     * knots and linear between them (constant density inside an interval).
+     * NULL / 0 when no component uses it. */
+    const double *table_keV;
+    const double *table_pdf;
+    int32_t n_table;
+    int32_t reserved2;
 } heart_source_desc;
+
+#define HEART_MAX_TABLE 8192
+
+/* User-supplied rays (Sec. 2.1: origins, energies, directions and optional
+ * polarisations instead of a sampled source).  Device arrays of n doubles
+ * each (structure of arrays, read coalesced); directions need not be
+ * normalised; pol_* may all be NULL (unpolarised), otherwise each is
+ * projected perpendicular to its ray.  Ray i has id ray_offset + i. */
+typedef struct {
+    const double *origin_x, *origin_y, *origin_z;
+    const double *dir_x, *dir_y, *dir_z;
+    const double *energy_keV;
+    const double *pol_x, *pol_y, *pol_z;
+} heart_ray_arrays;
+
+/* Detector quantum efficiency (Sec. 3): QE(E) linear between the knots,
+ * constant beyond the first and last; keV strictly increasing, 1..32 knots,
+ * qe in [0, 1]. */
+typedef struct {
+    const double *keV;              /* host array, n entries */
+    const double *qe;               /* host array, n entries */
+    int32_t n;
+    int32_t reserved;
+} heart_qe_table;
 
 typedef struct {
     uint64_t emitted, miss, absorbed, exit_front, exit_back, exit_side, capped, stuck;
@@ -177,6 +214,7 @@ typedef struct {
     double u_mm, v_mm;              /* detector-plane coordinates, NaN if the plane is not hit */
     int32_t ix, iy;                 /* pixel, -1 outside */
     int32_t det_hit, no_bragg;
+    double pol[3];                  /* final polarisation, zero if unpolarised */
 } heart_ray_record;
 
 /* Create a spectrometer: validates the descriptor, builds the mosaic
@@ -196,6 +234,28 @@ heart_status heart_spectrometer_destroy(heart_spectrometer *spec);
 heart_status heart_trace(heart_spectrometer *spec, const heart_source_desc *src, uint64_t n_rays,
                          uint64_t seed, uint64_t ray_offset, void *d_image,
                          heart_precision precision, void *stream, heart_tally *out);
+
+/* As heart_trace, and also adds each detected photon's energy times the
+ * detector quantum efficiency QE(E) to d_energy_image (device, uint64,
+ * det_ny x det_nx, 8-byte aligned, += ) in units of 1e-6 keV, rounded to the
+ * nearest unit per photon so sums do not depend on order (the summed-keV image
+ * of Sec. 2.3, QE of Sec. 3).  qe may be NULL (QE = 1).  d_image may be NULL
+ * when only the energy image is wanted; the counts then go to a scratch image
+ * of the handle.  Energy image / count image is the calibration map of a
+ * uniform spectrum (Sec. 3). */
+heart_status heart_trace_energy(heart_spectrometer *spec, const heart_source_desc *src, uint64_t n_rays,
+                                uint64_t seed, uint64_t ray_offset, void *d_image, uint64_t *d_energy_image,
+                                const heart_qe_table *qe, heart_precision precision, void *stream,
+                                heart_tally *out);
+
+/* Trace user-supplied rays (heart_ray_arrays, device memory) instead of a
+ * sampled source; the walk, detector and tallies are those of heart_trace.
+ * Polarised rays use G = 1 - (p . k_s)^2 (Eq. G_pol) and the polarisation
+ * update of Sec. 2.2.4.  d_records (device, n_rays heart_ray_record, may be
+ * NULL) receives one record per ray; the call then synchronises. */
+heart_status heart_trace_rays(heart_spectrometer *spec, const heart_ray_arrays *rays, uint64_t n_rays,
+                              uint64_t seed, uint64_t ray_offset, void *d_image, heart_precision precision,
+                              void *d_records, void *stream, heart_tally *out);
 
 /* As heart_trace, with host memory: h_image (host, += ) is copied to the
  * device, traced and copied back inside the call.  Synchronous. */

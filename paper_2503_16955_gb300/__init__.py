@@ -10,6 +10,7 @@ Functions carry the C names of include/heart.h:
     heart_trace(spec, source, n_rays, seed, ray_offset, d_image, precision, stream) -> tally
     heart_trace_host(spec, source, n_rays, seed, ray_offset, h_image, precision) -> tally
     heart_trace_records(spec, source, n_rays, seed, ray_offset, precision, d_image=None) -> (records, tally)
+    heart_trace_rays(spec, rays, seed, ray_offset, d_image, precision, records=False) -> tally [, records]
     heart_trace_batch(specs, sources, n_rays, seeds, d_images, stream) -> [tally]
     heart_server_create / heart_submit / heart_poll / heart_release / heart_server_destroy
 """
@@ -24,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libheart.so")
 GEOMETRY = {"flat": 0, "cyl": 1}
 MDF = {"gaussian": 0, "lorentzian": 1, "pseudo_voigt": 2, "vmf": 3, "wl": 4, "swl": 5, "uniform": 6}
 IRC = {"darwin": 0, "darwin_prins": 1, "pseudo_voigt": 2, "gaussian": 3, "lorentzian": 4, "box": 5}
-SRC = {"mono": 0, "gauss": 1, "lorentz": 2, "inv_e": 3, "uniform": 4}
+SRC = {"mono": 0, "gauss": 1, "lorentz": 2, "inv_e": 3, "uniform": 4, "table": 5}
 PRECISION = {"fp64": 0, "fp32": 1}
 COUNT = {"i32": 0, "i64": 1}
 STATUS = {0: "HEART_OK", 1: "HEART_EINVAL", 2: "HEART_ENOMEM", 3: "HEART_ECUDA", 4: "HEART_EBUSY",
@@ -64,7 +65,14 @@ class heart_spectral_component(C.Structure):
 class heart_source_desc(C.Structure):
     _fields_ = [("components", C.POINTER(heart_spectral_component)), ("n_components", C.c_int32),
                 ("reserved", C.c_int32), ("origin_mm", D3), ("axis", D3),
-                ("cone_half_angle_rad", C.c_double), ("spot_fwhm_mm", C.c_double * 2)]
+                ("cone_half_angle_rad", C.c_double), ("spot_fwhm_mm", C.c_double * 2),
+                ("polarization", D3), ("table_keV", C.POINTER(C.c_double)),
+                ("table_pdf", C.POINTER(C.c_double)), ("n_table", C.c_int32), ("reserved2", C.c_int32)]
+
+
+class heart_ray_arrays(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("origin_x", "origin_y", "origin_z", "dir_x", "dir_y", "dir_z",
+                                          "energy_keV", "pol_x", "pol_y", "pol_z")]
 
 
 class heart_tally(C.Structure):
@@ -78,6 +86,25 @@ class heart_tally(C.Structure):
         return d
 
 
+class heart_qe_table(C.Structure):
+    _fields_ = [("keV", C.POINTER(C.c_double)), ("qe", C.POINTER(C.c_double)), ("n", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+def make_qe(table):
+    """[(keV, qe), ...] -> heart_qe_table (keeps its arrays alive); None for no table"""
+    if not table:
+        return None
+    e = (C.c_double * len(table))(*[float(a) for a, _ in table])
+    q = (C.c_double * len(table))(*[float(b) for _, b in table])
+    t = heart_qe_table()
+    t.keV = e
+    t.qe = q
+    t.n = len(table)
+    t._keep = (e, q)
+    return t
+
+
 class heart_tune(C.Structure):
     _fields_ = [("blocks_per_sm", C.c_int32), ("refill_lanes", C.c_int32), ("max_chunk_rays", C.c_uint32),
                 ("reserved", C.c_int32), ("rays_per_s", C.c_double)]
@@ -87,10 +114,11 @@ RECORD_DTYPE = np.dtype([
     ("ray_id", np.uint64), ("outcome", np.int32), ("nrefl", np.int32), ("ncoll", np.int64),
     ("energy_keV", np.float64), ("pos", np.float64, 3), ("dir", np.float64, 3),
     ("u_mm", np.float64), ("v_mm", np.float64), ("ix", np.int32), ("iy", np.int32),
-    ("det_hit", np.int32), ("no_bragg", np.int32)])
-assert RECORD_DTYPE.itemsize == 112
+    ("det_hit", np.int32), ("no_bragg", np.int32), ("pol", np.float64, 3)])
+assert RECORD_DTYPE.itemsize == 136
 
-EXPORTS = ["heart_spectrometer_create", "heart_spectrometer_destroy", "heart_trace", "heart_trace_host",
+EXPORTS = ["heart_spectrometer_create", "heart_spectrometer_destroy", "heart_trace", "heart_trace_energy",
+           "heart_trace_host", "heart_trace_rays",
            "heart_trace_records", "heart_trace_batch", "heart_trace_batch_static", "heart_autotune", "heart_server_create", "heart_server_destroy",
            "heart_submit", "heart_poll", "heart_release", "heart_fetch_image", "heart_job_latency",
            "heart_last_error"]
@@ -121,8 +149,12 @@ def library(path=None):
                               C.POINTER(heart_tally)]
     L.heart_trace_host.argtypes = [vp, C.POINTER(heart_source_desc), u64, u64, u64, vp, i32,
                                    C.POINTER(heart_tally)]
+    L.heart_trace_energy.argtypes = [vp, C.POINTER(heart_source_desc), u64, u64, u64, vp, vp,
+                                     C.POINTER(heart_qe_table), i32, vp, C.POINTER(heart_tally)]
     L.heart_trace_records.argtypes = [vp, C.POINTER(heart_source_desc), u64, u64, u64, vp, i32, vp, vp,
                                       C.POINTER(heart_tally)]
+    L.heart_trace_rays.argtypes = [vp, C.POINTER(heart_ray_arrays), u64, u64, u64, vp, i32, vp, vp,
+                                   C.POINTER(heart_tally)]
     L.heart_trace_batch.argtypes = [C.POINTER(vp), C.POINTER(C.POINTER(heart_source_desc)),
                                     C.POINTER(u64), C.POINTER(u64), C.POINTER(vp), i32, vp,
                                     C.POINTER(heart_tally)]
@@ -207,7 +239,16 @@ def make_source(d):
     s.axis = D3(*d["axis"])
     s.cone_half_angle_rad = d["cone_half_angle_rad"]
     s.spot_fwhm_mm = (C.c_double * 2)(*d.get("spot_fwhm_mm", (0.0, 0.0)))
-    s._keep = arr
+    s.polarization = D3(*d.get("polarization", (0.0, 0.0, 0.0)))
+    keep = [arr]
+    if d.get("table") is not None:
+        keV = np.ascontiguousarray(np.asarray(d["table"][0], dtype=np.float64))
+        pdf = np.ascontiguousarray(np.asarray(d["table"][1], dtype=np.float64))
+        s.table_keV = keV.ctypes.data_as(C.POINTER(C.c_double))
+        s.table_pdf = pdf.ctypes.data_as(C.POINTER(C.c_double))
+        s.n_table = min(len(keV), len(pdf))
+        keep += [keV, pdf]
+    s._keep = keep
     return s
 
 
@@ -262,6 +303,36 @@ def heart_trace(spec, source, n_rays, seed, ray_offset, d_image, precision="fp32
     return t.as_dict() if want_tally else None
 
 
+def heart_trace_energy(spec, source, n_rays, seed, ray_offset, d_image, d_energy, qe=None, precision="fp32",
+                       stream=None):
+    """Counts into d_image (may be None) and energy x QE (uint64 / int64 CUDA
+    tensor, units of 1e-6 keV) into d_energy.  qe: [(keV, qe), ...] or None."""
+    src = make_source(source)
+    q = make_qe(qe)
+    t = heart_tally()
+    st = library().heart_trace_energy(spec.handle, C.byref(src), int(n_rays), int(seed), int(ray_offset),
+                                      C.c_void_p(d_image.data_ptr()) if d_image is not None else None,
+                                      C.c_void_p(d_energy.data_ptr()), C.byref(q) if q is not None else None,
+                                      PRECISION[precision], C.c_void_p(_stream_ptr(stream)), C.byref(t))
+    _check(st, allow=(0, 6))
+    return t.as_dict()
+
+
+def calibration_map(spec, source, min_keV, max_keV, n_rays, seed, precision="fp32", stream=None):
+    """Energy dispersion of the detector (Sec. 3): the source geometry with a
+    uniform spectrum on [min_keV, max_keV]; returns (mean keV per pixel as a
+    float64 CUDA tensor, NaN where no photon landed; count image)."""
+    import torch
+    src = dict(source)
+    src["components"] = [dict(kind="uniform", lo_keV=min_keV, hi_keV=max_keV, weight=1.0)]
+    counts = torch.zeros(spec.shape, dtype=torch.int64 if spec.count_dtype == "int64" else torch.int32,
+                         device="cuda")
+    energy = torch.zeros(spec.shape, dtype=torch.int64, device="cuda")
+    heart_trace_energy(spec, src, n_rays, seed, 0, counts, energy, None, precision, stream)
+    mean = energy.to(torch.float64) * 1e-6 / counts.to(torch.float64)
+    return mean, counts
+
+
 def heart_trace_host(spec, source, n_rays, seed, ray_offset, h_image, precision="fp32"):
     """Host-memory variant: h_image (numpy, C-contiguous, += counts)."""
     src = make_source(source)
@@ -286,6 +357,43 @@ def heart_trace_records(spec, source, n_rays, seed, ray_offset=0, precision="fp6
     _check(st, allow=(0, 6))
     out = np.frombuffer(rec.cpu().numpy().tobytes(), dtype=RECORD_DTYPE)
     return out, t.as_dict()
+
+
+def heart_trace_rays(spec, rays, seed, ray_offset, d_image, precision="fp32", records=False, stream=None):
+    """Trace user-supplied rays.  `rays` maps origin_x ... energy_keV (and
+    optionally pol_x, pol_y, pol_z) to contiguous float64 CUDA tensors of one
+    length.  Returns the tallies, and the per-ray records if asked for."""
+    import torch
+    names = [f for f, _ in heart_ray_arrays._fields_]
+    keep = {}
+    ra = heart_ray_arrays()
+    n = None
+    for f in names:
+        t = rays.get(f)
+        if t is None:
+            continue
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{f}: contiguous float64 CUDA tensor expected")
+        if n is None:
+            n = t.numel()
+        if t.numel() != n:
+            raise ValueError("ray arrays differ in length")
+        keep[f] = t
+        setattr(ra, f, t.data_ptr())
+    n = 0 if n is None else n
+    t = heart_tally()
+    rec = None
+    if records:
+        rec = torch.empty(max(n, 1) * RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    st = library().heart_trace_rays(spec.handle, C.byref(ra), int(n), int(seed), int(ray_offset),
+                                    C.c_void_p(d_image.data_ptr()) if d_image is not None else None,
+                                    PRECISION[precision], C.c_void_p(rec.data_ptr()) if rec is not None else None,
+                                    C.c_void_p(_stream_ptr(stream)), C.byref(t))
+    _check(st, allow=(0, 6))
+    if records:
+        out = np.frombuffer(rec.cpu().numpy().tobytes(), dtype=RECORD_DTYPE)[:n]
+        return out, t.as_dict()
+    return t.as_dict()
 
 
 def heart_trace_batch(specs, sources, n_rays, seeds, d_images, stream=None):

@@ -38,10 +38,22 @@ __device__ __forceinline__ void add_pixel<int64_t>(int64_t *img, size_t idx) {
     atomicAdd((unsigned long long *)img + idx, 1ull);
 }
 
+__device__ __forceinline__ double qe64(const QeParams &Q, double E) {
+    if (Q.n <= 0) return 1.0;
+    if (E <= Q.keV[0]) return Q.qe[0];
+    for (int i = 1; i < Q.n; ++i)
+        if (E <= Q.keV[i]) {
+            const double f = (E - Q.keV[i - 1]) / (Q.keV[i] - Q.keV[i - 1]);
+            return Q.qe[i - 1] + f * (Q.qe[i] - Q.qe[i - 1]);
+        }
+    return Q.qe[Q.n - 1];
+}
+
 template <typename CountT>
 __global__ void __launch_bounds__(256) k_trace_fp64(const SpecParams S, const SourceParams P, uint64_t n,
                                                     uint32_t k0, uint32_t k1, uint64_t offset, CountT *img,
-                                                    unsigned long long *tally, heart_ray_record *rec) {
+                                                    unsigned long long *tally, heart_ray_record *rec,
+                                                    const __grid_constant__ QeParams Q) {
     extern __shared__ double s_tab[];
     __shared__ unsigned long long s_t[kTallyN];
     for (int i = threadIdx.x; i < kMdfKnots; i += blockDim.x) s_tab[i] = S.mdf64[i];
@@ -51,15 +63,17 @@ __global__ void __launch_bounds__(256) k_trace_fp64(const SpecParams S, const So
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         RayOut64 r;
-        trace_ray64(S, P, k0, k1, offset + i, s_tab, r);
+        trace_ray64(S, P, k0, k1, offset + i, i, s_tab, r);
         ++my_emit;
         my_coll += (unsigned long long)r.ncoll;
         atomicAdd(&s_t[r.outcome == HEART_MISS ? T_MISS : T_ABSORBED + (r.outcome - HEART_ABSORBED)], 1ull);
         if (r.outcome != HEART_MISS) atomicAdd(&s_t[T_HIST0 + (r.nrefl < 15 ? r.nrefl : 15)], 1ull);
         if (r.no_bragg) atomicAdd(&s_t[T_NO_BRAGG], 1ull);
         if (r.det_hit) {
-            add_pixel<CountT>(img, (size_t)r.iy * (size_t)S.nx + (size_t)r.ix);
+            const size_t idx = (size_t)r.iy * (size_t)S.nx + (size_t)r.ix;
+            add_pixel<CountT>(img, idx);
             atomicAdd(&s_t[T_DET_HITS], 1ull);
+            if (Q.eimg) atomicAdd(Q.eimg + idx, (unsigned long long)llrint(r.E * qe64(Q, r.E) * 1e6));
         }
         if (rec) {
             heart_ray_record &o = rec[i];
@@ -75,6 +89,7 @@ __global__ void __launch_bounds__(256) k_trace_fp64(const SpecParams S, const So
             o.iy = r.iy;
             o.det_hit = r.det_hit;
             o.no_bragg = r.no_bragg;
+            for (int j = 0; j < 3; ++j) o.pol[j] = r.pol[j];
         }
     }
     for (int off = 16; off > 0; off >>= 1) {
@@ -102,8 +117,12 @@ int num_sms() {
 }
 
 heart_status launch_fp64(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
-                         void *img, unsigned long long *tally, heart_ray_record *rec, cudaStream_t st) {
+                         void *img, unsigned long long *tally, heart_ray_record *rec, cudaStream_t st,
+                         const QeParams *qe) {
     if (n == 0) return HEART_OK;
+    QeParams Q;
+    if (qe) Q = *qe;
+    else std::memset(&Q, 0, sizeof Q);
     const int threads = 256;
     const size_t smem = (size_t)kMdfKnots * sizeof(double);
     uint64_t want = (n + threads - 1) / threads;
@@ -113,11 +132,11 @@ heart_status launch_fp64(const SpecParams &S, const SourceParams &P, uint64_t n,
     if (S.count_type == HEART_COUNT_I64) {
         static bool attr = false;
         if (!attr) { cudaFuncSetAttribute(k_trace_fp64<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
-        k_trace_fp64<int64_t><<<blocks, threads, smem, st>>>(S, P, n, k0, k1, offset, (int64_t *)img, tally, rec);
+        k_trace_fp64<int64_t><<<blocks, threads, smem, st>>>(S, P, n, k0, k1, offset, (int64_t *)img, tally, rec, Q);
     } else {
         static bool attr = false;
         if (!attr) { cudaFuncSetAttribute(k_trace_fp64<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
-        k_trace_fp64<int32_t><<<blocks, threads, smem, st>>>(S, P, n, k0, k1, offset, (int32_t *)img, tally, rec);
+        k_trace_fp64<int32_t><<<blocks, threads, smem, st>>>(S, P, n, k0, k1, offset, (int32_t *)img, tally, rec, Q);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "FP64 kernel launch");
@@ -186,23 +205,44 @@ static void fill_tally(const unsigned long long *t, heart_tally *out) {
     std::memcpy(out, t, sizeof(heart_tally));
 }
 
-// common body of heart_trace / heart_trace_records
+// common body of heart_trace / heart_trace_records / heart_trace_energy / heart_trace_rays
 static heart_status trace_impl(heart_spectrometer *h, const heart_source_desc *src, uint64_t n_rays, uint64_t seed,
                                uint64_t ray_offset, void *d_image, heart_precision prec, void *d_records,
-                               void *stream, heart_tally *out, bool sync) {
+                               void *stream, heart_tally *out, bool sync, const QeParams *qe = nullptr,
+                               const SourceParams *prepared = nullptr) {
     if (!h) return fail(HEART_EINVAL, "null spectrometer");
     if (prec != HEART_FP64 && prec != HEART_FP32) return fail(HEART_EINVAL, "unknown precision");
     size_t elt = h->p.count_type == HEART_COUNT_I64 ? 8 : 4;
-    if (!d_image && !d_records) return fail(HEART_EINVAL, "null image");
+    if (!d_image && !d_records && !(qe && qe->eimg)) return fail(HEART_EINVAL, "null image");
     if (d_image && ((uintptr_t)d_image % elt) != 0) return fail(HEART_EINVAL, "image pointer misaligned");
     if (d_records && ((uintptr_t)d_records % 8) != 0) return fail(HEART_EINVAL, "records pointer misaligned");
     if (ray_offset + n_rays < ray_offset) return fail(HEART_EINVAL, "ray range overflows 64 bits");
     SourceParams P;
     char err[256] = {0};
-    heart_status st = build_source_params(src, &P, err, (int)sizeof err);
+    heart_status st = HEART_OK;
+    std::vector<unsigned char> spectrum;
+    if (prepared) P = *prepared;
+    else st = build_source_params(src, &P, err, (int)sizeof err, &spectrum);
     if (st != HEART_OK) return fail(st, err);
     cudaStream_t cs = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(h->d_scratch, 0, kScratchWords * sizeof(unsigned long long), cs);
+    // a tabulated spectrum gets a stream-ordered device copy for this call
+    struct FreeOnExit {
+        void *p = nullptr;
+        cudaStream_t s;
+        ~FreeOnExit() { if (p) cudaFreeAsync(p, s); }
+    } d_spec{nullptr, cs};
+    cudaError_t e;
+    if (!spectrum.empty()) {
+        if ((e = cudaMallocAsync(&d_spec.p, spectrum.size(), cs)) != cudaSuccess) {
+            d_spec.p = nullptr;
+            return cuda_fail(e, "cudaMallocAsync spectrum");
+        }
+        // pageable source: staged before the call returns
+        if ((e = cudaMemcpyAsync(d_spec.p, spectrum.data(), spectrum.size(), cudaMemcpyHostToDevice, cs)) != cudaSuccess)
+            return cuda_fail(e, "spectrum upload");
+        bind_spectrum(&P, d_spec.p);
+    }
+    e = cudaMemsetAsync(h->d_scratch, 0, kScratchWords * sizeof(unsigned long long), cs);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     void *img = d_image;
     if (!img) {
@@ -216,10 +256,13 @@ static heart_status trace_impl(heart_spectrometer *h, const heart_source_desc *s
         }
         img = h->d_image_host_path;
     }
-    if (prec == HEART_FP64 || d_records) {
-        st = launch_fp64(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, (heart_ray_record *)d_records, cs);
+    if (prec == HEART_FP64) {
+        st = launch_fp64(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, (heart_ray_record *)d_records, cs, qe);
+    } else if (d_records) {
+        st = launch_fp32_records(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, (heart_ray_record *)d_records,
+                                 cs, qe);
     } else {
-        st = launch_fp32(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, cs);
+        st = launch_fp32(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, cs, qe);
     }
     if (st != HEART_OK) return st;
     if (out || sync) {
@@ -245,40 +288,7 @@ extern "C" heart_status heart_trace_records(heart_spectrometer *h, const heart_s
                                             heart_precision precision, void *d_records, void *stream,
                                             heart_tally *out) {
     if (!d_records) return fail(HEART_EINVAL, "null records");
-    if (precision == HEART_FP32) {
-        // records come from the FP32 kernel's record variant
-        if (!h) return fail(HEART_EINVAL, "null spectrometer");
-        SourceParams P;
-        char err[256] = {0};
-        heart_status st = build_source_params(src, &P, err, (int)sizeof err);
-        if (st != HEART_OK) return fail(st, err);
-        if (((uintptr_t)d_records % 8) != 0) return fail(HEART_EINVAL, "records pointer misaligned");
-        cudaStream_t cs = (cudaStream_t)stream;
-        cudaError_t e = cudaMemsetAsync(h->d_scratch, 0, kScratchWords * sizeof(unsigned long long), cs);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-        void *img = d_image;
-        size_t elt = h->p.count_type == HEART_COUNT_I64 ? 8 : 4;
-        if (!img) {
-            size_t bytes = (size_t)h->p.nx * h->p.ny * elt;
-            if (!h->d_image_host_path || h->host_image_bytes < bytes) {
-                if (h->d_image_host_path) cudaFree(h->d_image_host_path);
-                h->d_image_host_path = nullptr;
-                if ((e = cudaMalloc(&h->d_image_host_path, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc image");
-                h->host_image_bytes = bytes;
-            }
-            img = h->d_image_host_path;
-        }
-        st = launch_fp32_records(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch,
-                                 (heart_ray_record *)d_records, cs);
-        if (st != HEART_OK) return st;
-        if ((e = cudaMemcpyAsync(h->h_scratch, h->d_scratch, kTallyN * sizeof(unsigned long long),
-                                 cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
-            return cuda_fail(e, "tally copy");
-        if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return cuda_fail(e, "trace");
-        if (out) fill_tally(h->h_scratch, out);
-        if (h->h_scratch[T_STUCK] > 0) return fail(HEART_ELIMIT, "a ray reached the collision cap");
-        return HEART_OK;
-    }
+    // FP32 records come from the FP32 kernel's record variant
     return trace_impl(h, src, n_rays, seed, ray_offset, d_image, precision, d_records, stream, out, true);
 }
 
@@ -311,4 +321,36 @@ extern "C" heart_status heart_trace_host(heart_spectrometer *h, const heart_sour
     if (out) fill_tally(h->h_scratch, out);
     if (h->h_scratch[T_STUCK] > 0) return fail(HEART_ELIMIT, "a ray reached the collision cap");
     return HEART_OK;
+}
+
+extern "C" heart_status heart_trace_energy(heart_spectrometer *h, const heart_source_desc *src, uint64_t n_rays,
+                                           uint64_t seed, uint64_t ray_offset, void *d_image,
+                                           uint64_t *d_energy_image, const heart_qe_table *qe,
+                                           heart_precision precision, void *stream, heart_tally *out) {
+    if (!h) return fail(HEART_EINVAL, "null spectrometer");
+    if (!d_energy_image || ((uintptr_t)d_energy_image % 8) != 0) return fail(HEART_EINVAL, "null or misaligned energy image");
+    QeParams Q;
+    char err[256] = {0};
+    heart_status st = build_qe_params(qe, (unsigned long long *)d_energy_image, &Q, err, (int)sizeof err);
+    if (st != HEART_OK) return fail(st, err);
+    return trace_impl(h, src, n_rays, seed, ray_offset, d_image, precision, nullptr, stream, out, false, &Q);
+}
+
+extern "C" heart_status heart_trace_rays(heart_spectrometer *h, const heart_ray_arrays *rays, uint64_t n_rays,
+                                         uint64_t seed, uint64_t ray_offset, void *d_image,
+                                         heart_precision precision, void *d_records, void *stream,
+                                         heart_tally *out) {
+    if (!h) return fail(HEART_EINVAL, "null spectrometer");
+    if (!rays) return fail(HEART_EINVAL, "null ray arrays");
+    if (n_rays == 0) {                       // nothing to read: empty arrays may be null
+        if (out) std::memset(out, 0, sizeof *out);
+        return HEART_OK;
+    }
+    SourceParams P;
+    char err[256] = {0};
+    heart_status st = build_ray_params(rays, &P, err, (int)sizeof err);
+    if (st != HEART_OK) return fail(st, err);
+    if (!d_image && !d_records) return fail(HEART_EINVAL, "null image");
+    return trace_impl(h, nullptr, n_rays, seed, ray_offset, d_image, precision, d_records, stream, out,
+                      d_records != nullptr, nullptr, &P);
 }

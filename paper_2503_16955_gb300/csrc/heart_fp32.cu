@@ -85,7 +85,20 @@ struct Launch32 {
     void *img;                            // this job's image (int32 or int64)
     unsigned long long *tally;            // this job's kTallyN tally words
     heart_ray_record *rec;                // per-ray records or nullptr
-    double fc[3], fa[3][3];               // local -> global frame (records only)
+    unsigned long long *eimg;             // energy image (1e-6 keV units) or nullptr
+    int32_t n_qe, pad_qe;
+    float qe_e[kMaxQe], qe_v[kMaxQe];     // detector QE knots
+    double fc[3], fa[3][3];               // local -> global frame (records, user rays)
+    // polarisation and user-supplied rays (the extended kernel only)
+    int32_t pol_on, user;
+    float pol[3];                         // source polarisation, local frame
+    double hc_2d, cs_shift, sn_shift;     // hc / 2d (keV); cos, sin Delta_M
+    const double *ray[10];                // user arrays: ox oy oz kx ky kz E px py pz
+    // tabulated spectrum: CDF thresholds on the raw word, in-interval offset and
+    // slope, knots relative to the table's mean energy (its e_ref)
+    int32_t n_tab, pad_tab;
+    const unsigned long long *tab_thr;
+    const float *tab_off, *tab_inv, *tab_dE, *tab_w;
 };
 
 // a spawned ray waiting for a lane (SoA per warp)
@@ -225,7 +238,21 @@ struct Lane {
     int32_t face, nrefl, ncoll, no_bragg;
     // cylinder: depth below the inner face at x0 and along-segment constants of k.N
     float rho0, cb1, cb2, cga, ck0, ctau0;
+    float p[3];                           // polarisation, crystal frame (extended kernel)
+    bool pol;
 };
+
+// absorption and majorant of a ray of energy E (Sec. 2.2.4): 1 / mu_bar, the
+// absorption probability pa and its integer threshold on the raw word
+__device__ __forceinline__ void absorb_consts(const Launch32 &L, float E, float Q, int nb, float &inv_mu, float &pa,
+                                              uint32_t &pa_thr) {
+    const float mu0 = 1.0f / (L.labs * __powf(E / L.labs_ref, L.labs_pow));
+    const float mubar = __fmaf_rn(Q, L.irc_max, mu0);
+    inv_mu = 1.0f / mubar;
+    pa = nb ? 1.0f : mu0 / mubar;
+    // absorb iff (w + 1/2) 2^-32 < pa  <=>  w < ceil(pa 2^32 - 1/2)
+    pa_thr = nb ? 0xFFFFFFFFu : __float2uint_ru(fminf(pa * 4294967296.0f, 4294967040.0f));
+}
 
 // ---------------------------------------------------------------------------
 // spawn: source sample + entry (Sec. 2.1, Sec. 2.2) in the crystal frame
@@ -301,6 +328,22 @@ __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3
         ds = s0 * expm1f(-g);
         break;
     }
+    case HEART_SRC_TABLE: {
+        // the interval with thr_i <= word < thr_i+1 (the FP64 path's decision
+        // u < C_i taken exactly on the word), then linear inside it
+        const unsigned long long wv = a[1];
+        int lo = 0, hi = L.n_tab - 1;
+        while (hi - lo > 1) {
+            const int m = (lo + hi) >> 1;
+            if (wv < L.tab_thr[m]) hi = m; else lo = m;
+        }
+        const float t = ((float)(wv - L.tab_thr[lo]) + L.tab_off[lo]) * L.tab_inv[lo];
+        const float dE = __fmaf_rn(t, L.tab_w[lo], L.tab_dE[lo]);
+        E = e0 + dE;
+        const float r = dE / e0;
+        ds = -s0 * r / (1.0f + r);
+        break;
+    }
     default: {
         float dE;
         if (L.kind[c] == HEART_SRC_GAUSS) {
@@ -337,13 +380,94 @@ __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3
         sB = 2.0f;
         A = 0.0f;
     }
-    const float mu0 = 1.0f / (L.labs * __powf(E / L.labs_ref, L.labs_pow));
-    const float mubar = __fmaf_rn(Q, L.irc_max, mu0);
-    inv_mu = 1.0f / mubar;
-    pa = nb ? 1.0f : mu0 / mubar;
-    // absorb iff (w + 1/2) 2^-32 < pa  <=>  w < ceil(pa 2^32 - 1/2)
-    pa_thr = nb ? 0xFFFFFFFFu : __float2uint_ru(fminf(pa * 4294967296.0f, 4294967040.0f));
+    absorb_consts(L, E, Q, nb, inv_mu, pa, pa_thr);
     return true;
+}
+
+// user-supplied ray: read, move to the crystal frame and enter in FP64 (once
+// per ray), so that the anchor A = |k.N| - sin(aB + Delta_M) is exact to FP32
+// rounding whatever the ray's energy and direction; p is the ray's
+// polarisation projected perpendicular to k, zero if unpolarised
+template <int GEOM_T>
+__device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float x[3], float k[3], float p[3],
+                                           float &A, float &sB, float &inv_mu, float &pa, uint32_t &pa_thr,
+                                           float &E32, int &nb) {
+    const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
+    double E = L.ray[6][id], og[3], kg[3], ol[3], kl[3];
+    for (int i = 0; i < 3; ++i) { og[i] = L.ray[i][id] - L.fc[i]; kg[i] = L.ray[3 + i][id]; }
+    const double kk = sqrt(kg[0] * kg[0] + kg[1] * kg[1] + kg[2] * kg[2]);
+    if (kk > 0.0) for (int i = 0; i < 3; ++i) kg[i] /= kk;
+    else E = __longlong_as_double(0x7ff8000000000000LL);      // a zero direction cannot enter
+    for (int i = 0; i < 3; ++i) {
+        ol[i] = og[0] * L.fa[i][0] + og[1] * L.fa[i][1] + og[2] * L.fa[i][2];
+        kl[i] = kg[0] * L.fa[i][0] + kg[1] * L.fa[i][1] + kg[2] * L.fa[i][2];
+        x[i] = (float)ol[i];
+        k[i] = (float)kl[i];
+        p[i] = 0.0f;
+    }
+    if (L.pol_on) {
+        double pg[3] = {L.ray[7][id], L.ray[8][id], L.ray[9][id]};
+        const double pk = pg[0] * kg[0] + pg[1] * kg[1] + pg[2] * kg[2];
+        for (int i = 0; i < 3; ++i) pg[i] -= pk * kg[i];
+        const double pn = sqrt(pg[0] * pg[0] + pg[1] * pg[1] + pg[2] * pg[2]);
+        if (pn > 1e-12)
+            for (int i = 0; i < 3; ++i)
+                p[i] = (float)((pg[0] * L.fa[i][0] + pg[1] * L.fa[i][1] + pg[2] * L.fa[i][2]) / pn);
+    }
+    E32 = (float)E;
+    if (!(E > 0.0) || !isfinite(E)) return false;
+    double kN;                                            // |k.N| at the entry point
+    if (GEOM == HEART_FLAT) {
+        if (!(kl[2] < 0.0) || !(ol[2] > 0.0)) return false;
+        const double t = ol[2] / (-kl[2]);
+        const double ex = ol[0] + t * kl[0], ey = ol[1] + t * kl[1];
+        if (fabs(ex) > (double)L.half_d || fabs(ey) > (double)L.half_n) return false;
+        x[0] = (float)ex; x[1] = (float)ey; x[2] = 0.0f;
+        kN = -kl[2];
+    } else {
+        const double aa = kl[1] * kl[1] + kl[2] * kl[2];
+        if (!(aa > 0.0)) return false;
+        const double R = (double)L.R;
+        const double c0 = ol[1] * ol[1] + ol[2] * ol[2] - R * R;
+        if (!(c0 < 0.0)) return false;
+        const double bo = ol[1] * kl[1] + ol[2] * kl[2];
+        const double sq = sqrt(bo * bo - aa * c0);
+        const double t = (bo > 0.0) ? -c0 / (bo + sq) : (sq - bo) / aa;
+        double xe[3];
+        for (int i = 0; i < 3; ++i) xe[i] = ol[i] + t * kl[i];
+        if (fabs(xe[0] - (double)L.zc) > (double)L.half_d) return false;
+        if (fabs(xe[2]) * (double)L.cphi > xe[1] * (double)L.sphi) return false;
+        for (int i = 0; i < 3; ++i) x[i] = (float)xe[i];
+        kN = (kl[1] * xe[1] + kl[2] * xe[2]) / R;
+    }
+    const double sr = L.hc_2d / E;                        // sin(aB), Eq. (BraggLaw)
+    nb = !(sr < 1.0);
+    float Q = 0.0f;
+    if (!nb) {
+        const double cr = sqrt(1.0 - sr * sr);
+        const double sb = sr * L.cs_shift + cr * L.sn_shift;
+        sB = (float)sb;
+        A = (float)(kN - sb);
+        const float lam = 12.398419843320026e-7f / E32;   // mm
+        Q = L.K2 * lam * lam * lam / (2.0f * (float)sr * (float)cr);
+    } else {
+        sB = 2.0f;
+        A = 0.0f;
+    }
+    absorb_consts(L, E32, Q, nb, inv_mu, pa, pa_thr);
+    return true;
+}
+
+// the source polarisation projected perpendicular to k (zero if parallel)
+__device__ __forceinline__ void project_pol32(const Launch32 &L, const float k[3], float p[3]) {
+    const float pk = L.pol[0] * k[0] + L.pol[1] * k[1] + L.pol[2] * k[2];
+    float n2 = 0.0f;
+    for (int i = 0; i < 3; ++i) {
+        p[i] = __fmaf_rn(-pk, k[i], L.pol[i]);
+        n2 = __fmaf_rn(p[i], p[i], n2);
+    }
+    const float sc = n2 > 1e-12f ? rsqrtf(n2) : 0.0f;
+    for (int i = 0; i < 3; ++i) p[i] *= sc;
 }
 
 // start a straight segment at x0 along k; s.A, s.sgn, s.sB and (cylinder) s.rho0 are set
@@ -409,6 +533,17 @@ __device__ __forceinline__ void to_global(const Launch32 &L, const float *p, dou
                (double)p[2] * L.fa[2][i];
 }
 
+__device__ __forceinline__ float qe32(const Launch32 &L, float E) {
+    if (L.n_qe <= 0) return 1.0f;
+    if (E <= L.qe_e[0]) return L.qe_v[0];
+    for (int i = 1; i < L.n_qe; ++i)
+        if (E <= L.qe_e[i]) {
+            const float f = (E - L.qe_e[i - 1]) / (L.qe_e[i] - L.qe_e[i - 1]);
+            return __fmaf_rn(f, L.qe_v[i] - L.qe_v[i - 1], L.qe_v[i - 1]);
+        }
+    return L.qe_v[L.n_qe - 1];
+}
+
 // tally slots in shared memory (32-bit per chunk, flushed as 64-bit)
 struct BlockTally {
     unsigned int t[kTallyN];
@@ -416,7 +551,7 @@ struct BlockTally {
 };
 
 // finish a ray: detector projection + binning + tallies (+ record)
-template <bool REC>
+template <bool REC, bool EXT>
 __device__ __forceinline__ void finish(const Launch32 &L, Lane &s, int outcome, BlockTally &bt) {
     int ix = -1, iy = -1, hit = 0;
     float u = __int_as_float(0x7fc00000), v = u;
@@ -443,6 +578,8 @@ __device__ __forceinline__ void finish(const Launch32 &L, Lane &s, int outcome, 
                     if (L.count64) atomicAdd((unsigned long long *)L.img + idx, 1ull);
                     else atomicAdd((int *)L.img + idx, 1);
                     atomicAdd(&bt.t[T_DET_HITS], 1u);
+                    if (L.eimg)
+                        atomicAdd(L.eimg + idx, (unsigned long long)__float2ll_rn(s.E * qe32(L, s.E) * 1.0e6f));
                 }
             }
         }
@@ -466,11 +603,34 @@ __device__ __forceinline__ void finish(const Launch32 &L, Lane &s, int outcome, 
         o.iy = iy;
         o.det_hit = hit;
         o.no_bragg = s.no_bragg;
+        if (EXT && s.pol) to_global(L, s.p, o.pol, false);
+        else o.pol[0] = o.pol[1] = o.pol[2] = 0.0;
     }
 }
 
 // one tentative collision; returns an outcome code, or -1 while the ray lives
-template <int GEOM_T, int IRC>
+// crystallite normal n at the current collision in the crystal frame, and on
+// a cylinder the radial change drho of the collision point from the segment start
+template <int GEOM_T>
+__device__ __forceinline__ void crystallite_normal(const Launch32 &L, const Lane &s, float st, float sx, float cx,
+                                                   float q, float eps, float rho, float n[3], float &drho) {
+    const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
+    const float ct = 1.0f - q;
+    if (GEOM == HEART_FLAT) {
+        n[0] = st * cx; n[1] = st * sx; n[2] = ct;
+        drho = 0.0f;
+    } else {
+        const float X = __fmaf_rn(s.Lsum, s.k[1], s.x0[1]), Y = __fmaf_rn(s.Lsum, s.k[2], s.x0[2]);
+        drho = (L.R + s.rho0) * eps / (1.0f + rho);           // r - r0 at the collision
+        const float ir = 1.0f / (L.R + s.rho0 + drho);
+        const float sxs = st * sx;
+        n[0] = st * cx;
+        n[1] = (-ct * X - sxs * Y) * ir;
+        n[2] = (-ct * Y + sxs * X) * ir;
+    }
+}
+
+template <int GEOM_T, int IRC, bool EXT>
 __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab) {
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
     if (s.ncoll >= L.max_coll) return HEART_STUCK;
@@ -516,27 +676,27 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
         sa = fminf(-sa, 1.0f);                                 // the normal flipped side
         delta = asinf(sa) - asinf(s.sB);
     }
-    const float c2 = __fmaf_rn(-2.0f * sa, sa, 1.0f);
-    const float G = 0.5f * __fmaf_rn(c2, c2, 1.0f);
+    const float kn = s.sgn * (s.sB + e);                       // k.n
+    float n[3], drho = 0.0f, G;
+    bool have_n = false;
+    if (EXT && s.pol) {
+        // Eq. (G_pol): G = 1 - (p . k_s)^2, k_s = k - 2 (k.n) n
+        crystallite_normal<GEOM_T>(L, s, st, sx, cx, q, eps, rho, n, drho);
+        have_n = true;
+        float pk = 0.0f, pn = 0.0f;
+        for (int i = 0; i < 3; ++i) { pk = __fmaf_rn(s.p[i], s.k[i], pk); pn = __fmaf_rn(s.p[i], n[i], pn); }
+        const float pks = __fmaf_rn(-2.0f * kn, pn, pk);
+        G = __fmaf_rn(-pks, pks, 1.0f);
+    } else {
+        const float c2 = __fmaf_rn(-2.0f * sa, sa, 1.0f);
+        G = 0.5f * __fmaf_rn(c2, c2, 1.0f);                    // Eq. (G_unpol)
+    }
     if (v < irc_rel32<IRC>(L, delta) * G) {
         ++s.nrefl;
         if (s.nrefl > L.max_refl) return HEART_CAPPED;
         // reflection k <- k - 2 (k.n) n (Sec. 2.2.4)
-        const float ct = 1.0f - q;
-        float n[3];
-        if (GEOM == HEART_FLAT) {
-            n[0] = st * cx; n[1] = st * sx; n[2] = ct;
-        } else {
-            const float X = __fmaf_rn(s.Lsum, s.k[1], s.x0[1]), Y = __fmaf_rn(s.Lsum, s.k[2], s.x0[2]);
-            const float drho = (L.R + s.rho0) * eps / (1.0f + rho);   // r - r0 at the collision
-            const float ir = 1.0f / (L.R + s.rho0 + drho);
-            const float sxs = st * sx;
-            n[0] = st * cx;
-            n[1] = (-ct * X - sxs * Y) * ir;
-            n[2] = (-ct * Y + sxs * X) * ir;
-            s.rho0 += drho;                                        // depth of the new segment start
-        }
-        const float kn = s.sgn * (s.sB + e);
+        if (!have_n) crystallite_normal<GEOM_T>(L, s, st, sx, cx, q, eps, rho, n, drho);
+        if (GEOM != HEART_FLAT) s.rho0 += drho;                // depth of the new segment start
         float kk = 0.0f;
         for (int i = 0; i < 3; ++i) {
             s.x0[i] = __fmaf_rn(s.Lsum, s.k[i], s.x0[i]);
@@ -545,6 +705,15 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
         }
         const float sc = rsqrtf(kk);
         for (int i = 0; i < 3; ++i) s.k[i] *= sc;
+        if (EXT && s.pol) {
+            // p_s = (p - (p.k_s) k_s) / |...| (Sec. 2.2.4)
+            float pk = 0.0f;
+            for (int i = 0; i < 3; ++i) pk = __fmaf_rn(s.p[i], s.k[i], pk);
+            float pp = 0.0f;
+            for (int i = 0; i < 3; ++i) { s.p[i] = __fmaf_rn(-pk, s.k[i], s.p[i]); pp = __fmaf_rn(s.p[i], s.p[i], pp); }
+            const float ps = rsqrtf(pp);
+            for (int i = 0; i < 3; ++i) s.p[i] *= ps;
+        }
         // new anchor from small terms: k'.N = sgn * T, T = Ac - sB - 2e + 2q (sB + e)
         const float T = Ac - s.sB - 2.0f * e + 2.0f * q * (s.sB + e);
         if (T < 0.0f) {
@@ -569,20 +738,24 @@ struct WorkPlan {
 };
 
 // GEOM >= 0: single-job kernel, parameters read from the launch's constant
-// bank; GEOM < 0: the generic batched kernel, the block's job staged in smem
-template <int GEOM, int IRC, bool REC, int OCC>
+// bank; GEOM < 0: the generic batched kernel, the block's job staged in smem.
+// EXT (generic kernel only): polarised sources and user-supplied rays.
+template <int GEOM, int IRC, bool REC, int OCC, bool EXT = false>
 __global__ void __launch_bounds__(kBlockThreads, OCC)
     k_trace_fp32(const __grid_constant__ Launch32 single, const __grid_constant__ WorkPlan W) {
     constexpr bool BATCH = GEOM < 0;
+    static_assert(!EXT || BATCH, "the extended kernel is the generic one");
     __shared__ Launch32 sL;
     __shared__ float s_tab[kMdfKnots];
     __shared__ WarpBuf s_buf[kWarpsPerBlock];
+    __shared__ float s_pol[EXT ? kWarpsPerBlock : 1][3][EXT ? kBuf : 1];   // buffered polarisations
     __shared__ BlockTally bt;
     __shared__ unsigned long long s_next, s_end, s_chunk;
     __shared__ int s_job;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     WarpBuf &B = s_buf[wid];
+    float (*Bp)[EXT ? kBuf : 1] = s_pol[EXT ? wid : 0];
     const Launch32 &L = BATCH ? sL : single;
     int cur_job = -1;
     for (;;) {
@@ -610,7 +783,8 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
         if (j != cur_job) {
             // this block's job changed: load its parameters, then its mosaic table
             if (BATCH) {
-                const uint32_t *src = (const uint32_t *)&W.jobs[j];
+                // a single-job launch of the generic kernel stages its parameter block
+                const uint32_t *src = (const uint32_t *)(W.jobs ? &W.jobs[j] : &single);
                 uint32_t *dst = (uint32_t *)&sL;
                 for (int i = threadIdx.x; i < (int)(sizeof(Launch32) / 4); i += blockDim.x) dst[i] = src[i];
                 __syncthreads();
@@ -640,12 +814,18 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                     if (base >= end) { more = false; break; }
                     const unsigned long long id = base + lane;
                     float x[3], k[3], A = 0.f, sB = 0.f, inv_mu = 0.f, pa = 0.f, E32 = 0.f;
+                    float pv[3] = {0.f, 0.f, 0.f};
                     uint32_t pa_thr = 0;
                     int nb = 0;
                     bool hit = false;
                     if (id < end) {
                         ++my_emit;
-                        hit = spawn<GEOM>(L, L.offset + id, x, k, A, sB, inv_mu, pa, pa_thr, E32, nb);
+                        if (EXT && L.user) {
+                            hit = spawn_user<GEOM>(L, id, x, k, pv, A, sB, inv_mu, pa, pa_thr, E32, nb);
+                        } else {
+                            hit = spawn<GEOM>(L, L.offset + id, x, k, A, sB, inv_mu, pa, pa_thr, E32, nb);
+                            if (EXT && L.pol_on) project_pol32(L, k, pv);
+                        }
                         if (!hit) {
                             ++my_miss;
                             if (REC) {
@@ -657,6 +837,7 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                                 to_global(L, k, o.dir, false);
                                 o.u_mm = __longlong_as_double(0x7ff8000000000000LL); o.v_mm = o.u_mm;
                                 o.ix = -1; o.iy = -1; o.det_hit = 0; o.no_bragg = 0;
+                                to_global(L, pv, o.pol, false);
                             }
                         }
                     }
@@ -674,6 +855,7 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                         B.pa_thr[slot] = pa_thr;
                         B.E[slot] = E32;
                         B.nb[slot] = nb;
+                        if (EXT) for (int i = 0; i < 3; ++i) Bp[i][slot] = pv[i];
                     }
                     __syncwarp();
                     if (lane == 0) B.count += __popc(hm);
@@ -701,6 +883,11 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                     s.call = 2u;
                     s.nrefl = 0;
                     s.ncoll = 0;
+                    s.pol = false;
+                    if (EXT) {
+                        for (int i = 0; i < 3; ++i) s.p[i] = Bp[i][slot];
+                        s.pol = s.p[0] != 0.0f || s.p[1] != 0.0f || s.p[2] != 0.0f;
+                    }
                     segment<GEOM>(L, s);
                     alive = true;
                 }
@@ -709,11 +896,11 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                 __syncwarp();
             }
             if (alive) {
-                int oc = step<GEOM, IRC>(L, s, s_tab);
-                if (oc < 0) oc = step<GEOM, IRC>(L, s, s_tab);    // two collisions per refill check
+                int oc = step<GEOM, IRC, EXT>(L, s, s_tab);
+                if (oc < 0) oc = step<GEOM, IRC, EXT>(L, s, s_tab);    // two collisions per refill check
                 if (oc >= 0) {
                     my_coll += (unsigned long long)s.ncoll;
-                    finish<REC>(L, s, oc, bt);
+                    finish<REC, EXT>(L, s, oc, bt);
                     alive = false;
                 }
             }
@@ -799,6 +986,7 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
             e_ref = 0.5 * (P.lo[i] + P.hi[i]);
             L.width[i] = (float)(P.hi[i] - P.lo[i]);
             break;
+        case HEART_SRC_TABLE: e_ref = P.tab_mean; break;
         default:
             L.width[i] = (float)P.width[i];
         }
@@ -885,18 +1073,36 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
     const double *a1 = S.geometry == HEART_FLAT ? S.en : S.cc;
     const double *a2 = S.geometry == HEART_FLAT ? S.N : S.ww;
     for (int i = 0; i < 3; ++i) { L.fc[i] = S.c[i]; L.fa[0][i] = a0[i]; L.fa[1][i] = a1[i]; L.fa[2][i] = a2[i]; }
+    L.pol_on = P.pol_on;
+    L.user = P.user;
+    if (P.pol_on && !P.user) {
+        double pl[3];
+        to_local(S, P.pol, pl, false);
+        for (int i = 0; i < 3; ++i) L.pol[i] = (float)pl[i];
+    }
+    L.hc_2d = 12.398419843320026 / (2.0 * S.d_A);
+    L.cs_shift = cs;
+    L.sn_shift = sn;
+    for (int i = 0; i < 10; ++i) L.ray[i] = P.ray[i];
+    L.n_tab = P.n_tab;
+    L.tab_thr = P.tab_thr;
+    L.tab_off = P.tab_off;
+    L.tab_inv = P.tab_inv;
+    L.tab_dE = P.tab_dE;
+    L.tab_w = P.tab_w;
 }
 
-template <int GEOM, int IRC, bool REC, int OCC>
+template <int GEOM, int IRC, bool REC, int OCC, bool EXT = false>
 static void launch_occ(const Launch32 &L, const WorkPlan &W, cudaStream_t st, uint64_t n_chunks) {
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_fp32<GEOM, IRC, REC, OCC>, kBlockThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_fp32<GEOM, IRC, REC, OCC, EXT>, kBlockThreads,
+                                                      0);
         if (per_sm < 1) per_sm = 1;
     }
     const uint64_t cap = (uint64_t)per_sm * (uint64_t)num_sms();
     const int blocks = (int)(n_chunks < cap ? n_chunks : cap);
-    if (blocks > 0) k_trace_fp32<GEOM, IRC, REC, OCC><<<blocks, kBlockThreads, 0, st>>>(L, W);
+    if (blocks > 0) k_trace_fp32<GEOM, IRC, REC, OCC, EXT><<<blocks, kBlockThreads, 0, st>>>(L, W);
 }
 
 template <int GEOM, int IRC, bool REC>
@@ -932,10 +1138,13 @@ static uint32_t chunk_for(uint64_t total_rays) {
     return c;
 }
 
+// ext: some job is polarised or reads user rays -> the extended generic kernel
 template <bool REC>
-static heart_status dispatch(const Launch32 &L, const WorkPlan &W, cudaStream_t st, bool generic) {
+static heart_status dispatch(const Launch32 &L, const WorkPlan &W, cudaStream_t st, bool generic, bool ext) {
     if (W.n_chunks == 0) return HEART_OK;
-    if (generic) {
+    if (ext) {
+        launch_occ<-1, -1, REC, 6, true>(L, W, st, W.n_chunks);
+    } else if (generic) {
         launch_t<-1, -1, REC>(L, W, st);
     } else {
 #define HEART_IRC_CASES(G)                                                                    \
@@ -957,31 +1166,37 @@ static heart_status dispatch(const Launch32 &L, const WorkPlan &W, cudaStream_t 
 
 static heart_status launch_single(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed,
                                   uint64_t offset, void *img, unsigned long long *scratch, heart_ray_record *rec,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, const QeParams *qe) {
     if (n == 0) return HEART_OK;
     Launch32 L;
     make_launch32(S, P, n, seed, offset, L);
     L.img = img;
     L.tally = scratch;
     L.rec = rec;
+    if (qe) {
+        L.eimg = qe->eimg;
+        L.n_qe = qe->n;
+        for (int i = 0; i < qe->n; ++i) { L.qe_e[i] = (float)qe->keV[i]; L.qe_v[i] = (float)qe->qe[i]; }
+    }
     WorkPlan W;
     std::memset(&W, 0, sizeof W);
     W.n_jobs = 1;
     W.chunk_rays = chunk_for(n);
     W.n_chunks = (n + W.chunk_rays - 1) / W.chunk_rays;
     W.counter = scratch + kCounterWord;
-    return rec ? dispatch<true>(L, W, st, false) : dispatch<false>(L, W, st, false);
+    const bool ext = L.pol_on || L.user;
+    return rec ? dispatch<true>(L, W, st, false, ext) : dispatch<false>(L, W, st, false, ext);
 }
 
 heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
-                         void *img, unsigned long long *scratch, cudaStream_t st) {
-    return launch_single(S, P, n, seed, offset, img, scratch, nullptr, st);
+                         void *img, unsigned long long *scratch, cudaStream_t st, const QeParams *qe) {
+    return launch_single(S, P, n, seed, offset, img, scratch, nullptr, st, qe);
 }
 
 heart_status launch_fp32_records(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed,
                                  uint64_t offset, void *img, unsigned long long *scratch, heart_ray_record *rec,
-                                 cudaStream_t st) {
-    return launch_single(S, P, n, seed, offset, img, scratch, rec, st);
+                                 cudaStream_t st, const QeParams *qe) {
+    return launch_single(S, P, n, seed, offset, img, scratch, rec, st, qe);
 }
 
 // Device block of a batched launch:
@@ -995,11 +1210,18 @@ size_t batch_bytes(int n) {
     return a;
 }
 
+size_t spectra_bytes(const std::vector<unsigned char> *spectra, int n) {
+    size_t a = 0;
+    for (int i = 0; spectra && i < n; ++i) a += (spectra[i].size() + 15) & ~(size_t)15;
+    return a;
+}
+
 heart_status launch_batch(const SpecParams *const *S, const SourceParams *P, const uint64_t *n_rays,
                           const uint64_t *seeds, const uint64_t *offsets, void *const *imgs, int n, void *dev,
                           std::vector<unsigned char> &host, cudaStream_t st, unsigned long long **tallies_dev,
-                          unsigned long long *const *tally_ptrs) {
-    const size_t total = batch_bytes(n);
+                          unsigned long long *const *tally_ptrs, const std::vector<unsigned char> *spectra) {
+    const size_t base = batch_bytes(n);
+    const size_t total = base + spectra_bytes(spectra, n);
     host.assign(total, 0);
     Launch32 *jobs = (Launch32 *)host.data();
     const size_t off_cb = ((size_t)n * sizeof(Launch32) + 15) & ~(size_t)15;
@@ -1008,11 +1230,23 @@ heart_status launch_batch(const SpecParams *const *S, const SourceParams *P, con
     unsigned long long *cb = (unsigned long long *)(host.data() + off_cb);
     unsigned char *d = (unsigned char *)dev;
     uint64_t all_rays = 0;
-    for (int i = 0; i < n; ++i) all_rays += n_rays[i];
+    bool ext = false;
+    for (int i = 0; i < n; ++i) {
+        all_rays += n_rays[i];
+        ext |= P[i].pol_on || P[i].user;
+    }
     const uint32_t chunk = chunk_for(all_rays);
     unsigned long long nch = 0;
+    size_t sp_off = base;
     for (int i = 0; i < n; ++i) {
-        make_launch32(*S[i], P[i], n_rays[i], seeds[i], offsets ? offsets[i] : 0, jobs[i]);
+        SourceParams Pi = P[i];
+        if (spectra && !spectra[i].empty()) {
+            // the job's tabulated spectrum rides after the work plan
+            std::memcpy(host.data() + sp_off, spectra[i].data(), spectra[i].size());
+            bind_spectrum(&Pi, d + sp_off);
+            sp_off += (spectra[i].size() + 15) & ~(size_t)15;
+        }
+        make_launch32(*S[i], Pi, n_rays[i], seeds[i], offsets ? offsets[i] : 0, jobs[i]);
         jobs[i].img = imgs[i];
         jobs[i].tally = tally_ptrs ? tally_ptrs[i] : (unsigned long long *)(d + off_t) + (size_t)i * kTallyN;
         jobs[i].rec = nullptr;
@@ -1035,7 +1269,7 @@ heart_status launch_batch(const SpecParams *const *S, const SourceParams *P, con
     W.counter = (unsigned long long *)(d + off_c);
     Launch32 dummy;
     std::memset(&dummy, 0, sizeof dummy);
-    return dispatch<false>(dummy, W, st, true);
+    return dispatch<false>(dummy, W, st, true, ext);
 }
 
 }  // namespace heart
@@ -1047,25 +1281,26 @@ extern "C" heart_status heart_trace_batch(heart_spectrometer *const *specs, cons
     if (n_jobs == 0) return HEART_OK;
     if (n_jobs < 0 || !specs || !srcs || !n_rays || !seeds || !d_images) return fail(HEART_EINVAL, "null batch array");
     std::vector<SourceParams> P((size_t)n_jobs);
+    std::vector<std::vector<unsigned char>> spectra((size_t)n_jobs);
     std::vector<const SpecParams *> S((size_t)n_jobs);
     char err[256] = {0};
     for (int i = 0; i < n_jobs; ++i) {
         if (!specs[i]) return fail(HEART_EINVAL, "null spectrometer in batch");
         const size_t elt = specs[i]->p.count_type == HEART_COUNT_I64 ? 8 : 4;
         if (!d_images[i] || ((uintptr_t)d_images[i] % elt) != 0) return fail(HEART_EINVAL, "null or misaligned image in batch");
-        heart_status st = build_source_params(srcs[i], &P[i], err, (int)sizeof err);
+        heart_status st = build_source_params(srcs[i], &P[i], err, (int)sizeof err, &spectra[i]);
         if (st != HEART_OK) return fail(st, err);
         S[i] = &specs[i]->p;
     }
     cudaStream_t cs = (cudaStream_t)stream;
     void *dev = nullptr;
-    const size_t bytes = batch_bytes(n_jobs);
+    const size_t bytes = batch_bytes(n_jobs) + spectra_bytes(spectra.data(), n_jobs);
     cudaError_t e = cudaMallocAsync(&dev, bytes, cs);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync batch");
     std::vector<unsigned char> host;
     unsigned long long *tall = nullptr;
     heart_status st = launch_batch(S.data(), P.data(), n_rays, seeds, nullptr, d_images, n_jobs, dev, host, cs, &tall,
-                                   nullptr);
+                                   nullptr, spectra.data());
     if (st == HEART_OK && out) {
         std::vector<unsigned long long> h((size_t)n_jobs * kTallyN);
         e = cudaMemcpyAsync(h.data(), tall, h.size() * 8, cudaMemcpyDeviceToHost, cs);
@@ -1092,9 +1327,25 @@ extern "C" heart_status heart_autotune(heart_spectrometer *h, const heart_source
     if (probe_rays < 4096) return fail(HEART_EINVAL, "probe needs at least 4096 rays");
     SourceParams P;
     char err[256] = {0};
-    heart_status st = build_source_params(src, &P, err, (int)sizeof err);
+    std::vector<unsigned char> spectrum;
+    heart_status st = build_source_params(src, &P, err, (int)sizeof err, &spectrum);
     if (st != HEART_OK) return fail(st, err);
     cudaStream_t cs = (cudaStream_t)stream;
+    void *d_spec = nullptr;
+    if (!spectrum.empty()) {
+        cudaError_t e0 = cudaMallocAsync(&d_spec, spectrum.size(), cs);
+        if (e0 == cudaSuccess) e0 = cudaMemcpyAsync(d_spec, spectrum.data(), spectrum.size(), cudaMemcpyHostToDevice, cs);
+        if (e0 != cudaSuccess) {
+            if (d_spec) cudaFreeAsync(d_spec, cs);
+            return cuda_fail(e0, "spectrum upload");
+        }
+        bind_spectrum(&P, d_spec);
+    }
+    struct FreeOnExit {
+        void *p;
+        cudaStream_t s;
+        ~FreeOnExit() { if (p) cudaFreeAsync(p, s); }
+    } free_spec{d_spec, cs};
     const size_t elt = h->p.count_type == HEART_COUNT_I64 ? 8 : 4;
     const size_t bytes = (size_t)h->p.nx * h->p.ny * elt;
     cudaError_t e;
@@ -1217,7 +1468,9 @@ extern "C" heart_status heart_trace_batch_static(heart_spectrometer *const *spec
     unsigned long long *d_tallies = (unsigned long long *)(d + kStaticJobsBytes + kStaticChunkBytes);
     const uint32_t chunk = g_tune.chunk_rays;
     unsigned long long nch = 0;
+    bool ext = false;
     for (int i = 0; i < n_jobs; ++i) {
+        ext |= g_static_src[i].pol_on != 0;
         make_launch32(specs[i]->p, g_static_src[i], n_rays[i], seeds[i], 0, jobs[i]);
         jobs[i].img = d_images[i];
         jobs[i].tally = d_tallies + (size_t)i * kTallyN;
@@ -1241,7 +1494,7 @@ extern "C" heart_status heart_trace_batch_static(heart_spectrometer *const *spec
         W.counter = (unsigned long long *)(d + kStaticJobsBytes + kStaticChunkBytes + kStaticTallyBytes);
         Launch32 dummy;
         std::memset(&dummy, 0, sizeof dummy);
-        heart_status st = dispatch<false>(dummy, W, cs, true);
+        heart_status st = dispatch<false>(dummy, W, cs, true, ext);
         if (st != HEART_OK) return st;
     }
     if (out) {

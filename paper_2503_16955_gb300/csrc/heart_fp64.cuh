@@ -35,8 +35,18 @@ __device__ __forceinline__ double dot3d(const double *a, const double *b) {
 struct RayOut64 {
     int outcome, nrefl, ix, iy, det_hit, no_bragg;
     long long ncoll;
-    double E, pos[3], dir[3], u, v;
+    double E, pos[3], dir[3], u, v, pol[3];
 };
+
+// polarisation of a ray: p0 projected perpendicular to k, or none
+__device__ __forceinline__ int project_pol64(const double p0[3], const double k[3], double p[3]) {
+    const double pk = dot3d(p0, k);
+    for (int i = 0; i < 3; ++i) p[i] = p0[i] - pk * k[i];
+    const double n = sqrt(dot3d(p, p));
+    if (!(n > 1e-12)) { p[0] = p[1] = p[2] = 0.0; return 0; }
+    for (int i = 0; i < 3; ++i) p[i] /= n;
+    return 1;
+}
 
 // mosaic quantile q = 1 - cos(theta) from one 32-bit word (table in smem)
 __device__ __forceinline__ double mdf_q64(const double *tab, uint32_t w) {
@@ -199,17 +209,30 @@ __device__ __forceinline__ void detector64(const SpecParams &S, const double x[3
     }
 }
 
-// one ray, source to detector
+// one ray, source (or user arrays) to detector
 __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, uint32_t k0, uint32_t k1,
-                            uint64_t ray, const double *tab, RayOut64 &r) {
+                                   uint64_t ray, uint64_t idx, const double *tab, RayOut64 &r) {
     constexpr double kTwoPi = 6.283185307179586476925;
     const uint32_t rl = (uint32_t)ray, rh = (uint32_t)(ray >> 32);
-    uint32_t a[4], b[4];
-    philox4x32_10(rl, rh, 0u, 0u, k0, k1, a);
-    philox4x32_10(rl, rh, 1u, 0u, k0, k1, b);
     r.outcome = HEART_MISS; r.nrefl = 0; r.ncoll = 0; r.ix = -1; r.iy = -1; r.det_hit = 0; r.no_bragg = 0;
     r.u = __longlong_as_double(0x7ff8000000000000LL);
     r.v = r.u;
+    double E, k[3], o[3], pv[3] = {0.0, 0.0, 0.0};
+    int pol = 0;
+    if (P.user) {
+        E = P.ray[6][idx];
+        for (int i = 0; i < 3; ++i) { o[i] = P.ray[i][idx]; k[i] = P.ray[3 + i][idx]; }
+        const double kk = sqrt(dot3d(k, k));
+        if (kk > 0) for (int i = 0; i < 3; ++i) k[i] /= kk;
+        else E = __longlong_as_double(0x7ff8000000000000LL);     // a zero direction cannot enter
+        if (P.pol_on) {
+            const double p0[3] = {P.ray[7][idx], P.ray[8][idx], P.ray[9][idx]};
+            pol = project_pol64(p0, k, pv);
+        }
+    } else {
+    uint32_t a[4], b[4];
+    philox4x32_10(rl, rh, 0u, 0u, k0, k1, a);
+    philox4x32_10(rl, rh, 1u, 0u, k0, k1, b);
 
     // energy (Sec. 2.1): component by cumulative weight, then its parameter
     const double uc = u01_64(a[0]);
@@ -217,7 +240,6 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
     for (int i = 0; i < P.n_comp; ++i)
         if (uc < P.cumw[i]) { c = i; break; }
     const double up = u01_64(a[1]);
-    double E;
     switch (P.kind[c]) {
     case HEART_SRC_MONO: E = P.e0[c]; break;
     case HEART_SRC_GAUSS:
@@ -229,26 +251,38 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
         break;
     }
     case HEART_SRC_INV_E: E = P.lo[c] * pow(P.hi[c] / P.lo[c], up); break;
+    case HEART_SRC_TABLE: {
+        // inverse of the piecewise-linear CDF: the interval with C_i <= up < C_i+1
+        int lo = 0, hi = P.n_tab - 1;
+        while (hi - lo > 1) {
+            const int m = (lo + hi) >> 1;
+            if (up < P.tab_cdf[m]) hi = m; else lo = m;
+        }
+        const double *C = P.tab_cdf, *x = P.tab_keV;
+        E = x[lo] + (up - C[lo]) / (C[lo + 1] - C[lo]) * (x[lo + 1] - x[lo]);
+        break;
+    }
     default: E = P.lo[c] + (P.hi[c] - P.lo[c]) * up; break;
     }
-    r.E = E;
     // direction uniform in solid angle inside the cone
     const double w = u01_64(a[2]) * P.one_minus_cos_max;
     const double cphi = 1.0 - w, sphi = sqrt(w * (2.0 - w));
     const double beta = kTwoPi * u01_64(a[3]);
     const double cb = cos(beta), sb = sin(beta);
-    double k[3], o[3];
     for (int i = 0; i < 3; ++i) k[i] = cphi * P.ax[i] + sphi * (cb * P.b1[i] + sb * P.b2[i]);
     // Gaussian spot
     const double rr = sqrt(-2.0 * log(u01_64(b[0])));
     const double ang = kTwoPi * u01_64(b[1]);
     const double z1 = rr * cos(ang), z2 = rr * sin(ang);
     for (int i = 0; i < 3; ++i) o[i] = P.origin[i] + P.sig1 * z1 * P.b1[i] + P.sig2 * z2 * P.b2[i];
+    if (P.pol_on) pol = project_pol64(P.pol, k, pv);
+    }
+    r.E = E;
 
     double x[3];
     const bool hit = (E > 0 && isfinite(E)) && entry64(S, o, k, x);
     if (!hit) {
-        for (int i = 0; i < 3; ++i) { r.pos[i] = o[i]; r.dir[i] = k[i]; }
+        for (int i = 0; i < 3; ++i) { r.pos[i] = o[i]; r.dir[i] = k[i]; r.pol[i] = pol ? pv[i] : 0.0; }
         return;
     }
     // per-ray constants: Bragg angle (Eq. BraggLaw), mu0, Q, majorant
@@ -299,20 +333,34 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
         double sa = fabs(kn);
         sa = sa > 1.0 ? 1.0 : sa;
         const double delta = asin(sa) - aB - S.irc_shift;
-        const double c2 = 1.0 - 2.0 * sa * sa;                // cos(2 a~)
-        const double G = 0.5 * (1.0 + c2 * c2);               // Eq. (G_unpol)
+        double ks[3];                                         // reflected direction
+        for (int i = 0; i < 3; ++i) ks[i] = k[i] - 2.0 * kn * n[i];
+        double G;
+        if (pol) {
+            const double pk = dot3d(pv, ks);
+            G = 1.0 - pk * pk;                                // Eq. (G_pol): 1 - (p . k_s)^2
+        } else {
+            const double c2 = 1.0 - 2.0 * sa * sa;            // cos(2 a~)
+            G = 0.5 * (1.0 + c2 * c2);                        // Eq. (G_unpol)
+        }
         if (v < irc64(S, delta) * G / S.irc_max) {
             ++nrefl;
             if (nrefl > S.max_refl) { outcome = HEART_CAPPED; break; }
-            for (int i = 0; i < 3; ++i) k[i] -= 2.0 * kn * n[i];
-            const double inv = 1.0 / sqrt(dot3d(k, k));
-            for (int i = 0; i < 3; ++i) k[i] *= inv;
+            const double inv = 1.0 / sqrt(dot3d(ks, ks));
+            for (int i = 0; i < 3; ++i) k[i] = ks[i] * inv;
+            if (pol) {                                        // p_s = (p - (p.k_s) k_s) / |...|
+                const double pk = dot3d(pv, k);
+                const double d = 1.0 / sqrt(1.0 - pk * pk);
+                for (int i = 0; i < 3; ++i) pv[i] = (pv[i] - pk * k[i]) * d;
+                const double pn = 1.0 / sqrt(dot3d(pv, pv));
+                for (int i = 0; i < 3; ++i) pv[i] *= pn;
+            }
         }
     }
     r.outcome = outcome;
     r.nrefl = nrefl;
     r.ncoll = ncoll;
-    for (int i = 0; i < 3; ++i) { r.pos[i] = x[i]; r.dir[i] = k[i]; }
+    for (int i = 0; i < 3; ++i) { r.pos[i] = x[i]; r.dir[i] = k[i]; r.pol[i] = pol ? pv[i] : 0.0; }
     if (outcome == HEART_EXIT_FRONT || outcome == HEART_EXIT_BACK || outcome == HEART_EXIT_SIDE)
         detector64(S, x, k, r);
 }

@@ -377,8 +377,10 @@ heart_status build_spec_params(const heart_spectrometer_desc *d, SpecParams *p, 
     return HEART_OK;
 }
 
-heart_status build_source_params(const heart_source_desc *s, SourceParams *p, char *err, int errlen) {
+heart_status build_source_params(const heart_source_desc *s, SourceParams *p, char *err, int errlen,
+                                 std::vector<unsigned char> *spectrum) {
     std::memset(p, 0, sizeof *p);
+    if (spectrum) spectrum->clear();
 #define REQUIRE(cond, msg) do { if (!(cond)) { set_err(err, errlen, msg); return HEART_EINVAL; } } while (0)
     REQUIRE(s, "null source descriptor");
     REQUIRE(s->components && s->n_components >= 1 && s->n_components <= kMaxComp, "1..16 components");
@@ -389,7 +391,7 @@ heart_status build_source_params(const heart_source_desc *s, SourceParams *p, ch
     for (int i = 0; i < s->n_components; ++i) {
         const heart_spectral_component &c = s->components[i];
         REQUIRE(c.weight >= 0 && std::isfinite(c.weight), "component weight >= 0");
-        REQUIRE(c.kind >= HEART_SRC_MONO && c.kind <= HEART_SRC_UNIFORM, "unknown component kind");
+        REQUIRE(c.kind >= HEART_SRC_MONO && c.kind <= HEART_SRC_TABLE, "unknown component kind");
         if (c.kind == HEART_SRC_MONO || c.kind == HEART_SRC_GAUSS || c.kind == HEART_SRC_LORENTZ)
             REQUIRE(c.e0_keV > 0 && std::isfinite(c.e0_keV), "e0_keV must be > 0");
         if (c.kind == HEART_SRC_GAUSS) REQUIRE(c.width_keV >= 0, "Gaussian sigma >= 0");
@@ -428,6 +430,101 @@ heart_status build_source_params(const heart_source_desc *s, SourceParams *p, ch
     p->one_minus_cos_max = 2.0 * h * h;
     p->sig1 = s->spot_fwhm_mm[0] / (2.0 * std::sqrt(2.0 * kLn2));
     p->sig2 = s->spot_fwhm_mm[1] / (2.0 * std::sqrt(2.0 * kLn2));
+    REQUIRE(finite3(s->polarization), "non-finite polarisation");
+    p->pol_on = unit(s->polarization, p->pol) ? 1 : 0;
+    bool table = false;
+    for (int i = 0; i < s->n_components; ++i) table |= s->components[i].kind == HEART_SRC_TABLE;
+    if (table) {
+        REQUIRE(spectrum, "tabulated spectra need a device copy this entry point cannot make");
+        const int n = s->n_table;
+        REQUIRE(s->table_keV && s->table_pdf && n >= 2 && n <= kMaxTable, "spectrum table: 2..8192 knots");
+        const double *x = s->table_keV, *f = s->table_pdf;
+        for (int i = 0; i < n; ++i) {
+            REQUIRE(std::isfinite(x[i]) && std::isfinite(f[i]) && f[i] >= 0.0, "spectrum table: finite, pdf >= 0");
+            if (i > 0) REQUIRE(x[i] > x[i - 1], "spectrum table: knots must ascend");
+        }
+        REQUIRE(x[0] > 0.0, "spectrum table: energies must be > 0");
+        // CDF at the knots by the trapezoid rule, in this order of operations
+        std::vector<double> C((size_t)n);
+        double run = 0.0, first = 0.0;
+        C[0] = 0.0;
+        for (int i = 0; i + 1 < n; ++i) {
+            const double m = 0.5 * (f[i] + f[i + 1]) * (x[i + 1] - x[i]);
+            run += m;
+            first += m * (0.5 * (x[i] + x[i + 1]));       // the interval's mean energy
+            C[i + 1] = run;
+        }
+        REQUIRE(run > 0.0 && std::isfinite(run), "spectrum table has no mass");
+        for (int i = 1; i < n; ++i) C[i] /= run;
+        C[n - 1] = 1.0;
+        p->n_tab = n;
+        p->tab_mean = first / run;
+        spectrum->assign(spectrum_bytes(n), 0);
+        unsigned char *b = spectrum->data();
+        double *cdf = (double *)b, *keV = (double *)(b + 8 * (size_t)n);
+        unsigned long long *thr = (unsigned long long *)(b + 16 * (size_t)n);
+        float *off = (float *)(b + 24 * (size_t)n), *inv = (float *)(b + 28 * (size_t)n);
+        float *dE = (float *)(b + 32 * (size_t)n), *w = (float *)(b + 36 * (size_t)n);
+        for (int i = 0; i < n; ++i) {
+            cdf[i] = C[i];
+            keV[i] = x[i];
+            // (word + 1/2) 2^-32 < C  <=>  word < ceil(C 2^32 - 1/2): the FP64 decision on words
+            const double t = std::ceil(C[i] * 4294967296.0 - 0.5);
+            thr[i] = t <= 0.0 ? 0ull : (unsigned long long)t;
+            off[i] = (float)((double)thr[i] + 0.5 - C[i] * 4294967296.0);   // in [0, 1)
+            inv[i] = (i + 1 < n && C[i + 1] > C[i]) ? (float)(1.0 / ((C[i + 1] - C[i]) * 4294967296.0)) : 0.0f;
+            dE[i] = (float)(x[i] - p->tab_mean);
+            w[i] = i + 1 < n ? (float)(x[i + 1] - x[i]) : 0.0f;
+        }
+    }
+#undef REQUIRE
+    return HEART_OK;
+}
+
+heart_status build_ray_params(const heart_ray_arrays *r, SourceParams *p, char *err, int errlen) {
+    std::memset(p, 0, sizeof *p);
+#define REQUIRE(cond, msg) do { if (!(cond)) { set_err(err, errlen, msg); return HEART_EINVAL; } } while (0)
+    REQUIRE(r, "null ray arrays");
+    REQUIRE(r->origin_x && r->origin_y && r->origin_z && r->dir_x && r->dir_y && r->dir_z && r->energy_keV,
+            "null ray array");
+    const bool any = r->pol_x || r->pol_y || r->pol_z, all = r->pol_x && r->pol_y && r->pol_z;
+    REQUIRE(!any || all, "polarisation needs all three arrays or none");
+    const double *a[10] = {r->origin_x, r->origin_y, r->origin_z, r->dir_x, r->dir_y, r->dir_z, r->energy_keV,
+                           r->pol_x, r->pol_y, r->pol_z};
+    for (int i = 0; i < 10; ++i) {
+        REQUIRE(((uintptr_t)a[i] % 8) == 0, "ray arrays must be 8-byte aligned");
+        p->ray[i] = a[i];
+    }
+    p->user = 1;
+    p->pol_on = all ? 1 : 0;
+    // a single nominal component so that per-component tables stay defined
+    p->n_comp = 1;
+    p->kind[0] = HEART_SRC_MONO;
+    p->e0[0] = 8.0;
+    p->cumw[0] = 1.0;
+    p->ax[2] = 1.0;
+    p->b1[0] = 1.0;
+    p->b2[1] = 1.0;
+#undef REQUIRE
+    return HEART_OK;
+}
+
+heart_status build_qe_params(const heart_qe_table *q, unsigned long long *eimg, QeParams *p, char *err,
+                             int errlen) {
+    std::memset(p, 0, sizeof *p);
+    p->eimg = eimg;
+    if (!q || q->n == 0) return HEART_OK;
+#define REQUIRE(cond, msg) do { if (!(cond)) { set_err(err, errlen, msg); return HEART_EINVAL; } } while (0)
+    REQUIRE(q->n > 0 && q->n <= kMaxQe, "QE table needs 1..32 knots");
+    REQUIRE(q->keV && q->qe, "null QE arrays");
+    for (int i = 0; i < q->n; ++i) {
+        REQUIRE(std::isfinite(q->keV[i]) && q->keV[i] > 0, "QE knot energies must be > 0");
+        REQUIRE(q->qe[i] >= 0 && q->qe[i] <= 1, "QE values must be in [0, 1]");
+        REQUIRE(i == 0 || q->keV[i] > q->keV[i - 1], "QE knot energies must increase");
+        p->keV[i] = q->keV[i];
+        p->qe[i] = q->qe[i];
+    }
+    p->n = q->n;
 #undef REQUIRE
     return HEART_OK;
 }

@@ -3,6 +3,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <vector>
+
 #include "heart.h"
 
 namespace heart {
@@ -11,7 +13,9 @@ constexpr int kMdfM = 4096;      // body knots of the mosaic inverse CDF, u = i 
 constexpr int kMdfT = 256;       // tail intervals, linear in tau = -log2(1 - u), tau in [12, 33]
 constexpr int kMdfKnots = kMdfM + kMdfT + 1;
 constexpr int kMaxComp = 16;
+constexpr int kMaxQe = 32;       // detector quantum-efficiency knots
 constexpr int kTallyN = 27;      // heart_tally as 27 uint64 words
+constexpr int kMaxTable = HEART_MAX_TABLE;   // knots of a tabulated spectrum
 
 // tally word indices (same order as heart_tally)
 enum : int {
@@ -51,11 +55,51 @@ struct SourceParams {
     double origin[3], ax[3], b1[3], b2[3];
     double one_minus_cos_max;        // 2 sin^2(cone / 2)
     double sig1, sig2;               // spot sigmas
+    double pol[3];                   // linear polarisation (unit), if pol_on
+    int32_t pol_on, user;            // polarised source; rays come from user arrays
+    const double *ray[10];           // user arrays: ox oy oz kx ky kz E px py pz (p* may be null)
+    // tabulated spectrum (device copy, see bind_spectrum): CDF and energies at
+    // the knots for the FP64 path; for the FP32 path the CDF as thresholds on
+    // the raw 32-bit word, the in-interval offsets and slopes, and the knots
+    // relative to the table's mean energy
+    int32_t n_tab, pad_tab;
+    double tab_mean;
+    const double *tab_cdf, *tab_keV;
+    const unsigned long long *tab_thr;
+    const float *tab_off, *tab_inv, *tab_dE, *tab_w;
+};
+
+// device image of a tabulated spectrum of n knots (bind_spectrum's layout)
+inline size_t spectrum_bytes(int n) { return (size_t)n * 40; }
+// point the table fields of p at a device copy of the host image
+inline void bind_spectrum(SourceParams *p, const void *dev) {
+    const unsigned char *d = (const unsigned char *)dev;
+    const size_t n = (size_t)p->n_tab;
+    p->tab_cdf = (const double *)d;
+    p->tab_keV = (const double *)(d + 8 * n);
+    p->tab_thr = (const unsigned long long *)(d + 16 * n);
+    p->tab_off = (const float *)(d + 24 * n);
+    p->tab_inv = (const float *)(d + 28 * n);
+    p->tab_dE = (const float *)(d + 32 * n);
+    p->tab_w = (const float *)(d + 36 * n);
+}
+
+// optional energy image: each detected photon adds round(E * QE(E) * 1e6)
+// (units of 1e-6 keV) to eimg; QE linear between knots, clamped beyond
+struct QeParams {
+    int32_t n, pad;
+    double keV[kMaxQe], qe[kMaxQe];
+    unsigned long long *eimg;
 };
 
 // host set-up (heart_host.cpp)
 heart_status build_spec_params(const heart_spectrometer_desc *d, SpecParams *p, double *mdf_table,
                                char *err, int errlen);
-heart_status build_source_params(const heart_source_desc *s, SourceParams *p, char *err, int errlen);
+// spectrum: host image of the source's tabulated spectrum when a component
+// uses it (then bind_spectrum after the upload); nullptr: tables rejected
+heart_status build_source_params(const heart_source_desc *s, SourceParams *p, char *err, int errlen,
+                                 std::vector<unsigned char> *spectrum = nullptr);
+heart_status build_ray_params(const heart_ray_arrays *r, SourceParams *p, char *err, int errlen);
+heart_status build_qe_params(const heart_qe_table *q, unsigned long long *eimg, QeParams *p, char *err, int errlen);
 
 }  // namespace heart

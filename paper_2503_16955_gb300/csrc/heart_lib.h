@@ -26,18 +26,23 @@ heart_status fail(heart_status st, const char *msg);
 heart_status cuda_fail(cudaError_t e, const char *what);
 int num_sms();
 
+// qe may be nullptr (no energy image)
 heart_status launch_fp64(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
-                         void *img, unsigned long long *tally, heart_ray_record *rec, cudaStream_t st);
+                         void *img, unsigned long long *tally, heart_ray_record *rec, cudaStream_t st,
+                         const QeParams *qe = nullptr);
 heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
-                         void *img, unsigned long long *scratch, cudaStream_t st);
+                         void *img, unsigned long long *scratch, cudaStream_t st, const QeParams *qe = nullptr);
 heart_status launch_fp32_records(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed,
                                  uint64_t offset, void *img, unsigned long long *scratch, heart_ray_record *rec,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const QeParams *qe = nullptr);
 size_t batch_bytes(int n);
+// device bytes of the jobs' tabulated spectra appended after the batch block
+size_t spectra_bytes(const std::vector<unsigned char> *spectra, int n);
 heart_status launch_batch(const SpecParams *const *S, const SourceParams *P, const uint64_t *n_rays,
                           const uint64_t *seeds, const uint64_t *offsets, void *const *imgs, int n, void *dev,
                           std::vector<unsigned char> &host, cudaStream_t st, unsigned long long **tallies_dev,
-                          unsigned long long *const *tally_ptrs);
+                          unsigned long long *const *tally_ptrs,
+                          const std::vector<unsigned char> *spectra = nullptr);
 }  // namespace heart
 
 struct heart_spectrometer {

@@ -35,6 +35,7 @@ struct Job {
     uint64_t id = 0;
     heart_spectrometer *spec = nullptr;
     SourceParams P;
+    std::vector<unsigned char> spectrum;     // tabulated spectrum, copied into d_block at admission
     uint64_t n = 0, seed = 0, scheduled = 0;
     heart_precision prec = HEART_FP32;
     size_t img_bytes = 0;
@@ -83,11 +84,21 @@ void admit(heart_server *s) {
     while (!s->queue.empty()) {
         Job *j = s->jobs[s->queue.front()];
         if (s->used + j->img_bytes > s->cap) break;
-        const size_t bytes = j->img_bytes + kTallyN * sizeof(unsigned long long) + 16;
+        // image, tallies, then the job's tabulated spectrum (if any)
+        const size_t off_tally = (j->img_bytes + 15) & ~(size_t)15;
+        const size_t off_spec = (off_tally + kTallyN * sizeof(unsigned long long) + 15) & ~(size_t)15;
+        const size_t bytes = off_spec + j->spectrum.size();
         cudaError_t e = cudaMallocAsync(&j->d_block, bytes, s->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(j->d_block, 0, bytes, s->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(j->d_block, 0, off_spec, s->stream);
+        if (e == cudaSuccess && !j->spectrum.empty()) {
+            e = cudaMemcpyAsync((char *)j->d_block + off_spec, j->spectrum.data(), j->spectrum.size(),
+                                cudaMemcpyHostToDevice, s->stream);
+            if (e == cudaSuccess) bind_spectrum(&j->P, (char *)j->d_block + off_spec);
+        }
         s->queue.pop_front();
         if (e != cudaSuccess) {
+            if (j->d_block) cudaFreeAsync(j->d_block, s->stream);
+            j->d_block = nullptr;
             j->state = FAILED;
             j->status = HEART_ENOMEM;
             j->t_done = Clock::now();
@@ -95,7 +106,7 @@ void admit(heart_server *s) {
             continue;
         }
         j->d_img = j->d_block;
-        j->d_tally = (unsigned long long *)((char *)j->d_block + ((j->img_bytes + 15) & ~(size_t)15));
+        j->d_tally = (unsigned long long *)((char *)j->d_block + off_tally);
         s->used += j->img_bytes;
         j->state = ADMITTED;
     }
@@ -268,7 +279,7 @@ extern "C" heart_status heart_submit(heart_server *s, heart_spectrometer *spec, 
     Job *j = new (std::nothrow) Job();
     if (!j) return fail(HEART_ENOMEM, "host allocation failed");
     char err[256] = {0};
-    heart_status st = build_source_params(src, &j->P, err, (int)sizeof err);
+    heart_status st = build_source_params(src, &j->P, err, (int)sizeof err, &j->spectrum);
     if (st != HEART_OK) { delete j; return fail(st, err); }
     const size_t elt = spec->p.count_type == HEART_COUNT_I64 ? 8 : 4;
     j->img_bytes = (size_t)spec->p.nx * spec->p.ny * elt;

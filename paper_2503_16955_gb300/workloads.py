@@ -209,6 +209,41 @@ def serving_stream(seed=4, n_jobs=10_000, rate_per_s=200.0, ray_range=(1e4, 1e8)
     return jobs
 
 
+def user_rays(workload, n, seed, polarised=False, e_sigma_keV=0.15):
+    """Seeded user-supplied rays for a workload (Sec. 2.1's ray arrays): origins
+    in the source spot, directions uniform over a disc of the cone's half angle
+    around its axis, energies Gaussian about the first line, optional random
+    linear polarisations (not yet perpendicular to the rays).  Also a few
+    degenerate rays: index 0 has a zero direction, index 1 a negative energy.
+    Returns a dict of float64 arrays ox, oy, oz, kx, ky, kz, E (px, py, pz)."""
+    src = workload["source"]
+    rng = np.random.default_rng(seed)
+    ax = np.array(_unit(src["axis"]))
+    t = np.array([1.0, 0.0, 0.0]) if abs(ax[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    b1 = np.array(_unit(np.cross(ax, t)))
+    b2 = np.cross(ax, b1)
+    cone = max(src["cone_half_angle_rad"], 1e-3)
+    r = cone * np.sqrt(rng.uniform(size=n))
+    phi = rng.uniform(0.0, 2.0 * math.pi, size=n)
+    d = ax[None, :] + (r * np.cos(phi))[:, None] * b1 + (r * np.sin(phi))[:, None] * b2
+    sig = np.asarray(src.get("spot_fwhm_mm", (0.0, 0.0)), float) / 2.3548200450309493
+    o = np.asarray(src["origin_mm"], float)[None, :] + \
+        (sig[0] * rng.normal(size=n))[:, None] * b1 + (sig[1] * rng.normal(size=n))[:, None] * b2
+    e0 = src["components"][0].get("e0_keV") or 0.5 * (src["components"][0]["lo_keV"] +
+                                                      src["components"][0]["hi_keV"])
+    E = e0 + e_sigma_keV * rng.normal(size=n)
+    if n > 0:
+        d[0] = 0.0
+    if n > 1:
+        E[1] = -1.0
+    out = dict(ox=o[:, 0].copy(), oy=o[:, 1].copy(), oz=o[:, 2].copy(),
+               kx=d[:, 0].copy(), ky=d[:, 1].copy(), kz=d[:, 2].copy(), E=E)
+    if polarised:
+        p = rng.normal(size=(n, 3))
+        out.update(px=p[:, 0].copy(), py=p[:, 1].copy(), pz=p[:, 2].copy())
+    return out
+
+
 def scaled(workload, n_rays):
     """Same workload with a different ray count."""
     w = dict(workload)

@@ -1,0 +1,151 @@
+"""Energy (keV) image with detector QE, and the calibration map (Sec. 2.3,
+Sec. 3), through the C ABI.
+
+Tolerances: FP64 kernel vs oracle -- count images identical, energy images
+within one unit (1e-6 keV) per detected photon (rounding of E * QE * 1e6);
+FP32 kernel vs FP64 on the same streams -- detected photons and energy move
+by at most the flip budget (1e-4 of the rays, one photon each), and the FP32
+energy image equals its own photons' sum (from the FP32 per-ray records)
+within four units (4e-6 keV) per photon; calibration map of a von Hamos spectrometer within
+10 eV of the focusing relation x(E) = 2 R cot(aB(E)) (the mosaic broadening of
+a 40 um crystal moves a column's mean by a few eV; one pixel is 0.6 eV)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import binding as ob
+from paper_2503_16955_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+QE = [(7.5, 0.92), (7.9, 0.85), (8.1, 0.80), (8.6, 0.55)]
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2503_16955_gb300 as H
+    return H
+
+
+def _trace(H, spec, w, n, seed, precision, qe):
+    import torch
+    img = torch.zeros(spec.shape, dtype=torch.int32, device="cuda")
+    e = torch.zeros(spec.shape, dtype=torch.int64, device="cuda")
+    t = H.heart_trace_energy(spec, w["source"], n, seed, 0, img, e, qe=qe, precision=precision)
+    return img.cpu().numpy().astype(np.int64), e.cpu().numpy(), t
+
+
+def test_fp64_energy_image_equals_oracle(H):
+    w = W.von_hamos_hapg()
+    s = H.heart_spectrometer_create(w["spec"])
+    img, e, t = _trace(H, s, w, 60_000, 17, "fp64", QE)
+    oimg, oe, ot, _ = ob.trace_energy(w["spec"], w["source"], 60_000, 17, qe=QE)
+    assert np.array_equal(img, oimg)
+    assert np.all(np.abs(e - oe) <= oimg)
+    assert t["det_hits"] == ot["det_hits"]
+    s.close()
+
+
+def test_fp32_energy_image_against_fp64(H):
+    w = W.von_hamos_hapg()
+    s = H.heart_spectrometer_create(w["spec"])
+    n = 2_000_000
+    i64, e64, t64 = _trace(H, s, w, n, 18, "fp64", QE)
+    i32, e32, t32 = _trace(H, s, w, n, 18, "fp32", QE)
+    # at most 1e-4 of the rays may flip; each flip moves at most one photon (< 9 keV)
+    n_flip_budget = 1e-4 * n
+    assert abs(int(i32.sum()) - int(i64.sum())) <= n_flip_budget
+    assert abs(int(e32.sum()) - int(e64.sum())) <= n_flip_budget * 9_000_000
+    # the FP32 energy image is its own photons' round(E QE 1e6): rebuilt from
+    # the FP32 kernel's per-ray records of the same streams (same pixels, same
+    # energies), each photon within 4 units: FP32 interpolation of QE, the FP32
+    # product E QE 1e6 (~7e6, relative error <= 4.5e-7 together) and the rounding
+    rec, _ = H.heart_trace_records(s, w["source"], n, 18, 0, precision="fp32")
+    hit = rec["det_hit"] == 1
+    E = rec["energy_keV"][hit]
+    units = np.rint(E * _qe_np(E) * 1e6).astype(np.int64)
+    ref = np.zeros_like(e32)
+    np.add.at(ref, (rec["iy"][hit], rec["ix"][hit]), units)
+    cnt = np.zeros_like(i32)
+    np.add.at(cnt, (rec["iy"][hit], rec["ix"][hit]), 1)
+    assert np.array_equal(cnt, i32)
+    d = np.abs(e32 - ref)
+    bad = d > 4 * cnt
+    assert not bad.any(), (int(bad.sum()), int(d.max()), int(cnt[bad].max()))
+    s.close()
+
+
+def _qe_np(E):
+    """QE of the table above, linear between knots and constant beyond (Sec. 3),
+    checked against the oracle's evaluation at a few energies"""
+    k = np.array([q[0] for q in QE])
+    v = np.array([q[1] for q in QE])
+    out = np.interp(E, k, v)
+    for e in (7.4, 7.7, 8.0, 8.3, 8.7):
+        assert abs(np.interp(e, k, v) - ob.qe_eval(QE, e)) < 1e-15
+    return out
+
+
+def test_energy_without_count_image_and_validation(H):
+    import torch
+    w = W.flat_hopg_mono()
+    s = H.heart_spectrometer_create(w["spec"])
+    e = torch.zeros(s.shape, dtype=torch.int64, device="cuda")
+    img = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    H.heart_trace_energy(s, w["source"], 50_000, 3, 0, None, e, precision="fp32")
+    H.heart_trace(s, w["source"], 50_000, 3, 0, img, precision="fp32")
+    # mono 8 keV, QE = 1: the energy image is 8e6 units per count
+    assert torch.equal(e, img.to(torch.int64) * 8_000_000)
+    with pytest.raises(H.HeartError):
+        H.heart_trace_energy(s, w["source"], 10, 3, 0, None, e, qe=[(8.0, 0.5), (7.0, 0.6)])
+    with pytest.raises(H.HeartError):
+        H.heart_trace_energy(s, w["source"], 10, 3, 0, None, e, qe=[(8.0, 1.5)])
+    bad = torch.zeros(s.shape[0] * s.shape[1] + 1, dtype=torch.int64, device="cuda").view(torch.uint8)[4:]
+    with pytest.raises(H.HeartError):
+        H.heart_trace_energy(s, w["source"], 10, 3, 0, None, bad)
+    s.close()
+
+
+def _column_means(H, spec, source, n, seed):
+    s = H.heart_spectrometer_create(spec)
+    emap, counts = H.calibration_map(s, source, 7.6, 8.4, n, seed)
+    s.close()
+    c = counts.cpu().numpy().astype(np.int64)
+    m = emap.cpu().numpy()
+    col_counts = c.sum(axis=0)
+    col_energy = np.nansum(np.where(c > 0, m * c, 0.0), axis=0)
+    good = col_counts >= 30
+    u = (np.arange(c.shape[1]) + 0.5 - c.shape[1] / 2) * spec["pixel_mm"]
+    x = spec["det_centre_mm"][0] + u
+    aB = np.arctan(2 * spec["radius_mm"] / x)
+    E_pred = 12.398419843320026 / (2 * 3.354 * np.sin(aB))
+    return good, col_energy / np.maximum(col_counts, 1), E_pred, u
+
+
+def test_calibration_map_follows_von_hamos_dispersion(H):
+    # thin crystal, Gaussian mosaic: a crystallite tilted by e sends a ray to
+    # x = R cot(aB - e) + R cot(aB + e) = 2 R cot aB + 2 R e^2 cot aB / sin^2 aB,
+    # here < 0.01 mm (0.1 eV), and depth moves it by < 2 t cot aB = 0.09 mm
+    # (1 eV): the column means follow x(E) = 2 R cot aB(E)
+    w = W.von_hamos_hapg()
+    spec = dict(w["spec"], thickness_mm=0.01, mdf="gaussian", mdf_fwhm_rad=0.1 * W.DEG, irc="darwin")
+    good, E_col, E_pred, u = _column_means(H, spec, w["source"], 400_000_000, 21)
+    assert good.sum() > 200
+    d = (E_col - E_pred)[good]
+    # no systematic offset (1 eV), and blocks of 16 columns (0.8 mm, ~8 eV of
+    # dispersion; a column's mean scatters by ~1 eV) within 2 eV of x(E)
+    assert abs(d.mean()) < 0.001, d.mean()
+    blocks = d[: d.size // 16 * 16].reshape(-1, 16).mean(axis=1)
+    assert np.max(np.abs(blocks)) < 0.002, np.max(np.abs(blocks))
+    assert np.corrcoef(u[good], E_col[good])[0, 1] > 0.99
+    # the workload's 50 % Lorentzian mosaic has heavy tilt tails: the shift
+    # 2 R e^2 cot aB / sin^2 aB > 0 always moves photons to larger x, so the
+    # column means lie below x(E)
+    good2, E_col2, E_pred2, _ = _column_means(H, w["spec"], w["source"], 200_000_000, 22)
+    assert np.mean(E_col2[good2] - E_pred2[good2]) < -0.002

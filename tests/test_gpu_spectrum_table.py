@@ -1,0 +1,122 @@
+"""Tabulated spectra (a density at knots whose CDF is linear between them)
+through the C ABI: single traces, batches and the request loop.
+
+Tolerances: the FP64 kernel replays the oracle ray by ray (decisions
+identical, energies within 1e-13 relative, positions within 1e-9); the FP32
+kernel follows FP64 on the same streams with at most 1e-4 of the rays flipped,
+energies within 2e-6 keV and hit positions within 1 um."""
+import numpy as np
+import pytest
+
+from oracle import binding as ob
+from paper_2503_16955_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+KEV = np.array([7.55, 7.7, 7.8, 7.82, 7.95, 8.0, 8.02, 8.2, 8.45])
+PDF = np.array([0.2, 0.4, 3.0, 0.0, 0.0, 5.0, 1.0, 0.8, 0.3])
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2503_16955_gb300 as H
+    return H
+
+
+def _source():
+    w = W.von_hamos_hapg()
+    src = dict(w["source"])
+    src["components"] = [dict(kind="table", weight=0.8), dict(kind="gauss", e0_keV=8.1, width_keV=0.004, weight=0.2)]
+    src["table"] = (KEV, PDF)
+    return w, src
+
+
+def test_fp64_table_source_replays_oracle(H):
+    w, src = _source()
+    s = H.heart_spectrometer_create(w["spec"])
+    g, gt = H.heart_trace_records(s, src, 60_000, 3, 11, precision="fp64")
+    _, ot, o = ob.trace(w["spec"], src, 60_000, 3, ray_offset=11, records=True)
+    s.close()
+    assert np.array_equal(g["ray_id"], o["ray_id"])
+    assert np.array_equal(g["outcome"], o["outcome"]) and np.array_equal(g["nrefl"], o["nrefl"])
+    assert np.array_equal(g["ncoll"], o["ncoll"])
+    assert np.allclose(g["energy_keV"], o["energy_keV"], rtol=1e-13, atol=0)
+    scale = np.maximum(np.abs(o["pos"]), 1.0)
+    assert np.all(np.abs(g["pos"] - o["pos"]) <= 1e-9 * scale)
+    assert gt == ot
+    # energies drawn from the table never fall inside its empty interval
+    E = g["energy_keV"]
+    assert not np.any((E > 7.82) & (E < 7.95))
+
+
+def test_fp32_table_source_follows_fp64(H):
+    w, src = _source()
+    s = H.heart_spectrometer_create(w["spec"])
+    n = 300_000
+    r64, t64 = H.heart_trace_records(s, src, n, 5, 0, precision="fp64")
+    r32, t32 = H.heart_trace_records(s, src, n, 5, 0, precision="fp32")
+    s.close()
+    entered = r64["outcome"] != 0
+    assert np.abs(r64["energy_keV"][entered] - r32["energy_keV"][entered]).max() <= 2e-6
+    flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"])
+    assert flip.sum() <= 1e-4 * n
+    same = ~flip & (r64["det_hit"] == 1) & (r32["det_hit"] == 1)
+    assert same.sum() > 100
+    assert np.abs(r64["u_mm"][same] - r32["u_mm"][same]).max() <= 1e-3
+    assert t32["miss"] == t64["miss"]
+
+
+def test_two_knot_table_equals_uniform_component_fp64(H):
+    import torch
+    w = W.von_hamos_hapg()
+    su = dict(w["source"], components=[dict(kind="uniform", lo_keV=7.7, hi_keV=8.3, weight=1.0)])
+    st = dict(w["source"], components=[dict(kind="table", weight=1.0)],
+              table=(np.array([7.7, 8.3]), np.array([1.0, 1.0])))
+    s = H.heart_spectrometer_create(w["spec"])
+    a = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    b = torch.zeros_like(a)
+    H.heart_trace(s, su, 2_000_000, 8, 0, a, precision="fp64")
+    H.heart_trace(s, st, 2_000_000, 8, 0, b, precision="fp64")
+    s.close()
+    assert torch.equal(a, b) and int(a.sum()) > 1000
+
+
+def test_table_source_in_batch_and_server_equals_single(H):
+    import torch
+    w, src = _source()
+    s = H.heart_spectrometer_create(w["spec"])
+    n = 3_000_000
+    single = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    t1 = H.heart_trace(s, src, n, 21, 0, single, precision="fp32")
+    bimg = [torch.zeros_like(single), torch.zeros_like(single)]
+    tb = H.heart_trace_batch([s, s], [w["source"], src], [1000, n], [1, 21], bimg)
+    assert torch.equal(bimg[1], single) and tb[1] == t1
+    srv = H.Server(1 << 30)
+    jid = srv.submit(s, src, n, 21)
+    _, t2, _ = srv.poll(jid, timeout_ms=60_000)
+    img = torch.zeros_like(single)
+    srv.fetch(jid, img)
+    srv.release(jid)
+    srv.close()
+    assert torch.equal(img, single) and t2 == t1
+    with pytest.raises(H.HeartError):                    # the no-allocation entry point cannot copy a table
+        H.heart_trace_batch_static([s], [src], [1000], [1], [torch.zeros_like(single)])
+    s.close()
+
+
+def test_table_validation(H):
+    import torch
+    w, src = _source()
+    s = H.heart_spectrometer_create(w["spec"])
+    img = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    for table in [None, (KEV[:1], PDF[:1]), (KEV[::-1], PDF), (KEV, -PDF), (KEV, 0 * PDF),
+                  (np.linspace(1, 9, 8193), np.ones(8193))]:
+        bad = dict(src, table=table)
+        with pytest.raises(H.HeartError):
+            H.heart_trace(s, bad, 10, 1, 0, img)
+    s.close()
