@@ -45,7 +45,10 @@ class Spec(C.Structure):
         ("det_centre", D3), ("det_u", D3), ("det_v", D3),
         ("det_nx", C.c_int32), ("det_ny", C.c_int32),
         ("pixel_mm", C.c_double),
+        ("sampler", C.c_int32), ("pad3", C.c_int32), ("thin_vstar", C.c_double),
     ]
+
+SAMPLER = {"plain": 0, "thinned": 1}
 
 
 class Component(C.Structure):
@@ -199,6 +202,8 @@ def make_spec(d):
     s.det_nx = d["det_nx"]
     s.det_ny = d["det_ny"]
     s.pixel_mm = d["pixel_mm"]
+    s.sampler = SAMPLER[d.get("sampler", "plain")]
+    s.thin_vstar = d.get("thin_vstar", 0.0)
     return s
 
 

@@ -27,6 +27,10 @@
  *                                    thresholds of two orthogonal p sum to twice the unpolarised one;
  *                                    closed-form reflected p; p stays unit and perpendicular to k)
  *   orc_trace_rays           pinned (rays repeating a zero-cone source reproduce orc_trace exactly)
+ *   thinned sampler          pinned (near-Bragg segments replay the plain walk word for word;
+ *                                    two-sample agreement with the plain walk on fans of directions for
+ *                                    all 7 MDFs and 6 IRCs and on the workloads; first-reflection
+ *                                    probability vs quadrature of Eq. ReflXsection)
  *   tabulated spectrum       pinned (KS against the piecewise-linear CDF written from the knots; a
  *                                    two-knot table reproduces the uniform component bit for bit)
  *   orc_trace_energy         pinned (mono line: energy image = E x QE x counts; QE interpolation)
@@ -86,7 +90,17 @@ typedef struct {
     double det_centre[3], det_u[3], det_v[3];
     int32_t det_nx, det_ny;
     double pixel_mm;
+    /* candidate sampler of the walk: ORC_SAMPLER_PLAIN draws every tentative
+     * collision at the constant majorant; ORC_SAMPLER_THINNED skips, per
+     * straight segment, the candidates that provably cannot reflect (same
+     * distribution of paths, fewer candidates).  thin_vstar: the acceptance
+     * level below which every candidate is still tested (0: 2^-10). */
+    int32_t sampler;
+    int32_t pad3;
+    double thin_vstar;
 } orc_spec;
+
+enum { ORC_SAMPLER_PLAIN = 0, ORC_SAMPLER_THINNED = 1 };
 
 typedef struct { int32_t kind; int32_t pad; double e0_keV, width_keV, lo_keV, hi_keV, weight; } orc_component;
 

@@ -539,7 +539,31 @@ typedef struct {
     double irc_max;
     irc_params irc;
     orc_mdf_table *mdf;
+    /* thinned sampler: v* and the IRC half-width X* beyond which R/R_max <= v* */
+    double vstar, xstar;
 } geom;
+
+/* X*: the smallest |x| such that R(x') / R_max <= v* for every |x'| >= X*.
+ * Found by scanning |x| down from 1 rad on a geometric grid (ratio 1.0005),
+ * then bisecting the last crossing; widened by 1e-6 relative. */
+static double irc_xstar(const irc_params *p, double rmax, double vstar) {
+    double hi = 1.0;
+    if (irc_eval(p, hi) / rmax > vstar || irc_eval(p, -hi) / rmax > vstar) return -1.0;
+    double x = hi;
+    for (;;) {
+        double y = x / 1.0005;
+        if (y < 1e-12) return 1e-12;
+        if (irc_eval(p, y) / rmax > vstar || irc_eval(p, -y) / rmax > vstar) {
+            double lo = y, up = x;                /* above vstar at lo, below at up */
+            for (int it = 0; it < 200 && up - lo > 1e-15 * up; ++it) {
+                double m = 0.5 * (lo + up);
+                if (irc_eval(p, m) / rmax > vstar || irc_eval(p, -m) / rmax > vstar) lo = m; else up = m;
+            }
+            return up * (1.0 + 1e-6);
+        }
+        x = y;
+    }
+}
 
 static int geom_init(geom *g, const orc_spec *s) {
     memset(g, 0, sizeof *g);
@@ -573,6 +597,14 @@ static int geom_init(geom *g, const orc_spec *s) {
     cross3(g->eu, g->ev, g->nd);
     irc_prepare(s, &g->irc);
     g->irc_max = irc_eval(&g->irc, 0.0);
+    if (s->sampler == ORC_SAMPLER_THINNED) {
+        g->vstar = s->thin_vstar > 0 ? s->thin_vstar : 1.0 / 1024.0;
+        if (!(g->vstar < 1.0)) return fail("thin_vstar must be < 1");
+        g->xstar = irc_xstar(&g->irc, g->irc_max, g->vstar);
+        if (!(g->xstar > 0)) return fail("rocking curve never drops below v*");
+    } else if (s->sampler != ORC_SAMPLER_PLAIN) {
+        return fail("unknown sampler");
+    }
     return 0;
 }
 
@@ -714,6 +746,120 @@ static int next4(wsrc *ws, uint32_t w[4]) {
     return 1;
 }
 
+/* ------------------------------------------------------------------ */
+/* thinned candidates: bounds of one straight segment                  */
+/* ------------------------------------------------------------------ */
+/* The scatter candidates (rate Q R_max, marks: the acceptance uniform v and
+ * the crystallite normal n) split by their marks into independent Poisson
+ * processes (marking theorem):
+ *   (a) v < v*: every candidate, tested as usual;
+ *   (b) v >= v*, q(n) in [q_min, 2 - q_min] and the azimuth of n in the arcs
+ *       where |Delta| < X*: tested as usual;
+ *   (c) the rest, which cannot reflect: with |Delta| >= X*, R / R_max <= v* <= v.
+ * On a straight segment the ray's grazing angle stays in [a_lo, a_hi]; a
+ * crystallite tilted by theta has asin|k.n| within theta of it, so if
+ * theta < d - X* (d = distance of alpha_B + Delta_M from [a_lo, a_hi]) then
+ * |Delta| >= X*.  Process (c) is never generated.  Process (b) is generated
+ * at rate Q R_max (1 - v*) P_A pbar: n's table word uniform over a word range
+ * covering [q_min, 2 - q_min] (mass P_A), then kept with probability
+ * P_xi(theta) / pbar (P_xi: the arc measure, pbar >= P_xi on the segment), its
+ * azimuth uniform over the arcs.  A segment with d <= X* keeps the plain
+ * candidate stream (v* = 1). */
+typedef struct {
+    double mu, pa;            /* majorant of the segment and the absorption share mu0 / mu */
+    double ra, vstar;         /* share of process (a) among scatter candidates, its v range */
+    double qmin, pbar;        /* process (b): tilt bound and arc-measure bound */
+    double S1, S2;            /* |k.n| window of |Delta| < X* */
+    uint64_t w0, wspan;       /* process (b): table words [w0, w0 + wspan) */
+} seg_bound;
+
+/* first word of the table interval containing q (conservative lower end) */
+static uint64_t word_floor(const orc_mdf_table *t, double q) {
+    if (!(q < t->body[ORC_MDF_M - 1])) return (uint64_t)(ORC_MDF_M - 1) << 20;
+    int lo = 0, hi = ORC_MDF_M - 1;            /* body[lo] <= q < body[hi] */
+    if (!(t->body[0] <= q)) return 0;
+    while (hi - lo > 1) {
+        int m = (lo + hi) / 2;
+        if (t->body[m] <= q) lo = m; else hi = m;
+    }
+    return (uint64_t)lo << 20;
+}
+
+/* one past the last word of the table interval containing q (conservative upper end) */
+static uint64_t word_ceil(const orc_mdf_table *t, double q) {
+    if (!(q < t->body[ORC_MDF_M - 1])) return 1ull << 32;
+    int lo = 0, hi = ORC_MDF_M - 1;            /* body[lo] <= q < body[hi] */
+    if (!(t->body[0] <= q)) return 1ull << 20;
+    while (hi - lo > 1) {
+        int m = (lo + hi) / 2;
+        if (t->body[m] <= q) lo = m; else hi = m;
+    }
+    return (uint64_t)hi << 20;
+}
+
+static void bound_segment(const geom *g, const orc_ray_consts *rc, const double x[3], const double k[3],
+                          seg_bound *b) {
+    const orc_spec *s = g->s;
+    memset(b, 0, sizeof *b);
+    b->mu = rc->mubar;
+    b->pa = rc->p_abs;
+    b->ra = 1.0;
+    b->vstar = 1.0;
+    b->pbar = 1.0;
+    b->wspan = 1ull << 32;
+    if (s->sampler != ORC_SAMPLER_THINNED || rc->no_bragg || !(rc->Q > 0)) return;
+    int face;
+    double se = exit_distance(g, x, k, &face);
+    double xe[3], N0[3], N1[3], t1[3], t2[3];
+    for (int i = 0; i < 3; ++i) xe[i] = x[i] + se * k[i];
+    local_frame(g, x, N0, t1, t2);
+    local_frame(g, xe, N1, t1, t2);
+    double k0 = dot3(k, N0), k1 = dot3(k, N1);
+    double lo = fmin(fabs(k0), fabs(k1)), hi = fmax(fabs(k0), fabs(k1));
+    if ((k0 < 0) != (k1 < 0)) lo = 0.0;             /* k.N is monotone along a line: it crossed 0 */
+    double alo = asin(fmin(lo, 1.0)), ahi = asin(fmin(hi, 1.0));
+    double aB = rc->alpha_B + s->irc_shift_rad;
+    double d = aB < alo ? alo - aB : (aB > ahi ? aB - ahi : 0.0);
+    double tmin = d - g->xstar;
+    if (!(tmin > 0)) return;                          /* near Bragg: the plain stream */
+    if (tmin > 0.5 * PI) tmin = 0.5 * PI;
+    double sh = sin(0.5 * tmin);
+    b->qmin = 2.0 * sh * sh;
+    b->w0 = word_floor(g->mdf, b->qmin);
+    uint64_t w1 = word_ceil(g->mdf, 2.0 - b->qmin);
+    b->wspan = w1 > b->w0 ? w1 - b->w0 : 0;
+    b->S1 = sin(fmax(0.0, aB - g->xstar));
+    b->S2 = sin(fmin(0.5 * PI, aB + g->xstar));
+    double bmin = cos(ahi) * sin(tmin);
+    double w = (b->S2 - b->S1) / bmin;
+    b->pbar = (w >= 2.0 || !(bmin > 0)) ? 1.0 : fmin(1.0, 2.0 * acos(1.0 - w) / PI);
+    double QR = rc->Q * g->irc_max;
+    double PA = (double)b->wspan / 4294967296.0;
+    double la = QR * g->vstar, lb = QR * (1.0 - g->vstar) * PA * b->pbar;
+    b->vstar = g->vstar;
+    b->mu = rc->mu0 + (la + lb);
+    b->pa = rc->mu0 / b->mu;
+    b->ra = la / (la + lb);
+}
+
+/* arc measure P_xi (in units of pi) of the azimuths xi' in [0, pi] with
+ * |a + b cos xi'| in (S1, S2); the arcs themselves in arc[4] (start, length) */
+static double azimuth_arcs(double a, double b, double S1, double S2, double arc[4]) {
+    double iv[2][2] = {{(S1 - a) / b, (S2 - a) / b}, {(-S2 - a) / b, (-S1 - a) / b}};
+    double tot = 0.0;
+    for (int j = 0; j < 2; ++j) {
+        double l = fmax(-1.0, iv[j][0]), h = fmin(1.0, iv[j][1]);
+        arc[2 * j] = 0.0;
+        arc[2 * j + 1] = 0.0;
+        if (l < h) {
+            arc[2 * j] = acos(h);
+            arc[2 * j + 1] = acos(l) - acos(h);
+            tot += arc[2 * j + 1];
+        }
+    }
+    return tot / PI;
+}
+
 /* the depth walk of one ray from its entry point (Sec. 2.2.4) */
 static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[3], int pol, double p[3],
                  wsrc *ws, orc_record *rec) {
@@ -721,11 +867,13 @@ static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[
     int nrefl = 0;
     int64_t ncoll = 0;
     int outcome = ORC_STUCK;
+    seg_bound sb;
+    bound_segment(g, rc, x, k, &sb);
     for (;;) {
         if (ncoll >= s->max_collisions) { outcome = ORC_STUCK; break; }
         uint32_t w[4];
         if (!next4(ws, w)) { outcome = ORC_STUCK; break; }
-        double l = -log(U(w[0])) / rc->mubar;          /* Eq. (AnyEvent) with the majorant */
+        double l = -log(U(w[0])) / sb.mu;              /* Eq. (AnyEvent) with the majorant */
         int face;
         double se = exit_distance(g, x, k, &face);
         if (l > se) {                                   /* leaves before the event */
@@ -736,13 +884,33 @@ static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[
         for (int i = 0; i < 3; ++i) x[i] += l * k[i];
         ++ncoll;
         double u1 = U(w[1]);
-        if (u1 < rc->p_abs) { outcome = ORC_ABSORBED; break; }
-        double v = (u1 - rc->p_abs) / (1.0 - rc->p_abs);
+        if (u1 < sb.pa) { outcome = ORC_ABSORBED; break; }
+        double v = (u1 - sb.pa) / (1.0 - sb.pa);
         double N[3], t1[3], t2[3];
         local_frame(g, x, N, t1, t2);
-        double q = orc_mdf_table_lookup(g->mdf, w[2]);
+        double q, xi;
+        if (v < sb.ra) {                                 /* process (a), or the plain stream */
+            v = sb.ra < 1.0 ? (v / sb.ra) * sb.vstar : v;
+            q = orc_mdf_table_lookup(g->mdf, w[2]);
+            xi = 2.0 * PI * U(w[3]);
+        } else {                                         /* process (b) */
+            v = sb.vstar + (1.0 - sb.vstar) * ((v - sb.ra) / (1.0 - sb.ra));
+            uint32_t wq = (uint32_t)(sb.w0 + (((uint64_t)w[2] * sb.wspan) >> 32));
+            q = orc_mdf_table_lookup(g->mdf, wq);
+            if (q < sb.qmin || q > 2.0 - sb.qmin) continue;    /* cannot reflect */
+            double kN = dot3(k, N), sa_ = fabs(kN), ca_ = sqrt(fmax(0.0, 1.0 - kN * kN));
+            double a = (kN < 0 ? -sa_ : sa_) * (1.0 - q), b = ca_ * sqrt(q * (2.0 - q));
+            double arc[4];
+            double Pxi = azimuth_arcs(a, b, sb.S1, sb.S2, arc);
+            double t3 = U(w[3]);
+            if (!(t3 * sb.pbar < Pxi)) continue;            /* outside the arcs: cannot reflect */
+            double L = arc[1] + arc[3];
+            double pos = (t3 * sb.pbar / Pxi) * 2.0 * L, sgn = 1.0;
+            if (pos >= L) { pos -= L; sgn = -1.0; }
+            double xp = pos < arc[1] ? arc[0] + pos : arc[2] + (pos - arc[1]);
+            xi = atan2(dot3(k, t2), dot3(k, t1)) + sgn * xp;
+        }
         double ct = 1.0 - q, st = sqrt(q * (2.0 - q));
-        double xi = 2.0 * PI * U(w[3]);
         double cx = cos(xi), sx = sin(xi);
         double n[3];
         for (int i = 0; i < 3; ++i) n[i] = ct * N[i] + st * (cx * t1[i] + sx * t2[i]);
@@ -773,6 +941,7 @@ static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[
                 for (int i = 0; i < 3; ++i) p[i] = (p[i] - pk * k[i]) / d;
                 normalize3(p);
             }
+            bound_segment(g, rc, x, k, &sb);             /* a new straight segment */
         }
     }
     rec->outcome = outcome;
