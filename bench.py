@@ -30,6 +30,7 @@ UNIT = "rays/s"
 # algorithmic work per unit ("Roofline"): lane-instructions
 INSTR_PER_COLLISION = 110      # Philox4x32-10 (60 int) + free path, table, sin/cos, Bragg offset, IRC, accept (~50)
 INSTR_PER_RAY = 240            # two Philox blocks, source, entry, per-ray constants, detector, tallies
+INSTR_PER_SEGMENT = 120        # exit distance, grazing-angle range, tilt bound, table search, majorant
 SM_COUNT = 152
 LANES_PER_SM_CLK = 128         # 4 SM sub-partitions x 32 lanes, one warp-instruction issue each per clock
 SM_MAX_MHZ = 2070.0
@@ -330,6 +331,8 @@ def main():
                         stream=stream)
     coll_per_ray = tal["collisions"] / n
     det_frac = tal["det_hits"] / n
+    # straight segments: one per entered ray plus one per reflection
+    seg_per_ray = ((n - tal["miss"]) + sum(h * c for h, c in enumerate(tal["refl_hist"]))) / n
 
     # end to end through the C ABI with host buffers (copies inside the call)
     h_img = np.zeros(spec.shape, dtype=np.int32)
@@ -344,7 +347,7 @@ def main():
     img_bytes = h_img.nbytes
 
     # roofline: issue-bound (FP32 / integer / SFU instructions), algorithmic count
-    per_launch = INSTR_PER_COLLISION * coll_per_ray * n + INSTR_PER_RAY * n
+    per_launch = (INSTR_PER_COLLISION * coll_per_ray + INSTR_PER_SEGMENT * seg_per_ray + INSTR_PER_RAY) * n
     mean_launch_s = total_max / args.steps
     achieved = per_launch / mean_launch_s / 1e12                  # tera lane-instructions / s
     peak = SM_COUNT * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
@@ -364,7 +367,9 @@ def main():
             "config": {"workload": w["name"], "rays_per_step": n, "precision": "fp32",
                        "detector": "%dx%d int32" % (w["spec"]["det_ny"], w["spec"]["det_nx"]),
                        "launch": tune,
-                       "collisions_per_ray": coll_per_ray, "det_hits_per_ray": det_frac,
+                       "sampler": "thinned",
+                       "collisions_per_ray": coll_per_ray, "segments_per_ray": seg_per_ray,
+                       "det_hits_per_ray": det_frac,
                        "detector_hits_per_s": value * det_frac,
                        "l2": "inputs are per-ray counters (no input data); the 4 MB image stays in L2"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-instr/s",
@@ -373,7 +378,8 @@ def main():
                                          "staging per block, does not grow with rays",
                          "kernel": "k_trace_fp32 (persistent, one launch per step)",
                          "peak_basis": "152 SMs x 128 lanes x 2070 MHz (max SM clock); algorithmic "
-                                       "%d instr/collision + %d instr/ray" % (INSTR_PER_COLLISION, INSTR_PER_RAY)},
+                                       "%d instr/collision + %d instr/segment + %d instr/ray"
+                                       % (INSTR_PER_COLLISION, INSTR_PER_SEGMENT, INSTR_PER_RAY)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": img_bytes,
                     "d2h_bytes_per_step": img_bytes + 27 * 8,
                     "path": "heart_trace_host (host image uploaded, traced, downloaded each step)"},

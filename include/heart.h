@@ -75,6 +75,14 @@ typedef enum {
 } heart_irc;
 
 typedef enum { HEART_FP64 = 0, HEART_FP32 = 1 } heart_precision;
+
+/* Candidate sampler of the depth walk.  THINNED (the default) never draws,
+ * per straight segment, the tentative collisions that provably cannot reflect
+ * (crystallite tilts and azimuths whose |Delta| exceeds the rocking curve's
+ * half-width X* at relative level v*): the same distribution of paths as
+ * PLAIN, the constant-majorant walk of Sec. 2.2.3-2.2.4, with several times
+ * fewer candidates off the Bragg angle. */
+typedef enum { HEART_SAMPLER_THINNED = 0, HEART_SAMPLER_PLAIN = 1 } heart_sampler;
 typedef enum { HEART_COUNT_I32 = 0, HEART_COUNT_I64 = 1 } heart_count_type;
 
 /* spectral component kinds (Sec. 2.1: an intensity profile used as a PDF) */
@@ -139,7 +147,8 @@ typedef struct {
     int32_t det_nx, det_ny;
     double pixel_mm;
     int32_t count_type;             /* heart_count_type of images traced with this handle */
-    int32_t reserved;
+    int32_t sampler;                /* heart_sampler */
+    double thin_vstar;              /* THINNED: relative IRC level v* in (0, 1); 0: 2^-10 */
 } heart_spectrometer_desc;
 
 typedef struct {
@@ -280,7 +289,7 @@ heart_status heart_trace_batch(heart_spectrometer *const *specs, const heart_sou
 
 /* Launch shape of the FP32 kernel chosen by heart_autotune. */
 typedef struct {
-    int32_t blocks_per_sm;          /* resident 128-thread blocks per SM: 6 (80 registers) or 8 (64) */
+    int32_t blocks_per_sm;          /* resident 128-thread blocks per SM: 6 (80 registers) or 5 (96) */
     int32_t refill_lanes;           /* a warp pops spawned rays when this many lanes are idle */
     uint32_t max_chunk_rays;        /* largest work item (rays) a block claims */
     int32_t reserved;

@@ -202,7 +202,7 @@ def make_spec(d):
     s.det_nx = d["det_nx"]
     s.det_ny = d["det_ny"]
     s.pixel_mm = d["pixel_mm"]
-    s.sampler = SAMPLER[d.get("sampler", "plain")]
+    s.sampler = SAMPLER[d.get("sampler", "thinned")]
     s.thin_vstar = d.get("thin_vstar", 0.0)
     return s
 

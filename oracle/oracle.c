@@ -758,13 +758,15 @@ static int next4(wsrc *ws, uint32_t w[4]) {
  *   (c) the rest, which cannot reflect: with |Delta| >= X*, R / R_max <= v* <= v.
  * On a straight segment the ray's grazing angle stays in [a_lo, a_hi]; a
  * crystallite tilted by theta has asin|k.n| within theta of it, so if
- * theta < d - X* (d = distance of alpha_B + Delta_M from [a_lo, a_hi]) then
- * |Delta| >= X*.  Process (c) is never generated.  Process (b) is generated
- * at rate Q R_max (1 - v*) P_A pbar: n's table word uniform over a word range
- * covering [q_min, 2 - q_min] (mass P_A), then kept with probability
- * P_xi(theta) / pbar (P_xi: the arc measure, pbar >= P_xi on the segment), its
- * azimuth uniform over the arcs.  A segment with d <= X* keeps the plain
- * candidate stream (v* = 1). */
+ * theta < d - X* (d <= the distance of alpha_B + Delta_M from [a_lo, a_hi])
+ * then |Delta| >= X*.  d is taken between the sines, which is never larger
+ * than between the angles (asin has slope >= 1).  Process (c) is never
+ * generated.  Process (b) is generated at rate Q R_max (1 - v*) P_A pbar:
+ * n's table word uniform over [w0, 2^32) (mass P_A), w0 the first word of
+ * the table interval holding the grid point q_j = 2^(j/8 - 48) just below
+ * q_min; then kept with probability P_xi(theta) / pbar (P_xi: the arc
+ * measure, pbar >= P_xi on the segment), its azimuth uniform over the arcs.
+ * A segment with d <= X* keeps the plain candidate stream (v* = 1). */
 typedef struct {
     double mu, pa;            /* majorant of the segment and the absorption share mu0 / mu */
     double ra, vstar;         /* share of process (a) among scatter candidates, its v range */
@@ -785,16 +787,13 @@ static uint64_t word_floor(const orc_mdf_table *t, double q) {
     return (uint64_t)lo << 20;
 }
 
-/* one past the last word of the table interval containing q (conservative upper end) */
-static uint64_t word_ceil(const orc_mdf_table *t, double q) {
-    if (!(q < t->body[ORC_MDF_M - 1])) return 1ull << 32;
-    int lo = 0, hi = ORC_MDF_M - 1;            /* body[lo] <= q < body[hi] */
-    if (!(t->body[0] <= q)) return 1ull << 20;
-    while (hi - lo > 1) {
-        int m = (lo + hi) / 2;
-        if (t->body[m] <= q) lo = m; else hi = m;
-    }
-    return (uint64_t)hi << 20;
+/* w0 for a tilt bound q_min: the grid point q_j = 2^(j/8 - 48) just below it
+ * (j = floor(8 log2 q_min) + 384, at most 391), then its table interval */
+static uint64_t word_floor_grid(const orc_mdf_table *t, double qmin) {
+    if (!(qmin >= exp2(-48.0))) return 0;
+    int j = (int)floor(8.0 * log2(qmin)) + 384;
+    if (j > 391) j = 391;
+    return word_floor(t, exp2(j / 8.0 - 48.0));
 }
 
 static void bound_segment(const geom *g, const orc_ray_consts *rc, const double x[3], const double k[3],
@@ -817,20 +816,21 @@ static void bound_segment(const geom *g, const orc_ray_consts *rc, const double 
     double k0 = dot3(k, N0), k1 = dot3(k, N1);
     double lo = fmin(fabs(k0), fabs(k1)), hi = fmax(fabs(k0), fabs(k1));
     if ((k0 < 0) != (k1 < 0)) lo = 0.0;             /* k.N is monotone along a line: it crossed 0 */
-    double alo = asin(fmin(lo, 1.0)), ahi = asin(fmin(hi, 1.0));
     double aB = rc->alpha_B + s->irc_shift_rad;
-    double d = aB < alo ? alo - aB : (aB > ahi ? aB - ahi : 0.0);
+    double sB = sin(aB);
+    double d = sB < lo ? lo - sB : (sB > hi ? sB - hi : 0.0);
     double tmin = d - g->xstar;
     if (!(tmin > 0)) return;                          /* near Bragg: the plain stream */
     if (tmin > 0.5 * PI) tmin = 0.5 * PI;
     double sh = sin(0.5 * tmin);
     b->qmin = 2.0 * sh * sh;
-    b->w0 = word_floor(g->mdf, b->qmin);
-    uint64_t w1 = word_ceil(g->mdf, 2.0 - b->qmin);
-    b->wspan = w1 > b->w0 ? w1 - b->w0 : 0;
+    b->w0 = word_floor_grid(g->mdf, b->qmin);
+    b->wspan = (1ull << 32) - b->w0;
     b->S1 = sin(fmax(0.0, aB - g->xstar));
     b->S2 = sin(fmin(0.5 * PI, aB + g->xstar));
-    double bmin = cos(ahi) * sin(tmin);
+    double bmin = sqrt(fmax(0.0, 1.0 - fmin(hi, 1.0) * fmin(hi, 1.0))) * sin(tmin);
+    /* each of the two |k.n| windows spans w = (S2 - S1) / b in cos(xi'); an
+     * interval of that width has arcsine measure at most acos(1 - w) / pi */
     double w = (b->S2 - b->S1) / bmin;
     b->pbar = (w >= 2.0 || !(bmin > 0)) ? 1.0 : fmin(1.0, 2.0 * acos(1.0 - w) / PI);
     double QR = rc->Q * g->irc_max;

@@ -28,6 +28,7 @@ IRC = {"darwin": 0, "darwin_prins": 1, "pseudo_voigt": 2, "gaussian": 3, "lorent
 SRC = {"mono": 0, "gauss": 1, "lorentz": 2, "inv_e": 3, "uniform": 4, "table": 5}
 PRECISION = {"fp64": 0, "fp32": 1}
 COUNT = {"i32": 0, "i64": 1}
+SAMPLER = {"thinned": 0, "plain": 1}
 STATUS = {0: "HEART_OK", 1: "HEART_EINVAL", 2: "HEART_ENOMEM", 3: "HEART_ECUDA", 4: "HEART_EBUSY",
           5: "HEART_ETIMEOUT", 6: "HEART_ELIMIT", 7: "HEART_ENOTFOUND"}
 OUTCOME = {0: "miss", 1: "absorbed", 2: "exit_front", 3: "exit_back", 4: "exit_side",
@@ -52,7 +53,7 @@ class heart_spectrometer_desc(C.Structure):
         ("max_collisions", C.c_int64),
         ("det_centre_mm", D3), ("det_u", D3), ("det_v", D3),
         ("det_nx", C.c_int32), ("det_ny", C.c_int32), ("pixel_mm", C.c_double),
-        ("count_type", C.c_int32), ("reserved", C.c_int32),
+        ("count_type", C.c_int32), ("sampler", C.c_int32), ("thin_vstar", C.c_double),
     ]
 
 
@@ -218,6 +219,8 @@ def make_desc(d):
     s.det_ny = d["det_ny"]
     s.pixel_mm = d["pixel_mm"]
     s.count_type = COUNT[d.get("count_type", "i32")]
+    s.sampler = SAMPLER[d.get("sampler", "thinned")]
+    s.thin_vstar = d.get("thin_vstar", 0.0)
     return s
 
 

@@ -152,6 +152,29 @@ using namespace heart;
 // ---------------------------------------------------------------------------
 extern "C" const char *heart_last_error(void) { return g_last_error.c_str(); }
 
+// X*: the smallest |x| with R(x') / R_max <= v* for all |x'| >= X* (the
+// rocking curves are even and fall off monotonically outside their core):
+// walk |x| down from 1 rad in steps of 1/2000 relative until R / R_max
+// exceeds v*, bisect that step, widen the result by 1e-6 relative
+static double rocking_half_width(const SpecParams &S) {
+    auto rel = [&](double x) { return irc64(S, x) / S.irc_max; };
+    double x = 1.0;
+    if (rel(x) > S.vstar) return -1.0;
+    for (;;) {
+        const double y = x / 1.0005;
+        if (y < 1e-12) return 1e-12;
+        if (rel(y) > S.vstar) {
+            double lo = y, hi = x;
+            for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+                const double m = 0.5 * (lo + hi);
+                if (rel(m) > S.vstar) lo = m; else hi = m;
+            }
+            return hi * (1.0 + 1e-6);
+        }
+        x = y;
+    }
+}
+
 extern "C" heart_status heart_spectrometer_create(const heart_spectrometer_desc *desc, heart_spectrometer **out) {
     if (!out) return fail(HEART_EINVAL, "null output pointer");
     *out = nullptr;
@@ -160,21 +183,44 @@ extern "C" heart_status heart_spectrometer_create(const heart_spectrometer_desc 
     char err[256] = {0};
     heart_status st = build_spec_params(desc, &p, tab.data(), err, (int)sizeof err);
     if (st != HEART_OK) return fail(st, err);
+    if (p.sampler == HEART_SAMPLER_THINNED) {
+        p.xstar = rocking_half_width(p);
+        if (!(p.xstar > 0)) return fail(HEART_EINVAL, "rocking curve does not fall below v* within 1 rad");
+    }
     std::vector<float> tab32(kMdfKnots);
     for (int i = 0; i < kMdfKnots; ++i) tab32[i] = (float)tab[i];
     heart_spectrometer *h = new (std::nothrow) heart_spectrometer();
     if (!h) return fail(HEART_ENOMEM, "host allocation failed");
     cudaError_t e;
     if ((e = cudaGetDevice(&h->device)) != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
-    // [FP64 table][FP32 table, padded to 8 bytes][scratch words]
+    // thinned sampler: first table word of the interval holding each grid point
+    // q_j = 2^(j/8 - 48) (the body knots are ascending; at or past the last one: the tail)
+    std::vector<uint32_t> qgrid(kQGrid);
+    for (int j = 0; j < kQGrid; ++j) {
+        const double q = std::exp2(j / 8.0 - 48.0);
+        uint32_t w = (uint32_t)(kMdfM - 1) << 20;
+        if (q < tab[kMdfM - 1]) {
+            int lo = 0, hi = kMdfM - 1;
+            if (!(tab[0] <= q)) { lo = 0; hi = 0; }
+            while (hi - lo > 1) {
+                const int m = (lo + hi) / 2;
+                if (tab[m] <= q) lo = m; else hi = m;
+            }
+            w = (uint32_t)lo << 20;
+        }
+        qgrid[j] = w;
+    }
+    // [FP64 table][FP32 table, padded to 8 bytes][scratch words][tilt grid words]
     size_t bytes = kMdfKnots * sizeof(double) + (kMdfKnots + (kMdfKnots & 1)) * sizeof(float) +
-                   kScratchWords * sizeof(unsigned long long);
+                   kScratchWords * sizeof(unsigned long long) + kQGrid * sizeof(uint32_t);
     if ((e = cudaMalloc(&h->d_block, bytes)) != cudaSuccess) { delete h; return cuda_fail(e, "cudaMalloc tables"); }
     h->d_tab64 = (double *)h->d_block;
     h->d_tab32 = (float *)(h->d_tab64 + kMdfKnots);
     h->d_scratch = (unsigned long long *)(h->d_tab32 + kMdfKnots + (kMdfKnots & 1));
+    uint32_t *d_qgrid = (uint32_t *)(h->d_scratch + kScratchWords);
     if ((e = cudaMemcpy(h->d_tab64, tab.data(), kMdfKnots * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(h->d_tab32, tab32.data(), kMdfKnots * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        (e = cudaMemcpy(h->d_tab32, tab32.data(), kMdfKnots * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(d_qgrid, qgrid.data(), kQGrid * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess) {
         cudaFree(h->d_block);
         delete h;
         return cuda_fail(e, "cudaMemcpy tables");
@@ -186,6 +232,7 @@ extern "C" heart_status heart_spectrometer_create(const heart_spectrometer_desc 
     }
     p.mdf64 = h->d_tab64;
     p.mdf32 = h->d_tab32;
+    p.qgrid = d_qgrid;
     h->p = p;
     h->desc = *desc;
     *out = h;

@@ -41,7 +41,8 @@ namespace heart {
 
 constexpr int kWarpsPerBlock = 4;
 constexpr int kBlockThreads = kWarpsPerBlock * 32;
-constexpr int kBuf = 64;                 // spawned rays buffered per warp
+constexpr int kBuf = 48;                 // spawned rays buffered per warp
+constexpr int kSpawnBelow = 16;          // spawn only while fewer are buffered (so <= 16 + 31 < kBuf)
 
 TuneConfig g_tune;                        // launch shape picked by the autotuner
 
@@ -82,6 +83,7 @@ struct Launch32 {
     int32_t refill;                       // pop when at least this many lanes are idle
     int32_t geometry, irc_kind;
     const float *tab;
+    const uint32_t *qgrid;                // tilt-grid table words (thinned sampler)
     void *img;                            // this job's image (int32 or int64)
     unsigned long long *tally;            // this job's kTallyN tally words
     heart_ray_record *rec;                // per-ray records or nullptr
@@ -89,6 +91,10 @@ struct Launch32 {
     int32_t n_qe, pad_qe;
     float qe_e[kMaxQe], qe_v[kMaxQe];     // detector QE knots
     double fc[3], fa[3][3];               // local -> global frame (records, user rays)
+    // thinned candidates: sampler, v*, X* and the window constants
+    // 2 sin^2(X*/2), sin X* (the |k.n| window of |Delta| < X* from sin(aB + dM))
+    int32_t sampler;
+    float vstar, xstar, hx2, sx;
     // polarisation and user-supplied rays (the extended kernel only)
     int32_t pol_on, user;
     float pol[3];                         // source polarisation, local frame
@@ -104,9 +110,13 @@ struct Launch32 {
 // a spawned ray waiting for a lane (SoA per warp)
 struct WarpBuf {
     float x[3][kBuf], k[3][kBuf];
-    float A[kBuf], sB[kBuf], inv_mu[kBuf], pa[kBuf], E[kBuf];
-    uint32_t rl[kBuf], rh[kBuf], pa_thr[kBuf];
+    float A[kBuf], sB[kBuf], mu0[kBuf], qr[kBuf], E[kBuf];
+    uint32_t rl[kBuf], rh[kBuf];
     int32_t nb[kBuf];
+    // the first segment, prepared while the warp spawns together
+    float s_exit[kBuf], inv_mu[kBuf], pa[kBuf], ra[kBuf], qmin[kBuf], pbar[kBuf];
+    uint32_t w0[kBuf];
+    int32_t face[kBuf];
     int count;
 };
 
@@ -233,8 +243,13 @@ struct Lane {
     float x0[3], k[3];                    // segment start and direction, crystal frame
     float A, sgn, sB, cB;                 // Bragg anchor, sign of k.N, sin / cos of aB + Delta_M
     float s_exit, Lsum, Lcomp;            // exit distance, Kahan sum of the path
-    float inv_mu, pa, inv_1mpa, E;
+    float inv_mu, pa, inv_1mpa, E;        // segment majorant: 1 / mu, mu0 / mu, 1 / (1 - mu0 / mu)
     uint32_t pa_thr, rl, rh, call;
+    float mu0, qr;                        // per ray: absorption rate, Q R_max
+    // thinned segment: share of process (a) (1: the plain stream), tilt bound,
+    // arc bound, first table word of process (b) (its words are [w0, 2^32))
+    float ra, qmin, pbar;
+    uint32_t w0;
     int32_t face, nrefl, ncoll, no_bragg;
     // cylinder: depth below the inner face at x0 and along-segment constants of k.N
     float rho0, cb1, cb2, cga, ck0, ctau0;
@@ -242,16 +257,10 @@ struct Lane {
     bool pol;
 };
 
-// absorption and majorant of a ray of energy E (Sec. 2.2.4): 1 / mu_bar, the
-// absorption probability pa and its integer threshold on the raw word
-__device__ __forceinline__ void absorb_consts(const Launch32 &L, float E, float Q, int nb, float &inv_mu, float &pa,
-                                              uint32_t &pa_thr) {
-    const float mu0 = 1.0f / (L.labs * __powf(E / L.labs_ref, L.labs_pow));
-    const float mubar = __fmaf_rn(Q, L.irc_max, mu0);
-    inv_mu = 1.0f / mubar;
-    pa = nb ? 1.0f : mu0 / mubar;
-    // absorb iff (w + 1/2) 2^-32 < pa  <=>  w < ceil(pa 2^32 - 1/2)
-    pa_thr = nb ? 0xFFFFFFFFu : __float2uint_ru(fminf(pa * 4294967296.0f, 4294967040.0f));
+// absorption rate mu0 and scatter-candidate rate Q R_max of a ray of energy E (Sec. 2.2.4)
+__device__ __forceinline__ void ray_rates(const Launch32 &L, float E, float Q, int nb, float &mu0, float &qr) {
+    mu0 = 1.0f / (L.labs * __powf(E / L.labs_ref, L.labs_pow));
+    qr = nb ? 0.0f : Q * L.irc_max;
 }
 
 // ---------------------------------------------------------------------------
@@ -259,7 +268,7 @@ __device__ __forceinline__ void absorb_consts(const Launch32 &L, float E, float 
 // ---------------------------------------------------------------------------
 template <int GEOM_T>
 __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3], float k[3], float &A,
-                                      float &sB, float &inv_mu, float &pa, uint32_t &pa_thr, float &E32, int &nb) {
+                                      float &sB, float &mu0, float &qr, float &E32, int &nb) {
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
     const uint32_t rl = (uint32_t)ray, rh = (uint32_t)(ray >> 32);
     uint32_t a[4], b[4];
@@ -380,7 +389,7 @@ __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3
         sB = 2.0f;
         A = 0.0f;
     }
-    absorb_consts(L, E, Q, nb, inv_mu, pa, pa_thr);
+    ray_rates(L, E, Q, nb, mu0, qr);
     return true;
 }
 
@@ -390,8 +399,7 @@ __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3
 // polarisation projected perpendicular to k, zero if unpolarised
 template <int GEOM_T>
 __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float x[3], float k[3], float p[3],
-                                           float &A, float &sB, float &inv_mu, float &pa, uint32_t &pa_thr,
-                                           float &E32, int &nb) {
+                                           float &A, float &sB, float &mu0, float &qr, float &E32, int &nb) {
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
     double E = L.ray[6][id], og[3], kg[3], ol[3], kl[3];
     for (int i = 0; i < 3; ++i) { og[i] = L.ray[i][id] - L.fc[i]; kg[i] = L.ray[3 + i][id]; }
@@ -454,7 +462,7 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
         sB = 2.0f;
         A = 0.0f;
     }
-    absorb_consts(L, E32, Q, nb, inv_mu, pa, pa_thr);
+    ray_rates(L, E32, Q, nb, mu0, qr);
     return true;
 }
 
@@ -470,12 +478,132 @@ __device__ __forceinline__ void project_pol32(const Launch32 &L, const float k[3
     for (int i = 0; i < 3; ++i) p[i] *= sc;
 }
 
+// the |k.n| window of |Delta| < X*: (sB + e1, sB + e2), clipped to [0, 1]
+__device__ __forceinline__ void bragg_window(const Launch32 &L, float sB, float cB, float &e1, float &e2) {
+    e1 = sB <= L.sx ? -sB : __fmaf_rn(-sB, L.hx2, -cB * L.sx);
+    e2 = cB <= L.sx ? 1.0f - sB : __fmaf_rn(-sB, L.hx2, cB * L.sx);
+}
+
+// acos(m / b) for b > 0, clamped to [0, pi]; near y = +-1 from the small
+// differences b -+ m, where acosf of the rounded ratio loses sqrt(ulp)
+__device__ __forceinline__ float acos_ratio(float m, float b) {
+    if (m >= b) return 0.0f;
+    if (m <= -b) return 3.14159265f;
+    const float y = m / b;
+    if (y > 0.5f) return 2.0f * asinf(sqrtf((b - m) / (2.0f * b)));
+    if (y < -0.5f) return 3.14159265f - 2.0f * asinf(sqrtf((b + m) / (2.0f * b)));
+    return acosf(y);
+}
+
+// Process (b), azimuth: the arcs of xi' in [0, pi] whose cos lies in
+// (iv0, iv1) / b or (iv2, iv3) / b; keep the candidate iff t3 pbar < P_xi (the
+// arc measure in units of pi), then place xi' uniformly over the arcs (sign
+// from the second half of the conditional uniform).  Out of line: rarely run.
+// Returns (kept, cos xi', sin xi', sign).
+__device__ __noinline__ float4 arc_sample(float iv0, float iv1, float iv2, float iv3, float b, float t3pbar) {
+    const float iv[4] = {iv0, iv1, iv2, iv3};
+    float start[2], len[2];
+    for (int j = 0; j < 2; ++j) {
+        start[j] = 0.0f;
+        len[j] = 0.0f;
+        if (iv[2 * j] < iv[2 * j + 1] && iv[2 * j] < b && iv[2 * j + 1] > -b) {
+            start[j] = acos_ratio(iv[2 * j + 1], b);
+            len[j] = acos_ratio(iv[2 * j], b) - start[j];
+        }
+    }
+    const float arcs = len[0] + len[1];
+    const float pxi = arcs * 0.318309886f;
+    if (!(t3pbar < pxi)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float pos = (t3pbar / pxi) * 2.0f * arcs, sg = 1.0f;
+    if (pos >= arcs) { pos -= arcs; sg = -1.0f; }
+    const float xp = pos < len[0] ? start[0] + pos : start[1] + (pos - len[0]);
+    float sxp, cxp;
+    sincosf(xp, &sxp, &cxp);
+    return make_float4(1.0f, cxp, sxp, sg);
+}
+
+// first table word of process (b): that of the tilt-grid point q_j = 2^(j/8 - 48) just below q_min
+__device__ __forceinline__ uint32_t tilt_word32(const Launch32 &L, float qmin) {
+    if (!(qmin >= 3.5527137e-15f)) return 0u;
+    const int j = min((int)floorf(8.0f * __log2f(qmin)) + 384, kQGrid - 1);
+    return L.qgrid[j];
+}
+
+// Majorant of a straight segment.  Plain: mu0 + Q R_max.  Thinned: the
+// scatter candidates split by their marks (v, n) into (a) v < v*, tested as
+// usual; (b) v >= v*, tilt q in [q_min, 2 - q_min] and azimuth in the arcs
+// where |Delta| < X*; (c) the rest, which cannot reflect and are never drawn.
+// |k.N| stays in [s_lo, s_hi] on the segment (k.N is monotone along a line); a
+// tilt theta < d - X*, d the distance of sin(aB + dM) from that range (never
+// more than the angular distance), keeps |Delta| >= X*.  Segments with
+// d <= X* keep the plain stream.  |k.N| is taken relative to sin(aB + dM)
+// from the small anchors.
+__device__ __forceinline__ void thin_segment(const Launch32 &L, Lane &s, float A_exit, bool flip) {
+    float la = s.qr, lb = 0.0f;
+    s.ra = 1.0f;
+    if (L.sampler == HEART_SAMPLER_THINNED && s.qr > 0.0f) {
+        // |k.N| at the exit is sB + A_exit, or -(sB + A_exit) if k.N changed sign
+        const float Ae = flip ? -2.0f * s.sB - A_exit : A_exit;
+        const float lo = flip ? -s.sB : fminf(s.A, Ae);   // relative to sB; |k.N| passes 0 on a flip
+        const float hi = fmaxf(s.A, Ae);
+        const float d = lo > 0.0f ? lo : (hi < 0.0f ? -hi : 0.0f);
+        float tmin = d - L.xstar;
+        if (tmin > 0.0f) {
+            tmin = fminf(tmin, 1.57079637f);
+            // sin to float precision: a short series below 0.1 rad, the SFU above (far off Bragg)
+            const float h = 0.5f * tmin, h2 = h * h;
+            const float sh = tmin < 0.1f ? h * __fmaf_rn(h2, __fmaf_rn(h2, 8.33333333e-3f, -0.166666667f), 1.0f)
+                                         : __sinf(h);
+            const float st = 2.0f * sh * sqrtf(fmaxf(0.0f, __fmaf_rn(-sh, sh, 1.0f)));   // sin(theta_min)
+            s.qmin = 2.0f * sh * sh;
+            s.w0 = tilt_word32(L, s.qmin);
+            // arc bound: two |k.n| windows of width S2 - S1 over b >= cos(a_hi) sin(theta_min)
+            const float shi = fminf(s.sB + hi, 1.0f);
+            const float bmin = sqrtf(fmaxf(0.0f, __fmaf_rn(-shi, shi, 1.0f))) * st * 0.999999f;
+            float e1, e2;
+            bragg_window(L, s.sB, s.cB, e1, e2);
+            // two windows of width w in cos(xi'), each of arc measure <= acos(1 - w) / pi
+            const float w = (e2 - e1) / bmin;
+            s.pbar = (w >= 2.0f || !(bmin > 0.0f)) ? 1.0f : fminf(1.0f, 0.636619772f * acosf(1.0f - w) * 1.000001f);
+            la = s.qr * L.vstar;
+            lb = s.qr * (1.0f - L.vstar) * ((float)((1ull << 32) - s.w0) * 2.3283064365386963e-10f) * s.pbar;
+            s.ra = la / (la + lb);
+        }
+    }
+    const float mu = s.mu0 + (la + lb);
+    s.inv_mu = 1.0f / mu;
+    s.pa = s.mu0 / mu;
+    s.inv_1mpa = s.pa < 1.0f ? 1.0f / (1.0f - s.pa) : 0.0f;
+    // absorb iff (w + 1/2) 2^-32 < pa  <=>  w < ceil(pa 2^32 - 1/2)
+    s.pa_thr = s.pa >= 1.0f ? 0xFFFFFFFFu : __float2uint_ru(fminf(s.pa * 4294967296.0f, 4294967040.0f));
+}
+
 // start a straight segment at x0 along k; s.A, s.sgn, s.sB and (cylinder) s.rho0 are set
+// cylinder: constants of k.N along the segment from x0: r(l)^2 = r0^2 (1 + l (cb1 + l cb2))
 template <int GEOM_T>
-__device__ __forceinline__ void segment(const Launch32 &L, Lane &s) {
+__device__ __forceinline__ void segment_consts(const Launch32 &L, Lane &s) {
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
     s.Lsum = 0.0f;
     s.Lcomp = 0.0f;
+    if (GEOM != HEART_FLAT) {
+        const float r0 = L.R + s.rho0;
+        const float X = s.x0[1], Y = s.x0[2];
+        const float kappa = s.sgn * (s.sB + s.A);           // k.N at x0
+        const float aa = __fmaf_rn(s.k[1], s.k[1], s.k[2] * s.k[2]);
+        const float bb = -kappa * r0;                        // (X, Y) . (kX, kY)
+        const float ir0 = 1.0f / r0;
+        s.cb1 = 2.0f * bb * ir0 * ir0;
+        s.cb2 = aa * ir0 * ir0;
+        s.cga = aa * ir0;
+        s.ck0 = kappa;
+        s.ctau0 = (X * s.k[2] - Y * s.k[1]) * ir0;          // k . t2 at x0 (t2 = N x axis)
+    }
+}
+
+template <int GEOM_T>
+__device__ __forceinline__ void segment(const Launch32 &L, Lane &s) {
+    const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
+    segment_consts<GEOM_T>(L, s);
     float best = 3.0e38f;
     int face = HEART_EXIT_SIDE;
     auto cand = [&](float v, int f) {
@@ -515,16 +643,21 @@ __device__ __forceinline__ void segment(const Launch32 &L, Lane &s) {
         if (rp > 0) cand(-gp / rp, HEART_EXIT_SIDE);
         const float gm = -X * L.sphi - Y * L.cphi, rm = -s.k[1] * L.sphi - s.k[2] * L.cphi;
         if (rm > 0) cand(-gm / rm, HEART_EXIT_SIDE);
-        // k.N along the segment: r(l)^2 = r0^2 (1 + l (cb1 + l cb2))
-        const float ir0 = 1.0f / r0;
-        s.cb1 = 2.0f * bb * ir0 * ir0;
-        s.cb2 = aa * ir0 * ir0;
-        s.cga = aa * ir0;
-        s.ck0 = kappa;
-        s.ctau0 = (X * s.k[2] - Y * s.k[1]) * ir0;          // k . t2 at x0 (t2 = N x axis)
     }
     s.s_exit = best;
     s.face = face;
+    // anchor at the exit point (cylinder: k.N changes along the segment)
+    float A_exit = s.A;
+    bool flip = false;
+    if (GEOM != HEART_FLAT) {
+        const float Lp = fminf(best, 1.0e6f);
+        const float eps = Lp * __fmaf_rn(Lp, s.cb2, s.cb1);
+        const float rho = sqrtf(fmaxf(1.0f + eps, 1e-30f));
+        const float dk = (s.ck0 * (-eps / (1.0f + rho)) - Lp * s.cga) / rho;
+        A_exit = __fmaf_rn(s.sgn, dk, s.A);
+        flip = s.sB + A_exit < 0.0f;
+    }
+    thin_segment(L, s, A_exit, flip);
 }
 
 __device__ __forceinline__ void to_global(const Launch32 &L, const float *p, double *g, bool point) {
@@ -645,25 +778,63 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
     s.Lsum = t;
     ++s.ncoll;
     if (w[1] < s.pa_thr) return HEART_ABSORBED;
-    const float v = (u01_32(w[1]) - s.pa) * s.inv_1mpa;
-    const float q = mdf_q32(tab, w[2]);
-    const float st = sqrtf(q * (2.0f - q));
-    float sx, cx;
-    sincos_2pi(u01_32(w[3]), &sx, &cx);
-    float D, dk = 0.0f, eps = 0.0f, rho = 1.0f;
+    float v = (u01_32(w[1]) - s.pa) * s.inv_1mpa;
+    // k.t2 and k.N at the collision point (cylinder: from the along-segment length)
+    float dk = 0.0f, eps = 0.0f, rho = 1.0f, kt2, kN;
     if (GEOM == HEART_FLAT) {
-        D = __fmaf_rn(st, __fmaf_rn(s.k[0], cx, s.k[1] * sx), -q * s.k[2]);
+        kt2 = s.k[1];
+        kN = s.k[2];
     } else {
-        // k.N and k.t2 at the collision point from the along-segment length
         const float Lp = s.Lsum;
         eps = Lp * __fmaf_rn(Lp, s.cb2, s.cb1);
         rho = sqrtf(1.0f + eps);
         const float rinv = 1.0f / rho;
         dk = (s.ck0 * (-eps / (1.0f + rho)) - Lp * s.cga) * rinv;
-        const float tau = s.ctau0 * rinv;
-        D = __fmaf_rn(st, __fmaf_rn(s.k[0], cx, tau * sx), -q * (s.ck0 + dk));
+        kt2 = s.ctau0 * rinv;
+        kN = s.ck0 + dk;
     }
     const float Ac = __fmaf_rn(s.sgn, dk, s.A);               // anchor at the collision point
+    float q, st, sx, cx, D;
+    if (v < s.ra) {                                           // process (a), or the plain stream
+        if (s.ra < 1.0f) v = (v / s.ra) * L.vstar;
+        q = mdf_q32(tab, w[2]);
+        st = sqrtf(q * (2.0f - q));
+        sincos_2pi(u01_32(w[3]), &sx, &cx);
+        D = __fmaf_rn(st, __fmaf_rn(s.k[0], cx, kt2 * sx), -q * kN);
+    } else {                                                  // process (b)
+        v = __fmaf_rn(1.0f - L.vstar, (v - s.ra) / (1.0f - s.ra), L.vstar);
+        q = mdf_q32(tab, s.w0 + __umulhi(w[2], 0u - s.w0) + (s.w0 == 0u ? w[2] : 0u));
+        if (q < s.qmin || q > 2.0f - s.qmin) return -1;        // cannot reflect
+        st = sqrtf(q * (2.0f - q));
+        const float ca = sqrtf(__fmaf_rn(s.k[0], s.k[0], kt2 * kt2));
+        const float b = ca * st, ib = 1.0f / b;
+        // intervals of y = cos(xi - xi_k) with |k.n| = |kN (1 - q) + b y| in the window,
+        // the same-side one from small quantities
+        float e1, e2;
+        bragg_window(L, s.sB, s.cB, e1, e2);
+        const float sa = s.sB + Ac;                           // |k.N| here while k.N keeps its sign
+        // interval ends times b: (iv[0], iv[1]) then (iv[2], iv[3])
+        float iv[4];
+        if (sa > 0.0f) {
+            const float m1 = __fmaf_rn(sa, q, e1 - Ac), m2 = __fmaf_rn(sa, q, e2 - Ac);
+            const float p1 = __fmaf_rn(sa, 1.0f - q, s.sB + e1), p2 = __fmaf_rn(sa, 1.0f - q, s.sB + e2);
+            if (s.sgn > 0.0f) { iv[0] = m1; iv[1] = m2; iv[2] = -p2; iv[3] = -p1; }
+            else { iv[0] = p1; iv[1] = p2; iv[2] = -m2; iv[3] = -m1; }
+        } else {
+            const float a = kN * (1.0f - q), S1 = s.sB + e1, S2 = s.sB + e2;
+            iv[0] = S1 - a; iv[1] = S2 - a; iv[2] = -S2 - a; iv[3] = -S1 - a;
+        }
+        const float t3pbar = u01_32(w[3]) * s.pbar;
+        // P_xi <= 2 acos(1 - w) / pi <= sqrt(2 w), w = (S2 - S1) / b: most candidates end here
+        if (t3pbar * t3pbar * b >= 2.0002f * (e2 - e1)) return -1;
+        const float4 r = arc_sample(iv[0], iv[1], iv[2], iv[3], b, t3pbar);
+        if (r.x == 0.0f) return -1;                           // outside the arcs: cannot reflect
+        const float cxp = r.y, sxp = r.z, sg = r.w;
+        const float ica = ib * st;                            // 1 / ca
+        cx = (s.k[0] * cxp - sg * kt2 * sxp) * ica;           // xi = xi_k + sg xp
+        sx = (kt2 * cxp + sg * s.k[0] * sxp) * ica;
+        D = __fmaf_rn(st * ca, cxp, -q * kN);
+    }
     const float e = __fmaf_rn(s.sgn, D, Ac);                  // |k.n| - sin(aB + Delta_M)
     if (v >= irc_bound32<IRC>(L, fabsf(e))) return -1;        // rejected whatever Delta is
     float sa = s.sB + e;
@@ -806,24 +977,23 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
             const int n_idle = __popc(idle);
             if (n_idle == 32 && !more && B.count == 0) break;
             if (n_idle >= L.refill || (n_idle > 0 && !more) || n_idle == 32) {
-                while (more && B.count < n_idle) {
+                while (more && B.count < n_idle && B.count < kSpawnBelow) {
                     unsigned long long base = 0;
                     if (lane == 0) base = atomicAdd(&s_next, 32ull);
                     base = __shfl_sync(0xffffffffu, base, 0);
                     const unsigned long long end = s_end;
                     if (base >= end) { more = false; break; }
                     const unsigned long long id = base + lane;
-                    float x[3], k[3], A = 0.f, sB = 0.f, inv_mu = 0.f, pa = 0.f, E32 = 0.f;
+                    float x[3], k[3], A = 0.f, sB = 0.f, mu0 = 0.f, qr = 0.f, E32 = 0.f;
                     float pv[3] = {0.f, 0.f, 0.f};
-                    uint32_t pa_thr = 0;
                     int nb = 0;
                     bool hit = false;
                     if (id < end) {
                         ++my_emit;
                         if (EXT && L.user) {
-                            hit = spawn_user<GEOM>(L, id, x, k, pv, A, sB, inv_mu, pa, pa_thr, E32, nb);
+                            hit = spawn_user<GEOM>(L, id, x, k, pv, A, sB, mu0, qr, E32, nb);
                         } else {
-                            hit = spawn<GEOM>(L, L.offset + id, x, k, A, sB, inv_mu, pa, pa_thr, E32, nb);
+                            hit = spawn<GEOM>(L, L.offset + id, x, k, A, sB, mu0, qr, E32, nb);
                             if (EXT && L.pol_on) project_pol32(L, k, pv);
                         }
                         if (!hit) {
@@ -843,6 +1013,17 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                     }
                     const unsigned hm = __ballot_sync(0xffffffffu, hit);
                     if (hit) {
+                        // the entry segment: exit face and distance, majorant and thinning bounds
+                        Lane t;
+                        for (int i = 0; i < 3; ++i) { t.x0[i] = x[i]; t.k[i] = k[i]; }
+                        t.A = A;
+                        t.sB = sB;
+                        t.cB = sqrtf(fmaxf(0.0f, __fmaf_rn(-sB, sB, 1.0f)));
+                        t.sgn = -1.0f;                           // entering: k.N < 0
+                        t.rho0 = 0.0f;                           // on the front face
+                        t.mu0 = mu0;
+                        t.qr = qr;
+                        segment<GEOM>(L, t);
                         const int slot = B.count + __popc(hm & lt_mask);
                         for (int i = 0; i < 3; ++i) { B.x[i][slot] = x[i]; B.k[i][slot] = k[i]; }
                         const uint64_t ray = L.offset + id;
@@ -850,11 +1031,18 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                         B.sB[slot] = sB;
                         B.rl[slot] = (uint32_t)ray;
                         B.rh[slot] = (uint32_t)(ray >> 32);
-                        B.inv_mu[slot] = inv_mu;
-                        B.pa[slot] = pa;
-                        B.pa_thr[slot] = pa_thr;
+                        B.mu0[slot] = mu0;
+                        B.qr[slot] = qr;
                         B.E[slot] = E32;
                         B.nb[slot] = nb;
+                        B.s_exit[slot] = t.s_exit;
+                        B.face[slot] = t.face;
+                        B.inv_mu[slot] = t.inv_mu;
+                        B.pa[slot] = t.pa;
+                        B.ra[slot] = t.ra;
+                        B.qmin[slot] = t.qmin;
+                        B.pbar[slot] = t.pbar;
+                        B.w0[slot] = t.w0;
                         if (EXT) for (int i = 0; i < 3; ++i) Bp[i][slot] = pv[i];
                     }
                     __syncwarp();
@@ -871,12 +1059,21 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                     s.sB = B.sB[slot];
                     s.rl = B.rl[slot];
                     s.rh = B.rh[slot];
-                    s.inv_mu = B.inv_mu[slot];
-                    s.pa = B.pa[slot];
-                    s.pa_thr = B.pa_thr[slot];
+                    s.mu0 = B.mu0[slot];
+                    s.qr = B.qr[slot];
                     s.E = B.E[slot];
                     s.no_bragg = B.nb[slot];
+                    s.s_exit = B.s_exit[slot];
+                    s.face = B.face[slot];
+                    s.inv_mu = B.inv_mu[slot];
+                    s.pa = B.pa[slot];
+                    s.ra = B.ra[slot];
+                    s.qmin = B.qmin[slot];
+                    s.pbar = B.pbar[slot];
+                    s.w0 = B.w0[slot];
                     s.inv_1mpa = s.pa < 1.0f ? 1.0f / (1.0f - s.pa) : 0.0f;
+                    s.pa_thr = s.pa >= 1.0f ? 0xFFFFFFFFu
+                                            : __float2uint_ru(fminf(s.pa * 4294967296.0f, 4294967040.0f));
                     s.cB = sqrtf(fmaxf(0.0f, __fmaf_rn(-s.sB, s.sB, 1.0f)));
                     s.sgn = -1.0f;                           // entering: k.N < 0
                     s.rho0 = 0.0f;                           // on the front face
@@ -888,7 +1085,7 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                         for (int i = 0; i < 3; ++i) s.p[i] = Bp[i][slot];
                         s.pol = s.p[0] != 0.0f || s.p[1] != 0.0f || s.p[2] != 0.0f;
                     }
-                    segment<GEOM>(L, s);
+                    segment_consts<GEOM>(L, s);               // the rest of the entry segment was prepared
                     alive = true;
                 }
                 __syncwarp();
@@ -896,8 +1093,7 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                 __syncwarp();
             }
             if (alive) {
-                int oc = step<GEOM, IRC, EXT>(L, s, s_tab);
-                if (oc < 0) oc = step<GEOM, IRC, EXT>(L, s, s_tab);    // two collisions per refill check
+                const int oc = step<GEOM, IRC, EXT>(L, s, s_tab);
                 if (oc >= 0) {
                     my_coll += (unsigned long long)s.ncoll;
                     finish<REC, EXT>(L, s, oc, bt);
@@ -1065,10 +1261,16 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
         a += 0x9E3779B9u;
         b += 0xBB67AE85u;
     }
+    L.sampler = S.sampler;
+    L.vstar = (float)S.vstar;
+    L.xstar = (float)S.xstar;
+    L.hx2 = (float)(2.0 * std::sin(0.5 * S.xstar) * std::sin(0.5 * S.xstar));
+    L.sx = (float)std::sin(S.xstar);
     L.refill = g_tune.refill;
     L.geometry = S.geometry;
     L.irc_kind = S.irc;
     L.tab = S.mdf32;
+    L.qgrid = S.qgrid;
     const double *a0 = S.geometry == HEART_FLAT ? S.ed : S.ax;
     const double *a1 = S.geometry == HEART_FLAT ? S.en : S.cc;
     const double *a2 = S.geometry == HEART_FLAT ? S.N : S.ww;
@@ -1109,8 +1311,8 @@ template <int GEOM, int IRC, bool REC>
 static void launch_t(const Launch32 &L, const WorkPlan &W, cudaStream_t st) {
     // records are a test path: one occupancy variant
     if constexpr (!REC) {
-        if (g_tune.blocks_per_sm >= 8) {
-            launch_occ<GEOM, IRC, REC, 8>(L, W, st, W.n_chunks);
+        if (g_tune.blocks_per_sm <= 5) {
+            launch_occ<GEOM, IRC, REC, 5>(L, W, st, W.n_chunks);
             return;
         }
     }
@@ -1120,9 +1322,9 @@ static void launch_t(const Launch32 &L, const WorkPlan &W, cudaStream_t st) {
 // resident blocks of the launch shape in use (for chunk sizing)
 static int resident_blocks() {
     static int per_sm[2] = {0, 0};
-    const int v = g_tune.blocks_per_sm >= 8 ? 1 : 0;
+    const int v = g_tune.blocks_per_sm <= 5 ? 1 : 0;
     if (per_sm[v] == 0) {
-        if (v) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[v], k_trace_fp32<-1, -1, false, 8>, kBlockThreads, 0);
+        if (v) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[v], k_trace_fp32<-1, -1, false, 5>, kBlockThreads, 0);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[v], k_trace_fp32<-1, -1, false, 6>, kBlockThreads, 0);
         if (per_sm[v] < 1) per_sm[v] = 1;
     }
@@ -1358,7 +1560,7 @@ extern "C" heart_status heart_autotune(heart_spectrometer *h, const heart_source
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
-    const int occs[2] = {6, 8};
+    const int occs[2] = {6, 5};
     const int refills[3] = {4, 8, 16};
     TuneConfig best = g_tune;
     double best_rate = -1.0;

@@ -65,7 +65,7 @@ __device__ __forceinline__ double mdf_q64(const double *tab, uint32_t w) {
     return a + f * (b - a);
 }
 
-__device__ __forceinline__ double dp_reflectivity64(double y, double g) {
+__host__ __device__ __forceinline__ double dp_reflectivity64(double y, double g) {
     const double ar = y * y - g * g - 1.0, ai = 2.0 * y * g;
     const double r = hypot(ar, ai);
     double zr, zi;
@@ -77,7 +77,7 @@ __device__ __forceinline__ double dp_reflectivity64(double y, double g) {
 }
 
 // unit-area rocking curve at x = Delta - Delta_M
-__device__ __forceinline__ double irc64(const SpecParams &S, double x) {
+__host__ __device__ __forceinline__ double irc64(const SpecParams &S, double x) {
     switch (S.irc) {
     case HEART_IRC_DARWIN: {
         const double y = fabs(x) / S.irc_delta;
@@ -209,6 +209,89 @@ __device__ __forceinline__ void detector64(const SpecParams &S, const double x[3
     }
 }
 
+// ---------------------------------------------------------------------------
+// thinned candidates (FP64): bounds of one straight segment.  The scatter
+// candidates of the majorant walk split by their marks (v, n) into (a) v < v*,
+// tested as usual; (b) v >= v*, tilt q in [q_min, 2 - q_min], azimuth in the
+// arcs where |Delta| < X*, tested as usual; (c) the rest, which cannot reflect
+// and are never drawn.  On the segment the grazing angle stays in
+// [a_lo, a_hi]; a tilt theta < d - X* (d: distance of alpha_B + Delta_M from
+// that range) keeps |Delta| >= X*.  Segments with d <= X* keep the plain stream.
+// ---------------------------------------------------------------------------
+struct Seg64 {
+    double mu, pa, ra, vstar, qmin, pbar, S1, S2;
+    unsigned long long w0, wspan;
+};
+
+// first table word of process (b): that of the tilt-grid point just below q_min
+__device__ __forceinline__ unsigned long long tilt_word64(const SpecParams &S, double qmin) {
+    if (!(qmin >= 3.552713678800501e-15)) return 0ull;                 // 2^-48
+    int j = (int)floor(8.0 * log2(qmin)) + 384;
+    j = j > kQGrid - 1 ? kQGrid - 1 : j;
+    return (unsigned long long)S.qgrid[j];
+}
+
+__device__ __forceinline__ void bound_segment64(const SpecParams &S, const double *tab, double aB, double Q,
+                                                double mu0, double mubar, double pa, const double x[3],
+                                                const double k[3], Seg64 &b) {
+    b.mu = mubar; b.pa = pa; b.ra = 1.0; b.vstar = 1.0; b.qmin = 0.0; b.pbar = 1.0;
+    b.S1 = 0.0; b.S2 = 0.0; b.w0 = 0ull; b.wspan = 1ull << 32;
+    if (S.sampler != HEART_SAMPLER_THINNED || !(Q > 0)) return;
+    int face;
+    const double se = exit_distance64(S, x, k, &face);
+    double xe[3], N0[3], N1[3], t1[3], t2[3];
+    for (int i = 0; i < 3; ++i) xe[i] = x[i] + se * k[i];
+    local_frame64(S, x, N0, t1, t2);
+    local_frame64(S, xe, N1, t1, t2);
+    const double k0 = dot3d(k, N0), k1 = dot3d(k, N1);
+    double lo = fmin(fabs(k0), fabs(k1));
+    const double hi = fmax(fabs(k0), fabs(k1));
+    if ((k0 < 0) != (k1 < 0)) lo = 0.0;                    // k.N is monotone along a line
+    // distance between sines: never more than between the angles
+    const double aBs = aB + S.irc_shift;
+    const double sBs = sin(aBs);
+    const double d = sBs < lo ? lo - sBs : (sBs > hi ? sBs - hi : 0.0);
+    double tmin = d - S.xstar;
+    if (!(tmin > 0)) return;
+    const double half_pi = 1.5707963267948966;
+    if (tmin > half_pi) tmin = half_pi;
+    const double sh = sin(0.5 * tmin);
+    b.qmin = 2.0 * sh * sh;
+    b.w0 = tilt_word64(S, b.qmin);
+    b.wspan = (1ull << 32) - b.w0;
+    b.S1 = sin(fmax(0.0, aBs - S.xstar));
+    b.S2 = sin(fmin(half_pi, aBs + S.xstar));
+    const double hc = fmin(hi, 1.0);
+    const double bmin = sqrt(fmax(0.0, 1.0 - hc * hc)) * sin(tmin);
+    // two windows of width w in cos(xi'), each of arc measure <= acos(1 - w) / pi
+    const double w = (b.S2 - b.S1) / bmin;
+    b.pbar = (w >= 2.0 || !(bmin > 0)) ? 1.0 : fmin(1.0, 2.0 * acos(1.0 - w) / 3.14159265358979323846);
+    const double QR = Q * S.irc_max;
+    const double PA = (double)b.wspan / 4294967296.0;
+    const double la = QR * S.vstar, lb = QR * (1.0 - S.vstar) * PA * b.pbar;
+    b.vstar = S.vstar;
+    b.mu = mu0 + (la + lb);
+    b.pa = mu0 / b.mu;
+    b.ra = la / (la + lb);
+}
+
+// arc measure (in units of pi) of xi' in [0, pi] with |a + b cos xi'| in (S1, S2), and the arcs
+__device__ __forceinline__ double azimuth_arcs64(double a, double b, double S1, double S2, double arc[4]) {
+    const double iv[2][2] = {{(S1 - a) / b, (S2 - a) / b}, {(-S2 - a) / b, (-S1 - a) / b}};
+    double tot = 0.0;
+    for (int j = 0; j < 2; ++j) {
+        const double l = fmax(-1.0, iv[j][0]), h = fmin(1.0, iv[j][1]);
+        arc[2 * j] = 0.0;
+        arc[2 * j + 1] = 0.0;
+        if (l < h) {
+            arc[2 * j] = acos(h);
+            arc[2 * j + 1] = acos(l) - acos(h);
+            tot += arc[2 * j + 1];
+        }
+    }
+    return tot / 3.14159265358979323846;
+}
+
 // one ray, source (or user arrays) to detector
 __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, uint32_t k0, uint32_t k1,
                                    uint64_t ray, uint64_t idx, const double *tab, RayOut64 &r) {
@@ -300,15 +383,17 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
     const double mubar = mu0 + Q * S.irc_max;
     const double pa = mu0 / mubar;
 
-    // null-collision walk (Sec. 2.2.4)
+    // null-collision walk (Sec. 2.2.4), candidates thinned per straight segment
     int outcome = HEART_STUCK, nrefl = 0;
     long long ncoll = 0;
     uint32_t call = 2;
+    Seg64 sb;
+    bound_segment64(S, tab, aB, Q, mu0, mubar, pa, x, k, sb);
     for (;;) {
         if (ncoll >= S.max_coll) { outcome = HEART_STUCK; break; }
         uint32_t wd[4];
         philox4x32_10(rl, rh, call++, 0u, k0, k1, wd);
-        const double l = -log(u01_64(wd[0])) / mubar;
+        const double l = -log(u01_64(wd[0])) / sb.mu;
         int face;
         const double se = exit_distance64(S, x, k, &face);
         if (l > se) {
@@ -319,14 +404,33 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
         for (int i = 0; i < 3; ++i) x[i] += l * k[i];
         ++ncoll;
         const double u1 = u01_64(wd[1]);
-        if (u1 < pa) { outcome = HEART_ABSORBED; break; }
-        const double v = (u1 - pa) / (1.0 - pa);
+        if (u1 < sb.pa) { outcome = HEART_ABSORBED; break; }
+        double v = (u1 - sb.pa) / (1.0 - sb.pa);
         double N[3], t1[3], t2[3];
         local_frame64(S, x, N, t1, t2);
-        const double q = mdf_q64(tab, wd[2]);
+        double q, sx, cx;
+        if (v < sb.ra) {                                      // process (a), or the plain stream
+            v = sb.ra < 1.0 ? (v / sb.ra) * sb.vstar : v;
+            q = mdf_q64(tab, wd[2]);
+            sincospi(2.0 * u01_64(wd[3]), &sx, &cx);
+        } else {                                              // process (b)
+            v = sb.vstar + (1.0 - sb.vstar) * ((v - sb.ra) / (1.0 - sb.ra));
+            const uint32_t wq = (uint32_t)(sb.w0 + (((unsigned long long)wd[2] * sb.wspan) >> 32));
+            q = mdf_q64(tab, wq);
+            if (q < sb.qmin || q > 2.0 - sb.qmin) continue;  // cannot reflect
+            const double kN = dot3d(k, N), sa_ = fabs(kN), ca_ = sqrt(fmax(0.0, 1.0 - kN * kN));
+            const double a = (kN < 0 ? -sa_ : sa_) * (1.0 - q), b = ca_ * sqrt(q * (2.0 - q));
+            double arc[4];
+            const double Pxi = azimuth_arcs64(a, b, sb.S1, sb.S2, arc);
+            const double t3 = u01_64(wd[3]);
+            if (!(t3 * sb.pbar < Pxi)) continue;              // outside the arcs: cannot reflect
+            const double L = arc[1] + arc[3];
+            double pos = (t3 * sb.pbar / Pxi) * 2.0 * L, sgn = 1.0;
+            if (pos >= L) { pos -= L; sgn = -1.0; }
+            const double xp = pos < arc[1] ? arc[0] + pos : arc[2] + (pos - arc[1]);
+            sincos(atan2(dot3d(k, t2), dot3d(k, t1)) + sgn * xp, &sx, &cx);
+        }
         const double ct = 1.0 - q, st = sqrt(q * (2.0 - q));
-        double sx, cx;
-        sincospi(2.0 * u01_64(wd[3]), &sx, &cx);
         double n[3];
         for (int i = 0; i < 3; ++i) n[i] = ct * N[i] + st * (cx * t1[i] + sx * t2[i]);
         const double kn = dot3d(k, n);
@@ -355,6 +459,7 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
                 const double pn = 1.0 / sqrt(dot3d(pv, pv));
                 for (int i = 0; i < 3; ++i) pv[i] *= pn;
             }
+            bound_segment64(S, tab, aB, Q, mu0, mubar, pa, x, k, sb);   // a new straight segment
         }
     }
     r.outcome = outcome;

@@ -295,6 +295,10 @@ heart_status build_spec_params(const heart_spectrometer_desc *d, SpecParams *p, 
     p->irc = d->irc;
     p->max_refl = d->max_reflections;
     p->count_type = d->count_type;
+    REQUIRE(d->sampler == HEART_SAMPLER_THINNED || d->sampler == HEART_SAMPLER_PLAIN, "sampler");
+    REQUIRE(d->thin_vstar >= 0 && d->thin_vstar < 1, "thin_vstar in [0, 1)");
+    p->sampler = d->sampler;
+    p->vstar = d->thin_vstar > 0 ? d->thin_vstar : 1.0 / 1024.0;   // X* is set by the caller
     p->max_coll = d->max_collisions;
     p->thickness = d->thickness_mm;
     p->radius = d->radius_mm;

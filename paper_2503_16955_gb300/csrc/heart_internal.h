@@ -16,6 +16,9 @@ constexpr int kMaxComp = 16;
 constexpr int kMaxQe = 32;       // detector quantum-efficiency knots
 constexpr int kTallyN = 27;      // heart_tally as 27 uint64 words
 constexpr int kMaxTable = HEART_MAX_TABLE;   // knots of a tabulated spectrum
+// thinned sampler: tilt-bound grid q_j = 2^(j/8 - 48), j < kQGrid, with the
+// first mosaic-table word of the interval holding each q_j
+constexpr int kQGrid = 392;
 
 // tally word indices (same order as heart_tally)
 enum : int {
@@ -42,9 +45,14 @@ struct SpecParams {
     double D0[3], eu[3], ev[3], nd[3];
     int32_t nx, ny;
     double pix;
+    // candidate sampler: thinned (0) or plain (1); v* and the IRC half-width X*
+    // beyond which R / R_max <= v*
+    int32_t sampler, pad_s;
+    double vstar, xstar;
     // device tables: q = 1 - cos(theta) at the body knots then the tail knots
     const double *mdf64;
     const float *mdf32;
+    const uint32_t *qgrid;           // kQGrid words (thinned sampler)
 };
 
 struct SourceParams {

@@ -17,7 +17,7 @@ constexpr int kCounterWord = 32;     // first work-counter word
 struct TuneConfig {
     int refill = 8;                    // pop new rays when this many lanes of a warp are idle
     uint32_t chunk_rays = 1u << 16;    // largest work item (rays) claimed by a block
-    int blocks_per_sm = 6;             // register budget: 6 (80 registers) or 8 (64 registers)
+    int blocks_per_sm = 6;             // register budget: 6 (80 registers) or 5 (96 registers)
 };
 extern TuneConfig g_tune;
 

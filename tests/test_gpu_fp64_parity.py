@@ -68,15 +68,17 @@ def compare(H, spec, source, n, seed, offset=0):
     return g, gt
 
 
-def test_flat_hopg_mono_replays_oracle(H):
+@pytest.mark.parametrize("sampler", ["thinned", "plain"])
+def test_flat_hopg_mono_replays_oracle(H, sampler):
     w = W.flat_hopg_mono()
-    g, t = compare(H, w["spec"], w["source"], 40_000, w["seed"])
+    g, t = compare(H, dict(w["spec"], sampler=sampler), w["source"], 40_000, w["seed"])
     assert t["det_hits"] > 50 and t["exit_front"] > 200
 
 
-def test_von_hamos_polychromatic_replays_oracle(H):
+@pytest.mark.parametrize("sampler", ["thinned", "plain"])
+def test_von_hamos_polychromatic_replays_oracle(H, sampler):
     w = W.von_hamos_hapg()
-    g, t = compare(H, w["spec"], w["source"], 40_000, w["seed"], offset=123_456_789_000)
+    g, t = compare(H, dict(w["spec"], sampler=sampler), w["source"], 40_000, w["seed"], offset=123_456_789_000)
     assert t["exit_front"] > 30
 
 

@@ -27,7 +27,8 @@ REJECT = 0xFFFFFFFF
 
 
 def flat(**kw):
-    s = dict(W.flat_hopg_mono()["spec"])
+    # the plain walk: the hand-traced rays below inject its word layout
+    s = dict(W.flat_hopg_mono()["spec"], sampler="plain")
     s.update(kw)
     return s
 

@@ -14,7 +14,8 @@ LN2 = math.log(2.0)
 
 
 def flat(**kw):
-    s = dict(W.flat_hopg_mono()["spec"])
+    # the plain walk: the hand-traced rays below inject its word layout
+    s = dict(W.flat_hopg_mono()["spec"], sampler="plain")
     s.update(kw)
     return s
 
