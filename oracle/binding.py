@@ -46,6 +46,10 @@ class Spec(C.Structure):
         ("det_nx", C.c_int32), ("det_ny", C.c_int32),
         ("pixel_mm", C.c_double),
         ("sampler", C.c_int32), ("pad3", C.c_int32), ("thin_vstar", C.c_double),
+        ("n_orders", C.c_int32), ("pad4", C.c_int32), ("order_m", C.c_int32 * 4),
+        ("order_K_rel", C.c_double * 4), ("order_w_rel", C.c_double * 4),
+        ("n_irc_e", C.c_int32), ("pad5", C.c_int32), ("irc_e_keV", C.c_double * 16),
+        ("irc_e_wscale", C.c_double * 16), ("irc_e_shift_rad", C.c_double * 16),
     ]
 
 SAMPLER = {"plain": 0, "thinned": 1}
@@ -90,7 +94,10 @@ RECORD_DTYPE = np.dtype([
 class RayConsts(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("E_keV", "lambda_A", "sin_aB", "alpha_B", "mu0", "Q",
                                           "mubar", "p_abs")] + [("no_bragg", C.c_int32),
-                                                                ("pad", C.c_int32)]
+                                                                ("pad", C.c_int32),
+                                                                ("n_orders", C.c_int32), ("pad2", C.c_int32),
+                                                                ("shift_rad", C.c_double)] + \
+        [(n, C.c_double * 4) for n in ("ord_sin", "ord_alpha", "ord_Q", "ord_w", "ord_qr")]
 
 
 class QE(C.Structure):
@@ -204,6 +211,20 @@ def make_spec(d):
     s.pixel_mm = d["pixel_mm"]
     s.sampler = SAMPLER[d.get("sampler", "thinned")]
     s.thin_vstar = d.get("thin_vstar", 0.0)
+    # reflection orders: list of (multiple m, K ratio, width ratio); absent: the single reflection
+    orders = d.get("orders") or []
+    s.n_orders = len(orders)
+    for h, (m, kr, wr) in enumerate(orders[:4]):
+        s.order_m[h] = int(m)
+        s.order_K_rel[h] = kr
+        s.order_w_rel[h] = wr
+    # energy-dependent rocking curve: list of (keV, width scale, added shift rad)
+    knots = d.get("irc_energy") or []
+    s.n_irc_e = len(knots)
+    for i, (e, ws, sh) in enumerate(knots[:16]):
+        s.irc_e_keV[i] = e
+        s.irc_e_wscale[i] = ws
+        s.irc_e_shift_rad[i] = sh
     return s
 
 
@@ -312,7 +333,10 @@ def ray_constants(spec_dict, E):
     s = make_spec(spec_dict)
     c = RayConsts()
     lib().orc_ray_constants(C.byref(s), E, C.byref(c))
-    return {n: getattr(c, n) for n, _ in RayConsts._fields_ if n != "pad"}
+    out = {n: getattr(c, n) for n, _ in RayConsts._fields_ if not n.startswith("pad")}
+    for n in ("ord_sin", "ord_alpha", "ord_Q", "ord_w", "ord_qr"):
+        out[n] = [float(x) for x in out[n]][: c.n_orders]
+    return out
 
 
 def trace(spec_dict, source_dict, n_rays, seed, ray_offset=0, n_threads=0, records=False):

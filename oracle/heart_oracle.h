@@ -31,6 +31,10 @@
  *                                    two-sample agreement with the plain walk on fans of directions for
  *                                    all 7 MDFs and 6 IRCs and on the workloads; first-reflection
  *                                    probability vs quadrature of Eq. ReflXsection)
+ *   reflection orders        pinned (explicit first order = single reflection word for word; order m on d =
+ *                                    order 1 on d/m; thin-slab reflection probability and per-order
+ *                                    shares vs the quadrature summed over orders)
+ *   energy-dependent IRC     pinned (constant table = wider, shifted curve; interpolation and clamping)
  *   tabulated spectrum       pinned (KS against the piecewise-linear CDF written from the knots; a
  *                                    two-knot table reproduces the uniform component bit for bit)
  *   orc_trace_energy         pinned (mono line: energy image = E x QE x counts; QE interpolation)
@@ -62,6 +66,8 @@ enum { ORC_MISS = 0, ORC_ABSORBED = 1, ORC_EXIT_FRONT = 2, ORC_EXIT_BACK = 3,
 #define ORC_MDF_T 256         /* tail intervals, uniform in -log2(1-u)      */
 #define ORC_MAX_COMP 16
 #define ORC_MAX_TABLE 8192    /* knots of a tabulated spectrum            */
+#define ORC_MAX_ORDERS 4      /* reflection orders summed in the walk      */
+#define ORC_MAX_IRC_E 16      /* knots of the energy-dependent IRC        */
 
 typedef struct {
     double d_spacing_A;       /* d_H of Eq. BraggLaw, Angstrom */
@@ -98,6 +104,19 @@ typedef struct {
     int32_t sampler;
     int32_t pad3;
     double thin_vstar;
+    /* higher-order reflections (Sec. 2.2.3: the cross-section is a sum over the
+     * reflections H).  n_orders = 0: the single reflection on d_spacing_A.
+     * Otherwise order h reflects on planes of spacing d_spacing_A / order_m[h],
+     * with K_h = order_K_rel[h] K and a rocking curve order_w_rel[h] times as
+     * wide as the one described above (same shape, same unit area). */
+    int32_t n_orders, pad4;
+    int32_t order_m[ORC_MAX_ORDERS];
+    double order_K_rel[ORC_MAX_ORDERS], order_w_rel[ORC_MAX_ORDERS];
+    /* energy-dependent rocking curve (Sec. 2.1 lets its width and peak shift be
+     * functions of energy): width scale and an added shift at knots
+     * irc_e_keV, linear between them, constant beyond; n_irc_e = 0: none */
+    int32_t n_irc_e, pad5;
+    double irc_e_keV[ORC_MAX_IRC_E], irc_e_wscale[ORC_MAX_IRC_E], irc_e_shift_rad[ORC_MAX_IRC_E];
 } orc_spec;
 
 enum { ORC_SAMPLER_PLAIN = 0, ORC_SAMPLER_THINNED = 1 };
@@ -151,8 +170,14 @@ typedef struct {
 } orc_mdf_table;
 
 typedef struct {
-    double E_keV, lambda_A, sin_aB, alpha_B, mu0, Q, mubar, p_abs;
-    int32_t no_bragg, pad;
+    double E_keV, lambda_A, sin_aB, alpha_B, mu0, Q, mubar, p_abs;   /* sin_aB, alpha_B, Q: the first order */
+    int32_t no_bragg, pad;                 /* no order has a Bragg solution */
+    int32_t n_orders, pad2;
+    double shift_rad;                      /* Delta_M(E) */
+    /* per order: sin(alpha_B), alpha_B (NaN without a Bragg solution), Q, the
+     * rocking-curve width scale, and Q R_max (its share of the majorant) */
+    double ord_sin[ORC_MAX_ORDERS], ord_alpha[ORC_MAX_ORDERS], ord_Q[ORC_MAX_ORDERS];
+    double ord_w[ORC_MAX_ORDERS], ord_qr[ORC_MAX_ORDERS];
 } orc_ray_consts;
 
 /* Philox4x32-10 (Salmon et al., SC'11) */
@@ -213,12 +238,14 @@ int orc_walk_injected(const orc_spec *s, double E_keV, const double pos[3], cons
 int orc_walk_injected_n(const orc_spec *s, int64_t n, const double *E_keV, const double *pos, const double *dir,
                         const double *pol, const uint32_t *words, int64_t words_per_ray, orc_record *rec);
 
-/* accepted crystallites at a fixed ray direction and surface normal:
- * returns Delta (= alpha~ - alpha_B - Delta_M) and psi of n accepted draws */
+/* accepted crystallites at a fixed ray direction and surface normal, first
+ * reflection order: returns Delta (= alpha~ - alpha_B - Delta_M) and psi of n
+ * accepted draws */
 int64_t orc_sample_crystallites(const orc_spec *s, double E_keV, double alpha_rad, int64_t n,
                                 uint64_t seed, double *delta_out, double *psi_out);
 
-/* reflection rate r(alpha) (per mm of path) by 2-D quadrature of Eq. ReflXsection */
+/* reflection rate r(alpha) (per mm of path) by 2-D quadrature of Eq. ReflXsection,
+ * summed over the reflection orders */
 double orc_reflection_rate(const orc_spec *s, double E_keV, double alpha_rad);
 
 const char *orc_last_error(void);

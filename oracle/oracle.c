@@ -503,24 +503,66 @@ static double refl_K(const orc_spec *s) {
     return PI * delta * (2.0 * sb * cb) / (lam_mm * lam_mm);
 }
 
+/* the energy-dependent rocking curve at E: width scale and added peak shift,
+ * linear between the knots and constant beyond them */
+static void irc_energy(const orc_spec *s, double E, double *wscale, double *shift) {
+    *wscale = 1.0;
+    *shift = 0.0;
+    int n = s->n_irc_e;
+    if (n <= 0) return;
+    const double *x = s->irc_e_keV;
+    if (n == 1 || E <= x[0]) { *wscale = s->irc_e_wscale[0]; *shift = s->irc_e_shift_rad[0]; return; }
+    if (E >= x[n - 1]) { *wscale = s->irc_e_wscale[n - 1]; *shift = s->irc_e_shift_rad[n - 1]; return; }
+    int i = 0;
+    while (!(E < x[i + 1])) ++i;
+    double f = (E - x[i]) / (x[i + 1] - x[i]);
+    *wscale = s->irc_e_wscale[i] + f * (s->irc_e_wscale[i + 1] - s->irc_e_wscale[i]);
+    *shift = s->irc_e_shift_rad[i] + f * (s->irc_e_shift_rad[i + 1] - s->irc_e_shift_rad[i]);
+}
+
+/* the reflection orders of a spectrometer: multiple m, K ratio, width ratio */
+static int spec_orders(const orc_spec *s, int m[ORC_MAX_ORDERS], double kr[ORC_MAX_ORDERS],
+                       double wr[ORC_MAX_ORDERS]) {
+    if (s->n_orders <= 0) { m[0] = 1; kr[0] = 1.0; wr[0] = 1.0; return 1; }
+    int n = s->n_orders > ORC_MAX_ORDERS ? ORC_MAX_ORDERS : s->n_orders;
+    for (int h = 0; h < n; ++h) { m[h] = s->order_m[h]; kr[h] = s->order_K_rel[h]; wr[h] = s->order_w_rel[h]; }
+    return n;
+}
+
 int orc_ray_constants(const orc_spec *s, double E, orc_ray_consts *c) {
     memset(c, 0, sizeof *c);
     c->E_keV = E;
     c->lambda_A = HC_KEV_A / E;
-    c->sin_aB = c->lambda_A / (2.0 * s->d_spacing_A);       /* Eq. (BraggLaw) */
     c->mu0 = 1.0 / (s->absorption_length_mm * pow(E / s->absorption_ref_keV, s->absorption_power));
-    if (!(c->sin_aB < 1.0)) {
-        c->no_bragg = 1;
-        c->alpha_B = NAN;
-        c->Q = 0.0;
-    } else {
-        c->alpha_B = asin(c->sin_aB);
-        double cb = sqrt(1.0 - c->sin_aB * c->sin_aB);
-        double lam_mm = c->lambda_A * 1e-7;
-        double K = refl_K(s);
-        c->Q = K * K * lam_mm * lam_mm * lam_mm / (2.0 * c->sin_aB * cb);
+    int m[ORC_MAX_ORDERS];
+    double kr[ORC_MAX_ORDERS], wr[ORC_MAX_ORDERS], wscale, shift;
+    c->n_orders = spec_orders(s, m, kr, wr);
+    irc_energy(s, E, &wscale, &shift);
+    c->shift_rad = s->irc_shift_rad + shift;
+    double K = refl_K(s), rmax = orc_irc_max(s), lam_mm = c->lambda_A * 1e-7;
+    double qr_sum = 0.0;
+    c->no_bragg = 1;
+    for (int h = 0; h < c->n_orders; ++h) {
+        /* Eq. (BraggLaw) on the planes d / m_h */
+        double sb = m[h] * c->lambda_A / (2.0 * s->d_spacing_A);
+        c->ord_sin[h] = sb;
+        c->ord_w[h] = wr[h] * wscale;
+        if (!(sb < 1.0)) {
+            c->ord_alpha[h] = NAN;
+            continue;
+        }
+        c->no_bragg = 0;
+        c->ord_alpha[h] = asin(sb);
+        double cb = sqrt(1.0 - sb * sb);
+        double Kh = K * kr[h];
+        c->ord_Q[h] = Kh * Kh * lam_mm * lam_mm * lam_mm / (2.0 * sb * cb);
+        c->ord_qr[h] = c->ord_Q[h] * (rmax / c->ord_w[h]);   /* a curve w times as wide peaks 1/w as high */
+        qr_sum += c->ord_qr[h];
     }
-    c->mubar = c->mu0 + c->Q * orc_irc_max(s);
+    c->sin_aB = c->ord_sin[0];
+    c->alpha_B = c->ord_alpha[0];
+    c->Q = c->ord_Q[0];
+    c->mubar = c->mu0 + qr_sum;
     c->p_abs = c->mu0 / c->mubar;
     return 0;
 }
@@ -597,6 +639,17 @@ static int geom_init(geom *g, const orc_spec *s) {
     cross3(g->eu, g->ev, g->nd);
     irc_prepare(s, &g->irc);
     g->irc_max = irc_eval(&g->irc, 0.0);
+    if (s->n_orders < 0 || s->n_orders > ORC_MAX_ORDERS) return fail("0..4 reflection orders");
+    for (int h = 0; h < s->n_orders; ++h)
+        if (s->order_m[h] < 1 || !(s->order_K_rel[h] >= 0) || !(s->order_w_rel[h] > 0) ||
+            !isfinite(s->order_K_rel[h]) || !isfinite(s->order_w_rel[h]))
+            return fail("order: multiple >= 1, K ratio >= 0, width ratio > 0");
+    if (s->n_irc_e < 0 || s->n_irc_e > ORC_MAX_IRC_E) return fail("0..16 energy knots of the rocking curve");
+    for (int i = 0; i < s->n_irc_e; ++i) {
+        if (!(s->irc_e_wscale[i] > 0) || !isfinite(s->irc_e_wscale[i]) || !isfinite(s->irc_e_shift_rad[i]))
+            return fail("rocking-curve energy knots: width scale > 0, finite shift");
+        if (i > 0 && !(s->irc_e_keV[i] > s->irc_e_keV[i - 1])) return fail("rocking-curve energy knots must ascend");
+    }
     if (s->sampler == ORC_SAMPLER_THINNED) {
         g->vstar = s->thin_vstar > 0 ? s->thin_vstar : 1.0 / 1024.0;
         if (!(g->vstar < 1.0)) return fail("thin_vstar must be < 1");
@@ -768,11 +821,18 @@ static int next4(wsrc *ws, uint32_t w[4]) {
  * measure, pbar >= P_xi on the segment), its azimuth uniform over the arcs.
  * A segment with d <= X* keeps the plain candidate stream (v* = 1). */
 typedef struct {
-    double mu, pa;            /* majorant of the segment and the absorption share mu0 / mu */
-    double ra, vstar;         /* share of process (a) among scatter candidates, its v range */
+    double ra, vstar;         /* share of process (a) among the order's scatter candidates, its v range */
     double qmin, pbar;        /* process (b): tilt bound and arc-measure bound */
     double S1, S2;            /* |k.n| window of |Delta| < X* */
     uint64_t w0, wspan;       /* process (b): table words [w0, w0 + wspan) */
+    double lam;               /* the order's candidate rate on the segment */
+} order_bound;
+
+typedef struct {
+    double mu, pa;            /* majorant of the segment and the absorption share mu0 / mu */
+    int n;                    /* reflection orders */
+    double cum[ORC_MAX_ORDERS];   /* cumulative shares of the orders among scatter candidates */
+    order_bound o[ORC_MAX_ORDERS];
 } seg_bound;
 
 /* first word of the table interval containing q (conservative lower end) */
@@ -796,50 +856,73 @@ static uint64_t word_floor_grid(const orc_mdf_table *t, double qmin) {
     return word_floor(t, exp2(j / 8.0 - 48.0));
 }
 
-static void bound_segment(const geom *g, const orc_ray_consts *rc, const double x[3], const double k[3],
-                          seg_bound *b) {
+/* the bound of one order h on the segment with |k.N| in [lo, hi] */
+static void bound_order(const geom *g, const orc_ray_consts *rc, int h, double lo, double hi, order_bound *b) {
     const orc_spec *s = g->s;
     memset(b, 0, sizeof *b);
-    b->mu = rc->mubar;
-    b->pa = rc->p_abs;
     b->ra = 1.0;
     b->vstar = 1.0;
     b->pbar = 1.0;
     b->wspan = 1ull << 32;
-    if (s->sampler != ORC_SAMPLER_THINNED || rc->no_bragg || !(rc->Q > 0)) return;
-    int face;
-    double se = exit_distance(g, x, k, &face);
-    double xe[3], N0[3], N1[3], t1[3], t2[3];
-    for (int i = 0; i < 3; ++i) xe[i] = x[i] + se * k[i];
-    local_frame(g, x, N0, t1, t2);
-    local_frame(g, xe, N1, t1, t2);
-    double k0 = dot3(k, N0), k1 = dot3(k, N1);
-    double lo = fmin(fabs(k0), fabs(k1)), hi = fmax(fabs(k0), fabs(k1));
-    if ((k0 < 0) != (k1 < 0)) lo = 0.0;             /* k.N is monotone along a line: it crossed 0 */
-    double aB = rc->alpha_B + s->irc_shift_rad;
+    b->lam = rc->ord_qr[h];
+    if (s->sampler != ORC_SAMPLER_THINNED || !(rc->ord_qr[h] > 0)) return;
+    double aB = rc->ord_alpha[h] + rc->shift_rad;
+    double xstar = g->xstar * rc->ord_w[h];          /* a curve w times as wide: X* scales by w */
     double sB = sin(aB);
     double d = sB < lo ? lo - sB : (sB > hi ? sB - hi : 0.0);
-    double tmin = d - g->xstar;
+    double tmin = d - xstar;
     if (!(tmin > 0)) return;                          /* near Bragg: the plain stream */
     if (tmin > 0.5 * PI) tmin = 0.5 * PI;
     double sh = sin(0.5 * tmin);
     b->qmin = 2.0 * sh * sh;
     b->w0 = word_floor_grid(g->mdf, b->qmin);
     b->wspan = (1ull << 32) - b->w0;
-    b->S1 = sin(fmax(0.0, aB - g->xstar));
-    b->S2 = sin(fmin(0.5 * PI, aB + g->xstar));
+    b->S1 = sin(fmax(0.0, aB - xstar));
+    b->S2 = sin(fmin(0.5 * PI, aB + xstar));
     double bmin = sqrt(fmax(0.0, 1.0 - fmin(hi, 1.0) * fmin(hi, 1.0))) * sin(tmin);
     /* each of the two |k.n| windows spans w = (S2 - S1) / b in cos(xi'); an
      * interval of that width has arcsine measure at most acos(1 - w) / pi */
     double w = (b->S2 - b->S1) / bmin;
     b->pbar = (w >= 2.0 || !(bmin > 0)) ? 1.0 : fmin(1.0, 2.0 * acos(1.0 - w) / PI);
-    double QR = rc->Q * g->irc_max;
+    double QR = rc->ord_qr[h];
     double PA = (double)b->wspan / 4294967296.0;
     double la = QR * g->vstar, lb = QR * (1.0 - g->vstar) * PA * b->pbar;
     b->vstar = g->vstar;
-    b->mu = rc->mu0 + (la + lb);
-    b->pa = rc->mu0 / b->mu;
+    b->lam = la + lb;
     b->ra = la / (la + lb);
+}
+
+static void bound_segment(const geom *g, const orc_ray_consts *rc, const double x[3], const double k[3],
+                          seg_bound *b) {
+    const orc_spec *s = g->s;
+    memset(b, 0, sizeof *b);
+    b->n = rc->n_orders;
+    double lo = 0.0, hi = 1.0;
+    if (s->sampler == ORC_SAMPLER_THINNED && !rc->no_bragg) {
+        int face;
+        double se = exit_distance(g, x, k, &face);
+        double xe[3], N0[3], N1[3], t1[3], t2[3];
+        for (int i = 0; i < 3; ++i) xe[i] = x[i] + se * k[i];
+        local_frame(g, x, N0, t1, t2);
+        local_frame(g, xe, N1, t1, t2);
+        double k0 = dot3(k, N0), k1 = dot3(k, N1);
+        lo = fmin(fabs(k0), fabs(k1));
+        hi = fmax(fabs(k0), fabs(k1));
+        if ((k0 < 0) != (k1 < 0)) lo = 0.0;         /* k.N is monotone along a line: it crossed 0 */
+    }
+    double lam = 0.0;
+    for (int h = 0; h < b->n; ++h) {
+        bound_order(g, rc, h, lo, hi, &b->o[h]);
+        lam += b->o[h].lam;
+    }
+    double run = 0.0;
+    for (int h = 0; h < b->n; ++h) {
+        run += b->o[h].lam;
+        b->cum[h] = lam > 0 ? run / lam : 1.0;
+    }
+    b->cum[b->n - 1] = 1.0;
+    b->mu = rc->mu0 + lam;
+    b->pa = rc->mu0 / b->mu;
 }
 
 /* arc measure P_xi (in units of pi) of the azimuths xi' in [0, pi] with
@@ -886,26 +969,35 @@ static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[
         double u1 = U(w[1]);
         if (u1 < sb.pa) { outcome = ORC_ABSORBED; break; }
         double v = (u1 - sb.pa) / (1.0 - sb.pa);
+        /* the reflection order, by its share of the candidate rate (superposition
+         * over H); the conditional uniform stays the acceptance uniform */
+        int h = 0;
+        if (sb.n > 1) {
+            while (h < sb.n - 1 && !(v < sb.cum[h])) ++h;
+            double c0 = h > 0 ? sb.cum[h - 1] : 0.0;
+            v = (v - c0) / (sb.cum[h] - c0);
+        }
+        const order_bound *ob = &sb.o[h];
         double N[3], t1[3], t2[3];
         local_frame(g, x, N, t1, t2);
         double q, xi;
-        if (v < sb.ra) {                                 /* process (a), or the plain stream */
-            v = sb.ra < 1.0 ? (v / sb.ra) * sb.vstar : v;
+        if (v < ob->ra) {                                /* process (a), or the plain stream */
+            v = ob->ra < 1.0 ? (v / ob->ra) * ob->vstar : v;
             q = orc_mdf_table_lookup(g->mdf, w[2]);
             xi = 2.0 * PI * U(w[3]);
         } else {                                         /* process (b) */
-            v = sb.vstar + (1.0 - sb.vstar) * ((v - sb.ra) / (1.0 - sb.ra));
-            uint32_t wq = (uint32_t)(sb.w0 + (((uint64_t)w[2] * sb.wspan) >> 32));
+            v = ob->vstar + (1.0 - ob->vstar) * ((v - ob->ra) / (1.0 - ob->ra));
+            uint32_t wq = (uint32_t)(ob->w0 + (((uint64_t)w[2] * ob->wspan) >> 32));
             q = orc_mdf_table_lookup(g->mdf, wq);
-            if (q < sb.qmin || q > 2.0 - sb.qmin) continue;    /* cannot reflect */
+            if (q < ob->qmin || q > 2.0 - ob->qmin) continue;  /* cannot reflect */
             double kN = dot3(k, N), sa_ = fabs(kN), ca_ = sqrt(fmax(0.0, 1.0 - kN * kN));
             double a = (kN < 0 ? -sa_ : sa_) * (1.0 - q), b = ca_ * sqrt(q * (2.0 - q));
             double arc[4];
-            double Pxi = azimuth_arcs(a, b, sb.S1, sb.S2, arc);
+            double Pxi = azimuth_arcs(a, b, ob->S1, ob->S2, arc);
             double t3 = U(w[3]);
-            if (!(t3 * sb.pbar < Pxi)) continue;            /* outside the arcs: cannot reflect */
+            if (!(t3 * ob->pbar < Pxi)) continue;           /* outside the arcs: cannot reflect */
             double L = arc[1] + arc[3];
-            double pos = (t3 * sb.pbar / Pxi) * 2.0 * L, sgn = 1.0;
+            double pos = (t3 * ob->pbar / Pxi) * 2.0 * L, sgn = 1.0;
             if (pos >= L) { pos -= L; sgn = -1.0; }
             double xp = pos < arc[1] ? arc[0] + pos : arc[2] + (pos - arc[1]);
             xi = atan2(dot3(k, t2), dot3(k, t1)) + sgn * xp;
@@ -918,7 +1010,7 @@ static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[
         double sa = fabs(kn);
         if (sa > 1.0) sa = 1.0;
         double at = asin(sa);                            /* incidence on the crystallite */
-        double delta = at - rc->alpha_B - s->irc_shift_rad;
+        double delta = at - rc->ord_alpha[h] - rc->shift_rad;
         double ks[3];                                    /* reflected direction (reflection equation) */
         for (int i = 0; i < 3; ++i) ks[i] = k[i] - 2.0 * kn * n[i];
         double G;
@@ -929,7 +1021,8 @@ static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[
             double c2 = cos(2.0 * at);
             G = 0.5 * (1.0 + c2 * c2);                   /* Eq. (G_unpol) */
         }
-        double P = irc_eval(&g->irc, delta) * G / g->irc_max;
+        /* the order's curve is the described one w_h times as wide: R_h / R_h,max = R(x / w_h) / R_max */
+        double P = irc_eval(&g->irc, delta / rc->ord_w[h]) * G / g->irc_max;
         if (v < P) {
             ++nrefl;
             if (nrefl > s->max_reflections) { outcome = ORC_CAPPED; break; }
@@ -1327,9 +1420,9 @@ int64_t orc_sample_crystallites(const orc_spec *s, double E, double alpha, int64
         double sa = fabs(kn);
         if (sa > 1) sa = 1;
         double at = asin(sa);
-        double delta = at - rc.alpha_B - s->irc_shift_rad;
+        double delta = at - rc.alpha_B - rc.shift_rad;
         double c2 = cos(2.0 * at);
-        double P = irc_eval(&ip, delta) * 0.5 * (1.0 + c2 * c2) / irc_max;
+        double P = irc_eval(&ip, delta / rc.ord_w[0]) * 0.5 * (1.0 + c2 * c2) / irc_max;   /* the first order */
         if (U(w[1]) < P) {
             double sgn = kn < 0 ? 1.0 : -1.0;   /* H or H-bar: the normal facing the ray */
             double np[3];
@@ -1349,7 +1442,7 @@ int64_t orc_sample_crystallites(const orc_spec *s, double E, double alpha, int64
 /* with f the MDF normalised on the sphere and theta from Eq. (ThetaPsi), */
 /* written as 1 - cos(theta) = 2 sin^2((alpha-a~)/2) + 2 cos(alpha) cos(a~) sin^2(psi/2). */
 /* ------------------------------------------------------------------ */
-typedef struct { const orc_spec *s; double alpha, at, Z, aB; irc_params irc; } rr_ctx;
+typedef struct { const orc_spec *s; double alpha, at, Z, aB, shift, w; irc_params irc; } rr_ctx;
 
 static double rr_inner(const void *vp, double psi) {
     const rr_ctx *c = (const rr_ctx *)vp;
@@ -1370,12 +1463,12 @@ static double rr_psi_integral(rr_ctx *c) {
 }
 static double rr_outer(const void *vp, double x) {
     rr_ctx *c = (rr_ctx *)vp;
-    double at = c->aB + c->s->irc_shift_rad + x;
+    double at = c->aB + c->shift + x;
     if (at < 0 || at > 0.5 * PI) return 0.0;
     c->at = at;
     double c2 = cos(2.0 * at);
     double G = 0.5 * (1.0 + c2 * c2);
-    double R = irc_eval(&c->irc, x);
+    double R = irc_eval(&c->irc, x / c->w) / c->w;       /* the order's curve: w times as wide, unit area */
     if (R == 0) return 0.0;
     return R * cos(at) * G * rr_psi_integral(c);
 }
@@ -1383,21 +1476,28 @@ double orc_reflection_rate(const orc_spec *s, double E, double alpha) {
     orc_ray_consts rc;
     orc_ray_constants(s, E, &rc);
     if (rc.no_bragg) return 0.0;
-    rr_ctx c = {s, alpha, 0.0, orc_mdf_norm(s), rc.alpha_B, {0}};
-    irc_prepare(s, &c.irc);
-    double lo = -(rc.alpha_B + s->irc_shift_rad), hi = 0.5 * PI - rc.alpha_B - s->irc_shift_rad;
-    /* geometric panels in |x| on each side of the IRC centre */
-    double w = s->irc_fwhm_rad > 0 ? s->irc_fwhm_rad : 1e-5;
-    double sum = 0.0;
-    for (int side = 0; side < 2; ++side) {
-        double lim = side ? hi : -lo;
-        double a = 0.0, b = 1e-3 * w;
-        while (a < lim) {
-            if (b > lim) b = lim;
-            double pa = side ? a : -b, pb = side ? b : -a;
-            sum += integrate(rr_outer, &c, pa, pb, 1e-9);
-            a = b; b *= 2.0;
+    /* the sum over the reflection orders H of the paper's cross-section */
+    double total = 0.0;
+    double Z = orc_mdf_norm(s);
+    for (int h = 0; h < rc.n_orders; ++h) {
+        if (!(rc.ord_Q[h] > 0)) continue;
+        rr_ctx c = {s, alpha, 0.0, Z, rc.ord_alpha[h], rc.shift_rad, rc.ord_w[h], {0}};
+        irc_prepare(s, &c.irc);
+        double lo = -(rc.ord_alpha[h] + rc.shift_rad), hi = 0.5 * PI - rc.ord_alpha[h] - rc.shift_rad;
+        /* geometric panels in |x| on each side of the IRC centre */
+        double w = (s->irc_fwhm_rad > 0 ? s->irc_fwhm_rad : 1e-5) * rc.ord_w[h];
+        double sum = 0.0;
+        for (int side = 0; side < 2; ++side) {
+            double lim = side ? hi : -lo;
+            double a = 0.0, b = 1e-3 * w;
+            while (a < lim) {
+                if (b > lim) b = lim;
+                double pa = side ? a : -b, pb = side ? b : -a;
+                sum += integrate(rr_outer, &c, pa, pb, 1e-9);
+                a = b; b *= 2.0;
+            }
         }
+        total += rc.ord_Q[h] * sum;
     }
-    return rc.Q * sum;
+    return total;
 }
