@@ -149,7 +149,29 @@ typedef struct {
     int32_t count_type;             /* heart_count_type of images traced with this handle */
     int32_t sampler;                /* heart_sampler */
     double thin_vstar;              /* THINNED: relative IRC level v* in (0, 1); 0: 2^-10 */
+    /* Higher-order reflections (Sec. 2.2.3: the cross-section is a sum over the
+     * reflections H, e.g. graphite (002), (004), (006)).  n_orders = 0: the
+     * single reflection on d_spacing_A.  Otherwise order h reflects on planes
+     * d_spacing_A / order_m[h] with K_h = order_K_rel[h] K and a rocking curve
+     * order_w_rel[h] times as wide (same shape and unit area).  A scatter
+     * candidate picks its order by the order's share of the candidate rate.
+     * Precision FP32 (heart_trace, batches, FP32 server jobs) takes one order
+     * only and returns HEART_EINVAL otherwise; FP64 takes up to HEART_MAX_ORDERS. */
+    int32_t n_orders;
+    int32_t reserved2;
+    int32_t order_m[4];
+    double order_K_rel[4], order_w_rel[4];
+    /* Energy-dependent rocking curve (Sec. 2.1: its width and peak shift as
+     * functions of energy): at the ascending knots irc_e_keV the width scale
+     * irc_e_wscale (> 0) and a shift irc_e_shift_rad added to irc_shift_rad,
+     * linear between knots and constant beyond them; n_irc_e = 0: none. */
+    int32_t n_irc_e;
+    int32_t reserved3;
+    double irc_e_keV[16], irc_e_wscale[16], irc_e_shift_rad[16];
 } heart_spectrometer_desc;
+
+#define HEART_MAX_ORDERS 4
+#define HEART_MAX_IRC_E 16
 
 typedef struct {
     int32_t kind;                   /* heart_source_kind */

@@ -54,6 +54,10 @@ class heart_spectrometer_desc(C.Structure):
         ("det_centre_mm", D3), ("det_u", D3), ("det_v", D3),
         ("det_nx", C.c_int32), ("det_ny", C.c_int32), ("pixel_mm", C.c_double),
         ("count_type", C.c_int32), ("sampler", C.c_int32), ("thin_vstar", C.c_double),
+        ("n_orders", C.c_int32), ("reserved2", C.c_int32), ("order_m", C.c_int32 * 4),
+        ("order_K_rel", C.c_double * 4), ("order_w_rel", C.c_double * 4),
+        ("n_irc_e", C.c_int32), ("reserved3", C.c_int32), ("irc_e_keV", C.c_double * 16),
+        ("irc_e_wscale", C.c_double * 16), ("irc_e_shift_rad", C.c_double * 16),
     ]
 
 
@@ -221,6 +225,20 @@ def make_desc(d):
     s.count_type = COUNT[d.get("count_type", "i32")]
     s.sampler = SAMPLER[d.get("sampler", "thinned")]
     s.thin_vstar = d.get("thin_vstar", 0.0)
+    # reflection orders: (multiple m, K ratio, width ratio) each; absent: the single reflection
+    orders = d.get("orders") or []
+    if len(orders) > 4:
+        raise ValueError("at most 4 reflection orders")
+    s.n_orders = len(orders)
+    for h, (m, kr, wr) in enumerate(orders):
+        s.order_m[h], s.order_K_rel[h], s.order_w_rel[h] = int(m), kr, wr
+    # energy-dependent rocking curve: (keV, width scale, added shift rad) knots
+    knots = d.get("irc_energy") or []
+    if len(knots) > 16:
+        raise ValueError("at most 16 rocking-curve energy knots")
+    s.n_irc_e = len(knots)
+    for i, (e, ws, sh) in enumerate(knots):
+        s.irc_e_keV[i], s.irc_e_wscale[i], s.irc_e_shift_rad[i] = e, ws, sh
     return s
 
 

@@ -66,7 +66,8 @@ struct Launch32 {
     float sB_raw[kMaxComp], cB_raw[kMaxComp];   // sin / cos aB(e_ref) without the shift
     // crystal
     float half_d, half_n, thick, R, zc, sphi, cphi;
-    float cos_shift, sin_shift, c_a;
+    float cos_shift[kMaxComp], sin_shift[kMaxComp];   // cos, sin of the peak shift at each reference energy
+    float c_a;
     // rocking curve (argument x = Delta - Delta_M), relative to its maximum
     float irc_fwhm, irc_eta, irc_delta, irc_g, irc_c, irc_gnorm;
     // physics
@@ -99,6 +100,12 @@ struct Launch32 {
     int32_t pol_on, user;
     float pol[3];                         // source polarisation, local frame
     double hc_2d, cs_shift, sn_shift;     // hc / 2d (keV); cos, sin Delta_M
+    double shift0;                        // Delta_M without the energy table
+    // energy-dependent rocking curve: knots, width scale, added shift (n_irc_e = 0: none),
+    // and the table's shift at each component's reference energy
+    int32_t n_irc_e, pad_ie;
+    float irc_e[HEART_MAX_IRC_E], irc_ws[HEART_MAX_IRC_E], irc_sh[HEART_MAX_IRC_E];
+    float sh_ref[kMaxComp];
     const double *ray[10];                // user arrays: ox oy oz kx ky kz E px py pz
     // tabulated spectrum: CDF thresholds on the raw word, in-interval offset and
     // slope, knots relative to the table's mean energy (its e_ref)
@@ -110,7 +117,7 @@ struct Launch32 {
 // a spawned ray waiting for a lane (SoA per warp)
 struct WarpBuf {
     float x[3][kBuf], k[3][kBuf];
-    float A[kBuf], sB[kBuf], mu0[kBuf], qr[kBuf], E[kBuf];
+    float A[kBuf], sB[kBuf], mu0[kBuf], qr[kBuf], E[kBuf], inv_ws[kBuf];
     uint32_t rl[kBuf], rh[kBuf];
     int32_t nb[kBuf];
     // the first segment, prepared while the warp spawns together
@@ -245,7 +252,8 @@ struct Lane {
     float s_exit, Lsum, Lcomp;            // exit distance, Kahan sum of the path
     float inv_mu, pa, inv_1mpa, E;        // segment majorant: 1 / mu, mu0 / mu, 1 / (1 - mu0 / mu)
     uint32_t pa_thr, rl, rh, call;
-    float mu0, qr;                        // per ray: absorption rate, Q R_max
+    float mu0, qr;                        // per ray: absorption rate, Q R_max / w
+    float inv_ws;                         // per ray: 1 / the rocking curve's width scale at E
     // thinned segment: share of process (a) (1: the plain stream), tilt bound,
     // arc bound, first table word of process (b) (its words are [w0, 2^32))
     float ra, qmin, pbar;
@@ -257,10 +265,25 @@ struct Lane {
     bool pol;
 };
 
-// absorption rate mu0 and scatter-candidate rate Q R_max of a ray of energy E (Sec. 2.2.4)
-__device__ __forceinline__ void ray_rates(const Launch32 &L, float E, float Q, int nb, float &mu0, float &qr) {
+// absorption rate mu0 and scatter-candidate rate Q R_max / w of a ray of energy E
+// (Sec. 2.2.4; a rocking curve w times as wide peaks 1/w as high)
+__device__ __forceinline__ void ray_rates(const Launch32 &L, float E, float Q, int nb, float inv_ws, float &mu0,
+                                          float &qr) {
     mu0 = 1.0f / (L.labs * __powf(E / L.labs_ref, L.labs_pow));
-    qr = nb ? 0.0f : Q * L.irc_max;
+    qr = nb ? 0.0f : Q * L.irc_max * inv_ws;
+}
+
+// the energy-dependent rocking curve at E: width scale and added shift, linear
+// between the knots and constant beyond them
+__device__ __forceinline__ void irc_energy32(const Launch32 &L, float E, float &ws, float &sh) {
+    const int n = L.n_irc_e;
+    if (n == 1 || E <= L.irc_e[0]) { ws = L.irc_ws[0]; sh = L.irc_sh[0]; return; }
+    if (E >= L.irc_e[n - 1]) { ws = L.irc_ws[n - 1]; sh = L.irc_sh[n - 1]; return; }
+    int i = 0;
+    while (!(E < L.irc_e[i + 1])) ++i;
+    const float f = (E - L.irc_e[i]) / (L.irc_e[i + 1] - L.irc_e[i]);
+    ws = __fmaf_rn(f, L.irc_ws[i + 1] - L.irc_ws[i], L.irc_ws[i]);
+    sh = __fmaf_rn(f, L.irc_sh[i + 1] - L.irc_sh[i], L.irc_sh[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -268,7 +291,7 @@ __device__ __forceinline__ void ray_rates(const Launch32 &L, float E, float Q, i
 // ---------------------------------------------------------------------------
 template <int GEOM_T>
 __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3], float k[3], float &A,
-                                      float &sB, float &mu0, float &qr, float &E32, int &nb) {
+                                      float &sB, float &mu0, float &qr, float &inv_ws, float &E32, int &nb) {
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
     const uint32_t rl = (uint32_t)ray, rh = (uint32_t)(ray >> 32);
     uint32_t a[4], b[4];
@@ -380,7 +403,7 @@ __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3
         // shift by Delta_M: sin(aB + dM) - sin(aB0 + dM) from small terms
         const float craw = sqrtf(fmaxf(0.0f, __fmaf_rn(-sraw, sraw, 1.0f)));
         const float dc = -ds * (sraw + s0) / (craw + L.cB_raw[c]);
-        const float dsp = __fmaf_rn(ds, L.cos_shift, dc * L.sin_shift);
+        const float dsp = __fmaf_rn(ds, L.cos_shift[c], dc * L.sin_shift[c]);
         sB = L.sB0[c] + dsp;
         A = L.A0[c] + dA - dsp;
         const float lam = 12.398419843320026e-7f / E;     // mm
@@ -389,7 +412,22 @@ __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3
         sB = 2.0f;
         A = 0.0f;
     }
-    ray_rates(L, E, Q, nb, mu0, qr);
+    inv_ws = 1.0f;
+    if (L.n_irc_e > 0) {
+        // energy-dependent curve: width scale, and the shift's small change dM
+        // from the component's reference: sin(a + dM) - sin(a) = c sin dM - 2 s sin^2(dM / 2)
+        float ws, sh;
+        irc_energy32(L, E, ws, sh);
+        inv_ws = 1.0f / ws;
+        if (!nb) {
+            const float dM = sh - L.sh_ref[c], dM2 = dM * dM;
+            const float cs = sqrtf(fmaxf(0.0f, __fmaf_rn(-sB, sB, 1.0f)));
+            const float inc = __fmaf_rn(cs * dM, __fmaf_rn(dM2, -0.166666667f, 1.0f), -0.5f * sB * dM2);
+            sB += inc;
+            A -= inc;
+        }
+    }
+    ray_rates(L, E, Q, nb, inv_ws, mu0, qr);
     return true;
 }
 
@@ -399,7 +437,8 @@ __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3
 // polarisation projected perpendicular to k, zero if unpolarised
 template <int GEOM_T>
 __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float x[3], float k[3], float p[3],
-                                           float &A, float &sB, float &mu0, float &qr, float &E32, int &nb) {
+                                           float &A, float &sB, float &mu0, float &qr, float &inv_ws, float &E32,
+                                           int &nb) {
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
     double E = L.ray[6][id], og[3], kg[3], ol[3], kl[3];
     for (int i = 0; i < 3; ++i) { og[i] = L.ray[i][id] - L.fc[i]; kg[i] = L.ray[3 + i][id]; }
@@ -451,9 +490,17 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
     const double sr = L.hc_2d / E;                        // sin(aB), Eq. (BraggLaw)
     nb = !(sr < 1.0);
     float Q = 0.0f;
+    double cs_s = L.cs_shift, sn_s = L.sn_shift;
+    inv_ws = 1.0f;
+    if (L.n_irc_e > 0) {                                  // energy-dependent rocking curve
+        float ws, sh;
+        irc_energy32(L, (float)E, ws, sh);
+        inv_ws = 1.0f / ws;
+        sincos(L.shift0 + (double)sh, &sn_s, &cs_s);
+    }
     if (!nb) {
         const double cr = sqrt(1.0 - sr * sr);
-        const double sb = sr * L.cs_shift + cr * L.sn_shift;
+        const double sb = sr * cs_s + cr * sn_s;
         sB = (float)sb;
         A = (float)(kN - sb);
         const float lam = 12.398419843320026e-7f / E32;   // mm
@@ -462,7 +509,7 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
         sB = 2.0f;
         A = 0.0f;
     }
-    ray_rates(L, E32, Q, nb, mu0, qr);
+    ray_rates(L, E32, Q, nb, inv_ws, mu0, qr);
     return true;
 }
 
@@ -478,10 +525,18 @@ __device__ __forceinline__ void project_pol32(const Launch32 &L, const float k[3
     for (int i = 0; i < 3; ++i) p[i] *= sc;
 }
 
-// the |k.n| window of |Delta| < X*: (sB + e1, sB + e2), clipped to [0, 1]
-__device__ __forceinline__ void bragg_window(const Launch32 &L, float sB, float cB, float &e1, float &e2) {
-    e1 = sB <= L.sx ? -sB : __fmaf_rn(-sB, L.hx2, -cB * L.sx);
-    e2 = cB <= L.sx ? 1.0f - sB : __fmaf_rn(-sB, L.hx2, cB * L.sx);
+// the |k.n| window of |Delta| < X* w: (sB + e1, sB + e2), clipped to [0, 1]
+// (w: the rocking curve's width scale at the ray's energy)
+__device__ __forceinline__ void bragg_window(const Launch32 &L, float sB, float cB, float inv_ws, float &e1,
+                                             float &e2) {
+    float sx = L.sx, hx2 = L.hx2;
+    if (L.n_irc_e > 0) {
+        const float x = L.xstar / inv_ws, x2 = x * x;     // sin x and 2 sin^2(x / 2) by their series
+        sx = x * __fmaf_rn(x2, __fmaf_rn(x2, 8.33333333e-3f, -0.166666667f), 1.0f);
+        hx2 = 0.5f * x2 * __fmaf_rn(x2, -0.0833333333f, 1.0f);
+    }
+    e1 = sB <= sx ? -sB : __fmaf_rn(-sB, hx2, -cB * sx);
+    e2 = cB <= sx ? 1.0f - sB : __fmaf_rn(-sB, hx2, cB * sx);
 }
 
 // acos(m / b) for b > 0, clamped to [0, pi]; near y = +-1 from the small
@@ -547,7 +602,7 @@ __device__ __forceinline__ void thin_segment(const Launch32 &L, Lane &s, float A
         const float lo = flip ? -s.sB : fminf(s.A, Ae);   // relative to sB; |k.N| passes 0 on a flip
         const float hi = fmaxf(s.A, Ae);
         const float d = lo > 0.0f ? lo : (hi < 0.0f ? -hi : 0.0f);
-        float tmin = d - L.xstar;
+        float tmin = d - (L.n_irc_e > 0 ? L.xstar / s.inv_ws : L.xstar);
         if (tmin > 0.0f) {
             tmin = fminf(tmin, 1.57079637f);
             // sin to float precision: a short series below 0.1 rad, the SFU above (far off Bragg)
@@ -561,7 +616,7 @@ __device__ __forceinline__ void thin_segment(const Launch32 &L, Lane &s, float A
             const float shi = fminf(s.sB + hi, 1.0f);
             const float bmin = sqrtf(fmaxf(0.0f, __fmaf_rn(-shi, shi, 1.0f))) * st * 0.999999f;
             float e1, e2;
-            bragg_window(L, s.sB, s.cB, e1, e2);
+            bragg_window(L, s.sB, s.cB, s.inv_ws, e1, e2);
             // two windows of width w in cos(xi'), each of arc measure <= acos(1 - w) / pi
             const float w = (e2 - e1) / bmin;
             s.pbar = (w >= 2.0f || !(bmin > 0.0f)) ? 1.0f : fminf(1.0f, 0.636619772f * acosf(1.0f - w) * 1.000001f);
@@ -811,7 +866,7 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
         // intervals of y = cos(xi - xi_k) with |k.n| = |kN (1 - q) + b y| in the window,
         // the same-side one from small quantities
         float e1, e2;
-        bragg_window(L, s.sB, s.cB, e1, e2);
+        bragg_window(L, s.sB, s.cB, s.inv_ws, e1, e2);
         const float sa = s.sB + Ac;                           // |k.N| here while k.N keeps its sign
         // interval ends times b: (iv[0], iv[1]) then (iv[2], iv[3])
         float iv[4];
@@ -836,7 +891,7 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
         D = __fmaf_rn(st * ca, cxp, -q * kN);
     }
     const float e = __fmaf_rn(s.sgn, D, Ac);                  // |k.n| - sin(aB + Delta_M)
-    if (v >= irc_bound32<IRC>(L, fabsf(e))) return -1;        // rejected whatever Delta is
+    if (v >= irc_bound32<IRC>(L, fabsf(e) * s.inv_ws)) return -1;   // rejected whatever Delta is
     float sa = s.sB + e;
     float delta;
     if (sa > 0.0f) {
@@ -862,7 +917,7 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
         const float c2 = __fmaf_rn(-2.0f * sa, sa, 1.0f);
         G = 0.5f * __fmaf_rn(c2, c2, 1.0f);                    // Eq. (G_unpol)
     }
-    if (v < irc_rel32<IRC>(L, delta) * G) {
+    if (v < irc_rel32<IRC>(L, delta * s.inv_ws) * G) {    // R(x / w) / R_max
         ++s.nrefl;
         if (s.nrefl > L.max_refl) return HEART_CAPPED;
         // reflection k <- k - 2 (k.n) n (Sec. 2.2.4)
@@ -984,16 +1039,16 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                     const unsigned long long end = s_end;
                     if (base >= end) { more = false; break; }
                     const unsigned long long id = base + lane;
-                    float x[3], k[3], A = 0.f, sB = 0.f, mu0 = 0.f, qr = 0.f, E32 = 0.f;
+                    float x[3], k[3], A = 0.f, sB = 0.f, mu0 = 0.f, qr = 0.f, inv_ws = 1.f, E32 = 0.f;
                     float pv[3] = {0.f, 0.f, 0.f};
                     int nb = 0;
                     bool hit = false;
                     if (id < end) {
                         ++my_emit;
                         if (EXT && L.user) {
-                            hit = spawn_user<GEOM>(L, id, x, k, pv, A, sB, mu0, qr, E32, nb);
+                            hit = spawn_user<GEOM>(L, id, x, k, pv, A, sB, mu0, qr, inv_ws, E32, nb);
                         } else {
-                            hit = spawn<GEOM>(L, L.offset + id, x, k, A, sB, mu0, qr, E32, nb);
+                            hit = spawn<GEOM>(L, L.offset + id, x, k, A, sB, mu0, qr, inv_ws, E32, nb);
                             if (EXT && L.pol_on) project_pol32(L, k, pv);
                         }
                         if (!hit) {
@@ -1023,6 +1078,7 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                         t.rho0 = 0.0f;                           // on the front face
                         t.mu0 = mu0;
                         t.qr = qr;
+                        t.inv_ws = inv_ws;
                         segment<GEOM>(L, t);
                         const int slot = B.count + __popc(hm & lt_mask);
                         for (int i = 0; i < 3; ++i) { B.x[i][slot] = x[i]; B.k[i][slot] = k[i]; }
@@ -1033,6 +1089,7 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                         B.rh[slot] = (uint32_t)(ray >> 32);
                         B.mu0[slot] = mu0;
                         B.qr[slot] = qr;
+                        B.inv_ws[slot] = inv_ws;
                         B.E[slot] = E32;
                         B.nb[slot] = nb;
                         B.s_exit[slot] = t.s_exit;
@@ -1061,6 +1118,7 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                     s.rh = B.rh[slot];
                     s.mu0 = B.mu0[slot];
                     s.qr = B.qr[slot];
+                    s.inv_ws = B.inv_ws[slot];
                     s.E = B.E[slot];
                     s.no_bragg = B.nb[slot];
                     s.s_exit = B.s_exit[slot];
@@ -1164,8 +1222,13 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
     const double axis_sine = std::sqrt(std::fmax(0.0, 1.0 - a_n * a_n));   // cylinder: |k.N| of the axis ray
     L.c_a = (float)axis_sine;
     const double cs = std::cos(S.irc_shift), sn = std::sin(S.irc_shift);
-    L.cos_shift = (float)cs;
-    L.sin_shift = (float)sn;
+    L.n_irc_e = S.n_irc_e;
+    for (int i = 0; i < S.n_irc_e; ++i) {
+        L.irc_e[i] = (float)S.irc_e[i];
+        L.irc_ws[i] = (float)S.irc_ws[i];
+        L.irc_sh[i] = (float)S.irc_sh[i];
+    }
+    L.shift0 = S.irc_shift;
     L.n_comp = P.n_comp;
     for (int i = 0; i < P.n_comp; ++i) {
         // first word w with (w + 1/2) 2^-32 >= cumw
@@ -1192,7 +1255,15 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
         L.sB_raw[i] = (float)s0;
         const double c0 = s0 < 1.0 ? std::sqrt(1.0 - s0 * s0) : 0.0;
         L.cB_raw[i] = (float)c0;
-        const double sBs = s0 < 1.0 ? s0 * cs + c0 * sn : s0;      // sin(aB + Delta_M)
+        // the peak shift at the reference energy: Delta_M plus the energy table's shift there
+        double ws_ref = 1.0, sh_ref = 0.0;
+        if (S.n_irc_e > 0) irc_energy64(S, e_ref, ws_ref, sh_ref);
+        L.sh_ref[i] = (float)sh_ref;
+        const double csi = S.n_irc_e > 0 ? std::cos(S.irc_shift + sh_ref) : cs;
+        const double sni = S.n_irc_e > 0 ? std::sin(S.irc_shift + sh_ref) : sn;
+        L.cos_shift[i] = (float)csi;
+        L.sin_shift[i] = (float)sni;
+        const double sBs = s0 < 1.0 ? s0 * csi + c0 * sni : s0;    // sin(aB + Delta_M)
         L.sB0[i] = (float)sBs;
         // anchor of the cone-axis ray: |a_n| (flat) or the axis sine (cylinder), minus sB
         const double kref = S.geometry == HEART_FLAT ? std::fabs(a_n) : axis_sine;
@@ -1370,6 +1441,7 @@ static heart_status launch_single(const SpecParams &S, const SourceParams &P, ui
                                   uint64_t offset, void *img, unsigned long long *scratch, heart_ray_record *rec,
                                   cudaStream_t st, const QeParams *qe) {
     if (n == 0) return HEART_OK;
+    if (S.n_orders > 1) return fail(HEART_EINVAL, "higher reflection orders need precision FP64");
     Launch32 L;
     make_launch32(S, P, n, seed, offset, L);
     L.img = img;
@@ -1434,6 +1506,7 @@ heart_status launch_batch(const SpecParams *const *S, const SourceParams *P, con
     uint64_t all_rays = 0;
     bool ext = false;
     for (int i = 0; i < n; ++i) {
+        if (S[i]->n_orders > 1) return fail(HEART_EINVAL, "higher reflection orders need precision FP64");
         all_rays += n_rays[i];
         ext |= P[i].pol_on || P[i].user;
     }
@@ -1660,6 +1733,7 @@ extern "C" heart_status heart_trace_batch_static(heart_spectrometer *const *spec
         if (!specs[i]) return fail(HEART_EINVAL, "null spectrometer in batch");
         const size_t elt = specs[i]->p.count_type == HEART_COUNT_I64 ? 8 : 4;
         if (!d_images[i] || ((uintptr_t)d_images[i] % elt) != 0) return fail(HEART_EINVAL, "null or misaligned image in batch");
+        if (specs[i]->p.n_orders > 1) return fail(HEART_EINVAL, "higher reflection orders need precision FP64");
         heart_status st = build_source_params(srcs[i], &g_static_src[i], err, (int)sizeof err);
         if (st != HEART_OK) return fail(st, err);
     }

@@ -218,9 +218,40 @@ __device__ __forceinline__ void detector64(const SpecParams &S, const double x[3
 // [a_lo, a_hi]; a tilt theta < d - X* (d: distance of alpha_B + Delta_M from
 // that range) keeps |Delta| >= X*.  Segments with d <= X* keep the plain stream.
 // ---------------------------------------------------------------------------
-struct Seg64 {
-    double mu, pa, ra, vstar, qmin, pbar, S1, S2;
+// per-ray constants of the reflection orders (Eq. BraggLaw on d / m_h, Q_h,
+// the rocking curve's width scale, and Q_h R_max / w_h, the order's share of
+// the majorant), and the energy-dependent peak shift
+struct Orders64 {
+    int n;
+    double shift;
+    double alpha[HEART_MAX_ORDERS], Q[HEART_MAX_ORDERS], w[HEART_MAX_ORDERS], qr[HEART_MAX_ORDERS];
+};
+
+// the energy-dependent rocking curve at E: width scale and added shift, linear
+// between the knots and constant beyond them
+__host__ __device__ __forceinline__ void irc_energy64(const SpecParams &S, double E, double &ws, double &sh) {
+    ws = 1.0;
+    sh = 0.0;
+    const int n = S.n_irc_e;
+    if (n <= 0) return;
+    if (n == 1 || E <= S.irc_e[0]) { ws = S.irc_ws[0]; sh = S.irc_sh[0]; return; }
+    if (E >= S.irc_e[n - 1]) { ws = S.irc_ws[n - 1]; sh = S.irc_sh[n - 1]; return; }
+    int i = 0;
+    while (!(E < S.irc_e[i + 1])) ++i;
+    const double f = (E - S.irc_e[i]) / (S.irc_e[i + 1] - S.irc_e[i]);
+    ws = S.irc_ws[i] + f * (S.irc_ws[i + 1] - S.irc_ws[i]);
+    sh = S.irc_sh[i] + f * (S.irc_sh[i + 1] - S.irc_sh[i]);
+}
+
+struct Bound64 {
+    double ra, vstar, qmin, pbar, S1, S2, lam;
     unsigned long long w0, wspan;
+};
+
+struct Seg64 {
+    double mu, pa;
+    double cum[HEART_MAX_ORDERS];
+    Bound64 o[HEART_MAX_ORDERS];
 };
 
 // first table word of process (b): that of the tilt-grid point just below q_min
@@ -231,27 +262,19 @@ __device__ __forceinline__ unsigned long long tilt_word64(const SpecParams &S, d
     return (unsigned long long)S.qgrid[j];
 }
 
-__device__ __forceinline__ void bound_segment64(const SpecParams &S, const double *tab, double aB, double Q,
-                                                double mu0, double mubar, double pa, const double x[3],
-                                                const double k[3], Seg64 &b) {
-    b.mu = mubar; b.pa = pa; b.ra = 1.0; b.vstar = 1.0; b.qmin = 0.0; b.pbar = 1.0;
-    b.S1 = 0.0; b.S2 = 0.0; b.w0 = 0ull; b.wspan = 1ull << 32;
-    if (S.sampler != HEART_SAMPLER_THINNED || !(Q > 0)) return;
-    int face;
-    const double se = exit_distance64(S, x, k, &face);
-    double xe[3], N0[3], N1[3], t1[3], t2[3];
-    for (int i = 0; i < 3; ++i) xe[i] = x[i] + se * k[i];
-    local_frame64(S, x, N0, t1, t2);
-    local_frame64(S, xe, N1, t1, t2);
-    const double k0 = dot3d(k, N0), k1 = dot3d(k, N1);
-    double lo = fmin(fabs(k0), fabs(k1));
-    const double hi = fmax(fabs(k0), fabs(k1));
-    if ((k0 < 0) != (k1 < 0)) lo = 0.0;                    // k.N is monotone along a line
+// the thinning bound of order h on a segment with |k.N| in [lo, hi]
+__device__ __forceinline__ void bound_order64(const SpecParams &S, const Orders64 &O, int h, double lo, double hi,
+                                              Bound64 &b) {
+    b.ra = 1.0; b.vstar = 1.0; b.qmin = 0.0; b.pbar = 1.0; b.S1 = 0.0; b.S2 = 0.0;
+    b.w0 = 0ull; b.wspan = 1ull << 32;
+    b.lam = O.qr[h];
+    if (S.sampler != HEART_SAMPLER_THINNED || !(O.qr[h] > 0)) return;
     // distance between sines: never more than between the angles
-    const double aBs = aB + S.irc_shift;
+    const double aBs = O.alpha[h] + O.shift;
+    const double xstar = S.xstar * O.w[h];                 // a curve w times as wide: X* scales by w
     const double sBs = sin(aBs);
     const double d = sBs < lo ? lo - sBs : (sBs > hi ? sBs - hi : 0.0);
-    double tmin = d - S.xstar;
+    double tmin = d - xstar;
     if (!(tmin > 0)) return;
     const double half_pi = 1.5707963267948966;
     if (tmin > half_pi) tmin = half_pi;
@@ -259,20 +282,49 @@ __device__ __forceinline__ void bound_segment64(const SpecParams &S, const doubl
     b.qmin = 2.0 * sh * sh;
     b.w0 = tilt_word64(S, b.qmin);
     b.wspan = (1ull << 32) - b.w0;
-    b.S1 = sin(fmax(0.0, aBs - S.xstar));
-    b.S2 = sin(fmin(half_pi, aBs + S.xstar));
+    b.S1 = sin(fmax(0.0, aBs - xstar));
+    b.S2 = sin(fmin(half_pi, aBs + xstar));
     const double hc = fmin(hi, 1.0);
     const double bmin = sqrt(fmax(0.0, 1.0 - hc * hc)) * sin(tmin);
     // two windows of width w in cos(xi'), each of arc measure <= acos(1 - w) / pi
     const double w = (b.S2 - b.S1) / bmin;
     b.pbar = (w >= 2.0 || !(bmin > 0)) ? 1.0 : fmin(1.0, 2.0 * acos(1.0 - w) / 3.14159265358979323846);
-    const double QR = Q * S.irc_max;
+    const double QR = O.qr[h];
     const double PA = (double)b.wspan / 4294967296.0;
     const double la = QR * S.vstar, lb = QR * (1.0 - S.vstar) * PA * b.pbar;
     b.vstar = S.vstar;
-    b.mu = mu0 + (la + lb);
-    b.pa = mu0 / b.mu;
+    b.lam = la + lb;
     b.ra = la / (la + lb);
+}
+
+__device__ __forceinline__ void bound_segment64(const SpecParams &S, const Orders64 &O, double mu0, bool any_bragg,
+                                                const double x[3], const double k[3], Seg64 &b) {
+    double lo = 0.0, hi = 1.0;
+    if (S.sampler == HEART_SAMPLER_THINNED && any_bragg) {
+        int face;
+        const double se = exit_distance64(S, x, k, &face);
+        double xe[3], N0[3], N1[3], t1[3], t2[3];
+        for (int i = 0; i < 3; ++i) xe[i] = x[i] + se * k[i];
+        local_frame64(S, x, N0, t1, t2);
+        local_frame64(S, xe, N1, t1, t2);
+        const double k0 = dot3d(k, N0), k1 = dot3d(k, N1);
+        lo = fmin(fabs(k0), fabs(k1));
+        hi = fmax(fabs(k0), fabs(k1));
+        if ((k0 < 0) != (k1 < 0)) lo = 0.0;                // k.N is monotone along a line
+    }
+    double lam = 0.0;
+    for (int h = 0; h < O.n; ++h) {
+        bound_order64(S, O, h, lo, hi, b.o[h]);
+        lam += b.o[h].lam;
+    }
+    double run = 0.0;
+    for (int h = 0; h < O.n; ++h) {
+        run += b.o[h].lam;
+        b.cum[h] = lam > 0 ? run / lam : 1.0;
+    }
+    b.cum[O.n - 1] = 1.0;
+    b.mu = mu0 + lam;
+    b.pa = mu0 / b.mu;
 }
 
 // arc measure (in units of pi) of xi' in [0, pi] with |a + b cos xi'| in (S1, S2), and the arcs
@@ -368,27 +420,39 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
         for (int i = 0; i < 3; ++i) { r.pos[i] = o[i]; r.dir[i] = k[i]; r.pol[i] = pol ? pv[i] : 0.0; }
         return;
     }
-    // per-ray constants: Bragg angle (Eq. BraggLaw), mu0, Q, majorant
+    // per-ray constants of each reflection order: Bragg angle (Eq. BraggLaw on
+    // d / m_h), Q_h, the rocking curve's width scale at E and its share of the
+    // majorant Q_h R_max / w_h; mu0 and the peak shift at E
     const double lam_A = 12.398419843320026 / E;
-    const double sB = lam_A / (2.0 * S.d_A);
     const double mu0 = 1.0 / (S.labs * pow(E / S.labs_ref, S.labs_pow));
-    double aB = 0.0, Q = 0.0;
-    if (!(sB < 1.0)) {
-        r.no_bragg = 1;
-    } else {
-        aB = asin(sB);
+    Orders64 O;
+    O.n = S.n_orders;
+    double ws, shE;
+    irc_energy64(S, E, ws, shE);
+    O.shift = S.irc_shift + shE;
+    bool any_bragg = false;
+    for (int h = 0; h < O.n; ++h) {
+        const double sb = S.ord_m[h] * lam_A / (2.0 * S.d_A);
+        O.w[h] = S.ord_w[h] * ws;
+        O.alpha[h] = 0.0;
+        O.Q[h] = 0.0;
+        O.qr[h] = 0.0;
+        if (!(sb < 1.0)) continue;
+        any_bragg = true;
+        O.alpha[h] = asin(sb);
         const double lam = lam_A * 1e-7;
-        Q = S.K * S.K * lam * lam * lam / (2.0 * sB * sqrt(1.0 - sB * sB));
+        const double Kh = S.K * S.ord_k[h];
+        O.Q[h] = Kh * Kh * lam * lam * lam / (2.0 * sb * sqrt(1.0 - sb * sb));
+        O.qr[h] = O.Q[h] * (S.irc_max / O.w[h]);        // a curve w times as wide peaks 1/w as high
     }
-    const double mubar = mu0 + Q * S.irc_max;
-    const double pa = mu0 / mubar;
+    if (!any_bragg) r.no_bragg = 1;
 
     // null-collision walk (Sec. 2.2.4), candidates thinned per straight segment
     int outcome = HEART_STUCK, nrefl = 0;
     long long ncoll = 0;
     uint32_t call = 2;
     Seg64 sb;
-    bound_segment64(S, tab, aB, Q, mu0, mubar, pa, x, k, sb);
+    bound_segment64(S, O, mu0, any_bragg, x, k, sb);
     for (;;) {
         if (ncoll >= S.max_coll) { outcome = HEART_STUCK; break; }
         uint32_t wd[4];
@@ -406,26 +470,35 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
         const double u1 = u01_64(wd[1]);
         if (u1 < sb.pa) { outcome = HEART_ABSORBED; break; }
         double v = (u1 - sb.pa) / (1.0 - sb.pa);
+        // the reflection order by its share of the candidate rate (sum over H);
+        // the conditional uniform stays the acceptance uniform
+        int h = 0;
+        if (O.n > 1) {
+            while (h < O.n - 1 && !(v < sb.cum[h])) ++h;
+            const double c0 = h > 0 ? sb.cum[h - 1] : 0.0;
+            v = (v - c0) / (sb.cum[h] - c0);
+        }
+        const Bound64 &ob = sb.o[h];
         double N[3], t1[3], t2[3];
         local_frame64(S, x, N, t1, t2);
         double q, sx, cx;
-        if (v < sb.ra) {                                      // process (a), or the plain stream
-            v = sb.ra < 1.0 ? (v / sb.ra) * sb.vstar : v;
+        if (v < ob.ra) {                                      // process (a), or the plain stream
+            v = ob.ra < 1.0 ? (v / ob.ra) * ob.vstar : v;
             q = mdf_q64(tab, wd[2]);
             sincospi(2.0 * u01_64(wd[3]), &sx, &cx);
         } else {                                              // process (b)
-            v = sb.vstar + (1.0 - sb.vstar) * ((v - sb.ra) / (1.0 - sb.ra));
-            const uint32_t wq = (uint32_t)(sb.w0 + (((unsigned long long)wd[2] * sb.wspan) >> 32));
+            v = ob.vstar + (1.0 - ob.vstar) * ((v - ob.ra) / (1.0 - ob.ra));
+            const uint32_t wq = (uint32_t)(ob.w0 + (((unsigned long long)wd[2] * ob.wspan) >> 32));
             q = mdf_q64(tab, wq);
-            if (q < sb.qmin || q > 2.0 - sb.qmin) continue;  // cannot reflect
+            if (q < ob.qmin || q > 2.0 - ob.qmin) continue;  // cannot reflect
             const double kN = dot3d(k, N), sa_ = fabs(kN), ca_ = sqrt(fmax(0.0, 1.0 - kN * kN));
             const double a = (kN < 0 ? -sa_ : sa_) * (1.0 - q), b = ca_ * sqrt(q * (2.0 - q));
             double arc[4];
-            const double Pxi = azimuth_arcs64(a, b, sb.S1, sb.S2, arc);
+            const double Pxi = azimuth_arcs64(a, b, ob.S1, ob.S2, arc);
             const double t3 = u01_64(wd[3]);
-            if (!(t3 * sb.pbar < Pxi)) continue;              // outside the arcs: cannot reflect
+            if (!(t3 * ob.pbar < Pxi)) continue;              // outside the arcs: cannot reflect
             const double L = arc[1] + arc[3];
-            double pos = (t3 * sb.pbar / Pxi) * 2.0 * L, sgn = 1.0;
+            double pos = (t3 * ob.pbar / Pxi) * 2.0 * L, sgn = 1.0;
             if (pos >= L) { pos -= L; sgn = -1.0; }
             const double xp = pos < arc[1] ? arc[0] + pos : arc[2] + (pos - arc[1]);
             sincos(atan2(dot3d(k, t2), dot3d(k, t1)) + sgn * xp, &sx, &cx);
@@ -436,7 +509,7 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
         const double kn = dot3d(k, n);
         double sa = fabs(kn);
         sa = sa > 1.0 ? 1.0 : sa;
-        const double delta = asin(sa) - aB - S.irc_shift;
+        const double delta = asin(sa) - O.alpha[h] - O.shift;
         double ks[3];                                         // reflected direction
         for (int i = 0; i < 3; ++i) ks[i] = k[i] - 2.0 * kn * n[i];
         double G;
@@ -447,7 +520,8 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
             const double c2 = 1.0 - 2.0 * sa * sa;            // cos(2 a~)
             G = 0.5 * (1.0 + c2 * c2);                        // Eq. (G_unpol)
         }
-        if (v < irc64(S, delta) * G / S.irc_max) {
+        // order h's curve is the described one w_h times as wide: R_h / R_h,max = R(x / w_h) / R_max
+        if (v < irc64(S, delta / O.w[h]) * G / S.irc_max) {
             ++nrefl;
             if (nrefl > S.max_refl) { outcome = HEART_CAPPED; break; }
             const double inv = 1.0 / sqrt(dot3d(ks, ks));
@@ -459,7 +533,7 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
                 const double pn = 1.0 / sqrt(dot3d(pv, pv));
                 for (int i = 0; i < 3; ++i) pv[i] *= pn;
             }
-            bound_segment64(S, tab, aB, Q, mu0, mubar, pa, x, k, sb);   // a new straight segment
+            bound_segment64(S, O, mu0, any_bragg, x, k, sb);   // a new straight segment
         }
     }
     r.outcome = outcome;

@@ -299,6 +299,31 @@ heart_status build_spec_params(const heart_spectrometer_desc *d, SpecParams *p, 
     REQUIRE(d->thin_vstar >= 0 && d->thin_vstar < 1, "thin_vstar in [0, 1)");
     p->sampler = d->sampler;
     p->vstar = d->thin_vstar > 0 ? d->thin_vstar : 1.0 / 1024.0;   // X* is set by the caller
+    REQUIRE(d->n_orders >= 0 && d->n_orders <= HEART_MAX_ORDERS, "0..4 reflection orders");
+    p->n_orders = d->n_orders > 0 ? d->n_orders : 1;
+    if (d->n_orders == 0) {
+        p->ord_m[0] = 1;
+        p->ord_k[0] = 1.0;
+        p->ord_w[0] = 1.0;
+    }
+    for (int h = 0; h < d->n_orders; ++h) {
+        REQUIRE(d->order_m[h] >= 1 && std::isfinite(d->order_K_rel[h]) && d->order_K_rel[h] >= 0 &&
+                    std::isfinite(d->order_w_rel[h]) && d->order_w_rel[h] > 0,
+                "order: multiple >= 1, K ratio >= 0, width ratio > 0");
+        p->ord_m[h] = d->order_m[h];
+        p->ord_k[h] = d->order_K_rel[h];
+        p->ord_w[h] = d->order_w_rel[h];
+    }
+    REQUIRE(d->n_irc_e >= 0 && d->n_irc_e <= HEART_MAX_IRC_E, "0..16 energy knots of the rocking curve");
+    p->n_irc_e = d->n_irc_e;
+    for (int i = 0; i < d->n_irc_e; ++i) {
+        REQUIRE(std::isfinite(d->irc_e_wscale[i]) && d->irc_e_wscale[i] > 0 && std::isfinite(d->irc_e_shift_rad[i]),
+                "rocking-curve energy knots: width scale > 0, finite shift");
+        if (i > 0) REQUIRE(d->irc_e_keV[i] > d->irc_e_keV[i - 1], "rocking-curve energy knots must ascend");
+        p->irc_e[i] = d->irc_e_keV[i];
+        p->irc_ws[i] = d->irc_e_wscale[i];
+        p->irc_sh[i] = d->irc_e_shift_rad[i];
+    }
     p->max_coll = d->max_collisions;
     p->thickness = d->thickness_mm;
     p->radius = d->radius_mm;

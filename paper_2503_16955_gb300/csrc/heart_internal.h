@@ -49,6 +49,12 @@ struct SpecParams {
     // beyond which R / R_max <= v*
     int32_t sampler, pad_s;
     double vstar, xstar;
+    // reflection orders (n_orders >= 1): multiple, K ratio, width ratio
+    int32_t n_orders, n_irc_e;
+    int32_t ord_m[HEART_MAX_ORDERS];
+    double ord_k[HEART_MAX_ORDERS], ord_w[HEART_MAX_ORDERS];
+    // energy-dependent rocking curve: knots, width scale, added shift
+    double irc_e[HEART_MAX_IRC_E], irc_ws[HEART_MAX_IRC_E], irc_sh[HEART_MAX_IRC_E];
     // device tables: q = 1 - cos(theta) at the body knots then the tail knots
     const double *mdf64;
     const float *mdf32;

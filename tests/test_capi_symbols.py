@@ -41,7 +41,8 @@ def _c_layout(tmp_path):
         "heart_source_desc": ["spot_fwhm_mm", "polarization", "table_keV", "n_table"],
         "heart_ray_arrays": ["energy_keV", "pol_z"],
         "heart_qe_table": ["n"],
-        "heart_spectrometer_desc": ["pixel_mm", "count_type", "sampler", "thin_vstar"],
+        "heart_spectrometer_desc": ["pixel_mm", "count_type", "sampler", "thin_vstar", "n_orders",
+                                    "order_K_rel", "irc_e_keV", "irc_e_shift_rad"],
         "heart_tune": ["rays_per_s"],
         "heart_ray_record": ["u_mm", "no_bragg", "pol"],
     }
