@@ -36,6 +36,8 @@ LANES_PER_SM_CLK = 128         # 4 SM sub-partitions x 32 lanes, one warp-instru
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) of one k_trace_fp32 launch, from the ncu capture in
 # profiles/k_trace_fp32_von_hamos.md; valid only for the kernel sources hashed there
+# rays per chunk of the two-pass trace (the library's largest hit-queue chunk)
+WAVE_CHUNK = 1 << 24
 TRAFFIC_BYTES = 607_744
 TRAFFIC_SOURCES = ("paper_2503_16955_gb300/csrc/heart_fp32.cu", "paper_2503_16955_gb300/csrc/heart_fp64.cuh",
                    "paper_2503_16955_gb300/csrc/heart_internal.h")
@@ -374,16 +376,16 @@ def main():
                        "l2": "inputs are per-ray counters (no input data); the 4 MB image stays in L2"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-instr/s",
                          "frac": achieved / peak, "traffic": measured_traffic(),
-                         "traffic_note": "ncu dram__bytes_read+write of one launch (2e7-ray capture); table "
-                                         "staging per block, does not grow with rays",
-                         "kernel": "k_trace_fp32 (persistent, one launch per step)",
+                         "traffic_note": "ncu dram__bytes_read+write of the step's launches (hit queue "
+                                         "written by the spawn pass and read by the walk pass)",
+                         "kernel": "k_spawn32 + k_walk32 (two passes per chunk of up to 2^24 rays)",
                          "peak_basis": "152 SMs x 128 lanes x 2070 MHz (max SM clock); algorithmic "
                                        "%d instr/collision + %d instr/segment + %d instr/ray"
                                        % (INSTR_PER_COLLISION, INSTR_PER_SEGMENT, INSTR_PER_RAY)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": img_bytes,
                     "d2h_bytes_per_step": img_bytes + 27 * 8,
                     "path": "heart_trace_host (host image uploaded, traced, downloaded each step)"},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * 2 * ((n + WAVE_CHUNK - 1) // WAVE_CHUNK),
             "clocks": clocks,
             "cpu_baseline": cpu,
             **extra,

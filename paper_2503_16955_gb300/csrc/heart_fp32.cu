@@ -1184,6 +1184,177 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
 }
 
 // ---------------------------------------------------------------------------
+// Two-pass ("wavefront") trace of one job, for image traces of one reflection
+// order without polarisation or user rays.  With the thinned sampler a ray
+// makes about one tentative collision, so the per-ray work (source, entry,
+// preparing the entry segment) weighs as much as the walk: doing it in a
+// separate pass, one thread per ray at full occupancy, and handing the hits
+// to the walk pass through a compacted queue in global memory (chunks of
+// kWaveCap rays, which keeps the queue near the L2) spends far fewer issue
+// slots than spawning inside the walk loop.  Both passes run the same device
+// functions as the persistent kernel, so every ray is traced identically.
+// ---------------------------------------------------------------------------
+// a prepared hit: 18 float fields and 5 word fields, structure of arrays
+enum : int {
+    WF_X = 0, WF_K = 3, WF_A = 6, WF_SB, WF_MU0, WF_QR, WF_IWS, WF_E, WF_SEXIT, WF_IMU, WF_PA, WF_RA, WF_QMIN, WF_PBAR,
+    WF_NF
+};
+enum : int { WU_RL = 0, WU_RH, WU_W0, WU_FACE, WU_NB, WU_N };
+
+__device__ __forceinline__ float *wave_f(const WaveBuf &B, int f) { return (float *)B.base + (size_t)f * B.cap; }
+__device__ __forceinline__ uint32_t *wave_u(const WaveBuf &B, int f) {
+    return (uint32_t *)B.base + (size_t)(WF_NF + f) * B.cap;
+}
+
+// pass 1: one thread per ray of [first, first + count): source, entry and the
+// entry segment; hits are appended to the queue (warp-aggregated), misses tallied
+template <int GEOM>
+__global__ void __launch_bounds__(256) k_spawn32(const __grid_constant__ Launch32 L, const __grid_constant__ WaveBuf B,
+                                                 uint64_t first, uint32_t count, unsigned long long *n_hits) {
+    __shared__ unsigned int s_emit, s_miss;
+    if (threadIdx.x == 0) { s_emit = 0u; s_miss = 0u; }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < count;
+    const uint64_t id = first + i;
+    float x[3] = {0.f, 0.f, 0.f}, k[3] = {0.f, 0.f, 0.f};
+    float A = 0.f, sB = 0.f, mu0 = 0.f, qr = 0.f, inv_ws = 1.f, E32 = 0.f;
+    int nb = 0;
+    bool hit = false;
+    if (valid) hit = spawn<GEOM>(L, L.offset + id, x, k, A, sB, mu0, qr, inv_ws, E32, nb);
+    Lane t;
+    if (hit) {
+        for (int j = 0; j < 3; ++j) { t.x0[j] = x[j]; t.k[j] = k[j]; }
+        t.A = A;
+        t.sB = sB;
+        t.cB = sqrtf(fmaxf(0.0f, __fmaf_rn(-sB, sB, 1.0f)));
+        t.sgn = -1.0f;                                       // entering: k.N < 0
+        t.rho0 = 0.0f;                                       // on the front face
+        t.mu0 = mu0;
+        t.qr = qr;
+        t.inv_ws = inv_ws;
+        segment<GEOM>(L, t);
+    }
+    const unsigned hm = __ballot_sync(0xffffffffu, hit);
+    const unsigned vm = __ballot_sync(0xffffffffu, valid);
+    unsigned long long base = 0;
+    if (lane == 0 && hm) base = atomicAdd(n_hits, (unsigned long long)__popc(hm));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (hit) {
+        const size_t slot = base + __popc(hm & ((1u << lane) - 1u));
+        for (int j = 0; j < 3; ++j) { wave_f(B, WF_X + j)[slot] = t.x0[j]; wave_f(B, WF_K + j)[slot] = t.k[j]; }
+        wave_f(B, WF_A)[slot] = A;
+        wave_f(B, WF_SB)[slot] = sB;
+        wave_f(B, WF_MU0)[slot] = mu0;
+        wave_f(B, WF_QR)[slot] = qr;
+        wave_f(B, WF_IWS)[slot] = inv_ws;
+        wave_f(B, WF_E)[slot] = E32;
+        wave_f(B, WF_SEXIT)[slot] = t.s_exit;
+        wave_f(B, WF_IMU)[slot] = t.inv_mu;
+        wave_f(B, WF_PA)[slot] = t.pa;
+        wave_f(B, WF_RA)[slot] = t.ra;
+        wave_f(B, WF_QMIN)[slot] = t.qmin;
+        wave_f(B, WF_PBAR)[slot] = t.pbar;
+        const uint64_t ray = L.offset + id;
+        wave_u(B, WU_RL)[slot] = (uint32_t)ray;
+        wave_u(B, WU_RH)[slot] = (uint32_t)(ray >> 32);
+        wave_u(B, WU_W0)[slot] = t.w0;
+        wave_u(B, WU_FACE)[slot] = (uint32_t)t.face;
+        wave_u(B, WU_NB)[slot] = (uint32_t)nb;
+    }
+    if (lane == 0) {
+        atomicAdd(&s_emit, (unsigned)__popc(vm));
+        atomicAdd(&s_miss, (unsigned)__popc(vm & ~hm));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_emit) atomicAdd(&L.tally[T_EMITTED], (unsigned long long)s_emit);
+        if (s_miss) atomicAdd(&L.tally[T_MISS], (unsigned long long)s_miss);
+    }
+}
+
+// pass 2: a persistent grid walks the queued hits; idle lanes take the next
+// ones (warp-aggregated) once at least `refill` lanes of the warp are idle
+template <int GEOM, int IRC, int OCC>
+__global__ void __launch_bounds__(kBlockThreads, OCC)
+    k_walk32(const __grid_constant__ Launch32 L, const __grid_constant__ WaveBuf B,
+             const unsigned long long *n_hits, unsigned long long *head) {
+    __shared__ float s_tab[kMdfKnots];
+    __shared__ BlockTally bt;
+    for (int i = threadIdx.x; i < kMdfKnots; i += blockDim.x) s_tab[i] = L.tab[i];
+    for (int i = threadIdx.x; i < kTallyN; i += blockDim.x) bt.t[i] = 0u;
+    if (threadIdx.x == 0) { bt.coll = 0ull; bt.emit = 0ull; bt.miss = 0ull; }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const unsigned long long nh = *(volatile const unsigned long long *)n_hits;
+    Lane s;
+    bool alive = false, more = true;
+    unsigned long long my_coll = 0;
+    for (;;) {
+        const unsigned idle = __ballot_sync(0xffffffffu, !alive);
+        const int n_idle = __popc(idle);
+        if (!more && n_idle == 32) break;
+        if (more && (n_idle >= L.refill || n_idle == 32)) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(head, (unsigned long long)n_idle);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base + n_idle >= nh) more = false;
+            const unsigned long long slot = base + __popc(idle & lt_mask);
+            if (!alive && slot < nh) {
+                for (int j = 0; j < 3; ++j) { s.x0[j] = wave_f(B, WF_X + j)[slot]; s.k[j] = wave_f(B, WF_K + j)[slot]; }
+                s.A = wave_f(B, WF_A)[slot];
+                s.sB = wave_f(B, WF_SB)[slot];
+                s.mu0 = wave_f(B, WF_MU0)[slot];
+                s.qr = wave_f(B, WF_QR)[slot];
+                s.inv_ws = wave_f(B, WF_IWS)[slot];
+                s.E = wave_f(B, WF_E)[slot];
+                s.s_exit = wave_f(B, WF_SEXIT)[slot];
+                s.inv_mu = wave_f(B, WF_IMU)[slot];
+                s.pa = wave_f(B, WF_PA)[slot];
+                s.ra = wave_f(B, WF_RA)[slot];
+                s.qmin = wave_f(B, WF_QMIN)[slot];
+                s.pbar = wave_f(B, WF_PBAR)[slot];
+                s.rl = wave_u(B, WU_RL)[slot];
+                s.rh = wave_u(B, WU_RH)[slot];
+                s.w0 = wave_u(B, WU_W0)[slot];
+                s.face = (int)wave_u(B, WU_FACE)[slot];
+                s.no_bragg = (int)wave_u(B, WU_NB)[slot];
+                s.inv_1mpa = s.pa < 1.0f ? 1.0f / (1.0f - s.pa) : 0.0f;
+                s.pa_thr = s.pa >= 1.0f ? 0xFFFFFFFFu
+                                        : __float2uint_ru(fminf(s.pa * 4294967296.0f, 4294967040.0f));
+                s.cB = sqrtf(fmaxf(0.0f, __fmaf_rn(-s.sB, s.sB, 1.0f)));
+                s.sgn = -1.0f;
+                s.rho0 = 0.0f;
+                s.call = 2u;
+                s.nrefl = 0;
+                s.ncoll = 0;
+                s.pol = false;
+                segment_consts<GEOM>(L, s);
+                alive = true;
+            }
+        }
+        if (alive) {
+            const int oc = step<GEOM, IRC, false>(L, s, s_tab);
+            if (oc >= 0) {
+                my_coll += (unsigned long long)s.ncoll;
+                finish<false, false>(L, s, oc, bt);
+                alive = false;
+            }
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) my_coll += __shfl_down_sync(0xffffffffu, my_coll, off);
+    if (lane == 0) atomicAdd(&bt.coll, my_coll);
+    __syncthreads();
+    unsigned long long *T = L.tally;
+    for (int i = threadIdx.x; i < kTallyN; i += blockDim.x) {
+        const unsigned long long v = i == T_COLLISIONS ? bt.coll : (unsigned long long)bt.t[i];
+        if (v && i != T_EMITTED && i != T_MISS) atomicAdd(&T[i], v);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side: crystal-frame parameters, small-quantity anchors and launch
 // ---------------------------------------------------------------------------
 namespace {
@@ -1462,9 +1633,78 @@ static heart_status launch_single(const SpecParams &S, const SourceParams &P, ui
     return rec ? dispatch<true>(L, W, st, false, ext) : dispatch<false>(L, W, st, false, ext);
 }
 
+template <int GEOM, int IRC>
+static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t n, unsigned long long *ctr,
+                                  cudaStream_t st) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk32<GEOM, IRC, 6>, kBlockThreads, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int walk_blocks = per_sm * num_sms();
+    const uint64_t chunks = (n + B.cap - 1) / B.cap;
+    for (uint64_t c = 0; c < chunks; ++c) {
+        const uint64_t g = c % kWaveGroup;
+        if (g == 0) {
+            const uint64_t left = chunks - c < (uint64_t)kWaveGroup ? chunks - c : (uint64_t)kWaveGroup;
+            cudaError_t e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long) * left, st);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync hit counters");
+        }
+        unsigned long long *cc = ctr + 2 * g;
+        const uint64_t first = c * B.cap;
+        const uint32_t count = (uint32_t)(n - first < B.cap ? n - first : B.cap);
+        k_spawn32<GEOM><<<(count + 255) / 256, 256, 0, st>>>(L, B, first, count, cc);
+        k_walk32<GEOM, IRC, 6><<<walk_blocks, kBlockThreads, 0, st>>>(L, B, cc, cc + 1);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "FP32 two-pass launch");
+    return HEART_OK;
+}
+
+heart_status ensure_wave(heart_spectrometer *h, uint64_t n) {
+    const uint32_t cap = wave_cap_for(n);
+    if (h->d_wave && h->wave_cap >= cap) return HEART_OK;
+    if (h->d_wave) cudaFree(h->d_wave);          // a larger trace than before: grow
+    h->d_wave = nullptr;
+    h->wave_cap = 0;
+    cudaError_t e = cudaMalloc(&h->d_wave, wave_bytes(cap));
+    if (e != cudaSuccess) { h->d_wave = nullptr; return cuda_fail(e, "cudaMalloc hit queue"); }
+    h->wave_cap = cap;
+    return HEART_OK;
+}
+
 heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
-                         void *img, unsigned long long *scratch, cudaStream_t st, const QeParams *qe) {
-    return launch_single(S, P, n, seed, offset, img, scratch, nullptr, st, qe);
+                         void *img, unsigned long long *scratch, cudaStream_t st, const QeParams *qe, void *wave,
+                         uint32_t wave_cap) {
+    if (!wave || n == 0 || S.n_orders > 1 || P.pol_on || P.user)
+        return launch_single(S, P, n, seed, offset, img, scratch, nullptr, st, qe);
+    // the two-pass trace: the per-ray work in its own pass, then the walk
+    Launch32 L;
+    make_launch32(S, P, n, seed, offset, L);
+    L.img = img;
+    L.tally = scratch;
+    L.rec = nullptr;
+    if (qe) {
+        L.eimg = qe->eimg;
+        L.n_qe = qe->n;
+        for (int i = 0; i < qe->n; ++i) { L.qe_e[i] = (float)qe->keV[i]; L.qe_v[i] = (float)qe->qe[i]; }
+    }
+    WaveBuf B;
+    B.base = wave;
+    B.cap = wave_cap;
+    B.pad = 0;
+    unsigned long long *ctr = (unsigned long long *)((char *)wave + (size_t)23 * 4 * wave_cap);
+#define HEART_WAVE_CASES(G)                                                                          \
+    switch (L.irc_kind) {                                                                            \
+    case HEART_IRC_DARWIN: return launch_wave_t<G, HEART_IRC_DARWIN>(L, B, n, ctr, st);             \
+    case HEART_IRC_DARWIN_PRINS: return launch_wave_t<G, HEART_IRC_DARWIN_PRINS>(L, B, n, ctr, st); \
+    case HEART_IRC_PSEUDO_VOIGT: return launch_wave_t<G, HEART_IRC_PSEUDO_VOIGT>(L, B, n, ctr, st); \
+    case HEART_IRC_GAUSSIAN: return launch_wave_t<G, HEART_IRC_GAUSSIAN>(L, B, n, ctr, st);         \
+    case HEART_IRC_LORENTZIAN: return launch_wave_t<G, HEART_IRC_LORENTZIAN>(L, B, n, ctr, st);     \
+    default: return launch_wave_t<G, HEART_IRC_BOX>(L, B, n, ctr, st);                               \
+    }
+    if (L.geometry == HEART_FLAT) { HEART_WAVE_CASES(HEART_FLAT) } else { HEART_WAVE_CASES(HEART_CYL_VON_HAMOS) }
+#undef HEART_WAVE_CASES
 }
 
 heart_status launch_fp32_records(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed,
@@ -1606,6 +1846,10 @@ extern "C" heart_status heart_autotune(heart_spectrometer *h, const heart_source
     heart_status st = build_source_params(src, &P, err, (int)sizeof err, &spectrum);
     if (st != HEART_OK) return fail(st, err);
     cudaStream_t cs = (cudaStream_t)stream;
+    if (!P.pol_on && !P.user && h->p.n_orders == 1) {
+        st = ensure_wave(h, probe_rays);
+        if (st != HEART_OK) return st;
+    }
     void *d_spec = nullptr;
     if (!spectrum.empty()) {
         cudaError_t e0 = cudaMallocAsync(&d_spec, spectrum.size(), cs);
@@ -1646,7 +1890,8 @@ extern "C" heart_status heart_autotune(heart_spectrometer *h, const heart_source
             for (int rep = 0; rep < 2; ++rep) {       // first repetition warms up
                 cudaMemsetAsync(h->d_scratch, 0, kScratchWords * sizeof(unsigned long long), cs);
                 cudaEventRecord(t0, cs);
-                st = launch_fp32(h->p, P, probe_rays, 0x5eed + rep, 0, h->d_image_host_path, h->d_scratch, cs);
+                st = launch_fp32(h->p, P, probe_rays, 0x5eed + rep, 0, h->d_image_host_path, h->d_scratch, cs,
+                                 nullptr, h->d_wave, h->wave_cap);
                 cudaEventRecord(t1, cs);
                 if (st != HEART_OK) break;
                 if ((e = cudaEventSynchronize(t1)) != cudaSuccess) { st = cuda_fail(e, "autotune probe"); break; }

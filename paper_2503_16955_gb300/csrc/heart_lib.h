@@ -8,6 +8,7 @@
 #include "heart.h"
 #include "heart_internal.h"
 
+struct heart_spectrometer;
 namespace heart {
 // device scratch words per handle: tallies, then work counters of the
 // persistent kernels
@@ -30,8 +31,27 @@ int num_sms();
 heart_status launch_fp64(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
                          void *img, unsigned long long *tally, heart_ray_record *rec, cudaStream_t st,
                          const QeParams *qe = nullptr);
+// queue of prepared hits for the two-pass FP32 trace: chunks of `cap` rays
+// (a power of two from 2^20 to 2^24), 23 four-byte fields per hit, then 2
+// counters per chunk for kWaveGroup chunks
+constexpr uint32_t kWaveMinCap = 1u << 20, kWaveMaxCap = 1u << 24;
+constexpr int kWaveGroup = 1024;
+inline size_t wave_bytes(uint32_t cap) { return (size_t)23 * 4 * cap + (size_t)2 * 8 * kWaveGroup; }
+inline uint32_t wave_cap_for(uint64_t n) {
+    uint32_t c = kWaveMinCap;
+    while (c < kWaveMaxCap && (uint64_t)c < n) c <<= 1;
+    return c;
+}
+struct WaveBuf {
+    void *base;
+    uint32_t cap, pad;
+};
+// wave / wave_cap: the handle's queue (nullptr: the one-pass persistent kernel)
 heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
-                         void *img, unsigned long long *scratch, cudaStream_t st, const QeParams *qe = nullptr);
+                         void *img, unsigned long long *scratch, cudaStream_t st, const QeParams *qe = nullptr,
+                         void *wave = nullptr, uint32_t wave_cap = 0);
+// make sure the handle's queue holds chunks of wave_cap_for(n) rays (grows, never shrinks)
+heart_status ensure_wave(heart_spectrometer *h, uint64_t n);
 heart_status launch_fp32_records(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed,
                                  uint64_t offset, void *img, unsigned long long *scratch, heart_ray_record *rec,
                                  cudaStream_t st, const QeParams *qe = nullptr);
@@ -56,4 +76,6 @@ struct heart_spectrometer {
     unsigned long long *h_scratch = nullptr;   // pinned tally copy
     void *d_image_host_path = nullptr;    // image buffer of heart_trace_host
     size_t host_image_bytes = 0;
+    void *d_wave = nullptr;               // hit queue of the two-pass FP32 trace (on first use)
+    uint32_t wave_cap = 0;                // rays per chunk the queue holds
 };
