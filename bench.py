@@ -34,24 +34,25 @@ INSTR_PER_SEGMENT = 120        # exit distance, grazing-angle range, tilt bound,
 SM_COUNT = 152
 LANES_PER_SM_CLK = 128         # 4 SM sub-partitions x 32 lanes, one warp-instruction issue each per clock
 SM_MAX_MHZ = 2070.0
-# DRAM bytes (read + write) of one k_trace_fp32 launch, from the ncu capture in
-# profiles/k_trace_fp32_von_hamos.md; valid only for the kernel sources hashed there
 # rays per chunk of the two-pass trace (the library's largest hit-queue chunk)
 WAVE_CHUNK = 1 << 24
-TRAFFIC_BYTES = 607_744
+# DRAM bytes (read + write) of the two passes per traced ray, from the ncu capture in
+# profiles/k_spawn32_k_walk32_von_hamos.md (1168.7 MB for 1.6e7 rays: the hit queue written
+# and read back); valid only for the kernel sources hashed there
+TRAFFIC_BYTES_PER_RAY = 1168.736e6 / 1.6e7
 TRAFFIC_SOURCES = ("paper_2503_16955_gb300/csrc/heart_fp32.cu", "paper_2503_16955_gb300/csrc/heart_fp64.cuh",
                    "paper_2503_16955_gb300/csrc/heart_internal.h")
-TRAFFIC_SOURCE_HASH = "5510d27ebc6dcb49"
+TRAFFIC_SOURCE_HASH = "e5ccc0a79f7fc182"
 
 
-def measured_traffic():
-    """per-launch DRAM traffic, or None if the kernel changed since the capture"""
+def measured_traffic(n_rays):
+    """DRAM traffic of one step of n_rays, or None if the kernels changed since the capture"""
     import hashlib
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    return TRAFFIC_BYTES if h.hexdigest()[:16] == TRAFFIC_SOURCE_HASH else None
+    return TRAFFIC_BYTES_PER_RAY * n_rays if h.hexdigest()[:16] == TRAFFIC_SOURCE_HASH else None
 
 
 def parse():
@@ -375,9 +376,10 @@ def main():
                        "detector_hits_per_s": value * det_frac,
                        "l2": "inputs are per-ray counters (no input data); the 4 MB image stays in L2"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-instr/s",
-                         "frac": achieved / peak, "traffic": measured_traffic(),
-                         "traffic_note": "ncu dram__bytes_read+write of the step's launches (hit queue "
-                                         "written by the spawn pass and read by the walk pass)",
+                         "frac": achieved / peak, "traffic": measured_traffic(n),
+                         "traffic_note": "ncu dram__bytes_read+write of the step's launches, per step (hit "
+                                         "queue written by the spawn pass and read by the walk pass; "
+                                         "captured on 1.6e7 rays, scaled by rays)",
                          "kernel": "k_spawn32 + k_walk32 (two passes per chunk of up to 2^24 rays)",
                          "peak_basis": "152 SMs x 128 lanes x 2070 MHz (max SM clock); algorithmic "
                                        "%d instr/collision + %d instr/segment + %d instr/ray"
