@@ -14,7 +14,8 @@ from . import build as _build
 
 GEOMETRY = {"flat": 0, "cyl": 1}
 MDF = {"gaussian": 0, "lorentzian": 1, "pseudo_voigt": 2, "vmf": 3, "wl": 4, "swl": 5, "uniform": 6}
-IRC = {"darwin": 0, "darwin_prins": 1, "pseudo_voigt": 2, "gaussian": 3, "lorentzian": 4, "box": 5}
+IRC = {"darwin": 0, "darwin_prins": 1, "pseudo_voigt": 2, "gaussian": 3, "lorentzian": 4, "box": 5,
+       "none": 6}
 SRC = {"mono": 0, "gauss": 1, "lorentz": 2, "inv_e": 3, "uniform": 4, "table": 5}
 OUTCOME = {0: "miss", 1: "absorbed", 2: "exit_front", 3: "exit_back", 4: "exit_side",
            5: "capped", 6: "stuck"}
@@ -443,6 +444,8 @@ def sample_crystallites(spec_dict, E, alpha, n, seed):
     got = lib().orc_sample_crystallites(C.byref(s), E, alpha, n, seed,
                                         dl.ctypes.data_as(C.POINTER(C.c_double)),
                                         ps.ctypes.data_as(C.POINTER(C.c_double)))
+    if got < 0:
+        raise RuntimeError(_err())
     return dl[:got], ps[:got]
 
 

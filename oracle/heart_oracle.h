@@ -35,6 +35,9 @@
  *                                    order 1 on d/m; thin-slab reflection probability and per-order
  *                                    shares vs the quadrature summed over orders)
  *   energy-dependent IRC     pinned (constant table = wider, shifted curve; interpolation and clamping)
+ *   IRC "none" (Bragg cone)  pinned (k_in . k_out = cos 2a~0 on every single reflection; thin-slab reflection
+ *                                    probability vs quadrature along the cone and, for vMF, the Bessel closed
+ *                                    form; the limit of ever narrower box curves; accepted psi ~ W(theta(psi)))
  *   tabulated spectrum       pinned (KS against the piecewise-linear CDF written from the knots; a
  *                                    two-knot table reproduces the uniform component bit for bit)
  *   orc_trace_energy         pinned (mono line: energy image = E x QE x counts; QE interpolation)
@@ -56,7 +59,10 @@ enum { ORC_FLAT = 0, ORC_CYL = 1 };
 enum { ORC_MDF_GAUSSIAN = 0, ORC_MDF_LORENTZIAN = 1, ORC_MDF_PSEUDO_VOIGT = 2,
        ORC_MDF_VMF = 3, ORC_MDF_WL = 4, ORC_MDF_SWL = 5, ORC_MDF_UNIFORM = 6 };
 enum { ORC_IRC_DARWIN = 0, ORC_IRC_DARWIN_PRINS = 1, ORC_IRC_PSEUDO_VOIGT = 2,
-       ORC_IRC_GAUSSIAN = 3, ORC_IRC_LORENTZIAN = 4, ORC_IRC_BOX = 5 };
+       ORC_IRC_GAUSSIAN = 3, ORC_IRC_LORENTZIAN = 4, ORC_IRC_BOX = 5,
+       /* no rocking curve (Sec. 2.2.1, "none"): R(Delta) = delta(Delta), unit
+        * area; crystallites reflect only at a~ = aB + Delta_M exactly */
+       ORC_IRC_NONE = 6 };
 enum { ORC_SRC_MONO = 0, ORC_SRC_GAUSS = 1, ORC_SRC_LORENTZ = 2, ORC_SRC_INV_E = 3,
        ORC_SRC_UNIFORM = 4, ORC_SRC_TABLE = 5 };
 enum { ORC_MISS = 0, ORC_ABSORBED = 1, ORC_EXIT_FRONT = 2, ORC_EXIT_BACK = 3,
@@ -186,7 +192,8 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 /* pseudo-Voigt total width and eta (Sec. 2.2.1) */
 void orc_pv_width(double fg, double fl, double *fwhm, double *eta);
 
-/* IRC, unit area, argument = Delta - Delta_M (rad) */
+/* IRC, unit area, argument = Delta - Delta_M (rad); ORC_IRC_NONE has no
+ * finite value and returns 0 */
 double orc_irc(const orc_spec *s, double x);
 double orc_irc_max(const orc_spec *s);
 double orc_darwin_prins_area(double g);       /* integral of R(y) dy */

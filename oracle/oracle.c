@@ -28,6 +28,13 @@
  *    equation of Sec. 2.2.4).  The walk ends at the first boundary crossing of
  *    the free path (exit), at absorption, at the (n_max+1)-th reflection
  *    (CAPPED) or at the per-ray collision cap (STUCK).
+ *  No rocking curve (Sec. 2.2.1, IRC "none"): R(Delta) = delta(Delta).  Only
+ *    crystallites at exactly a~0 = aB + Delta_M reflect; their normals lie on
+ *    the two cones k.n = -/+ sin a~0 about k, and with dOmega = cos a~ da~ dpsi
+ *    the rate becomes Q cos a~0 sum_cones int_0^2pi f(n(psi)) G dpsi.  The
+ *    candidates then carry the bound Q cos a~0 * 2 cones * 2 pi f(0) instead of
+ *    Q max R, and a candidate picks a cone and a uniform psi and is kept with
+ *    probability f(n) G / f(0) (f from the MDF's own formula).
  *  Detector (Sec. 2.3): exiting rays are propagated to the detector plane and
  *    binned into integer pixel counts.
  *
@@ -251,6 +258,7 @@ static double irc_eval(const irc_params *p, double x) {
     case ORC_IRC_GAUSSIAN: return gauss_shape(x, p->fwhm);
     case ORC_IRC_LORENTZIAN: return lorentz_shape(x, p->fwhm);
     case ORC_IRC_BOX: return fabs(x) <= 0.5 * p->fwhm ? 1.0 / p->fwhm : 0.0;
+    case ORC_IRC_NONE: return 0.0;           /* a delta function: no finite value */
     }
     return 0.0;
 }
@@ -529,7 +537,20 @@ static int spec_orders(const orc_spec *s, int m[ORC_MAX_ORDERS], double kr[ORC_M
     return n;
 }
 
+/* no rocking curve: the scatter-candidate rate of an order is Q cos a~0 times
+ * 2 cones x 2 pi f(0), f = W / (2 pi int W dq) the MDF per unit solid angle;
+ * this returns 2 * 2 pi f(0) = 2 W(0) / int W dq */
+static double none_factor(const orc_spec *s) {
+    return 2.0 * orc_mdf_W(s, 0.0) / orc_mdf_norm(s);
+}
+
+static int ray_constants(const orc_spec *s, double E, double none_fac, orc_ray_consts *c);
+
 int orc_ray_constants(const orc_spec *s, double E, orc_ray_consts *c) {
+    return ray_constants(s, E, s->irc == ORC_IRC_NONE ? none_factor(s) : 0.0, c);
+}
+
+static int ray_constants(const orc_spec *s, double E, double none_fac, orc_ray_consts *c) {
     memset(c, 0, sizeof *c);
     c->E_keV = E;
     c->lambda_A = HC_KEV_A / E;
@@ -557,6 +578,10 @@ int orc_ray_constants(const orc_spec *s, double E, orc_ray_consts *c) {
         double Kh = K * kr[h];
         c->ord_Q[h] = Kh * Kh * lam_mm * lam_mm * lam_mm / (2.0 * sb * cb);
         c->ord_qr[h] = c->ord_Q[h] * (rmax / c->ord_w[h]);   /* a curve w times as wide peaks 1/w as high */
+        if (s->irc == ORC_IRC_NONE) {
+            double a0 = c->ord_alpha[h] + c->shift_rad;          /* the only reflecting incidence */
+            c->ord_qr[h] = (a0 > 0.0 && a0 < 0.5 * PI) ? c->ord_Q[h] * cos(a0) * none_fac : 0.0;
+        }
         qr_sum += c->ord_qr[h];
     }
     c->sin_aB = c->ord_sin[0];
@@ -583,6 +608,9 @@ typedef struct {
     orc_mdf_table *mdf;
     /* thinned sampler: v* and the IRC half-width X* beyond which R/R_max <= v* */
     double vstar, xstar;
+    /* no rocking curve: the factor of none_factor() and W(0) */
+    int irc_none;
+    double none_fac, W0;
 } geom;
 
 /* X*: the smallest |x| such that R(x') / R_max <= v* for every |x'| >= X*.
@@ -650,7 +678,14 @@ static int geom_init(geom *g, const orc_spec *s) {
             return fail("rocking-curve energy knots: width scale > 0, finite shift");
         if (i > 0 && !(s->irc_e_keV[i] > s->irc_e_keV[i - 1])) return fail("rocking-curve energy knots must ascend");
     }
-    if (s->sampler == ORC_SAMPLER_THINNED) {
+    if (s->irc == ORC_IRC_NONE) {
+        /* candidates on the Bragg cones; the thinned bounds (which need X*) do not apply */
+        g->irc_none = 1;
+        g->W0 = orc_mdf_W(s, 0.0);
+        g->none_fac = none_factor(s);
+        if (!(g->W0 > 0) || !(g->none_fac > 0) || !isfinite(g->none_fac)) return fail("MDF has no mass at theta = 0");
+        if (s->sampler != ORC_SAMPLER_PLAIN && s->sampler != ORC_SAMPLER_THINNED) return fail("unknown sampler");
+    } else if (s->sampler == ORC_SAMPLER_THINNED) {
         g->vstar = s->thin_vstar > 0 ? s->thin_vstar : 1.0 / 1024.0;
         if (!(g->vstar < 1.0)) return fail("thin_vstar must be < 1");
         g->xstar = irc_xstar(&g->irc, g->irc_max, g->vstar);
@@ -865,7 +900,7 @@ static void bound_order(const geom *g, const orc_ray_consts *rc, int h, double l
     b->pbar = 1.0;
     b->wspan = 1ull << 32;
     b->lam = rc->ord_qr[h];
-    if (s->sampler != ORC_SAMPLER_THINNED || !(rc->ord_qr[h] > 0)) return;
+    if (s->sampler != ORC_SAMPLER_THINNED || s->irc == ORC_IRC_NONE || !(rc->ord_qr[h] > 0)) return;
     double aB = rc->ord_alpha[h] + rc->shift_rad;
     double xstar = g->xstar * rc->ord_w[h];          /* a curve w times as wide: X* scales by w */
     double sB = sin(aB);
@@ -898,7 +933,7 @@ static void bound_segment(const geom *g, const orc_ray_consts *rc, const double 
     memset(b, 0, sizeof *b);
     b->n = rc->n_orders;
     double lo = 0.0, hi = 1.0;
-    if (s->sampler == ORC_SAMPLER_THINNED && !rc->no_bragg) {
+    if (s->sampler == ORC_SAMPLER_THINNED && s->irc != ORC_IRC_NONE && !rc->no_bragg) {
         int face;
         double se = exit_distance(g, x, k, &face);
         double xe[3], N0[3], N1[3], t1[3], t2[3];
@@ -943,6 +978,45 @@ static double azimuth_arcs(double a, double b, double S1, double S2, double arc[
     return tot / PI;
 }
 
+/* unit vectors perpendicular to k: e1 along the part of N perpendicular to k
+ * (t1's part when k is along N), e2 = k x e1 */
+static void cone_axes(const double k[3], const double N[3], const double t1[3], double e1[3], double e2[3]) {
+    double kN = dot3(k, N);
+    for (int i = 0; i < 3; ++i) e1[i] = N[i] - kN * k[i];
+    if (normalize3(e1)) {
+        double kt = dot3(k, t1);
+        for (int i = 0; i < 3; ++i) e1[i] = t1[i] - kt * k[i];
+        normalize3(e1);
+    }
+    cross3(k, e1, e2);
+}
+
+/* a scatter candidate of order h without rocking curve: the crystallite normal
+ * n = sg sin(a~0) k + cos(a~0) (cos(psi) e1 + sin(psi) e2) on the cone
+ * k.n = sg sin(a~0), sg = -1 if the top bit of u2 is clear, +1 if set;
+ * psi = 2 pi u3.  P = f(n) G / f(0) = W(1 - n.N) G / W(0). */
+static void cone_candidate(const geom *g, const orc_ray_consts *rc, int h, const double x[3], const double k[3],
+                           int pol, const double p[3], const uint32_t w[4], double ks[3], double *P) {
+    double N[3], t1[3], t2[3], e1[3], e2[3], n[3];
+    local_frame(g, x, N, t1, t2);
+    cone_axes(k, N, t1, e1, e2);
+    double a0 = rc->ord_alpha[h] + rc->shift_rad, s0 = sin(a0), c0 = cos(a0);
+    double sg = (w[2] & 0x80000000u) ? 1.0 : -1.0;
+    double psi = 2.0 * PI * U(w[3]);
+    for (int i = 0; i < 3; ++i) n[i] = sg * s0 * k[i] + c0 * (cos(psi) * e1[i] + sin(psi) * e2[i]);
+    double q = 1.0 - dot3(n, N);                     /* 1 - cos(theta), the crystallite's tilt */
+    for (int i = 0; i < 3; ++i) ks[i] = k[i] - 2.0 * (sg * s0) * n[i];   /* k.n = sg s0 */
+    double G;
+    if (pol) {
+        double pk = dot3(p, ks);
+        G = 1.0 - pk * pk;                           /* Eq. (G_pol) */
+    } else {
+        double c2 = cos(2.0 * a0);
+        G = 0.5 * (1.0 + c2 * c2);                   /* Eq. (G_unpol) at a~0 */
+    }
+    *P = orc_mdf_W(g->s, q) / g->W0 * G;
+}
+
 /* the depth walk of one ray from its entry point (Sec. 2.2.4) */
 static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[3], int pol, double p[3],
                  wsrc *ws, orc_record *rec) {
@@ -976,6 +1050,11 @@ static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[
             while (h < sb.n - 1 && !(v < sb.cum[h])) ++h;
             double c0 = h > 0 ? sb.cum[h - 1] : 0.0;
             v = (v - c0) / (sb.cum[h] - c0);
+        }
+        double ks[3], P;                                 /* reflected direction, acceptance probability */
+        if (g->irc_none) {
+            cone_candidate(g, rc, h, x, k, pol, p, w, ks, &P);
+            goto decide;
         }
         const order_bound *ob = &sb.o[h];
         double N[3], t1[3], t2[3];
@@ -1011,8 +1090,7 @@ static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[
         if (sa > 1.0) sa = 1.0;
         double at = asin(sa);                            /* incidence on the crystallite */
         double delta = at - rc->ord_alpha[h] - rc->shift_rad;
-        double ks[3];                                    /* reflected direction (reflection equation) */
-        for (int i = 0; i < 3; ++i) ks[i] = k[i] - 2.0 * kn * n[i];
+        for (int i = 0; i < 3; ++i) ks[i] = k[i] - 2.0 * kn * n[i];   /* reflection equation */
         double G;
         if (pol) {
             double pk = dot3(p, ks);
@@ -1022,7 +1100,8 @@ static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[
             G = 0.5 * (1.0 + c2 * c2);                   /* Eq. (G_unpol) */
         }
         /* the order's curve is the described one w_h times as wide: R_h / R_h,max = R(x / w_h) / R_max */
-        double P = irc_eval(&g->irc, delta / rc->ord_w[h]) * G / g->irc_max;
+        P = irc_eval(&g->irc, delta / rc->ord_w[h]) * G / g->irc_max;
+    decide:
         if (v < P) {
             ++nrefl;
             if (nrefl > s->max_reflections) { outcome = ORC_CAPPED; break; }
@@ -1181,7 +1260,7 @@ static void trace_one(job *J, uint64_t i) {
         rec.u_mm = NAN; rec.v_mm = NAN; rec.ix = -1; rec.iy = -1;
     } else {
         orc_ray_consts rc;
-        orc_ray_constants(s, E, &rc);
+        ray_constants(s, E, g->none_fac, &rc);
         if (rc.no_bragg) J->tally.no_bragg++;
         rec.no_bragg = rc.no_bragg;
         walk(g, &rc, p, k, pol, pv, &ws, &rec);
@@ -1363,7 +1442,7 @@ int orc_walk_injected_n(const orc_spec *s, int64_t n, const double *E, const dou
     g.mdf = tab;
     for (int64_t i = 0; i < n; ++i) {
         orc_ray_consts rc;
-        orc_ray_constants(s, E[i], &rc);
+        ray_constants(s, E[i], g.none_fac, &rc);
         wsrc ws = {0};
         ws.words = words + i * words_per_ray; ws.n = words_per_ray; ws.pos = 0;
         double x[3], k[3];
@@ -1391,6 +1470,7 @@ int orc_walk_injected(const orc_spec *s, double E, const double pos[3], const do
 /* ------------------------------------------------------------------ */
 int64_t orc_sample_crystallites(const orc_spec *s, double E, double alpha, int64_t n,
                                 uint64_t seed, double *delta_out, double *psi_out) {
+    if (s->irc == ORC_IRC_NONE) return fail("no rocking curve: every accepted Delta is 0");
     orc_mdf_table *tab = (orc_mdf_table *)malloc(sizeof(orc_mdf_table));
     if (!tab) return fail("out of memory");
     if (orc_mdf_build_table(s, tab)) { free(tab); return -1; }
@@ -1483,6 +1563,15 @@ double orc_reflection_rate(const orc_spec *s, double E, double alpha) {
         if (!(rc.ord_Q[h] > 0)) continue;
         rr_ctx c = {s, alpha, 0.0, Z, rc.ord_alpha[h], rc.shift_rad, rc.ord_w[h], {0}};
         irc_prepare(s, &c.irc);
+        if (s->irc == ORC_IRC_NONE) {
+            /* R = delta(Delta): the outer integral is its integrand at Delta = 0 */
+            double at = rc.ord_alpha[h] + rc.shift_rad;
+            if (!(at > 0 && at < 0.5 * PI)) continue;
+            c.at = at;
+            double c2 = cos(2.0 * at);
+            total += rc.ord_Q[h] * cos(at) * 0.5 * (1.0 + c2 * c2) * rr_psi_integral(&c);
+            continue;
+        }
         double lo = -(rc.ord_alpha[h] + rc.shift_rad), hi = 0.5 * PI - rc.ord_alpha[h] - rc.shift_rad;
         /* geometric panels in |x| on each side of the IRC centre */
         double w = (s->irc_fwhm_rad > 0 ? s->irc_fwhm_rad : 1e-5) * rc.ord_w[h];
