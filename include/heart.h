@@ -71,7 +71,15 @@ typedef enum {
     HEART_IRC_PSEUDO_VOIGT = 2,      /* pseudo-Voigt from Gaussian/Lorentz FWHM */
     HEART_IRC_GAUSSIAN = 3,
     HEART_IRC_LORENTZIAN = 4,
-    HEART_IRC_BOX = 5
+    HEART_IRC_BOX = 5,
+    /* no rocking curve (Sec. 2.2.1, "none"): R(Delta) = delta(Delta), so only
+     * crystallites at exactly aB + Delta_M reflect (irc_fwhm_rad is ignored).
+     * Candidates are drawn on the two Bragg cones k.n = -/+ sin(aB + Delta_M)
+     * about the ray, at the rate Q cos(aB + Delta_M) 4 pi f(0) (f: the MDF per
+     * unit solid angle), and kept with probability f(n) G / f(0); the sampler
+     * field does not apply.  The cost per ray grows as 1 / Gamma^2 for narrow
+     * mosaics. */
+    HEART_IRC_NONE = 6
 } heart_irc;
 
 typedef enum { HEART_FP64 = 0, HEART_FP32 = 1 } heart_precision;
@@ -132,7 +140,7 @@ typedef struct {
     double mdf_eta;                 /* pseudo-Voigt MDF Lorentzian fraction */
     int32_t irc;                    /* heart_irc */
     int32_t max_reflections;        /* the (n+1)-th reflection ends the ray as CAPPED */
-    double irc_fwhm_rad;            /* Darwin/DP: Darwin FWHM; G/L/box: FWHM; pV: Gaussian FWHM */
+    double irc_fwhm_rad;            /* Darwin/DP: Darwin FWHM; G/L/box: FWHM; pV: Gaussian FWHM; none: unused */
     double irc_lorentz_fwhm_rad;    /* pV: Lorentzian FWHM */
     double irc_shift_rad;           /* Delta_M, peak position of the IRC */
     double prins_g;                 /* Darwin-Prins absorption parameter */

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libheart.so")
 
 GEOMETRY = {"flat": 0, "cyl": 1}
 MDF = {"gaussian": 0, "lorentzian": 1, "pseudo_voigt": 2, "vmf": 3, "wl": 4, "swl": 5, "uniform": 6}
-IRC = {"darwin": 0, "darwin_prins": 1, "pseudo_voigt": 2, "gaussian": 3, "lorentzian": 4, "box": 5}
+IRC = {"darwin": 0, "darwin_prins": 1, "pseudo_voigt": 2, "gaussian": 3, "lorentzian": 4, "box": 5, "none": 6}
 SRC = {"mono": 0, "gauss": 1, "lorentz": 2, "inv_e": 3, "uniform": 4, "table": 5}
 PRECISION = {"fp64": 0, "fp32": 1}
 COUNT = {"i32": 0, "i64": 1}

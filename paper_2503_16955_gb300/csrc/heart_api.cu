@@ -183,7 +183,7 @@ extern "C" heart_status heart_spectrometer_create(const heart_spectrometer_desc 
     char err[256] = {0};
     heart_status st = build_spec_params(desc, &p, tab.data(), err, (int)sizeof err);
     if (st != HEART_OK) return fail(st, err);
-    if (p.sampler == HEART_SAMPLER_THINNED) {
+    if (p.sampler == HEART_SAMPLER_THINNED && p.irc != HEART_IRC_NONE) {
         p.xstar = rocking_half_width(p);
         if (!(p.xstar > 0)) return fail(HEART_EINVAL, "rocking curve does not fall below v* within 1 rad");
     }
@@ -311,7 +311,7 @@ static heart_status trace_impl(heart_spectrometer *h, const heart_source_desc *s
                                  cs, qe);
     } else {
         // the two-pass trace needs the handle's hit queue (allocated on first use)
-        if (!P.pol_on && !P.user && h->p.n_orders == 1) {
+        if (!P.pol_on && !P.user && h->p.n_orders == 1 && h->p.irc != HEART_IRC_NONE) {
             st = ensure_wave(h, n_rays);
             if (st != HEART_OK) return st;
         }

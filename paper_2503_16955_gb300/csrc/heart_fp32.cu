@@ -96,6 +96,10 @@ struct Launch32 {
     // 2 sin^2(X*/2), sin X* (the |k.n| window of |Delta| < X* from sin(aB + dM))
     int32_t sampler;
     float vstar, xstar, hx2, sx;
+    // no rocking curve: cone-candidate factor 2 W(0) / int W dq and the mosaic
+    // distribution's W(q) / W(0) in closed form (mdf_ratio32)
+    int32_t mdf;
+    float none_fac, w_a2, w_c, w_wl, w_wg, w_b, w_qmax;
     // polarisation and user-supplied rays (the extended kernel only)
     int32_t pol_on, user;
     float pol[3];                         // source polarisation, local frame
@@ -266,11 +270,33 @@ struct Lane {
 };
 
 // absorption rate mu0 and scatter-candidate rate Q R_max / w of a ray of energy E
-// (Sec. 2.2.4; a rocking curve w times as wide peaks 1/w as high)
-__device__ __forceinline__ void ray_rates(const Launch32 &L, float E, float Q, int nb, float inv_ws, float &mu0,
-                                          float &qr) {
+// (Sec. 2.2.4; a rocking curve w times as wide peaks 1/w as high); without a
+// rocking curve Q cos(aB + Delta_M) x 2 cones x 2 pi f(0), sB = sin(aB + Delta_M)
+__device__ __forceinline__ void ray_rates(const Launch32 &L, float E, float Q, int nb, float inv_ws, float sB,
+                                          float &mu0, float &qr) {
     mu0 = 1.0f / (L.labs * __powf(E / L.labs_ref, L.labs_pow));
-    qr = nb ? 0.0f : Q * L.irc_max * inv_ws;
+    if (L.irc_kind == HEART_IRC_NONE)
+        qr = (nb || !(sB > 0.0f)) ? 0.0f : Q * sqrtf(fmaxf(0.0f, __fmaf_rn(-sB, sB, 1.0f))) * L.none_fac;
+    else
+        qr = nb ? 0.0f : Q * L.irc_max * inv_ws;
+}
+
+// W(q) / W(0) of the mosaic distribution, q = 1 - cos(theta)
+__device__ __forceinline__ float mdf_ratio32(const Launch32 &L, float q) {
+    switch (L.mdf) {
+    case HEART_MDF_VMF: return __expf(-L.w_c * q);
+    case HEART_MDF_WRAPPED_LORENTZIAN: return __fdividef(L.w_a2, __fmaf_rn(2.0f, q, L.w_a2));
+    case HEART_MDF_SPHERICAL_WRAPPED_LORENTZIAN: {
+        const float r = __fdividef(L.w_b, L.w_b + q);
+        return r * r;
+    }
+    case HEART_MDF_UNIFORM: return q <= L.w_qmax ? 1.0f : 0.0f;
+    default: {
+        const float th = 2.0f * asinf(sqrtf(0.5f * fminf(fmaxf(q, 0.0f), 2.0f)));
+        const float t2 = th * th;
+        return __fmaf_rn(L.w_wl, __fdividef(L.w_a2, L.w_a2 + t2), L.w_wg * __expf(-L.w_c * t2));
+    }
+    }
 }
 
 // the energy-dependent rocking curve at E: width scale and added shift, linear
@@ -427,7 +453,7 @@ __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3
             A -= inc;
         }
     }
-    ray_rates(L, E, Q, nb, inv_ws, mu0, qr);
+    ray_rates(L, E, Q, nb, inv_ws, sB, mu0, qr);
     return true;
 }
 
@@ -509,7 +535,7 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
         sB = 2.0f;
         A = 0.0f;
     }
-    ray_rates(L, E32, Q, nb, inv_ws, mu0, qr);
+    ray_rates(L, E32, Q, nb, inv_ws, sB, mu0, qr);
     return true;
 }
 
@@ -596,7 +622,7 @@ __device__ __forceinline__ uint32_t tilt_word32(const Launch32 &L, float qmin) {
 __device__ __forceinline__ void thin_segment(const Launch32 &L, Lane &s, float A_exit, bool flip) {
     float la = s.qr, lb = 0.0f;
     s.ra = 1.0f;
-    if (L.sampler == HEART_SAMPLER_THINNED && s.qr > 0.0f) {
+    if (L.sampler == HEART_SAMPLER_THINNED && s.qr > 0.0f && L.irc_kind != HEART_IRC_NONE) {
         // |k.N| at the exit is sB + A_exit, or -(sB + A_exit) if k.N changed sign
         const float Ae = flip ? -2.0f * s.sB - A_exit : A_exit;
         const float lo = flip ? -s.sB : fminf(s.A, Ae);   // relative to sB; |k.N| passes 0 on a flip
@@ -818,6 +844,91 @@ __device__ __forceinline__ void crystallite_normal(const Launch32 &L, const Lane
     }
 }
 
+// A scatter candidate without rocking curve (R a delta function): the
+// crystallite normal on the Bragg cone k.n = sg sin(a~0), a~0 = aB + Delta_M,
+// sg = +1 if the top bit of u2 is set, at azimuth psi = 2 pi u3 about k
+// measured from the part of N perpendicular to k; kept with probability
+// W(q) G / W(0).  In the collision's frame (t1, t2, N) with k = (k0, kt, kN)
+// and c = sqrt(1 - kN^2): e1 = (-kN k0, -kN kt, c^2) / c, e2 = (kt, -k0, 0) / c,
+// and the tilt q = 1 - n.N = q0 + c0 c (1 - cos psi) with q0 = 1 - cos(g -+ a~0),
+// sin g = |kN|.  On the cone facing the ray (sg = sign kN) q0 comes from the
+// anchor Ac = |kN| - sin a~0 without cancellation:
+//   q0 = Ac^2 (c0 + s0 (2 s0 + Ac) / (c0 + c)) / (c0 + c).
+template <int GEOM_T, bool EXT>
+__device__ __forceinline__ int cone_step(const Launch32 &L, Lane &s, uint32_t w2, uint32_t w3, float v, float Ac,
+                                         float kN, float kt2, float eps, float rho) {
+    const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
+    const float s0 = s.sB, c0 = s.cB;
+    const float sa = s0 + Ac;                                   // |k.N| at the collision
+    const float cb = sqrtf(fmaxf(0.0f, __fmaf_rn(-sa, sa, 1.0f)));
+    const float sg = (w2 & 0x80000000u) ? 1.0f : -1.0f;
+    float q0;
+    if (sg == s.sgn) {
+        const float cs = c0 + cb;
+        q0 = Ac * Ac * __fdividef(__fmaf_rn(s0, __fdividef(__fmaf_rn(2.0f, s0, Ac), cs), c0), cs);
+    } else {
+        q0 = __fmaf_rn(s0, sa, __fmaf_rn(-c0, cb, 1.0f));       // 1 - cos(g + a~0)
+    }
+    float sh, ch;
+    sincospif(u01_32(w3), &sh, &ch);                         // psi / 2, accurate near 0
+    const float C = c0 * cb;
+    const float omc = 2.0f * sh * sh;                           // 1 - cos psi
+    const float q = __fmaf_rn(C, omc, q0);
+    // n in the collision frame
+    const float k0 = s.k[0], cp = 1.0f - omc, sp = 2.0f * sh * ch;
+    const float ic = cb > 1e-20f ? 1.0f / cb : 0.0f;
+    float nl0, nl1;
+    if (cb > 1e-20f) {
+        nl0 = __fmaf_rn(sg * s0, k0, c0 * (__fmaf_rn(cp, -kN * k0, sp * kt2)) * ic);
+        nl1 = __fmaf_rn(sg * s0, kt2, c0 * (__fmaf_rn(cp, -kN * kt2, -sp * k0)) * ic);
+    } else {                                                    // k along N: any axes perpendicular to k
+        nl0 = c0 * cp;
+        nl1 = c0 * sp;
+    }
+    float n[3], drho = 0.0f, G;
+    crystallite_normal<GEOM_T>(L, s, 1.0f, nl1, nl0, q, eps, rho, n, drho);
+    const float kn = sg * s0;                                   // k.n
+    if (EXT && s.pol) {
+        float pk = 0.0f, pn = 0.0f;
+        for (int i = 0; i < 3; ++i) { pk = __fmaf_rn(s.p[i], s.k[i], pk); pn = __fmaf_rn(s.p[i], n[i], pn); }
+        const float pks = __fmaf_rn(-2.0f * kn, pn, pk);
+        G = __fmaf_rn(-pks, pks, 1.0f);                         // Eq. (G_pol)
+    } else {
+        const float c2 = __fmaf_rn(-2.0f * s0, s0, 1.0f);
+        G = 0.5f * __fmaf_rn(c2, c2, 1.0f);                     // Eq. (G_unpol) at a~0
+    }
+    if (!(v < mdf_ratio32(L, q) * G)) return -1;
+    ++s.nrefl;
+    if (s.nrefl > L.max_refl) return HEART_CAPPED;
+    if (GEOM != HEART_FLAT) s.rho0 += drho;
+    float kk = 0.0f;
+    for (int i = 0; i < 3; ++i) {
+        s.x0[i] = __fmaf_rn(s.Lsum, s.k[i], s.x0[i]);
+        s.k[i] = __fmaf_rn(-2.0f * kn, n[i], s.k[i]);
+        kk = __fmaf_rn(s.k[i], s.k[i], kk);
+    }
+    const float sc = rsqrtf(kk);
+    for (int i = 0; i < 3; ++i) s.k[i] *= sc;
+    if (EXT && s.pol) {
+        float pk = 0.0f;
+        for (int i = 0; i < 3; ++i) pk = __fmaf_rn(s.p[i], s.k[i], pk);
+        float pp = 0.0f;
+        for (int i = 0; i < 3; ++i) { s.p[i] = __fmaf_rn(-pk, s.k[i], s.p[i]); pp = __fmaf_rn(s.p[i], s.p[i], pp); }
+        const float ps = rsqrtf(pp);
+        for (int i = 0; i < 3; ++i) s.p[i] *= ps;
+    }
+    // k'.N = sign(kN) T: T = Ac - s0 + 2 q s0 on the facing cone, sa + 2 s0 (1 - q) on the other
+    const float T = (sg == s.sgn) ? __fmaf_rn(2.0f * q, s0, Ac - s0) : __fmaf_rn(2.0f * s0, 1.0f - q, sa);
+    if (T < 0.0f) {
+        s.A = (sg == s.sgn) ? __fmaf_rn(-2.0f * q, s0, -Ac) : -T - s0;
+        s.sgn = -s.sgn;
+    } else {
+        s.A = T - s0;
+    }
+    segment<GEOM_T>(L, s);
+    return -1;
+}
+
 template <int GEOM_T, int IRC, bool EXT>
 __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab) {
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
@@ -849,6 +960,7 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
         kN = s.ck0 + dk;
     }
     const float Ac = __fmaf_rn(s.sgn, dk, s.A);               // anchor at the collision point
+    if ((IRC >= 0 ? IRC : L.irc_kind) == HEART_IRC_NONE) return cone_step<GEOM_T, EXT>(L, s, w[2], w[3], v, Ac, kN, kt2, eps, rho);
     float q, st, sx, cx, D;
     if (v < s.ra) {                                           // process (a), or the plain stream
         if (s.ra < 1.0f) v = (v / s.ra) * L.vstar;
@@ -1473,6 +1585,14 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
     L.labs_pow = (float)S.labs_pow;
     L.K2 = (float)(S.K * S.K);
     L.irc_max = (float)S.irc_max;
+    L.mdf = S.mdf;
+    L.none_fac = (float)S.none_fac;
+    L.w_a2 = (float)S.w_a2;
+    L.w_c = (float)S.w_c;
+    L.w_wl = (float)S.w_wl;
+    L.w_wg = (float)S.w_wg;
+    L.w_b = (float)S.w_b;
+    L.w_qmax = (float)S.w_qmax;
     L.max_refl = S.max_refl;
     L.max_coll = S.max_coll;
     double D0[3], eu[3], ev[3], nd[3];
@@ -1588,7 +1708,8 @@ static heart_status dispatch(const Launch32 &L, const WorkPlan &W, cudaStream_t 
     if (W.n_chunks == 0) return HEART_OK;
     if (ext) {
         launch_occ<-1, -1, REC, 6, true>(L, W, st, W.n_chunks);
-    } else if (generic) {
+    } else if (generic || L.irc_kind == HEART_IRC_NONE) {
+        // no rocking curve: the generic kernel's run-time branch (rare option, no own instantiation)
         launch_t<-1, -1, REC>(L, W, st);
     } else {
 #define HEART_IRC_CASES(G)                                                                    \
@@ -1676,7 +1797,7 @@ heart_status ensure_wave(heart_spectrometer *h, uint64_t n) {
 heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
                          void *img, unsigned long long *scratch, cudaStream_t st, const QeParams *qe, void *wave,
                          uint32_t wave_cap) {
-    if (!wave || n == 0 || S.n_orders > 1 || P.pol_on || P.user)
+    if (!wave || n == 0 || S.n_orders > 1 || P.pol_on || P.user || S.irc == HEART_IRC_NONE)
         return launch_single(S, P, n, seed, offset, img, scratch, nullptr, st, qe);
     // the two-pass trace: the per-ray work in its own pass, then the walk
     Launch32 L;
@@ -1846,7 +1967,7 @@ extern "C" heart_status heart_autotune(heart_spectrometer *h, const heart_source
     heart_status st = build_source_params(src, &P, err, (int)sizeof err, &spectrum);
     if (st != HEART_OK) return fail(st, err);
     cudaStream_t cs = (cudaStream_t)stream;
-    if (!P.pol_on && !P.user && h->p.n_orders == 1) {
+    if (!P.pol_on && !P.user && h->p.n_orders == 1 && h->p.irc != HEART_IRC_NONE) {
         st = ensure_wave(h, probe_rays);
         if (st != HEART_OK) return st;
     }

@@ -104,6 +104,43 @@ __host__ __device__ __forceinline__ double irc64(const SpecParams &S, double x) 
     }
 }
 
+// W(q) / W(0) of the mosaic distribution, q = 1 - cos(theta) (the closed forms
+// set up by the host: theta shapes, vMF, WL, SWL, uniform)
+__device__ __forceinline__ double mdf_ratio64(const SpecParams &S, double q) {
+    switch (S.mdf) {
+    case HEART_MDF_VMF: return exp(-S.w_c * q);
+    case HEART_MDF_WRAPPED_LORENTZIAN: return S.w_a2 / (S.w_a2 + 2.0 * q);
+    case HEART_MDF_SPHERICAL_WRAPPED_LORENTZIAN: {
+        const double r = S.w_b / (S.w_b + q);
+        return r * r;
+    }
+    case HEART_MDF_UNIFORM: return q <= S.w_qmax ? 1.0 : 0.0;
+    default: {
+        const double th = 2.0 * asin(sqrt(0.5 * fmin(fmax(q, 0.0), 2.0)));
+        return S.w_wl * (S.w_a2 / (S.w_a2 + th * th)) + S.w_wg * exp(-S.w_c * th * th);
+    }
+    }
+}
+
+// unit vectors perpendicular to k: e1 along the part of N perpendicular to k
+// (t1's part when k is along N), e2 = k x e1
+__device__ __forceinline__ void cone_axes64(const double k[3], const double N[3], const double t1[3], double e1[3],
+                                            double e2[3]) {
+    const double kN = dot3d(k, N);
+    for (int i = 0; i < 3; ++i) e1[i] = N[i] - kN * k[i];
+    double n2 = dot3d(e1, e1);
+    if (!(n2 > 1e-300)) {
+        const double kt = dot3d(k, t1);
+        for (int i = 0; i < 3; ++i) e1[i] = t1[i] - kt * k[i];
+        n2 = dot3d(e1, e1);
+    }
+    const double inv = 1.0 / sqrt(n2);
+    for (int i = 0; i < 3; ++i) e1[i] *= inv;
+    e2[0] = k[1] * e1[2] - k[2] * e1[1];
+    e2[1] = k[2] * e1[0] - k[0] * e1[2];
+    e2[2] = k[0] * e1[1] - k[1] * e1[0];
+}
+
 // entry point on the front face; true on a hit
 __device__ __forceinline__ bool entry64(const SpecParams &S, const double o[3], const double k[3], double p[3]) {
     const double rel[3] = {o[0] - S.c[0], o[1] - S.c[1], o[2] - S.c[2]};
@@ -268,7 +305,7 @@ __device__ __forceinline__ void bound_order64(const SpecParams &S, const Orders6
     b.ra = 1.0; b.vstar = 1.0; b.qmin = 0.0; b.pbar = 1.0; b.S1 = 0.0; b.S2 = 0.0;
     b.w0 = 0ull; b.wspan = 1ull << 32;
     b.lam = O.qr[h];
-    if (S.sampler != HEART_SAMPLER_THINNED || !(O.qr[h] > 0)) return;
+    if (S.sampler != HEART_SAMPLER_THINNED || S.irc == HEART_IRC_NONE || !(O.qr[h] > 0)) return;
     // distance between sines: never more than between the angles
     const double aBs = O.alpha[h] + O.shift;
     const double xstar = S.xstar * O.w[h];                 // a curve w times as wide: X* scales by w
@@ -300,7 +337,7 @@ __device__ __forceinline__ void bound_order64(const SpecParams &S, const Orders6
 __device__ __forceinline__ void bound_segment64(const SpecParams &S, const Orders64 &O, double mu0, bool any_bragg,
                                                 const double x[3], const double k[3], Seg64 &b) {
     double lo = 0.0, hi = 1.0;
-    if (S.sampler == HEART_SAMPLER_THINNED && any_bragg) {
+    if (S.sampler == HEART_SAMPLER_THINNED && S.irc != HEART_IRC_NONE && any_bragg) {
         int face;
         const double se = exit_distance64(S, x, k, &face);
         double xe[3], N0[3], N1[3], t1[3], t2[3];
@@ -444,6 +481,11 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
         const double Kh = S.K * S.ord_k[h];
         O.Q[h] = Kh * Kh * lam * lam * lam / (2.0 * sb * sqrt(1.0 - sb * sb));
         O.qr[h] = O.Q[h] * (S.irc_max / O.w[h]);        // a curve w times as wide peaks 1/w as high
+        if (S.irc == HEART_IRC_NONE) {
+            // no rocking curve: Q cos a~0 x 2 cones x 2 pi f(0), a~0 = aB + Delta_M
+            const double a0 = O.alpha[h] + O.shift;
+            O.qr[h] = (a0 > 0.0 && a0 < 1.5707963267948966) ? O.Q[h] * cos(a0) * S.none_fac : 0.0;
+        }
     }
     if (!any_bragg) r.no_bragg = 1;
 
@@ -478,9 +520,31 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
             const double c0 = h > 0 ? sb.cum[h - 1] : 0.0;
             v = (v - c0) / (sb.cum[h] - c0);
         }
-        const Bound64 &ob = sb.o[h];
+        double ks[3], P;                                      // reflected direction, acceptance probability
         double N[3], t1[3], t2[3];
         local_frame64(S, x, N, t1, t2);
+        if (S.irc == HEART_IRC_NONE) {
+            // no rocking curve: the crystallite normal on the cone k.n = sg sin a~0
+            // (sg by the top bit of u2) at azimuth psi = 2 pi u3 about k
+            const double a0 = O.alpha[h] + O.shift, s0 = sin(a0), c0 = cos(a0);
+            const double sg = (wd[2] & 0x80000000u) ? 1.0 : -1.0;
+            double sp, cp, e1[3], e2[3], n[3];
+            sincospi(2.0 * u01_64(wd[3]), &sp, &cp);
+            cone_axes64(k, N, t1, e1, e2);
+            for (int i = 0; i < 3; ++i) n[i] = sg * s0 * k[i] + c0 * (cp * e1[i] + sp * e2[i]);
+            const double q = 1.0 - dot3d(n, N);                 // the crystallite's tilt, 1 - cos(theta)
+            for (int i = 0; i < 3; ++i) ks[i] = k[i] - 2.0 * (sg * s0) * n[i];
+            double G;
+            if (pol) {
+                const double pk = dot3d(pv, ks);
+                G = 1.0 - pk * pk;
+            } else {
+                const double c2 = cos(2.0 * a0);
+                G = 0.5 * (1.0 + c2 * c2);
+            }
+            P = mdf_ratio64(S, q) * G;
+        } else {
+        const Bound64 &ob = sb.o[h];
         double q, sx, cx;
         if (v < ob.ra) {                                      // process (a), or the plain stream
             v = ob.ra < 1.0 ? (v / ob.ra) * ob.vstar : v;
@@ -510,8 +574,7 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
         double sa = fabs(kn);
         sa = sa > 1.0 ? 1.0 : sa;
         const double delta = asin(sa) - O.alpha[h] - O.shift;
-        double ks[3];                                         // reflected direction
-        for (int i = 0; i < 3; ++i) ks[i] = k[i] - 2.0 * kn * n[i];
+        for (int i = 0; i < 3; ++i) ks[i] = k[i] - 2.0 * kn * n[i];   // reflected direction
         double G;
         if (pol) {
             const double pk = dot3d(pv, ks);
@@ -521,7 +584,9 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
             G = 0.5 * (1.0 + c2 * c2);                        // Eq. (G_unpol)
         }
         // order h's curve is the described one w_h times as wide: R_h / R_h,max = R(x / w_h) / R_max
-        if (v < irc64(S, delta / O.w[h]) * G / S.irc_max) {
+        P = irc64(S, delta / O.w[h]) * G / S.irc_max;
+        }
+        if (v < P) {
             ++nrefl;
             if (nrefl > S.max_refl) { outcome = HEART_CAPPED; break; }
             const double inv = 1.0 / sqrt(dot3d(ks, ks));

@@ -261,6 +261,58 @@ double dp_area(double g) {
     return 2.0 * (double)s;
 }
 
+// W(q) / W(0) of the mosaic distribution in closed form, and for a spectrometer
+// without rocking curve the cone-candidate factor 2 W(0) / int_0^qmax W dq
+// (2 cones x 2 pi f(0), f = W / (2 pi int W dq) per unit solid angle)
+void mdf_ratio_params(const heart_spectrometer_desc *d, SpecParams *p) {
+    const double G = d->mdf_fwhm_rad;
+    p->mdf = d->mdf;
+    p->w_a2 = 0.25 * G * G;
+    double W0 = 1.0, norm = 0.0;
+    switch (d->mdf) {
+    case HEART_MDF_GAUSSIAN:
+    case HEART_MDF_LORENTZIAN:
+    case HEART_MDF_PSEUDO_VOIGT: {
+        const double c = 4.0 * kLn2 / (G * G);
+        p->w_c = c;
+        const MdfShape sh{d->mdf, G, d->mdf_eta};
+        W0 = sh.W(0.0);
+        if (d->mdf == HEART_MDF_GAUSSIAN) { p->w_wl = 0.0; p->w_wg = 1.0; }
+        else if (d->mdf == HEART_MDF_LORENTZIAN) { p->w_wl = 1.0; p->w_wg = 0.0; }
+        else {
+            p->w_wl = d->mdf_eta * (2.0 / (kPi * G)) / W0;
+            p->w_wg = (1.0 - d->mdf_eta) * std::sqrt(c / kPi) / W0;
+        }
+        if (d->irc == HEART_IRC_NONE) norm = NumericMdf(sh).total();
+        break;
+    }
+    case HEART_MDF_VMF: {
+        const double s2 = G * G / (8.0 * kLn2);
+        p->w_c = 1.0 / s2;
+        norm = -s2 * std::expm1(-2.0 / s2);
+        break;
+    }
+    case HEART_MDF_WRAPPED_LORENTZIAN:
+        W0 = 1.0 / p->w_a2;
+        norm = 0.5 * std::log1p(4.0 / p->w_a2);
+        break;
+    case HEART_MDF_SPHERICAL_WRAPPED_LORENTZIAN: {
+        const double sh = std::sinh(0.25 * G);
+        p->w_b = 2.0 * sh * sh;
+        W0 = 1.0 / (p->w_b * p->w_b);
+        norm = 1.0 / p->w_b - 1.0 / (p->w_b + 2.0);
+        break;
+    }
+    default: {
+        const double h = std::sin(0.25 * G);
+        p->w_qmax = 2.0 * h * h;
+        norm = p->w_qmax;
+        break;
+    }
+    }
+    p->none_fac = (d->irc == HEART_IRC_NONE && norm > 0) ? 2.0 * W0 / norm : 0.0;
+}
+
 }  // namespace
 
 heart_status build_spec_params(const heart_spectrometer_desc *d, SpecParams *p, double *tab,
@@ -275,8 +327,9 @@ heart_status build_spec_params(const heart_spectrometer_desc *d, SpecParams *p, 
     REQUIRE(d->mdf >= HEART_MDF_GAUSSIAN && d->mdf <= HEART_MDF_UNIFORM, "unknown mdf");
     REQUIRE(d->mdf_fwhm_rad > 0 && d->mdf_fwhm_rad < 1.0, "mdf_fwhm_rad must be in (0, 1) rad");
     REQUIRE(d->mdf != HEART_MDF_PSEUDO_VOIGT || (d->mdf_eta >= 0 && d->mdf_eta <= 1), "mdf_eta in [0,1]");
-    REQUIRE(d->irc >= HEART_IRC_DARWIN && d->irc <= HEART_IRC_BOX, "unknown irc");
-    REQUIRE(d->irc_fwhm_rad > 0 && d->irc_fwhm_rad < 0.1, "irc_fwhm_rad must be in (0, 0.1) rad");
+    REQUIRE(d->irc >= HEART_IRC_DARWIN && d->irc <= HEART_IRC_NONE, "unknown irc");
+    REQUIRE(d->irc == HEART_IRC_NONE || (d->irc_fwhm_rad > 0 && d->irc_fwhm_rad < 0.1),
+            "irc_fwhm_rad must be in (0, 0.1) rad");
     REQUIRE(d->irc != HEART_IRC_PSEUDO_VOIGT || d->irc_lorentz_fwhm_rad >= 0, "irc_lorentz_fwhm_rad >= 0");
     REQUIRE(d->irc != HEART_IRC_DARWIN_PRINS || d->prins_g >= 0, "prins_g >= 0");
     REQUIRE(std::isfinite(d->irc_shift_rad) && std::fabs(d->irc_shift_rad) < 0.1, "irc_shift_rad");
@@ -383,7 +436,9 @@ heart_status build_spec_params(const heart_spectrometer_desc *d, SpecParams *p, 
     case HEART_IRC_GAUSSIAN: p->irc_max = std::sqrt(4.0 * kLn2 / kPi) / p->irc_fwhm; break;
     case HEART_IRC_LORENTZIAN: p->irc_max = 2.0 / (kPi * p->irc_fwhm); break;
     case HEART_IRC_BOX: p->irc_max = 1.0 / p->irc_fwhm; break;
+    case HEART_IRC_NONE: p->irc_max = 0.0; break;    // a delta function: the cone candidates take over
     }
+    mdf_ratio_params(d, p);
 
     // physics
     p->d_A = d->d_spacing_A;

@@ -55,6 +55,12 @@ struct SpecParams {
     double ord_k[HEART_MAX_ORDERS], ord_w[HEART_MAX_ORDERS];
     // energy-dependent rocking curve: knots, width scale, added shift
     double irc_e[HEART_MAX_IRC_E], irc_ws[HEART_MAX_IRC_E], irc_sh[HEART_MAX_IRC_E];
+    // no rocking curve: the cone-candidate rate factor 2 W(0) / int W dq, and
+    // the mosaic distribution's W(q) / W(0) in closed form (mdf_ratio): theta
+    // shapes w_wl a2 / (a2 + theta^2) + w_wg exp(-w_c theta^2); vMF
+    // exp(-w_c q); WL a2 / (a2 + 2 q); SWL w_b^2 / (w_b + q)^2; uniform q <= w_qmax
+    int32_t mdf, pad_m;
+    double none_fac, w_a2, w_c, w_wl, w_wg, w_b, w_qmax;
     // device tables: q = 1 - cos(theta) at the body knots then the tail knots
     const double *mdf64;
     const float *mdf32;

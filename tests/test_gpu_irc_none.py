@@ -1,0 +1,123 @@
+"""No rocking curve (Sec. 2.2.1, IRC "none") through the C ABI.  The FP64 kernel
+replays the oracle's cone candidates ray by ray (decisions identical, positions
+within 1e-9 relative) on flat and cylindrical crystals, with several orders and
+an energy-dependent peak shift; the FP32 kernels (plain and polarised) follow
+the FP64 kernel on the same streams within the usual budget (<= 1e-4 of rays
+flipped, hit positions within 1 um); batched jobs without rocking curve give
+the images of their single traces."""
+import numpy as np
+import pytest
+
+from oracle import binding as ob
+from paper_2503_16955_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2503_16955_gb300 as H
+    return H
+
+
+def vh(**kw):
+    w = W.von_hamos_hapg()
+    s = dict(w["spec"], irc="none", mdf="gaussian", mdf_fwhm_rad=0.05, refl_K_per_mm2=5e9)
+    s.update(kw)
+    return s, w["source"]
+
+
+def _replay(H, spec, src, n, seed):
+    s = H.heart_spectrometer_create(spec)
+    g, gt = H.heart_trace_records(s, src, n, seed, 0, precision="fp64")
+    _, ot, o = ob.trace(spec, src, n, seed, records=True)
+    s.close()
+    bad = (g["outcome"] != o["outcome"]) | (g["nrefl"] != o["nrefl"]) | (g["ncoll"] != o["ncoll"])
+    assert not bad.any(), np.flatnonzero(bad)[:5]
+    scale = np.maximum(np.abs(o["pos"]), 1.0)
+    assert np.all(np.abs(g["pos"] - o["pos"]) <= 1e-9 * scale)
+    for k in ("emitted", "miss", "absorbed", "exit_front", "exit_back", "exit_side", "collisions", "refl_hist"):
+        assert gt[k] == ot[k], k
+    return gt
+
+
+@pytest.mark.parametrize("sampler", ["thinned", "plain"])
+def test_fp64_replays_oracle_von_hamos(H, sampler):
+    spec, src = vh(sampler=sampler)
+    t = _replay(H, spec, src, 40_000, 3)
+    assert t["exit_front"] > 500 and t["refl_hist"][2] > 10
+
+
+def test_fp64_replays_oracle_flat_orders_shift_table(H):
+    w = W.flat_hopg_mono()
+    spec = dict(w["spec"], irc="none", mdf="gaussian", mdf_fwhm_rad=0.03, refl_K_per_mm2=4e9,
+                irc_shift_rad=2e-4, orders=[(1, 1.0, 1.0), (2, 0.5, 1.0)],
+                irc_energy=[(7.9, 1.0, -1e-4), (8.1, 1.0, 3e-4)])
+    src = dict(w["source"], components=[dict(kind="uniform", lo_keV=7.8, hi_keV=8.2, weight=1.0)])
+    t = _replay(H, spec, src, 40_000, 5)
+    assert t["exit_front"] > 200
+
+
+@pytest.mark.parametrize("mdf", ["pseudo_voigt", "vmf", "wl", "swl", "uniform"])
+def test_fp64_replays_oracle_every_mosaic_shape(H, mdf):
+    spec, src = vh(mdf=mdf, mdf_fwhm_rad=0.04, mdf_eta=0.4)
+    t = _replay(H, spec, src, 15_000, 8)
+    assert t["exit_front"] > 50
+
+
+def _fp32_vs_fp64(H, spec, src, n, seed):
+    s = H.heart_spectrometer_create(spec)
+    r64, t64 = H.heart_trace_records(s, src, n, seed, 0, precision="fp64")
+    r32, t32 = H.heart_trace_records(s, src, n, seed, 0, precision="fp32")
+    s.close()
+    flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"])
+    assert flip.sum() <= max(2, 1e-4 * n), int(flip.sum())
+    same = ~flip & (r64["det_hit"] == 1) & (r32["det_hit"] == 1)
+    assert same.sum() > 100
+    assert np.abs(r64["u_mm"][same] - r32["u_mm"][same]).max() <= 1e-3
+    assert np.abs(r64["v_mm"][same] - r32["v_mm"][same]).max() <= 1e-3
+    return t32
+
+
+def test_fp32_follows_fp64_von_hamos(H):
+    spec, src = vh()
+    t = _fp32_vs_fp64(H, spec, src, 200_000, 6)
+    assert t["refl_hist"][1] > 1000
+
+
+def test_fp32_follows_fp64_flat_narrow_mosaic(H):
+    # a 0.4 degree mosaic: ~1e3 cone candidates per entering ray
+    w = W.flat_hopg_mono()
+    spec = dict(w["spec"], irc="none")
+    _fp32_vs_fp64(H, spec, w["source"], 50_000, 7)
+
+
+def test_fp32_polarised_follows_fp64(H):
+    spec, src = vh()
+    src = dict(src, polarization=[0.3, 0.9, -0.2])
+    _fp32_vs_fp64(H, spec, src, 100_000, 9)
+
+
+def test_batch_images_equal_single_traces(H):
+    import torch
+    spec, src = vh()
+    w = W.flat_hopg_mono()
+    s1 = H.heart_spectrometer_create(spec)
+    s2 = H.heart_spectrometer_create(w["spec"])
+    single = []
+    for s, sr, n, seed in ((s1, src, 300_000, 11), (s2, w["source"], 200_000, 12)):
+        img = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+        H.heart_trace(s, sr, n, seed, 0, img, precision="fp32")
+        single.append(img.cpu().numpy())
+    imgs = [torch.zeros(s.shape, dtype=torch.int32, device="cuda") for s in (s1, s2)]
+    tal = H.heart_trace_batch([s1, s2], [src, w["source"]], [300_000, 200_000], [11, 12], imgs)
+    for a, b in zip(single, imgs):
+        assert np.array_equal(a, b.cpu().numpy())
+    assert tal[0]["det_hits"] > 100
+    s1.close()
+    s2.close()
