@@ -156,7 +156,7 @@ typedef struct {
     double pixel_mm;
     int32_t count_type;             /* heart_count_type of images traced with this handle */
     int32_t sampler;                /* heart_sampler */
-    double thin_vstar;              /* THINNED: relative IRC level v* in (0, 1); 0: 2^-10 */
+    double thin_vstar;              /* THINNED: relative IRC level v* in (0, 1); 0: 2^-6 */
     /* Higher-order reflections (Sec. 2.2.3: the cross-section is a sum over the
      * reflections H, e.g. graphite (002), (004), (006)).  n_orders = 0: the
      * single reflection on d_spacing_A.  Otherwise order h reflects on planes

@@ -106,7 +106,7 @@ typedef struct {
      * collision at the constant majorant; ORC_SAMPLER_THINNED skips, per
      * straight segment, the candidates that provably cannot reflect (same
      * distribution of paths, fewer candidates).  thin_vstar: the acceptance
-     * level below which every candidate is still tested (0: 2^-10). */
+     * level below which every candidate is still tested (0: 2^-6). */
     int32_t sampler;
     int32_t pad3;
     double thin_vstar;

@@ -686,7 +686,7 @@ static int geom_init(geom *g, const orc_spec *s) {
         if (!(g->W0 > 0) || !(g->none_fac > 0) || !isfinite(g->none_fac)) return fail("MDF has no mass at theta = 0");
         if (s->sampler != ORC_SAMPLER_PLAIN && s->sampler != ORC_SAMPLER_THINNED) return fail("unknown sampler");
     } else if (s->sampler == ORC_SAMPLER_THINNED) {
-        g->vstar = s->thin_vstar > 0 ? s->thin_vstar : 1.0 / 1024.0;
+        g->vstar = s->thin_vstar > 0 ? s->thin_vstar : 1.0 / 64.0;
         if (!(g->vstar < 1.0)) return fail("thin_vstar must be < 1");
         g->xstar = irc_xstar(&g->irc, g->irc_max, g->vstar);
         if (!(g->xstar > 0)) return fail("rocking curve never drops below v*");

@@ -1306,16 +1306,12 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
 // slots than spawning inside the walk loop.  Both passes run the same device
 // functions as the persistent kernel, so every ray is traced identically.
 // ---------------------------------------------------------------------------
-// a prepared hit: 18 float fields and 5 word fields, structure of arrays
-enum : int {
-    WF_X = 0, WF_K = 3, WF_A = 6, WF_SB, WF_MU0, WF_QR, WF_IWS, WF_E, WF_SEXIT, WF_IMU, WF_PA, WF_RA, WF_QMIN, WF_PBAR,
-    WF_NF
-};
-enum : int { WU_RL = 0, WU_RH, WU_W0, WU_FACE, WU_NB, WU_N };
-
-__device__ __forceinline__ float *wave_f(const WaveBuf &B, int f) { return (float *)B.base + (size_t)f * B.cap; }
-__device__ __forceinline__ uint32_t *wave_u(const WaveBuf &B, int f) {
-    return (uint32_t *)B.base + (size_t)(WF_NF + f) * B.cap;
+// a prepared hit: one 96-byte record of six 16-byte words, written and read
+// with vector stores and loads (consecutive lanes touch consecutive records):
+//   [x0 x1 x2 k0] [k1 k2 A sB] [mu0 qr inv_ws E] [s_exit inv_mu pa ra]
+//   [qmin pbar ray_lo ray_hi] [w0 face no_bragg -]
+__device__ __forceinline__ float4 *wave_rec(const WaveBuf &B, size_t slot) {
+    return (float4 *)B.base + slot * (size_t)kWaveRec16;
 }
 
 // pass 1: one thread per ray of [first, first + count): source, entry and the
@@ -1355,25 +1351,14 @@ __global__ void __launch_bounds__(256) k_spawn32(const __grid_constant__ Launch3
     base = __shfl_sync(0xffffffffu, base, 0);
     if (hit) {
         const size_t slot = base + __popc(hm & ((1u << lane) - 1u));
-        for (int j = 0; j < 3; ++j) { wave_f(B, WF_X + j)[slot] = t.x0[j]; wave_f(B, WF_K + j)[slot] = t.k[j]; }
-        wave_f(B, WF_A)[slot] = A;
-        wave_f(B, WF_SB)[slot] = sB;
-        wave_f(B, WF_MU0)[slot] = mu0;
-        wave_f(B, WF_QR)[slot] = qr;
-        wave_f(B, WF_IWS)[slot] = inv_ws;
-        wave_f(B, WF_E)[slot] = E32;
-        wave_f(B, WF_SEXIT)[slot] = t.s_exit;
-        wave_f(B, WF_IMU)[slot] = t.inv_mu;
-        wave_f(B, WF_PA)[slot] = t.pa;
-        wave_f(B, WF_RA)[slot] = t.ra;
-        wave_f(B, WF_QMIN)[slot] = t.qmin;
-        wave_f(B, WF_PBAR)[slot] = t.pbar;
         const uint64_t ray = L.offset + id;
-        wave_u(B, WU_RL)[slot] = (uint32_t)ray;
-        wave_u(B, WU_RH)[slot] = (uint32_t)(ray >> 32);
-        wave_u(B, WU_W0)[slot] = t.w0;
-        wave_u(B, WU_FACE)[slot] = (uint32_t)t.face;
-        wave_u(B, WU_NB)[slot] = (uint32_t)nb;
+        float4 *r = wave_rec(B, slot);
+        r[0] = make_float4(t.x0[0], t.x0[1], t.x0[2], t.k[0]);
+        r[1] = make_float4(t.k[1], t.k[2], A, sB);
+        r[2] = make_float4(mu0, qr, inv_ws, E32);
+        r[3] = make_float4(t.s_exit, t.inv_mu, t.pa, t.ra);
+        r[4] = make_float4(t.qmin, t.pbar, __uint_as_float((uint32_t)ray), __uint_as_float((uint32_t)(ray >> 32)));
+        r[5] = make_float4(__uint_as_float(t.w0), __int_as_float(t.face), __int_as_float(nb), 0.0f);
     }
     if (lane == 0) {
         atomicAdd(&s_emit, (unsigned)__popc(vm));
@@ -1415,24 +1400,15 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
             if (base + n_idle >= nh) more = false;
             const unsigned long long slot = base + __popc(idle & lt_mask);
             if (!alive && slot < nh) {
-                for (int j = 0; j < 3; ++j) { s.x0[j] = wave_f(B, WF_X + j)[slot]; s.k[j] = wave_f(B, WF_K + j)[slot]; }
-                s.A = wave_f(B, WF_A)[slot];
-                s.sB = wave_f(B, WF_SB)[slot];
-                s.mu0 = wave_f(B, WF_MU0)[slot];
-                s.qr = wave_f(B, WF_QR)[slot];
-                s.inv_ws = wave_f(B, WF_IWS)[slot];
-                s.E = wave_f(B, WF_E)[slot];
-                s.s_exit = wave_f(B, WF_SEXIT)[slot];
-                s.inv_mu = wave_f(B, WF_IMU)[slot];
-                s.pa = wave_f(B, WF_PA)[slot];
-                s.ra = wave_f(B, WF_RA)[slot];
-                s.qmin = wave_f(B, WF_QMIN)[slot];
-                s.pbar = wave_f(B, WF_PBAR)[slot];
-                s.rl = wave_u(B, WU_RL)[slot];
-                s.rh = wave_u(B, WU_RH)[slot];
-                s.w0 = wave_u(B, WU_W0)[slot];
-                s.face = (int)wave_u(B, WU_FACE)[slot];
-                s.no_bragg = (int)wave_u(B, WU_NB)[slot];
+                const float4 *r = wave_rec(B, slot);
+                const float4 r0 = __ldcs(r), r1 = __ldcs(r + 1), r2 = __ldcs(r + 2), r3 = __ldcs(r + 3),
+                             r4 = __ldcs(r + 4), r5 = __ldcs(r + 5);
+                s.x0[0] = r0.x; s.x0[1] = r0.y; s.x0[2] = r0.z; s.k[0] = r0.w;
+                s.k[1] = r1.x; s.k[2] = r1.y; s.A = r1.z; s.sB = r1.w;
+                s.mu0 = r2.x; s.qr = r2.y; s.inv_ws = r2.z; s.E = r2.w;
+                s.s_exit = r3.x; s.inv_mu = r3.y; s.pa = r3.z; s.ra = r3.w;
+                s.qmin = r4.x; s.pbar = r4.y; s.rl = __float_as_uint(r4.z); s.rh = __float_as_uint(r4.w);
+                s.w0 = __float_as_uint(r5.x); s.face = __float_as_int(r5.y); s.no_bragg = __float_as_int(r5.z);
                 s.inv_1mpa = s.pa < 1.0f ? 1.0f / (1.0f - s.pa) : 0.0f;
                 s.pa_thr = s.pa >= 1.0f ? 0xFFFFFFFFu
                                         : __float2uint_ru(fminf(s.pa * 4294967296.0f, 4294967040.0f));
@@ -1814,7 +1790,7 @@ heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n,
     B.base = wave;
     B.cap = wave_cap;
     B.pad = 0;
-    unsigned long long *ctr = (unsigned long long *)((char *)wave + (size_t)23 * 4 * wave_cap);
+    unsigned long long *ctr = (unsigned long long *)((char *)wave + (size_t)16 * kWaveRec16 * wave_cap);
 #define HEART_WAVE_CASES(G)                                                                          \
     switch (L.irc_kind) {                                                                            \
     case HEART_IRC_DARWIN: return launch_wave_t<G, HEART_IRC_DARWIN>(L, B, n, ctr, st);             \

@@ -351,7 +351,7 @@ heart_status build_spec_params(const heart_spectrometer_desc *d, SpecParams *p, 
     REQUIRE(d->sampler == HEART_SAMPLER_THINNED || d->sampler == HEART_SAMPLER_PLAIN, "sampler");
     REQUIRE(d->thin_vstar >= 0 && d->thin_vstar < 1, "thin_vstar in [0, 1)");
     p->sampler = d->sampler;
-    p->vstar = d->thin_vstar > 0 ? d->thin_vstar : 1.0 / 1024.0;   // X* is set by the caller
+    p->vstar = d->thin_vstar > 0 ? d->thin_vstar : 1.0 / 64.0;     // X* is set by the caller
     REQUIRE(d->n_orders >= 0 && d->n_orders <= HEART_MAX_ORDERS, "0..4 reflection orders");
     p->n_orders = d->n_orders > 0 ? d->n_orders : 1;
     if (d->n_orders == 0) {
