@@ -1315,14 +1315,18 @@ __device__ __forceinline__ float4 *wave_rec(const WaveBuf &B, size_t slot) {
 }
 
 // pass 1: one thread per ray of [first, first + count): source, entry and the
-// entry segment; hits are appended to the queue (warp-aggregated), misses tallied
+// entry segment; the block's hits are appended to the queue with one global
+// atomic per block (warp offsets from a scan of the warps' hit counts: a
+// counter that every warp of the grid incremented itself serialised the pass);
+// emitted rays and misses are tallied by the walk pass from count and the hits
+constexpr int kSpawnThreads = 512, kSpawnWarps = kSpawnThreads / 32;
 template <int GEOM>
-__global__ void __launch_bounds__(256) k_spawn32(const __grid_constant__ Launch32 L, const __grid_constant__ WaveBuf B,
-                                                 uint64_t first, uint32_t count, unsigned long long *n_hits) {
-    __shared__ unsigned int s_emit, s_miss;
-    if (threadIdx.x == 0) { s_emit = 0u; s_miss = 0u; }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kSpawnThreads) k_spawn32(const __grid_constant__ Launch32 L,
+                                                           const __grid_constant__ WaveBuf B, uint64_t first,
+                                                           uint32_t count, unsigned long long *n_hits) {
+    __shared__ unsigned int s_ofs[kSpawnWarps];
+    __shared__ unsigned long long s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < count;
     const uint64_t id = first + i;
@@ -1345,12 +1349,25 @@ __global__ void __launch_bounds__(256) k_spawn32(const __grid_constant__ Launch3
         segment<GEOM>(L, t);
     }
     const unsigned hm = __ballot_sync(0xffffffffu, hit);
-    const unsigned vm = __ballot_sync(0xffffffffu, valid);
-    unsigned long long base = 0;
-    if (lane == 0 && hm) base = atomicAdd(n_hits, (unsigned long long)__popc(hm));
-    base = __shfl_sync(0xffffffffu, base, 0);
+    if (lane == 0) s_ofs[warp] = __popc(hm);
+    __syncthreads();
+    if (warp == 0) {
+        // exclusive scan of the warps' hit counts, one global atomic for the block
+        const unsigned c = lane < kSpawnWarps ? s_ofs[lane] : 0u;
+        unsigned inc = c;
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += y;
+        }
+        const unsigned total = __shfl_sync(0xffffffffu, inc, 31);
+        unsigned long long b = 0;
+        if (lane == 0 && total) b = atomicAdd(n_hits, (unsigned long long)total);
+        if (lane < kSpawnWarps) s_ofs[lane] = inc - c;
+        if (lane == 0) s_base = b;
+    }
+    __syncthreads();
     if (hit) {
-        const size_t slot = base + __popc(hm & ((1u << lane) - 1u));
+        const size_t slot = s_base + s_ofs[warp] + __popc(hm & ((1u << lane) - 1u));
         const uint64_t ray = L.offset + id;
         float4 *r = wave_rec(B, slot);
         r[0] = make_float4(t.x0[0], t.x0[1], t.x0[2], t.k[0]);
@@ -1360,15 +1377,6 @@ __global__ void __launch_bounds__(256) k_spawn32(const __grid_constant__ Launch3
         r[4] = make_float4(t.qmin, t.pbar, __uint_as_float((uint32_t)ray), __uint_as_float((uint32_t)(ray >> 32)));
         r[5] = make_float4(__uint_as_float(t.w0), __int_as_float(t.face), __int_as_float(nb), 0.0f);
     }
-    if (lane == 0) {
-        atomicAdd(&s_emit, (unsigned)__popc(vm));
-        atomicAdd(&s_miss, (unsigned)__popc(vm & ~hm));
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (s_emit) atomicAdd(&L.tally[T_EMITTED], (unsigned long long)s_emit);
-        if (s_miss) atomicAdd(&L.tally[T_MISS], (unsigned long long)s_miss);
-    }
 }
 
 // pass 2: a persistent grid walks the queued hits; idle lanes take the next
@@ -1376,7 +1384,7 @@ __global__ void __launch_bounds__(256) k_spawn32(const __grid_constant__ Launch3
 template <int GEOM, int IRC, int OCC>
 __global__ void __launch_bounds__(kBlockThreads, OCC)
     k_walk32(const __grid_constant__ Launch32 L, const __grid_constant__ WaveBuf B,
-             const unsigned long long *n_hits, unsigned long long *head) {
+             const unsigned long long *n_hits, unsigned long long *head, uint32_t count) {
     __shared__ float s_tab[kMdfKnots];
     __shared__ BlockTally bt;
     for (int i = threadIdx.x; i < kMdfKnots; i += blockDim.x) s_tab[i] = L.tab[i];
@@ -1386,6 +1394,11 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const unsigned long long nh = *(volatile const unsigned long long *)n_hits;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // the chunk's emitted rays and misses (every ray of the chunk that is not queued missed)
+        atomicAdd(&L.tally[T_EMITTED], (unsigned long long)count);
+        atomicAdd(&L.tally[T_MISS], (unsigned long long)count - nh);
+    }
     Lane s;
     bool alive = false, more = true;
     unsigned long long my_coll = 0;
@@ -1750,8 +1763,8 @@ static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t 
         unsigned long long *cc = ctr + 2 * g;
         const uint64_t first = c * B.cap;
         const uint32_t count = (uint32_t)(n - first < B.cap ? n - first : B.cap);
-        k_spawn32<GEOM><<<(count + 255) / 256, 256, 0, st>>>(L, B, first, count, cc);
-        k_walk32<GEOM, IRC, 6><<<walk_blocks, kBlockThreads, 0, st>>>(L, B, cc, cc + 1);
+        k_spawn32<GEOM><<<(count + kSpawnThreads - 1) / kSpawnThreads, kSpawnThreads, 0, st>>>(L, B, first, count, cc);
+        k_walk32<GEOM, IRC, 6><<<walk_blocks, kBlockThreads, 0, st>>>(L, B, cc, cc + 1, count);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "FP32 two-pass launch");
