@@ -315,12 +315,15 @@ __device__ __forceinline__ void irc_energy32(const Launch32 &L, float E, float &
 // ---------------------------------------------------------------------------
 // spawn: source sample + entry (Sec. 2.1, Sec. 2.2) in the crystal frame
 // ---------------------------------------------------------------------------
+// The geometric part of a sampled ray: its two Philox blocks, the direction,
+// the origin and the entry.  On a hit x is the entry point and dA is |k.N|
+// there minus its value for the cone axis; a and b keep the words that the
+// energy part uses.
 template <int GEOM_T>
-__device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3], float k[3], float &A,
-                                      float &sB, float &mu0, float &qr, float &inv_ws, float &E32, int &nb) {
+__device__ __forceinline__ bool spawn_entry(const Launch32 &L, uint64_t ray, float x[3], float k[3], float &dA,
+                                            uint32_t a[4], uint32_t b[4]) {
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
     const uint32_t rl = (uint32_t)ray, rh = (uint32_t)(ray >> 32);
-    uint32_t a[4], b[4];
     philox_l<(GEOM_T >= 0)>(L, rl, rh, 0u, 0u, a);
     philox_l<(GEOM_T >= 0)>(L, rl, rh, 1u, 0u, b);
     // direction, uniform in solid angle in the cone; dn = k.n_ref - axis.n_ref
@@ -341,7 +344,6 @@ __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3
         for (int i = 0; i < 3; ++i) o[i] = __fmaf_rn(z2, L.b2[i], __fmaf_rn(z1, L.b1[i], o[i]));
     }
     for (int i = 0; i < 3; ++i) x[i] = o[i];              // a miss reports its origin
-    float dA;                                             // |k.N| at entry minus the cone-axis value
     if (GEOM == HEART_FLAT) {
         if (!(k[2] < 0.0f) || !(o[2] > 0.0f)) return false;
         const float t = o[2] / (-k[2]);
@@ -370,12 +372,21 @@ __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3
         const float num = -dn * (2.0f * L.a_n + dn) - aa * eps_o;   // |k.N|^2 - c_a^2
         dA = num / (kabs + L.c_a);
     }
-    // energy (only rays that entered need it), as a small offset from the
-    // component's reference energy so that sin(aB) keeps ~1e-9 accuracy
+    return true;
+}
+
+// The energy part of a ray that entered (words a0, a1 of its first Philox
+// block, b2, b3 of its second; dA from spawn_entry): spectral component and
+// energy, as a small offset from the component's reference energy so that
+// sin(aB) keeps ~1e-9 accuracy, the Bragg anchor and the rates.  False if the
+// energy is not positive and finite (the ray counts as a miss).
+__device__ __forceinline__ bool spawn_energy(const Launch32 &L, uint32_t a0, uint32_t a1, uint32_t b2, uint32_t b3,
+                                             float dA, float &A, float &sB, float &mu0, float &qr, float &inv_ws,
+                                             float &E32, int &nb) {
     int c = L.n_comp - 1;
     for (int i = 0; i < L.n_comp - 1; ++i)
-        if (a[0] < L.comp_thr[i]) { c = i; break; }
-    const float up = u01_32(a[1]);
+        if (a0 < L.comp_thr[i]) { c = i; break; }
+    const float up = u01_32(a1);
     float E, ds;                                          // ds = sin(aB(E)) - sin(aB(e_ref))
     const float e0 = L.e_ref[c], s0 = L.sB_raw[c];
     switch (L.kind[c]) {
@@ -389,7 +400,7 @@ __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3
     case HEART_SRC_TABLE: {
         // the interval with thr_i <= word < thr_i+1 (the FP64 path's decision
         // u < C_i taken exactly on the word), then linear inside it
-        const unsigned long long wv = a[1];
+        const unsigned long long wv = a1;
         int lo = 0, hi = L.n_tab - 1;
         while (hi - lo > 1) {
             const int m = (lo + hi) >> 1;
@@ -406,8 +417,8 @@ __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3
         float dE;
         if (L.kind[c] == HEART_SRC_GAUSS) {
             float s, co;
-            sincos_2pi(u01_32(b[3]), &s, &co);
-            dE = L.width[c] * sqrtf(-2.0f * __logf(u01_32(b[2]))) * co;
+            sincos_2pi(u01_32(b3), &s, &co);
+            dE = L.width[c] * sqrtf(-2.0f * __logf(u01_32(b2))) * co;
         } else if (L.kind[c] == HEART_SRC_LORENTZ) {
             const float uu = __fmaf_rn(up, 1.0f - L.lF0[c], L.lF0[c]);
             dE = 0.5f * L.width[c] * tanf(3.14159265f * (uu - 0.5f));
@@ -455,6 +466,16 @@ __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3
     }
     ray_rates(L, E, Q, nb, inv_ws, sB, mu0, qr);
     return true;
+}
+
+// a sampled ray: spawn_entry, then spawn_energy for a hit
+template <int GEOM_T>
+__device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3], float k[3], float &A,
+                                      float &sB, float &mu0, float &qr, float &inv_ws, float &E32, int &nb) {
+    uint32_t a[4], b[4];
+    float dA;
+    if (!spawn_entry<GEOM_T>(L, ray, x, k, dA, a, b)) return false;
+    return spawn_energy(L, a[0], a[1], b[2], b[3], dA, A, sB, mu0, qr, inv_ws, E32, nb);
 }
 
 // user-supplied ray: read, move to the crystal frame and enter in FP64 (once
@@ -1314,30 +1335,75 @@ __device__ __forceinline__ float4 *wave_rec(const WaveBuf &B, size_t slot) {
     return (float4 *)B.base + slot * (size_t)kWaveRec16;
 }
 
-// pass 1: one thread per ray of [first, first + count): source, entry and the
-// entry segment; the block's hits are appended to the queue with one global
-// atomic per block (warp offsets from a scan of the warps' hit counts: a
-// counter that every warp of the grid incremented itself serialised the pass);
-// emitted rays and misses are tallied by the walk pass from count and the hits
+// pass 1: one thread per ray of [first, first + count), in two phases.  First
+// every thread draws its ray's geometry and tests the entry; the rays that
+// entered are compacted through shared memory (block offsets from a scan of
+// the warps' hit counts, one global atomic per block reserving their queue
+// slots).  Then the first `hits` threads of the block take one entered ray
+// each and do the rest of its set-up with full warps: energy, Bragg anchor,
+// rates and the entry segment, and write its record.  (A counter that every
+// warp of the grid incremented serialised the pass; preparing the segments in
+// the threads that drew the rays left 59 % of their lanes idle.)  A ray whose
+// energy is not positive and finite is queued as a dead record (no_bragg = 2)
+// that the walk counts as a miss.  Emitted rays and misses are tallied by the
+// walk pass from count and the queue length.
 constexpr int kSpawnThreads = 512, kSpawnWarps = kSpawnThreads / 32;
+struct SpawnStage {
+    float x[3][kSpawnThreads], k[3][kSpawnThreads], dA[kSpawnThreads];
+    uint32_t a0[kSpawnThreads], a1[kSpawnThreads], b2[kSpawnThreads], b3[kSpawnThreads];
+    uint32_t idx[kSpawnThreads];
+};
 template <int GEOM>
 __global__ void __launch_bounds__(kSpawnThreads) k_spawn32(const __grid_constant__ Launch32 L,
                                                            const __grid_constant__ WaveBuf B, uint64_t first,
                                                            uint32_t count, unsigned long long *n_hits) {
+    __shared__ SpawnStage sg;
     __shared__ unsigned int s_ofs[kSpawnWarps];
     __shared__ unsigned long long s_base;
+    __shared__ unsigned int s_hits;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = i < count;
-    const uint64_t id = first + i;
-    float x[3] = {0.f, 0.f, 0.f}, k[3] = {0.f, 0.f, 0.f};
+    {
+        float x[3], k[3], dA = 0.0f;
+        uint32_t a[4], b[4];
+        const bool hit = i < count && spawn_entry<GEOM>(L, L.offset + first + i, x, k, dA, a, b);
+        const unsigned hm = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) s_ofs[warp] = __popc(hm);
+        __syncthreads();
+        if (warp == 0) {
+            // exclusive scan of the warps' hit counts, one global atomic for the block
+            const unsigned c = lane < kSpawnWarps ? s_ofs[lane] : 0u;
+            unsigned inc = c;
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
+                if (lane >= off) inc += y;
+            }
+            const unsigned total = __shfl_sync(0xffffffffu, inc, 31);
+            unsigned long long bs = 0;
+            if (lane == 0 && total) bs = atomicAdd(n_hits, (unsigned long long)total);
+            if (lane < kSpawnWarps) s_ofs[lane] = inc - c;
+            if (lane == 0) { s_base = bs; s_hits = total; }
+        }
+        __syncthreads();
+        if (hit) {
+            const unsigned j = s_ofs[warp] + __popc(hm & ((1u << lane) - 1u));
+            for (int m = 0; m < 3; ++m) { sg.x[m][j] = x[m]; sg.k[m][j] = k[m]; }
+            sg.dA[j] = dA;
+            sg.a0[j] = a[0]; sg.a1[j] = a[1]; sg.b2[j] = b[2]; sg.b3[j] = b[3];
+            sg.idx[j] = threadIdx.x;
+        }
+        __syncthreads();
+    }
+    const unsigned j = threadIdx.x;
+    if (j >= s_hits) return;
     float A = 0.f, sB = 0.f, mu0 = 0.f, qr = 0.f, inv_ws = 1.f, E32 = 0.f;
     int nb = 0;
-    bool hit = false;
-    if (valid) hit = spawn<GEOM>(L, L.offset + id, x, k, A, sB, mu0, qr, inv_ws, E32, nb);
+    const float dA = sg.dA[j];
+    const bool ok = spawn_energy(L, sg.a0[j], sg.a1[j], sg.b2[j], sg.b3[j], dA, A, sB, mu0, qr, inv_ws, E32, nb);
     Lane t;
-    if (hit) {
-        for (int j = 0; j < 3; ++j) { t.x0[j] = x[j]; t.k[j] = k[j]; }
+    for (int m = 0; m < 3; ++m) { t.x0[m] = sg.x[m][j]; t.k[m] = sg.k[m][j]; }
+    t.s_exit = 0.f; t.inv_mu = 0.f; t.pa = 0.f; t.ra = 0.f; t.qmin = 0.f; t.pbar = 0.f; t.w0 = 0u; t.face = 0;
+    if (ok) {
         t.A = A;
         t.sB = sB;
         t.cB = sqrtf(fmaxf(0.0f, __fmaf_rn(-sB, sB, 1.0f)));
@@ -1348,35 +1414,14 @@ __global__ void __launch_bounds__(kSpawnThreads) k_spawn32(const __grid_constant
         t.inv_ws = inv_ws;
         segment<GEOM>(L, t);
     }
-    const unsigned hm = __ballot_sync(0xffffffffu, hit);
-    if (lane == 0) s_ofs[warp] = __popc(hm);
-    __syncthreads();
-    if (warp == 0) {
-        // exclusive scan of the warps' hit counts, one global atomic for the block
-        const unsigned c = lane < kSpawnWarps ? s_ofs[lane] : 0u;
-        unsigned inc = c;
-        for (int off = 1; off < 32; off <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
-            if (lane >= off) inc += y;
-        }
-        const unsigned total = __shfl_sync(0xffffffffu, inc, 31);
-        unsigned long long b = 0;
-        if (lane == 0 && total) b = atomicAdd(n_hits, (unsigned long long)total);
-        if (lane < kSpawnWarps) s_ofs[lane] = inc - c;
-        if (lane == 0) s_base = b;
-    }
-    __syncthreads();
-    if (hit) {
-        const size_t slot = s_base + s_ofs[warp] + __popc(hm & ((1u << lane) - 1u));
-        const uint64_t ray = L.offset + id;
-        float4 *r = wave_rec(B, slot);
-        r[0] = make_float4(t.x0[0], t.x0[1], t.x0[2], t.k[0]);
-        r[1] = make_float4(t.k[1], t.k[2], A, sB);
-        r[2] = make_float4(mu0, qr, inv_ws, E32);
-        r[3] = make_float4(t.s_exit, t.inv_mu, t.pa, t.ra);
-        r[4] = make_float4(t.qmin, t.pbar, __uint_as_float((uint32_t)ray), __uint_as_float((uint32_t)(ray >> 32)));
-        r[5] = make_float4(__uint_as_float(t.w0), __int_as_float(t.face), __int_as_float(nb), 0.0f);
-    }
+    const uint64_t ray = L.offset + first + (uint64_t)blockIdx.x * blockDim.x + sg.idx[j];
+    float4 *r = wave_rec(B, s_base + j);
+    r[0] = make_float4(t.x0[0], t.x0[1], t.x0[2], t.k[0]);
+    r[1] = make_float4(t.k[1], t.k[2], A, sB);
+    r[2] = make_float4(mu0, qr, inv_ws, E32);
+    r[3] = make_float4(t.s_exit, t.inv_mu, t.pa, t.ra);
+    r[4] = make_float4(t.qmin, t.pbar, __uint_as_float((uint32_t)ray), __uint_as_float((uint32_t)(ray >> 32)));
+    r[5] = make_float4(__uint_as_float(t.w0), __int_as_float(t.face), __int_as_float(ok ? nb : 2), 0.0f);
 }
 
 // pass 2: a persistent grid walks the queued hits; idle lanes take the next
@@ -1402,6 +1447,7 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
     Lane s;
     bool alive = false, more = true;
     unsigned long long my_coll = 0;
+    unsigned my_dead = 0;
     for (;;) {
         const unsigned idle = __ballot_sync(0xffffffffu, !alive);
         const int n_idle = __popc(idle);
@@ -1422,18 +1468,22 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                 s.s_exit = r3.x; s.inv_mu = r3.y; s.pa = r3.z; s.ra = r3.w;
                 s.qmin = r4.x; s.pbar = r4.y; s.rl = __float_as_uint(r4.z); s.rh = __float_as_uint(r4.w);
                 s.w0 = __float_as_uint(r5.x); s.face = __float_as_int(r5.y); s.no_bragg = __float_as_int(r5.z);
-                s.inv_1mpa = s.pa < 1.0f ? 1.0f / (1.0f - s.pa) : 0.0f;
-                s.pa_thr = s.pa >= 1.0f ? 0xFFFFFFFFu
-                                        : __float2uint_ru(fminf(s.pa * 4294967296.0f, 4294967040.0f));
-                s.cB = sqrtf(fmaxf(0.0f, __fmaf_rn(-s.sB, s.sB, 1.0f)));
-                s.sgn = -1.0f;
-                s.rho0 = 0.0f;
-                s.call = 2u;
-                s.nrefl = 0;
-                s.ncoll = 0;
-                s.pol = false;
-                segment_consts<GEOM>(L, s);
-                alive = true;
+                if (s.no_bragg == 2) {
+                    ++my_dead;                                // no valid energy: a miss, nothing to walk
+                } else {
+                    s.inv_1mpa = s.pa < 1.0f ? 1.0f / (1.0f - s.pa) : 0.0f;
+                    s.pa_thr = s.pa >= 1.0f ? 0xFFFFFFFFu
+                                            : __float2uint_ru(fminf(s.pa * 4294967296.0f, 4294967040.0f));
+                    s.cB = sqrtf(fmaxf(0.0f, __fmaf_rn(-s.sB, s.sB, 1.0f)));
+                    s.sgn = -1.0f;
+                    s.rho0 = 0.0f;
+                    s.call = 2u;
+                    s.nrefl = 0;
+                    s.ncoll = 0;
+                    s.pol = false;
+                    segment_consts<GEOM>(L, s);
+                    alive = true;
+                }
             }
         }
         if (alive) {
@@ -1445,8 +1495,14 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
             }
         }
     }
-    for (int off = 16; off > 0; off >>= 1) my_coll += __shfl_down_sync(0xffffffffu, my_coll, off);
-    if (lane == 0) atomicAdd(&bt.coll, my_coll);
+    for (int off = 16; off > 0; off >>= 1) {
+        my_coll += __shfl_down_sync(0xffffffffu, my_coll, off);
+        my_dead += __shfl_down_sync(0xffffffffu, my_dead, off);
+    }
+    if (lane == 0) {
+        atomicAdd(&bt.coll, my_coll);
+        if (my_dead) atomicAdd(&L.tally[T_MISS], (unsigned long long)my_dead);
+    }
     __syncthreads();
     unsigned long long *T = L.tally;
     for (int i = threadIdx.x; i < kTallyN; i += blockDim.x) {

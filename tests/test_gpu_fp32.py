@@ -135,3 +135,26 @@ def test_fp32_int64_image_and_chunking_invariance(H):
     assert ta["emitted"] == 1_000_000
     assert ta["emitted"] == (ta["miss"] + ta["absorbed"] + ta["exit_front"] + ta["exit_back"] +
                              ta["exit_side"] + ta["capped"] + ta["stuck"])
+
+
+def test_two_pass_trace_equals_persistent_kernel_with_invalid_energies(H):
+    # A Gaussian line 4 keV wide about 8 keV draws E <= 0 for ~2 % of the rays: such a ray is a
+    # miss.  The image trace (two passes: entry, then the energy of the rays that entered, whose
+    # invalid ones travel through the queue as dead records) gives the image and tallies of the
+    # persistent kernel (the per-ray-record path) on the same streams.
+    import torch
+    w = W.von_hamos_hapg()
+    src = dict(w["source"], components=[dict(kind="gauss", e0_keV=8.0, width_keV=4.0, weight=1.0)],
+               cone_half_angle_rad=0.03)
+    s = H.heart_spectrometer_create(w["spec"])
+    n = 3_000_000
+    img = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    t2 = H.heart_trace(s, src, n, 17, 0, img, precision="fp32")
+    img_r = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    rec, tr = H.heart_trace_records(s, src, n, 17, 0, precision="fp32", d_image=img_r)
+    s.close()
+    assert t2 == tr
+    assert torch.equal(img, img_r)
+    neg = rec["energy_keV"] < 0                          # entered, then drew a negative energy
+    assert neg.sum() > 1000 and np.all(rec["outcome"][neg] == 0)
+    assert t2["miss"] > int(neg.sum()) and t2["emitted"] == n
