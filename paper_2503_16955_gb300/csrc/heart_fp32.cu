@@ -586,15 +586,26 @@ __device__ __forceinline__ void bragg_window(const Launch32 &L, float sB, float 
     e2 = cB <= sx ? 1.0f - sB : __fmaf_rn(-sB, hx2, cB * sx);
 }
 
-// acos(m / b) for b > 0, clamped to [0, pi]; near y = +-1 from the small
-// differences b -+ m, where acosf of the rounded ratio loses sqrt(ulp)
+// acos(m / b) for b > 0, clamped to [0, pi], by Abramowitz & Stegun 4.4.46:
+// acos(x) = sqrt(1 - x) (a0 + a1 x + ... + a7 x^7) on [0, 1] with absolute
+// error <= 2e-8, acos(-x) = pi - acos(x).  1 -+ x is formed as (b -+ m) / b,
+// so the result keeps its accuracy near x = +-1.  (An arc end off by 1e-6 rad
+// moves the Bragg offset by b 1e-6 ~ 1e-9, far below the rocking-curve scale.)
 __device__ __forceinline__ float acos_ratio(float m, float b) {
     if (m >= b) return 0.0f;
     if (m <= -b) return 3.14159265f;
-    const float y = m / b;
-    if (y > 0.5f) return 2.0f * asinf(sqrtf((b - m) / (2.0f * b)));
-    if (y < -0.5f) return 3.14159265f - 2.0f * asinf(sqrtf((b + m) / (2.0f * b)));
-    return acosf(y);
+    const float ib = 1.0f / b;
+    const float x = fabsf(m) * ib, omx = (b - fabsf(m)) * ib;
+    float p = -0.0012624911f;
+    p = __fmaf_rn(p, x, 0.0066700901f);
+    p = __fmaf_rn(p, x, -0.0170881256f);
+    p = __fmaf_rn(p, x, 0.0308918810f);
+    p = __fmaf_rn(p, x, -0.0501743046f);
+    p = __fmaf_rn(p, x, 0.0889789874f);
+    p = __fmaf_rn(p, x, -0.2145988016f);
+    p = __fmaf_rn(p, x, 1.5707963050f);
+    const float r = sqrtf(omx) * p;
+    return m >= 0.0f ? r : 3.14159265f - r;
 }
 
 // Process (b), azimuth: the arcs of xi' in [0, pi] whose cos lies in
@@ -620,7 +631,7 @@ __device__ __noinline__ float4 arc_sample(float iv0, float iv1, float iv2, float
     if (pos >= arcs) { pos -= arcs; sg = -1.0f; }
     const float xp = pos < len[0] ? start[0] + pos : start[1] + (pos - len[0]);
     float sxp, cxp;
-    sincosf(xp, &sxp, &cxp);
+    __sincosf(xp, &sxp, &cxp);                        // xp in [0, pi]: absolute error < 1e-6
     return make_float4(1.0f, cxp, sxp, sg);
 }
 
@@ -982,18 +993,20 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
     }
     const float Ac = __fmaf_rn(s.sgn, dk, s.A);               // anchor at the collision point
     if ((IRC >= 0 ? IRC : L.irc_kind) == HEART_IRC_NONE) return cone_step<GEOM_T, EXT>(L, s, w[2], w[3], v, Ac, kN, kt2, eps, rho);
-    float q, st, sx, cx, D;
-    if (v < s.ra) {                                           // process (a), or the plain stream
-        if (s.ra < 1.0f) v = (v / s.ra) * L.vstar;
-        q = mdf_q32(tab, w[2]);
-        st = sqrtf(q * (2.0f - q));
+    // the candidate's stream: (a), or the plain stream, takes the table word over
+    // its full range, (b) maps it onto [w0, 2^32); one table lookup for both
+    // (a warp almost always holds candidates of both streams)
+    const bool in_a = v < s.ra;
+    v = in_a ? (s.ra < 1.0f ? (v / s.ra) * L.vstar : v) : __fmaf_rn(1.0f - L.vstar, (v - s.ra) / (1.0f - s.ra), L.vstar);
+    const uint32_t wq = in_a ? w[2] : s.w0 + __umulhi(w[2], 0u - s.w0) + (s.w0 == 0u ? w[2] : 0u);
+    const float q = mdf_q32(tab, wq);
+    if (!in_a && (q < s.qmin || q > 2.0f - s.qmin)) return -1;   // (b): cannot reflect
+    const float st = sqrtf(q * (2.0f - q));
+    float sx, cx, D;
+    if (in_a) {                                               // process (a), or the plain stream
         sincos_2pi(u01_32(w[3]), &sx, &cx);
         D = __fmaf_rn(st, __fmaf_rn(s.k[0], cx, kt2 * sx), -q * kN);
     } else {                                                  // process (b)
-        v = __fmaf_rn(1.0f - L.vstar, (v - s.ra) / (1.0f - s.ra), L.vstar);
-        q = mdf_q32(tab, s.w0 + __umulhi(w[2], 0u - s.w0) + (s.w0 == 0u ? w[2] : 0u));
-        if (q < s.qmin || q > 2.0f - s.qmin) return -1;        // cannot reflect
-        st = sqrtf(q * (2.0f - q));
         const float ca = sqrtf(__fmaf_rn(s.k[0], s.k[0], kt2 * kt2));
         const float b = ca * st, ib = 1.0f / b;
         // intervals of y = cos(xi - xi_k) with |k.n| = |kN (1 - q) + b y| in the window,
