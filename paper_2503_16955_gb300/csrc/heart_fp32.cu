@@ -188,15 +188,17 @@ __device__ __forceinline__ float irc_rel32(const Launch32 &L, float x) {
         const float d = y + sqrtf(__fmaf_rn(y, y, -1.0f));
         return __frcp_rn(d * d);
     } else if (IRC == HEART_IRC_DARWIN_PRINS) {
+        // |eta -+ z|^2 formed directly; for |y| <= 1e4 the fourth powers stay far
+        // inside the FP32 range, beyond that hypotf takes the modulus
         const float y = x * L.irc_delta, g = L.irc_g;
         const float ar = __fmaf_rn(y, y, -__fmaf_rn(g, g, 1.0f)), ai = 2.0f * y * g;
-        const float r = hypotf(ar, ai);
+        const float r = fabsf(y) <= 1.0e4f ? sqrtf(__fmaf_rn(ar, ar, ai * ai)) : hypotf(ar, ai);
         float zr, zi;
         if (ar >= 0) { zr = sqrtf(0.5f * (r + ar)); zi = zr > 0 ? 0.5f * ai / zr : 0.0f; }
         else { zi = copysignf(sqrtf(0.5f * (r - ar)), ai); zr = 0.5f * ai / zi; }
-        const float m1 = hypotf(y - zr, g - zi), m2 = hypotf(y + zr, g + zi);
-        const float m = fmaxf(m1, m2);
-        return __frcp_rn(m * m) * L.irc_gnorm;              // irc_gnorm = 1 / max R
+        const float d1r = y - zr, d1i = g - zi, d2r = y + zr, d2i = g + zi;
+        const float m2 = fmaxf(__fmaf_rn(d1r, d1r, d1i * d1i), __fmaf_rn(d2r, d2r, d2i * d2i));
+        return __frcp_rn(m2) * L.irc_gnorm;                 // irc_gnorm = 1 / max R
     } else if (IRC == HEART_IRC_PSEUDO_VOIGT) {
         const float hf = 0.5f * L.irc_fwhm;
         const float lor = __fdividef(hf * hf, __fmaf_rn(x, x, hf * hf));   // L(x)/L(0)
@@ -1043,7 +1045,10 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
     if (sa > 0.0f) {
         sa = fminf(sa, 1.0f);
         const float cs = sqrtf(fmaxf(0.0f, 1.0f - sa * sa));
-        delta = asinf(fmaxf(-1.0f, fminf(1.0f, e * (2.0f * s.sB + e) / __fmaf_rn(sa, s.cB, s.sB * cs))));
+        const float t = fmaxf(-1.0f, fminf(1.0f, e * (2.0f * s.sB + e) / __fmaf_rn(sa, s.cB, s.sB * cs)));
+        // asin t = t + t^3/6 + 3 t^5/40 + ... : three terms reach FP32 rounding for |t| < 0.01
+        const float t2 = t * t;
+        delta = fabsf(t) < 0.01f ? __fmaf_rn(t * t2, __fmaf_rn(t2, 0.075f, 0.166666667f), t) : asinf(t);
     } else {
         sa = fminf(-sa, 1.0f);                                 // the normal flipped side
         delta = asinf(sa) - asinf(s.sB);
