@@ -237,6 +237,60 @@ def fp64_measurement(H, W, torch, stream):
     return {"workload": w["name"], "fp64_rays_per_s": fp64, "fp32_rays_per_s": fp32, "fp32_speedup": fp32 / fp64}
 
 
+def features_measurement(H, W, torch, stream):
+    """Throughput of the path's options on the von Hamos workload (device-timed,
+    inputs resident): energy image, polarised source, user-supplied rays, no
+    rocking curve (FP32), and three reflection orders with an energy-dependent
+    rocking curve (FP64, the precision that takes several orders)."""
+    w = W.von_hamos_hapg()
+    out = {}
+
+    def timed(fn, n):
+        fn(0)                                                 # warm (autotune-free path)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t = fn(n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return n / (e0.elapsed_time(e1) / 1e3), t
+
+    s = H.heart_spectrometer_create(w["spec"])
+    img = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    eimg = torch.zeros(s.shape, dtype=torch.int64, device="cuda")
+    n = 50_000_000
+    r, _ = timed(lambda off: H.heart_trace_energy(s, w["source"], n, w["seed"], off, img, eimg,
+                                                 qe=[(7.0, 0.8), (9.0, 0.6)], stream=stream), n)
+    out["energy_image_rays_per_s"] = r
+    pol = dict(w["source"], polarization=[0.0, 1.0, 0.0])
+    r, _ = timed(lambda off: H.heart_trace(s, pol, n, w["seed"], off, img, stream=stream), n)
+    out["polarised_rays_per_s"] = r
+    nu = 10_000_000
+    rays = W.user_rays(w, nu, seed=7, polarised=True)
+    names = dict(ox="origin_x", oy="origin_y", oz="origin_z", kx="dir_x", ky="dir_y", kz="dir_z",
+                 E="energy_keV", px="pol_x", py="pol_y", pz="pol_z")
+    dev = {names[k]: torch.as_tensor(v, dtype=torch.float64, device="cuda").contiguous() for k, v in rays.items()}
+    r, _ = timed(lambda off: H.heart_trace_rays(s, dev, w["seed"], off, img, stream=stream), nu)
+    out["user_rays_polarised_rays_per_s"] = r
+    s.close()
+    s = H.heart_spectrometer_create(dict(w["spec"], irc="none"))
+    nn = 10_000_000
+    r, t = timed(lambda off: H.heart_trace(s, w["source"], nn, w["seed"], off, img, stream=stream), nn)
+    out["irc_none_rays_per_s"] = r
+    out["irc_none_collisions_per_ray"] = t["collisions"] / nn
+    s.close()
+    s = H.heart_spectrometer_create(dict(w["spec"], orders=[(1, 1.0, 1.0), (2, 0.45, 0.6), (3, 0.2, 0.4)],
+                                         irc_energy=[(7.6, 0.8, -1e-5), (8.4, 1.4, 2e-5)]))
+    n64 = 1_000_000
+    r, _ = timed(lambda off: H.heart_trace(s, w["source"], n64, w["seed"], off, img, precision="fp64",
+                                           stream=stream), n64)
+    out["orders3_energy_table_fp64_rays_per_s"] = r
+    s.close()
+    out["note"] = ("von_hamos_hapg; energy image with a 2-knot QE; polarised: source p0 = y; user rays: 1e7 "
+                   "polarised arrays in HBM; irc none: FP32 cone candidates; orders: FP64")
+    return out
+
+
 def run_reference(args):
     import torch.distributed as dist  # noqa: F401
     rank = int(os.environ.get("RANK", "0"))
@@ -362,6 +416,7 @@ def main():
         extra["batched"] = batched_measurement(H, W, torch, stream)
         extra["fp64_plain"] = fp64_measurement(H, W, torch, stream)
         extra["serving"] = serving_measurement(H, W, args.serving_jobs, 200.0)
+        extra["features"] = features_measurement(H, W, torch, stream)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
