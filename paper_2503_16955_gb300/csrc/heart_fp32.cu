@@ -1349,8 +1349,10 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
 // with vector stores and loads (consecutive lanes touch consecutive records):
 //   [x0 x1 x2 k0] [k1 k2 A sB] [mu0 qr inv_ws E] [s_exit inv_mu pa ra]
 //   [qmin pbar ray_lo ray_hi] [w0 face no_bragg -]
+// and for a polarised source a seventh word [p0 p1 p2 -] (112-byte records)
+template <bool POL>
 __device__ __forceinline__ float4 *wave_rec(const WaveBuf &B, size_t slot) {
-    return (float4 *)B.base + slot * (size_t)kWaveRec16;
+    return (float4 *)B.base + slot * (size_t)(POL ? kWaveRec16 + 1 : kWaveRec16);
 }
 
 // pass 1: one thread per ray of [first, first + count), in two phases.  First
@@ -1366,16 +1368,18 @@ __device__ __forceinline__ float4 *wave_rec(const WaveBuf &B, size_t slot) {
 // that the walk counts as a miss.  Emitted rays and misses are tallied by the
 // walk pass from count and the queue length.
 constexpr int kSpawnThreads = 512, kSpawnWarps = kSpawnThreads / 32;
+template <bool POL>
 struct SpawnStage {
     float x[3][kSpawnThreads], k[3][kSpawnThreads], dA[kSpawnThreads];
     uint32_t a0[kSpawnThreads], a1[kSpawnThreads], b2[kSpawnThreads], b3[kSpawnThreads];
     uint32_t idx[kSpawnThreads];
+    float p[3][POL ? kSpawnThreads : 1];                 // polarisation (polarised sources)
 };
-template <int GEOM>
+template <int GEOM, bool POL>
 __global__ void __launch_bounds__(kSpawnThreads) k_spawn32(const __grid_constant__ Launch32 L,
                                                            const __grid_constant__ WaveBuf B, uint64_t first,
                                                            uint32_t count, unsigned long long *n_hits) {
-    __shared__ SpawnStage sg;
+    __shared__ SpawnStage<POL> sg;
     __shared__ unsigned int s_ofs[kSpawnWarps];
     __shared__ unsigned long long s_base;
     __shared__ unsigned int s_hits;
@@ -1409,6 +1413,11 @@ __global__ void __launch_bounds__(kSpawnThreads) k_spawn32(const __grid_constant
             sg.dA[j] = dA;
             sg.a0[j] = a[0]; sg.a1[j] = a[1]; sg.b2[j] = b[2]; sg.b3[j] = b[3];
             sg.idx[j] = threadIdx.x;
+            if (POL) {
+                float pv[3];
+                project_pol32(L, k, pv);
+                for (int m = 0; m < 3; ++m) sg.p[m][POL ? j : 0] = pv[m];
+            }
         }
         __syncthreads();
     }
@@ -1433,7 +1442,8 @@ __global__ void __launch_bounds__(kSpawnThreads) k_spawn32(const __grid_constant
         segment<GEOM>(L, t);
     }
     const uint64_t ray = L.offset + first + (uint64_t)blockIdx.x * blockDim.x + sg.idx[j];
-    float4 *r = wave_rec(B, s_base + j);
+    float4 *r = wave_rec<POL>(B, s_base + j);
+    if (POL) r[kWaveRec16] = make_float4(sg.p[0][POL ? j : 0], sg.p[1][POL ? j : 0], sg.p[2][POL ? j : 0], 0.0f);
     r[0] = make_float4(t.x0[0], t.x0[1], t.x0[2], t.k[0]);
     r[1] = make_float4(t.k[1], t.k[2], A, sB);
     r[2] = make_float4(mu0, qr, inv_ws, E32);
@@ -1444,7 +1454,7 @@ __global__ void __launch_bounds__(kSpawnThreads) k_spawn32(const __grid_constant
 
 // pass 2: a persistent grid walks the queued hits; idle lanes take the next
 // ones (warp-aggregated) once at least `refill` lanes of the warp are idle
-template <int GEOM, int IRC, int OCC>
+template <int GEOM, int IRC, int OCC, bool POL>
 __global__ void __launch_bounds__(kBlockThreads, OCC)
     k_walk32(const __grid_constant__ Launch32 L, const __grid_constant__ WaveBuf B,
              const unsigned long long *n_hits, unsigned long long *head, uint32_t count) {
@@ -1477,9 +1487,13 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
             if (base + n_idle >= nh) more = false;
             const unsigned long long slot = base + __popc(idle & lt_mask);
             if (!alive && slot < nh) {
-                const float4 *r = wave_rec(B, slot);
+                const float4 *r = wave_rec<POL>(B, slot);
                 const float4 r0 = __ldcs(r), r1 = __ldcs(r + 1), r2 = __ldcs(r + 2), r3 = __ldcs(r + 3),
                              r4 = __ldcs(r + 4), r5 = __ldcs(r + 5);
+                if (POL) {
+                    const float4 r6 = __ldcs(r + kWaveRec16);
+                    s.p[0] = r6.x; s.p[1] = r6.y; s.p[2] = r6.z;
+                }
                 s.x0[0] = r0.x; s.x0[1] = r0.y; s.x0[2] = r0.z; s.k[0] = r0.w;
                 s.k[1] = r1.x; s.k[2] = r1.y; s.A = r1.z; s.sB = r1.w;
                 s.mu0 = r2.x; s.qr = r2.y; s.inv_ws = r2.z; s.E = r2.w;
@@ -1498,17 +1512,17 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                     s.call = 2u;
                     s.nrefl = 0;
                     s.ncoll = 0;
-                    s.pol = false;
+                    s.pol = POL && (s.p[0] != 0.0f || s.p[1] != 0.0f || s.p[2] != 0.0f);
                     segment_consts<GEOM>(L, s);
                     alive = true;
                 }
             }
         }
         if (alive) {
-            const int oc = step<GEOM, IRC, false>(L, s, s_tab);
+            const int oc = step<GEOM, IRC, POL>(L, s, s_tab);
             if (oc >= 0) {
                 my_coll += (unsigned long long)s.ncoll;
-                finish<false, false>(L, s, oc, bt);
+                finish<false, POL>(L, s, oc, bt);
                 alive = false;
             }
         }
@@ -1817,12 +1831,13 @@ static heart_status launch_single(const SpecParams &S, const SourceParams &P, ui
     return rec ? dispatch<true>(L, W, st, false, ext) : dispatch<false>(L, W, st, false, ext);
 }
 
-template <int GEOM, int IRC>
+template <int GEOM, int IRC, bool POL = false>
 static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t n, unsigned long long *ctr,
                                   cudaStream_t st) {
+    constexpr int OCC = POL ? 5 : 6;
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk32<GEOM, IRC, 6>, kBlockThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk32<GEOM, IRC, OCC, POL>, kBlockThreads, 0);
         if (per_sm < 1) per_sm = 1;
     }
     const int walk_blocks = per_sm * num_sms();
@@ -1837,8 +1852,9 @@ static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t 
         unsigned long long *cc = ctr + 2 * g;
         const uint64_t first = c * B.cap;
         const uint32_t count = (uint32_t)(n - first < B.cap ? n - first : B.cap);
-        k_spawn32<GEOM><<<(count + kSpawnThreads - 1) / kSpawnThreads, kSpawnThreads, 0, st>>>(L, B, first, count, cc);
-        k_walk32<GEOM, IRC, 6><<<walk_blocks, kBlockThreads, 0, st>>>(L, B, cc, cc + 1, count);
+        k_spawn32<GEOM, POL><<<(count + kSpawnThreads - 1) / kSpawnThreads, kSpawnThreads, 0, st>>>(L, B, first,
+                                                                                                     count, cc);
+        k_walk32<GEOM, IRC, OCC, POL><<<walk_blocks, kBlockThreads, 0, st>>>(L, B, cc, cc + 1, count);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "FP32 two-pass launch");
@@ -1860,7 +1876,7 @@ heart_status ensure_wave(heart_spectrometer *h, uint64_t n) {
 heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
                          void *img, unsigned long long *scratch, cudaStream_t st, const QeParams *qe, void *wave,
                          uint32_t wave_cap) {
-    if (!wave || n == 0 || S.n_orders > 1 || P.pol_on || P.user || S.irc == HEART_IRC_NONE)
+    if (!wave || n == 0 || S.n_orders > 1 || P.user || S.irc == HEART_IRC_NONE)
         return launch_single(S, P, n, seed, offset, img, scratch, nullptr, st, qe);
     // the two-pass trace: the per-ray work in its own pass, then the walk
     Launch32 L;
@@ -1877,7 +1893,13 @@ heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n,
     B.base = wave;
     B.cap = wave_cap;
     B.pad = 0;
-    unsigned long long *ctr = (unsigned long long *)((char *)wave + (size_t)16 * kWaveRec16 * wave_cap);
+    unsigned long long *ctr = (unsigned long long *)((char *)wave + (size_t)16 * kWaveRecMax16 * wave_cap);
+    if (P.pol_on) {
+        // polarised source: 112-byte records and the walk variant that carries p,
+        // with the rocking curve dispatched at run time (one instantiation per geometry)
+        if (L.geometry == HEART_FLAT) return launch_wave_t<HEART_FLAT, -1, true>(L, B, n, ctr, st);
+        return launch_wave_t<HEART_CYL_VON_HAMOS, -1, true>(L, B, n, ctr, st);
+    }
 #define HEART_WAVE_CASES(G)                                                                          \
     switch (L.irc_kind) {                                                                            \
     case HEART_IRC_DARWIN: return launch_wave_t<G, HEART_IRC_DARWIN>(L, B, n, ctr, st);             \
@@ -2030,7 +2052,7 @@ extern "C" heart_status heart_autotune(heart_spectrometer *h, const heart_source
     heart_status st = build_source_params(src, &P, err, (int)sizeof err, &spectrum);
     if (st != HEART_OK) return fail(st, err);
     cudaStream_t cs = (cudaStream_t)stream;
-    if (!P.pol_on && !P.user && h->p.n_orders == 1 && h->p.irc != HEART_IRC_NONE) {
+    if (!P.user && h->p.n_orders == 1 && h->p.irc != HEART_IRC_NONE) {
         st = ensure_wave(h, probe_rays);
         if (st != HEART_OK) return st;
     }

@@ -175,3 +175,23 @@ def test_user_rays_validation_and_empty(H):
     assert r["outcome"][0] == 0 and r["outcome"][1] == 0
     assert t["emitted"] == 100
     s.close()
+
+
+@pytest.mark.parametrize("name", ["flat_hopg_mono", "von_hamos_hapg"])
+def test_polarised_image_path_equals_record_path(H, name):
+    # the image trace of a polarised source runs the two-pass kernels (spawn, then the
+    # walk variant that carries p); the per-ray-record path runs the persistent extended
+    # kernel: on the same streams, images and tallies are identical
+    import torch
+    w = getattr(W, name)()
+    src = dict(w["source"], polarization=[0.2, 0.9, -0.3])
+    s = H.heart_spectrometer_create(w["spec"])
+    n = 2_000_000
+    img = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    t2 = H.heart_trace(s, src, n, 23, 0, img, precision="fp32")
+    img_r = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    _, tr = H.heart_trace_records(s, src, n, 23, 0, precision="fp32", d_image=img_r)
+    s.close()
+    assert t2 == tr
+    assert torch.equal(img, img_r)
+    assert t2["det_hits"] > 100
