@@ -311,7 +311,7 @@ static heart_status trace_impl(heart_spectrometer *h, const heart_source_desc *s
                                  cs, qe);
     } else {
         // the two-pass trace needs the handle's hit queue (allocated on first use)
-        if (!P.user && h->p.n_orders == 1 && h->p.irc != HEART_IRC_NONE) {
+        if (h->p.n_orders == 1 && h->p.irc != HEART_IRC_NONE) {
             st = ensure_wave(h, n_rays);
             if (st != HEART_OK) return st;
         }

@@ -1368,27 +1368,46 @@ __device__ __forceinline__ float4 *wave_rec(const WaveBuf &B, size_t slot) {
 // that the walk counts as a miss.  Emitted rays and misses are tallied by the
 // walk pass from count and the queue length.
 constexpr int kSpawnThreads = 512, kSpawnWarps = kSpawnThreads / 32;
-template <bool POL>
+// staged entered rays: sampled sources keep dA and the energy words (a0 a1 b2
+// b3); user-supplied rays, set up in full by spawn_user, keep A in dA and sB,
+// mu0, qr, inv_ws in the word slots, with E and no_bragg beside them
+template <bool POL, bool USER>
 struct SpawnStage {
     float x[3][kSpawnThreads], k[3][kSpawnThreads], dA[kSpawnThreads];
     uint32_t a0[kSpawnThreads], a1[kSpawnThreads], b2[kSpawnThreads], b3[kSpawnThreads];
     uint32_t idx[kSpawnThreads];
-    float p[3][POL ? kSpawnThreads : 1];                 // polarisation (polarised sources)
+    float p[3][POL ? kSpawnThreads : 1];                 // polarisation (polarised sources, user rays)
+    float e[USER ? kSpawnThreads : 1];
+    int32_t nb[USER ? kSpawnThreads : 1];
 };
-template <int GEOM, bool POL>
+template <int GEOM, bool POL, bool USER>
 __global__ void __launch_bounds__(kSpawnThreads) k_spawn32(const __grid_constant__ Launch32 L,
                                                            const __grid_constant__ WaveBuf B, uint64_t first,
                                                            uint32_t count, unsigned long long *n_hits) {
-    __shared__ SpawnStage<POL> sg;
+    static_assert(!USER || POL, "user rays travel with their polarisation word");
+    __shared__ SpawnStage<POL, USER> sg;
     __shared__ unsigned int s_ofs[kSpawnWarps];
     __shared__ unsigned long long s_base;
     __shared__ unsigned int s_hits;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     {
-        float x[3], k[3], dA = 0.0f;
+        float x[3], k[3], dA = 0.0f, pv[3] = {0.0f, 0.0f, 0.0f};
         uint32_t a[4], b[4];
-        const bool hit = i < count && spawn_entry<GEOM>(L, L.offset + first + i, x, k, dA, a, b);
+        float uE = 0.0f;
+        int unb = 0;
+        bool hit;
+        if (USER) {
+            // the ray's own origin, direction, energy and polarisation, entered in FP64
+            float A = 0.f, sB = 0.f, mu0 = 0.f, qr = 0.f, inv_ws = 1.f;
+            hit = i < count && spawn_user<GEOM>(L, first + i, x, k, pv, A, sB, mu0, qr, inv_ws, uE, unb);
+            dA = A;
+            a[0] = __float_as_uint(sB); a[1] = __float_as_uint(mu0);
+            b[2] = __float_as_uint(qr); b[3] = __float_as_uint(inv_ws);
+        } else {
+            hit = i < count && spawn_entry<GEOM>(L, L.offset + first + i, x, k, dA, a, b);
+            if (POL && hit) project_pol32(L, k, pv);
+        }
         const unsigned hm = __ballot_sync(0xffffffffu, hit);
         if (lane == 0) s_ofs[warp] = __popc(hm);
         __syncthreads();
@@ -1413,11 +1432,9 @@ __global__ void __launch_bounds__(kSpawnThreads) k_spawn32(const __grid_constant
             sg.dA[j] = dA;
             sg.a0[j] = a[0]; sg.a1[j] = a[1]; sg.b2[j] = b[2]; sg.b3[j] = b[3];
             sg.idx[j] = threadIdx.x;
-            if (POL) {
-                float pv[3];
-                project_pol32(L, k, pv);
+            if (POL)
                 for (int m = 0; m < 3; ++m) sg.p[m][POL ? j : 0] = pv[m];
-            }
+            if (USER) { sg.e[USER ? j : 0] = uE; sg.nb[USER ? j : 0] = unb; }
         }
         __syncthreads();
     }
@@ -1425,8 +1442,16 @@ __global__ void __launch_bounds__(kSpawnThreads) k_spawn32(const __grid_constant
     if (j >= s_hits) return;
     float A = 0.f, sB = 0.f, mu0 = 0.f, qr = 0.f, inv_ws = 1.f, E32 = 0.f;
     int nb = 0;
-    const float dA = sg.dA[j];
-    const bool ok = spawn_energy(L, sg.a0[j], sg.a1[j], sg.b2[j], sg.b3[j], dA, A, sB, mu0, qr, inv_ws, E32, nb);
+    bool ok = true;
+    if (USER) {
+        A = sg.dA[j];
+        sB = __uint_as_float(sg.a0[j]); mu0 = __uint_as_float(sg.a1[j]);
+        qr = __uint_as_float(sg.b2[j]); inv_ws = __uint_as_float(sg.b3[j]);
+        E32 = sg.e[USER ? j : 0];
+        nb = sg.nb[USER ? j : 0];
+    } else {
+        ok = spawn_energy(L, sg.a0[j], sg.a1[j], sg.b2[j], sg.b3[j], sg.dA[j], A, sB, mu0, qr, inv_ws, E32, nb);
+    }
     Lane t;
     for (int m = 0; m < 3; ++m) { t.x0[m] = sg.x[m][j]; t.k[m] = sg.k[m][j]; }
     t.s_exit = 0.f; t.inv_mu = 0.f; t.pa = 0.f; t.ra = 0.f; t.qmin = 0.f; t.pbar = 0.f; t.w0 = 0u; t.face = 0;
@@ -1831,7 +1856,7 @@ static heart_status launch_single(const SpecParams &S, const SourceParams &P, ui
     return rec ? dispatch<true>(L, W, st, false, ext) : dispatch<false>(L, W, st, false, ext);
 }
 
-template <int GEOM, int IRC, bool POL = false>
+template <int GEOM, int IRC, bool POL = false, bool USER = false>
 static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t n, unsigned long long *ctr,
                                   cudaStream_t st) {
     constexpr int OCC = POL ? 5 : 6;
@@ -1852,8 +1877,8 @@ static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t 
         unsigned long long *cc = ctr + 2 * g;
         const uint64_t first = c * B.cap;
         const uint32_t count = (uint32_t)(n - first < B.cap ? n - first : B.cap);
-        k_spawn32<GEOM, POL><<<(count + kSpawnThreads - 1) / kSpawnThreads, kSpawnThreads, 0, st>>>(L, B, first,
-                                                                                                     count, cc);
+        k_spawn32<GEOM, POL, USER><<<(count + kSpawnThreads - 1) / kSpawnThreads, kSpawnThreads, 0, st>>>(
+            L, B, first, count, cc);
         k_walk32<GEOM, IRC, OCC, POL><<<walk_blocks, kBlockThreads, 0, st>>>(L, B, cc, cc + 1, count);
     }
     cudaError_t e = cudaGetLastError();
@@ -1876,7 +1901,7 @@ heart_status ensure_wave(heart_spectrometer *h, uint64_t n) {
 heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
                          void *img, unsigned long long *scratch, cudaStream_t st, const QeParams *qe, void *wave,
                          uint32_t wave_cap) {
-    if (!wave || n == 0 || S.n_orders > 1 || P.user || S.irc == HEART_IRC_NONE)
+    if (!wave || n == 0 || S.n_orders > 1 || S.irc == HEART_IRC_NONE)
         return launch_single(S, P, n, seed, offset, img, scratch, nullptr, st, qe);
     // the two-pass trace: the per-ray work in its own pass, then the walk
     Launch32 L;
@@ -1894,6 +1919,12 @@ heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n,
     B.cap = wave_cap;
     B.pad = 0;
     unsigned long long *ctr = (unsigned long long *)((char *)wave + (size_t)16 * kWaveRecMax16 * wave_cap);
+    if (P.user) {
+        // user-supplied rays (polarised or not): entered in FP64 by the spawn pass,
+        // walked by the variant that carries p
+        if (L.geometry == HEART_FLAT) return launch_wave_t<HEART_FLAT, -1, true, true>(L, B, n, ctr, st);
+        return launch_wave_t<HEART_CYL_VON_HAMOS, -1, true, true>(L, B, n, ctr, st);
+    }
     if (P.pol_on) {
         // polarised source: 112-byte records and the walk variant that carries p,
         // with the rocking curve dispatched at run time (one instantiation per geometry)
@@ -2052,7 +2083,7 @@ extern "C" heart_status heart_autotune(heart_spectrometer *h, const heart_source
     heart_status st = build_source_params(src, &P, err, (int)sizeof err, &spectrum);
     if (st != HEART_OK) return fail(st, err);
     cudaStream_t cs = (cudaStream_t)stream;
-    if (!P.user && h->p.n_orders == 1 && h->p.irc != HEART_IRC_NONE) {
+    if (h->p.n_orders == 1 && h->p.irc != HEART_IRC_NONE) {
         st = ensure_wave(h, probe_rays);
         if (st != HEART_OK) return st;
     }

@@ -195,3 +195,23 @@ def test_polarised_image_path_equals_record_path(H, name):
     assert t2 == tr
     assert torch.equal(img, img_r)
     assert t2["det_hits"] > 100
+
+
+@pytest.mark.parametrize("name", ["flat_hopg_mono", "von_hamos_hapg"])
+@pytest.mark.parametrize("polarised", [False, True])
+def test_user_rays_image_path_equals_record_path(H, name, polarised):
+    # the image trace of user rays runs the two-pass kernels (FP64 entry in the spawn pass);
+    # the per-ray-record path runs the persistent extended kernel: identical images and tallies
+    import torch
+    w = getattr(W, name)()
+    n = 1_000_000
+    rays = _device_rays(W.user_rays(w, n, seed=41, polarised=polarised))
+    s = H.heart_spectrometer_create(w["spec"])
+    a = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    b = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    ta = H.heart_trace_rays(s, rays, 19, 0, a, precision="fp32")
+    _, tb = H.heart_trace_rays(s, rays, 19, 0, b, precision="fp32", records=True)
+    s.close()
+    assert ta == tb
+    assert torch.equal(a, b)
+    assert ta["det_hits"] > 50 and ta["miss"] >= 2          # two degenerate rays are misses
