@@ -588,15 +588,14 @@ __device__ __forceinline__ void bragg_window(const Launch32 &L, float sB, float 
     e2 = cB <= sx ? 1.0f - sB : __fmaf_rn(-sB, hx2, cB * sx);
 }
 
-// acos(m / b) for b > 0, clamped to [0, pi], by Abramowitz & Stegun 4.4.46:
+// acos(m / b) for b > 0 (ib = 1 / b), clamped to [0, pi], by Abramowitz & Stegun 4.4.46:
 // acos(x) = sqrt(1 - x) (a0 + a1 x + ... + a7 x^7) on [0, 1] with absolute
 // error <= 2e-8, acos(-x) = pi - acos(x).  1 -+ x is formed as (b -+ m) / b,
 // so the result keeps its accuracy near x = +-1.  (An arc end off by 1e-6 rad
 // moves the Bragg offset by b 1e-6 ~ 1e-9, far below the rocking-curve scale.)
-__device__ __forceinline__ float acos_ratio(float m, float b) {
+__device__ __forceinline__ float acos_ratio(float m, float b, float ib) {
     if (m >= b) return 0.0f;
     if (m <= -b) return 3.14159265f;
-    const float ib = 1.0f / b;
     const float x = fabsf(m) * ib, omx = (b - fabsf(m)) * ib;
     float p = -0.0012624911f;
     p = __fmaf_rn(p, x, 0.0066700901f);
@@ -615,15 +614,16 @@ __device__ __forceinline__ float acos_ratio(float m, float b) {
 // arc measure in units of pi), then place xi' uniformly over the arcs (sign
 // from the second half of the conditional uniform).  Out of line: rarely run.
 // Returns (kept, cos xi', sin xi', sign).
-__device__ __noinline__ float4 arc_sample(float iv0, float iv1, float iv2, float iv3, float b, float t3pbar) {
+__device__ __forceinline__ float4 arc_sample(float iv0, float iv1, float iv2, float iv3, float b, float ib,
+                                          float t3pbar) {
     const float iv[4] = {iv0, iv1, iv2, iv3};
     float start[2], len[2];
     for (int j = 0; j < 2; ++j) {
         start[j] = 0.0f;
         len[j] = 0.0f;
         if (iv[2 * j] < iv[2 * j + 1] && iv[2 * j] < b && iv[2 * j + 1] > -b) {
-            start[j] = acos_ratio(iv[2 * j + 1], b);
-            len[j] = acos_ratio(iv[2 * j], b) - start[j];
+            start[j] = acos_ratio(iv[2 * j + 1], b, ib);
+            len[j] = acos_ratio(iv[2 * j], b, ib) - start[j];
         }
     }
     const float arcs = len[0] + len[1];
@@ -1030,7 +1030,7 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
         const float t3pbar = u01_32(w[3]) * s.pbar;
         // P_xi <= 2 acos(1 - w) / pi <= sqrt(2 w), w = (S2 - S1) / b: most candidates end here
         if (t3pbar * t3pbar * b >= 2.0002f * (e2 - e1)) return -1;
-        const float4 r = arc_sample(iv[0], iv[1], iv[2], iv[3], b, t3pbar);
+        const float4 r = arc_sample(iv[0], iv[1], iv[2], iv[3], b, ib, t3pbar);
         if (r.x == 0.0f) return -1;                           // outside the arcs: cannot reflect
         const float cxp = r.y, sxp = r.z, sg = r.w;
         const float ica = ib * st;                            // 1 / ca
