@@ -39,6 +39,22 @@ def _pair(H, spec, src, n, seed, offset=0):
     return r64, t64, r32, t32
 
 
+def assert_same_up_to_flips(ta, tb, ia, ib, n):
+    """Two FP32 kernel instantiations trace the same streams; a compiler may contract
+    their arithmetic differently, so a borderline decision can round the other way
+    for a rare ray.  Tallies agree within max(2, 1e-5 n) rays per count (collisions
+    within 100 per such ray), images within two counts per such ray."""
+    lim = max(2, int(1e-5 * n))
+    assert ta["emitted"] == tb["emitted"]
+    for k in ("miss", "absorbed", "exit_front", "exit_back", "exit_side", "capped", "stuck", "no_bragg",
+              "det_hits"):
+        assert abs(ta[k] - tb[k]) <= lim, (k, ta[k], tb[k])
+    assert abs(ta["collisions"] - tb["collisions"]) <= 100 * lim
+    assert all(abs(x - y) <= lim for x, y in zip(ta["refl_hist"], tb["refl_hist"]))
+    diff = int((ia.long() - ib.long()).abs().sum())
+    assert diff <= 2 * lim, diff
+
+
 def _profile_stats(u):
     """centroid and FWHM of a 1-D hit profile (histogram at 1/4 of its rms)"""
     c = float(np.mean(u))
@@ -141,7 +157,7 @@ def test_two_pass_trace_equals_persistent_kernel_with_invalid_energies(H):
     # A Gaussian line 4 keV wide about 8 keV draws E <= 0 for ~2 % of the rays: such a ray is a
     # miss.  The image trace (two passes: entry, then the energy of the rays that entered, whose
     # invalid ones travel through the queue as dead records) gives the image and tallies of the
-    # persistent kernel (the per-ray-record path) on the same streams.
+    # persistent kernel (the per-ray-record path) on the same streams, up to rare rounding flips.
     import torch
     w = W.von_hamos_hapg()
     src = dict(w["source"], components=[dict(kind="gauss", e0_keV=8.0, width_keV=4.0, weight=1.0)],
@@ -153,8 +169,7 @@ def test_two_pass_trace_equals_persistent_kernel_with_invalid_energies(H):
     img_r = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
     rec, tr = H.heart_trace_records(s, src, n, 17, 0, precision="fp32", d_image=img_r)
     s.close()
-    assert t2 == tr
-    assert torch.equal(img, img_r)
+    assert_same_up_to_flips(t2, tr, img, img_r, n)
     neg = rec["energy_keV"] < 0                          # entered, then drew a negative energy
     assert neg.sum() > 1000 and np.all(rec["outcome"][neg] == 0)
     assert t2["miss"] > int(neg.sum()) and t2["emitted"] == n

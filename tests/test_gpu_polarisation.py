@@ -30,6 +30,22 @@ def H():
     return H
 
 
+def assert_same_up_to_flips(ta, tb, ia, ib, n):
+    """Two FP32 kernel instantiations trace the same streams; a compiler may contract
+    their arithmetic differently, so a borderline decision can round the other way
+    for a rare ray.  Tallies agree within max(2, 1e-5 n) rays per count (collisions
+    within 100 per such ray), images within two counts per such ray."""
+    lim = max(2, int(1e-5 * n))
+    assert ta["emitted"] == tb["emitted"]
+    for k in ("miss", "absorbed", "exit_front", "exit_back", "exit_side", "capped", "stuck", "no_bragg",
+              "det_hits"):
+        assert abs(ta[k] - tb[k]) <= lim, (k, ta[k], tb[k])
+    assert abs(ta["collisions"] - tb["collisions"]) <= 100 * lim
+    assert all(abs(x - y) <= lim for x, y in zip(ta["refl_hist"], tb["refl_hist"]))
+    diff = int((ia.long() - ib.long()).abs().sum())
+    assert diff <= 2 * lim, diff
+
+
 def _device_rays(rays):
     import torch
     return {C_NAMES[k]: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in rays.items()}
@@ -130,8 +146,8 @@ def test_fp32_user_rays_follow_fp64(H, name, polarised):
 
 
 def test_fp32_image_path_equals_record_path_and_batch(H):
-    # the image-only launch, the record launch and a batched launch of a
-    # polarised source trace the same streams with the same kernel
+    # the image-only launch (two-pass kernels), the record launch and a batched launch
+    # (persistent extended kernel) of a polarised source trace the same streams
     import torch
     w = W.flat_hopg_mono()
     src = dict(w["source"], polarization=[0.0, 1.0, 0.0])
@@ -139,12 +155,13 @@ def test_fp32_image_path_equals_record_path_and_batch(H):
     a = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
     b = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
     c = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
-    ta = H.heart_trace(s, src, 300_000, 12, 0, a, precision="fp32")
-    H.heart_trace_records(s, src, 300_000, 12, 0, precision="fp32", d_image=b)
-    tb = H.heart_trace_batch([s, s], [src, w["source"]], [300_000, 1000], [12, 13], [c, torch.zeros_like(c)])
+    n = 300_000
+    ta = H.heart_trace(s, src, n, 12, 0, a, precision="fp32")
+    _, tr = H.heart_trace_records(s, src, n, 12, 0, precision="fp32", d_image=b)
+    tb = H.heart_trace_batch([s, s], [src, w["source"]], [n, 1000], [12, 13], [c, torch.zeros_like(c)])
     s.close()
-    assert torch.equal(a, b) and torch.equal(a, c)
-    assert ta == tb[0]
+    assert_same_up_to_flips(tr, tb[0], b, c, n)
+    assert_same_up_to_flips(ta, tb[0], a, c, n)
     # sigma polarisation reflects more often than unpolarised light
     u = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
     s2 = H.heart_spectrometer_create(w["spec"])
@@ -181,7 +198,7 @@ def test_user_rays_validation_and_empty(H):
 def test_polarised_image_path_equals_record_path(H, name):
     # the image trace of a polarised source runs the two-pass kernels (spawn, then the
     # walk variant that carries p); the per-ray-record path runs the persistent extended
-    # kernel: on the same streams, images and tallies are identical
+    # kernel: on the same streams, images and tallies agree up to rare rounding flips
     import torch
     w = getattr(W, name)()
     src = dict(w["source"], polarization=[0.2, 0.9, -0.3])
@@ -192,8 +209,7 @@ def test_polarised_image_path_equals_record_path(H, name):
     img_r = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
     _, tr = H.heart_trace_records(s, src, n, 23, 0, precision="fp32", d_image=img_r)
     s.close()
-    assert t2 == tr
-    assert torch.equal(img, img_r)
+    assert_same_up_to_flips(t2, tr, img, img_r, n)
     assert t2["det_hits"] > 100
 
 
@@ -201,7 +217,8 @@ def test_polarised_image_path_equals_record_path(H, name):
 @pytest.mark.parametrize("polarised", [False, True])
 def test_user_rays_image_path_equals_record_path(H, name, polarised):
     # the image trace of user rays runs the two-pass kernels (FP64 entry in the spawn pass);
-    # the per-ray-record path runs the persistent extended kernel: identical images and tallies
+    # the per-ray-record path runs the persistent extended kernel: images and tallies agree up
+    # to rare rounding flips
     import torch
     w = getattr(W, name)()
     n = 1_000_000
@@ -212,6 +229,6 @@ def test_user_rays_image_path_equals_record_path(H, name, polarised):
     ta = H.heart_trace_rays(s, rays, 19, 0, a, precision="fp32")
     _, tb = H.heart_trace_rays(s, rays, 19, 0, b, precision="fp32", records=True)
     s.close()
-    assert ta == tb
-    assert torch.equal(a, b)
+    assert_same_up_to_flips(ta, tb, a, b, n)
+    assert ta["miss"] == tb["miss"]                          # decided by the same FP64 entry
     assert ta["det_hits"] > 50 and ta["miss"] >= 2          # two degenerate rays are misses
