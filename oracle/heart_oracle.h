@@ -37,7 +37,8 @@
  *   energy-dependent IRC     pinned (constant table = wider, shifted curve; interpolation and clamping)
  *   IRC "none" (Bragg cone)  pinned (k_in . k_out = cos 2a~0 on every single reflection; thin-slab reflection
  *                                    probability vs quadrature along the cone and, for vMF, the Bessel closed
- *                                    form; the limit of ever narrower box curves; accepted psi ~ W(theta(psi)))
+ *                                    form; the limit of ever narrower box curves; both samplers: the plain
+ *                                    bound f(0) and the per-segment cone bounds agree)
  *   tabulated spectrum       pinned (KS against the piecewise-linear CDF written from the knots; a
  *                                    two-knot table reproduces the uniform component bit for bit)
  *   orc_trace_energy         pinned (mono line: energy image = E x QE x counts; QE interpolation)

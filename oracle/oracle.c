@@ -34,7 +34,12 @@
  *    the rate becomes Q cos a~0 sum_cones int_0^2pi f(n(psi)) G dpsi.  The
  *    candidates then carry the bound Q cos a~0 * 2 cones * 2 pi f(0) instead of
  *    Q max R, and a candidate picks a cone and a uniform psi and is kept with
- *    probability f(n) G / f(0) (f from the MDF's own formula).
+ *    probability f(n) G / f(0) (f from the MDF's own formula).  The thinned
+ *    sampler bounds each cone per straight segment instead: the cone facing
+ *    the ray by f at the tilt 2 sin^2(d/2) (d: distance of sin a~0 from the
+ *    segment's |k.N| range), the other by f at 2 sin^2(a~0/2); the cone is
+ *    then drawn by its share of the bound and the candidate kept with
+ *    f(n) G / (its cone's bound).
  *  Detector (Sec. 2.3): exiting rays are propagated to the detector plane and
  *    binned into integer pixel counts.
  *
@@ -861,6 +866,9 @@ typedef struct {
     double S1, S2;            /* |k.n| window of |Delta| < X* */
     uint64_t w0, wspan;       /* process (b): table words [w0, w0 + wspan) */
     double lam;               /* the order's candidate rate on the segment */
+    /* no rocking curve, thinned: W at the smallest tilt each Bragg cone can
+     * reach on the segment, relative to W(0), and the facing cone's share */
+    double wn, wf, pnear;
 } order_bound;
 
 typedef struct {
@@ -900,6 +908,23 @@ static void bound_order(const geom *g, const orc_ray_consts *rc, int h, double l
     b->pbar = 1.0;
     b->wspan = 1ull << 32;
     b->lam = rc->ord_qr[h];
+    b->wn = b->wf = 1.0;
+    b->pnear = 0.5;
+    if (s->sampler == ORC_SAMPLER_THINNED && s->irc == ORC_IRC_NONE && rc->ord_qr[h] > 0) {
+        /* the cone facing the ray (k.n of the sign of k.N): its crystallites are tilted
+         * by at least the angle between a~0 and the grazing-angle range of the segment,
+         * at least d, the distance between the sines; the other cone's by at least a~0.
+         * The MDF decreases with the tilt, so W there bounds the cone on the segment:
+         * rate Q cos a~0 2 pi (f(q_near) + f(q_far)) = ord_qr (wn + wf) / 2. */
+        double a0 = rc->ord_alpha[h] + rc->shift_rad, s0 = sin(a0);
+        double d = s0 < lo ? lo - s0 : (s0 > hi ? s0 - hi : 0.0);
+        double hn = sin(0.5 * d), hf = sin(0.5 * a0);
+        b->wn = orc_mdf_W(s, 2.0 * hn * hn) / g->W0;
+        b->wf = orc_mdf_W(s, 2.0 * hf * hf) / g->W0;
+        b->lam = 0.5 * rc->ord_qr[h] * (b->wn + b->wf);
+        b->pnear = b->wn + b->wf > 0 ? b->wn / (b->wn + b->wf) : 1.0;
+        return;
+    }
     if (s->sampler != ORC_SAMPLER_THINNED || s->irc == ORC_IRC_NONE || !(rc->ord_qr[h] > 0)) return;
     double aB = rc->ord_alpha[h] + rc->shift_rad;
     double xstar = g->xstar * rc->ord_w[h];          /* a curve w times as wide: X* scales by w */
@@ -933,7 +958,7 @@ static void bound_segment(const geom *g, const orc_ray_consts *rc, const double 
     memset(b, 0, sizeof *b);
     b->n = rc->n_orders;
     double lo = 0.0, hi = 1.0;
-    if (s->sampler == ORC_SAMPLER_THINNED && s->irc != ORC_IRC_NONE && !rc->no_bragg) {
+    if (s->sampler == ORC_SAMPLER_THINNED && !rc->no_bragg) {
         int face;
         double se = exit_distance(g, x, k, &face);
         double xe[3], N0[3], N1[3], t1[3], t2[3];
@@ -995,13 +1020,23 @@ static void cone_axes(const double k[3], const double N[3], const double t1[3], 
  * n = sg sin(a~0) k + cos(a~0) (cos(psi) e1 + sin(psi) e2) on the cone
  * k.n = sg sin(a~0), sg = -1 if the top bit of u2 is clear, +1 if set;
  * psi = 2 pi u3.  P = f(n) G / f(0) = W(1 - n.N) G / W(0). */
-static void cone_candidate(const geom *g, const orc_ray_consts *rc, int h, const double x[3], const double k[3],
-                           int pol, const double p[3], const uint32_t w[4], double ks[3], double *P) {
+static void cone_candidate(const geom *g, const orc_ray_consts *rc, int h, const order_bound *ob, const double x[3],
+                           const double k[3], int pol, const double p[3], const uint32_t w[4], double ks[3],
+                           double *P) {
     double N[3], t1[3], t2[3], e1[3], e2[3], n[3];
     local_frame(g, x, N, t1, t2);
     cone_axes(k, N, t1, e1, e2);
     double a0 = rc->ord_alpha[h] + rc->shift_rad, s0 = sin(a0), c0 = cos(a0);
-    double sg = (w[2] & 0x80000000u) ? 1.0 : -1.0;
+    double sg, wb = 1.0;                             /* the cone, and the bound of W / W(0) on it */
+    if (g->s->sampler == ORC_SAMPLER_THINNED) {
+        /* the facing cone (k.n of the sign of k.N) with probability pnear, by u2 */
+        double kN = dot3(k, N), side = kN < 0 ? -1.0 : 1.0;
+        int near_ = U(w[2]) < ob->pnear;
+        sg = near_ ? side : -side;
+        wb = near_ ? ob->wn : ob->wf;
+    } else {
+        sg = (w[2] & 0x80000000u) ? 1.0 : -1.0;
+    }
     double psi = 2.0 * PI * U(w[3]);
     for (int i = 0; i < 3; ++i) n[i] = sg * s0 * k[i] + c0 * (cos(psi) * e1[i] + sin(psi) * e2[i]);
     double q = 1.0 - dot3(n, N);                     /* 1 - cos(theta), the crystallite's tilt */
@@ -1014,7 +1049,7 @@ static void cone_candidate(const geom *g, const orc_ray_consts *rc, int h, const
         double c2 = cos(2.0 * a0);
         G = 0.5 * (1.0 + c2 * c2);                   /* Eq. (G_unpol) at a~0 */
     }
-    *P = orc_mdf_W(g->s, q) / g->W0 * G;
+    *P = orc_mdf_W(g->s, q) / g->W0 / wb * G;
 }
 
 /* the depth walk of one ray from its entry point (Sec. 2.2.4) */
@@ -1053,7 +1088,7 @@ static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[
         }
         double ks[3], P;                                 /* reflected direction, acceptance probability */
         if (g->irc_none) {
-            cone_candidate(g, rc, h, x, k, pol, p, w, ks, &P);
+            cone_candidate(g, rc, h, &sb.o[h], x, k, pol, p, w, ks, &P);
             goto decide;
         }
         const order_bound *ob = &sb.o[h];
