@@ -656,7 +656,25 @@ __device__ __forceinline__ uint32_t tilt_word32(const Launch32 &L, float qmin) {
 __device__ __forceinline__ void thin_segment(const Launch32 &L, Lane &s, float A_exit, bool flip) {
     float la = s.qr, lb = 0.0f;
     s.ra = 1.0f;
-    if (L.sampler == HEART_SAMPLER_THINNED && s.qr > 0.0f && L.irc_kind != HEART_IRC_NONE) {
+    if (L.irc_kind == HEART_IRC_NONE) {
+        // no rocking curve: the Bragg cones' bounds (ra: the facing cone's share of the
+        // candidates; qmin, pbar: the bounds of W / W(0) on the facing and the other cone)
+        s.ra = 0.5f; s.qmin = 1.0f; s.pbar = 1.0f;
+        if (L.sampler == HEART_SAMPLER_THINNED && s.qr > 0.0f) {
+            const float Ae = flip ? -2.0f * s.sB - A_exit : A_exit;
+            const float lo = flip ? -s.sB : fminf(s.A, Ae), hi = fmaxf(s.A, Ae);
+            const float d = lo > 0.0f ? lo : (hi < 0.0f ? -hi : 0.0f);
+            const float h = 0.5f * d, h2 = h * h;
+            const float sh = d < 0.1f ? h * __fmaf_rn(h2, __fmaf_rn(h2, 8.33333333e-3f, -0.166666667f), 1.0f)
+                                      : __sinf(h);
+            const float wn = mdf_ratio32(L, 2.0f * sh * sh);
+            const float wf = mdf_ratio32(L, s.sB * s.sB / (1.0f + s.cB));   // 2 sin^2(a~0 / 2)
+            s.qmin = wn;
+            s.pbar = wf;
+            s.ra = wn + wf > 0.0f ? wn / (wn + wf) : 1.0f;
+            la = 0.5f * s.qr * (wn + wf);
+        }
+    } else if (L.sampler == HEART_SAMPLER_THINNED && s.qr > 0.0f) {
         // |k.N| at the exit is sB + A_exit, or -(sB + A_exit) if k.N changed sign
         const float Ae = flip ? -2.0f * s.sB - A_exit : A_exit;
         const float lo = flip ? -s.sB : fminf(s.A, Ae);   // relative to sB; |k.N| passes 0 on a flip
@@ -895,7 +913,16 @@ __device__ __forceinline__ int cone_step(const Launch32 &L, Lane &s, uint32_t w2
     const float s0 = s.sB, c0 = s.cB;
     const float sa = s0 + Ac;                                   // |k.N| at the collision
     const float cb = sqrtf(fmaxf(0.0f, __fmaf_rn(-sa, sa, 1.0f)));
-    const float sg = (w2 & 0x80000000u) ? 1.0f : -1.0f;
+    // the cone: with the thinned sampler the one facing the ray (k.n of the sign of k.N)
+    // by its share of the segment's bound (lane fields ra, qmin, pbar), else by the top bit
+    float sg, wb = 1.0f;
+    if (L.sampler == HEART_SAMPLER_THINNED) {
+        const bool near_ = u01_32(w2) < s.ra;
+        sg = near_ ? s.sgn : -s.sgn;
+        wb = near_ ? s.qmin : s.pbar;
+    } else {
+        sg = (w2 & 0x80000000u) ? 1.0f : -1.0f;
+    }
     float q0;
     if (sg == s.sgn) {
         const float cs = c0 + cb;
@@ -931,7 +958,7 @@ __device__ __forceinline__ int cone_step(const Launch32 &L, Lane &s, uint32_t w2
         const float c2 = __fmaf_rn(-2.0f * s0, s0, 1.0f);
         G = 0.5f * __fmaf_rn(c2, c2, 1.0f);                     // Eq. (G_unpol) at a~0
     }
-    if (!(v < mdf_ratio32(L, q) * G)) return -1;
+    if (!(v * wb < mdf_ratio32(L, q) * G)) return -1;
     ++s.nrefl;
     if (s.nrefl > L.max_refl) return HEART_CAPPED;
     if (GEOM != HEART_FLAT) s.rho0 += drho;

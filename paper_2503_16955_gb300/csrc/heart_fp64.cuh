@@ -283,6 +283,7 @@ __host__ __device__ __forceinline__ void irc_energy64(const SpecParams &S, doubl
 struct Bound64 {
     double ra, vstar, qmin, pbar, S1, S2, lam;
     unsigned long long w0, wspan;
+    double wn, wf, pnear;          // no rocking curve, thinned: W / W(0) bounds of the two cones, facing share
 };
 
 struct Seg64 {
@@ -305,6 +306,20 @@ __device__ __forceinline__ void bound_order64(const SpecParams &S, const Orders6
     b.ra = 1.0; b.vstar = 1.0; b.qmin = 0.0; b.pbar = 1.0; b.S1 = 0.0; b.S2 = 0.0;
     b.w0 = 0ull; b.wspan = 1ull << 32;
     b.lam = O.qr[h];
+    b.wn = 1.0; b.wf = 1.0; b.pnear = 0.5;
+    if (S.sampler == HEART_SAMPLER_THINNED && S.irc == HEART_IRC_NONE && O.qr[h] > 0) {
+        // no rocking curve: the facing cone's crystallites are tilted by at least d
+        // (distance of sin a~0 from the segment's |k.N| range), the other cone's by at
+        // least a~0; W there, relative to W(0), bounds each cone on the segment
+        const double a0 = O.alpha[h] + O.shift, s0 = sin(a0);
+        const double d = s0 < lo ? lo - s0 : (s0 > hi ? s0 - hi : 0.0);
+        const double hn = sin(0.5 * d), hf = sin(0.5 * a0);
+        b.wn = mdf_ratio64(S, 2.0 * hn * hn);
+        b.wf = mdf_ratio64(S, 2.0 * hf * hf);
+        b.lam = 0.5 * O.qr[h] * (b.wn + b.wf);
+        b.pnear = b.wn + b.wf > 0 ? b.wn / (b.wn + b.wf) : 1.0;
+        return;
+    }
     if (S.sampler != HEART_SAMPLER_THINNED || S.irc == HEART_IRC_NONE || !(O.qr[h] > 0)) return;
     // distance between sines: never more than between the angles
     const double aBs = O.alpha[h] + O.shift;
@@ -337,7 +352,7 @@ __device__ __forceinline__ void bound_order64(const SpecParams &S, const Orders6
 __device__ __forceinline__ void bound_segment64(const SpecParams &S, const Orders64 &O, double mu0, bool any_bragg,
                                                 const double x[3], const double k[3], Seg64 &b) {
     double lo = 0.0, hi = 1.0;
-    if (S.sampler == HEART_SAMPLER_THINNED && S.irc != HEART_IRC_NONE && any_bragg) {
+    if (S.sampler == HEART_SAMPLER_THINNED && any_bragg) {
         int face;
         const double se = exit_distance64(S, x, k, &face);
         double xe[3], N0[3], N1[3], t1[3], t2[3];
@@ -527,7 +542,16 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
             // no rocking curve: the crystallite normal on the cone k.n = sg sin a~0
             // (sg by the top bit of u2) at azimuth psi = 2 pi u3 about k
             const double a0 = O.alpha[h] + O.shift, s0 = sin(a0), c0 = cos(a0);
-            const double sg = (wd[2] & 0x80000000u) ? 1.0 : -1.0;
+            double sg, wb = 1.0;                                // the cone, and its bound of W / W(0)
+            if (S.sampler == HEART_SAMPLER_THINNED) {
+                // the facing cone (k.n of the sign of k.N) by its share of the bound
+                const double side = dot3d(k, N) < 0 ? -1.0 : 1.0;
+                const bool near_ = u01_64(wd[2]) < sb.o[h].pnear;
+                sg = near_ ? side : -side;
+                wb = near_ ? sb.o[h].wn : sb.o[h].wf;
+            } else {
+                sg = (wd[2] & 0x80000000u) ? 1.0 : -1.0;
+            }
             double sp, cp, e1[3], e2[3], n[3];
             sincospi(2.0 * u01_64(wd[3]), &sp, &cp);
             cone_axes64(k, N, t1, e1, e2);
@@ -542,7 +566,7 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
                 const double c2 = cos(2.0 * a0);
                 G = 0.5 * (1.0 + c2 * c2);
             }
-            P = mdf_ratio64(S, q) * G;
+            P = mdf_ratio64(S, q) / wb * G;
         } else {
         const Bound64 &ob = sb.o[h];
         double q, sx, cx;
