@@ -291,6 +291,28 @@ def features_measurement(H, W, torch, stream):
     return out
 
 
+def large_measurement(H, W, torch, stream):
+    """The large single job: von Hamos R = 100 mm, Lorentzian mosaic, elastic +
+    inelastic lines, 4096^2 int64 detector, 1e10 rays in one call (streamed by
+    the library in chunks of 2^24 rays), FP32; device-timed."""
+    w = W.von_hamos_large()
+    s = H.heart_spectrometer_create(w["spec"])
+    img = torch.zeros(s.shape, dtype=torch.int64, device="cuda")
+    H.heart_trace(s, w["source"], 1 << 26, w["seed"], 0, img, stream=stream)          # warm (queue, tables)
+    torch.cuda.synchronize()
+    n = w["n_rays"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t = H.heart_trace(s, w["source"], n, w["seed"], 1 << 26, img, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    s.close()
+    return {"workload": w["name"], "rays": n, "seconds": sec, "rays_per_s": n / sec,
+            "collisions_per_ray": t["collisions"] / n, "det_hits": t["det_hits"],
+            "detector": "%dx%d int64" % (w["spec"]["det_ny"], w["spec"]["det_nx"])}
+
+
 def run_reference(args):
     import torch.distributed as dist  # noqa: F401
     rank = int(os.environ.get("RANK", "0"))
@@ -417,6 +439,7 @@ def main():
         extra["fp64_plain"] = fp64_measurement(H, W, torch, stream)
         extra["serving"] = serving_measurement(H, W, args.serving_jobs, 200.0)
         extra["features"] = features_measurement(H, W, torch, stream)
+        extra["large_job"] = large_measurement(H, W, torch, stream)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
