@@ -317,20 +317,24 @@ heart_status heart_trace_batch(heart_spectrometer *const *specs, const heart_sou
                                const uint64_t *n_rays, const uint64_t *seeds, void *const *d_images,
                                int32_t n_jobs, void *stream, heart_tally *out);
 
-/* Launch shape of the FP32 kernel chosen by heart_autotune. */
+/* Launch shape of the FP32 kernels chosen by heart_autotune. */
 typedef struct {
-    int32_t blocks_per_sm;          /* resident 128-thread blocks per SM: 6 (80 registers) or 5 (96) */
-    int32_t refill_lanes;           /* a warp pops spawned rays when this many lanes are idle */
-    uint32_t max_chunk_rays;        /* largest work item (rays) a block claims */
+    int32_t blocks_per_sm;          /* persistent kernel: resident 128-thread blocks per SM, 6 (80
+                                       registers) or 5 (96) */
+    int32_t refill_lanes;           /* a warp pops queued or spawned rays when this many lanes are idle */
+    uint32_t max_chunk_rays;        /* largest work item (rays) a block of the persistent kernel claims */
     int32_t reserved;
-    double rays_per_s;              /* measured on the probe */
+    double rays_per_s;              /* this trace's rate on the probe with the chosen refill threshold */
 } heart_tune;
 
-/* Time the FP32 kernel on probe_rays rays of this spectrometer and source for
- * each candidate launch shape (blocks per SM x refill threshold) and keep the
- * fastest for all later FP32 launches of the process (single, batched,
- * server).  Call it before tracing, not concurrently with traces.  Uses the
- * handle's scratch image; `out` (may be NULL) receives the choice. */
+/* Time FP32 traces of probe_rays rays of this spectrometer and source: first
+ * the refill threshold (4, 8 or 16 idle lanes) on the path this trace takes
+ * (the two-pass trace for image traces it covers), then the persistent
+ * kernel's blocks per SM (6 or 5), which batched and served jobs and per-ray
+ * records use, on that kernel.  The fastest choices hold for all later FP32
+ * launches of the process.  Call it before tracing, not concurrently with
+ * traces.  Uses the handle's scratch image; `out` (may be NULL) receives the
+ * choice. */
 heart_status heart_autotune(heart_spectrometer *spec, const heart_source_desc *src, uint64_t probe_rays,
                             void *stream, heart_tune *out);
 

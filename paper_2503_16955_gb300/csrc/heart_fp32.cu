@@ -2141,33 +2141,45 @@ extern "C" heart_status heart_autotune(heart_spectrometer *h, const heart_source
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
-    const int occs[2] = {6, 5};
-    const int refills[3] = {4, 8, 16};
-    TuneConfig best = g_tune;
-    double best_rate = -1.0;
+    // Two knots, each timed on the kernel it shapes: the refill threshold on this
+    // trace's own path (the two-pass trace when it applies), then the persistent
+    // kernel's blocks per SM (batched and served jobs, records) on that kernel
+    // with the chosen threshold.  A probe is timed after one warm-up run.
     const TuneConfig saved = g_tune;
-    for (int oi = 0; oi < 2; ++oi) {
-        for (int ri = 0; ri < 3; ++ri) {
-            g_tune.blocks_per_sm = occs[oi];
-            g_tune.refill = refills[ri];
-            float ms = 0.0f;
-            for (int rep = 0; rep < 2; ++rep) {       // first repetition warms up
-                cudaMemsetAsync(h->d_scratch, 0, kScratchWords * sizeof(unsigned long long), cs);
-                cudaEventRecord(t0, cs);
-                st = launch_fp32(h->p, P, probe_rays, 0x5eed + rep, 0, h->d_image_host_path, h->d_scratch, cs,
-                                 nullptr, h->d_wave, h->wave_cap);
-                cudaEventRecord(t1, cs);
-                if (st != HEART_OK) break;
-                if ((e = cudaEventSynchronize(t1)) != cudaSuccess) { st = cuda_fail(e, "autotune probe"); break; }
-                cudaEventElapsedTime(&ms, t0, t1);
-            }
-            if (st != HEART_OK) { g_tune = saved; cudaEventDestroy(t0); cudaEventDestroy(t1); return st; }
-            const double rate = (double)probe_rays / (ms * 1e-3);
-            if (rate > best_rate) { best_rate = rate; best = g_tune; }
+    auto probe = [&](bool persistent, double &rate) -> heart_status {
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaMemsetAsync(h->d_scratch, 0, kScratchWords * sizeof(unsigned long long), cs);
+            cudaEventRecord(t0, cs);
+            heart_status s2 = launch_fp32(h->p, P, probe_rays, 0x5eed + rep, 0, h->d_image_host_path, h->d_scratch,
+                                          cs, nullptr, persistent ? nullptr : h->d_wave, h->wave_cap);
+            cudaEventRecord(t1, cs);
+            if (s2 != HEART_OK) return s2;
+            if ((e = cudaEventSynchronize(t1)) != cudaSuccess) return cuda_fail(e, "autotune probe");
+            cudaEventElapsedTime(&ms, t0, t1);
         }
+        rate = (double)probe_rays / (ms * 1e-3);
+        return HEART_OK;
+    };
+    const int refills[3] = {4, 8, 16};
+    const int occs[2] = {6, 5};
+    TuneConfig best = g_tune;
+    double best_rate = -1.0, rate = 0.0;
+    for (int ri = 0; ri < 3 && st == HEART_OK; ++ri) {
+        g_tune.refill = refills[ri];
+        st = probe(false, rate);
+        if (st == HEART_OK && rate > best_rate) { best_rate = rate; best.refill = refills[ri]; }
+    }
+    g_tune.refill = best.refill;
+    double best_occ_rate = -1.0;
+    for (int oi = 0; oi < 2 && st == HEART_OK; ++oi) {
+        g_tune.blocks_per_sm = occs[oi];
+        st = probe(true, rate);
+        if (st == HEART_OK && rate > best_occ_rate) { best_occ_rate = rate; best.blocks_per_sm = occs[oi]; }
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
+    if (st != HEART_OK) { g_tune = saved; return st; }
     g_tune = best;
     if (out) {
         out->blocks_per_sm = best.blocks_per_sm;
