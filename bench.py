@@ -201,13 +201,36 @@ def serving_measurement(H, W, n_jobs, rate):
     done.wait()
     wall = time.perf_counter() - t0
     srv.close()
-    for s in specs:
-        s.close()
     lat_ms = sorted(1e3 * x for x in lat)
-    q = lambda p: lat_ms[min(len(lat_ms) - 1, int(p * len(lat_ms)))]
+    q = lambda v, p: v[min(len(v) - 1, int(p * len(v)))]
     offered = rays / stream[-1]["arrival_s"]
-    return {"jobs": n_jobs, "rate_per_s": rate, "p50_ms": q(0.50), "p99_ms": q(0.99), "max_ms": lat_ms[-1],
-            "rays_per_s": rays / wall, "offered_rays_per_s": offered,
+    # the same jobs as serial single-job launches (one heart_trace each, FP32, synchronised):
+    # their service times, and the latencies of a first-come-first-served serial server fed
+    # by the same arrivals
+    import torch
+    imgs = [torch.zeros(sp.shape, dtype=torch.int64 if j["spec"]["count_type"] == "i64" else torch.int32,
+                        device="cuda") for sp, j in zip(specs, pool)]
+    service = []
+    for k, job in enumerate(stream):
+        j = k % len(specs)
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        H.heart_trace(specs[j], pool[j]["source"], job["n_rays"], job["seed"], 0, imgs[j], want_tally=False)
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - c0)
+    for sp in specs:
+        sp.close()
+    finish, serial_lat = 0.0, []
+    for job, sv in zip(stream, service):
+        finish = max(job["arrival_s"], finish) + sv
+        serial_lat.append(1e3 * (finish - job["arrival_s"]))
+    serial_lat.sort()
+    return {"jobs": n_jobs, "rate_per_s": rate, "p50_ms": q(lat_ms, 0.50), "p99_ms": q(lat_ms, 0.99),
+            "max_ms": lat_ms[-1], "rays_per_s": rays / wall, "offered_rays_per_s": offered,
+            "serial_fp32": {"rays_per_s": rays / sum(service), "p50_ms": q(serial_lat, 0.50),
+                            "p99_ms": q(serial_lat, 0.99), "max_ms": serial_lat[-1],
+                            "note": "the same jobs, one synchronised heart_trace each, queued first come first "
+                                    "served at the same arrival times"},
             "note": "spectrometers drawn from a pool of 64 (seed 4); rays log-uniform 1e4-1e8"}
 
 

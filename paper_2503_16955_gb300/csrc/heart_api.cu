@@ -244,7 +244,6 @@ extern "C" heart_status heart_spectrometer_destroy(heart_spectrometer *h) {
     cudaFree(h->d_block);
     cudaFreeHost(h->h_scratch);
     if (h->d_image_host_path) cudaFree(h->d_image_host_path);
-    if (h->d_wave) cudaFree(h->d_wave);
     delete h;
     return HEART_OK;
 }
@@ -310,12 +309,16 @@ static heart_status trace_impl(heart_spectrometer *h, const heart_source_desc *s
         st = launch_fp32_records(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, (heart_ray_record *)d_records,
                                  cs, qe);
     } else {
-        // the two-pass trace needs the handle's hit queue (allocated on first use)
+        // the two-pass trace runs on the device's shared hit queue (leased while enqueued)
         if (h->p.n_orders == 1 && h->p.irc != HEART_IRC_NONE) {
-            st = ensure_wave(h, n_rays);
+            WaveLease lease;
+            st = wave_acquire(n_rays, cs, &lease);
             if (st != HEART_OK) return st;
+            st = launch_fp32(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, cs, qe, lease.buf, lease.cap);
+            wave_release(lease, cs);
+        } else {
+            st = launch_fp32(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, cs, qe);
         }
-        st = launch_fp32(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, cs, qe, h->d_wave, h->wave_cap);
     }
     if (st != HEART_OK) return st;
     if (out || sync) {

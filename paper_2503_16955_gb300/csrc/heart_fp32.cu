@@ -1913,16 +1913,54 @@ static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t 
     return HEART_OK;
 }
 
-heart_status ensure_wave(heart_spectrometer *h, uint64_t n) {
+namespace {
+struct DeviceWave {
+    std::mutex m;
+    void *buf = nullptr;
+    uint32_t cap = 0;
+    cudaEvent_t done = nullptr;               // recorded after the queue's last user
+};
+constexpr int kMaxDevices = 64;
+DeviceWave g_wave[kMaxDevices];
+}  // namespace
+
+heart_status wave_acquire(uint64_t n, cudaStream_t st, WaveLease *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(HEART_EINVAL, "device index beyond the hit-queue table");
+    DeviceWave &W = g_wave[dev];
+    W.m.lock();
+    if (!W.done && (e = cudaEventCreateWithFlags(&W.done, cudaEventDisableTiming)) != cudaSuccess) {
+        W.done = nullptr;
+        W.m.unlock();
+        return cuda_fail(e, "cudaEventCreate hit queue");
+    }
     const uint32_t cap = wave_cap_for(n);
-    if (h->d_wave && h->wave_cap >= cap) return HEART_OK;
-    if (h->d_wave) cudaFree(h->d_wave);          // a larger trace than before: grow
-    h->d_wave = nullptr;
-    h->wave_cap = 0;
-    cudaError_t e = cudaMalloc(&h->d_wave, wave_bytes(cap));
-    if (e != cudaSuccess) { h->d_wave = nullptr; return cuda_fail(e, "cudaMalloc hit queue"); }
-    h->wave_cap = cap;
+    if (!W.buf || W.cap < cap) {
+        // a larger chunk than before: the previous user must be done before the queue is replaced
+        if ((e = cudaEventSynchronize(W.done)) != cudaSuccess) { W.m.unlock(); return cuda_fail(e, "hit queue"); }
+        if (W.buf) cudaFree(W.buf);
+        W.buf = nullptr;
+        W.cap = 0;
+        if ((e = cudaMalloc(&W.buf, wave_bytes(cap))) != cudaSuccess) {
+            W.buf = nullptr;
+            W.m.unlock();
+            return cuda_fail(e, "cudaMalloc hit queue");
+        }
+        W.cap = cap;
+    }
+    if ((e = cudaStreamWaitEvent(st, W.done, 0)) != cudaSuccess) { W.m.unlock(); return cuda_fail(e, "hit queue"); }
+    out->buf = W.buf;
+    out->cap = W.cap;
+    out->device = dev;
     return HEART_OK;
+}
+
+void wave_release(const WaveLease &lease, cudaStream_t st) {
+    DeviceWave &W = g_wave[lease.device];
+    cudaEventRecord(W.done, st);
+    W.m.unlock();
 }
 
 heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
@@ -2110,10 +2148,19 @@ extern "C" heart_status heart_autotune(heart_spectrometer *h, const heart_source
     heart_status st = build_source_params(src, &P, err, (int)sizeof err, &spectrum);
     if (st != HEART_OK) return fail(st, err);
     cudaStream_t cs = (cudaStream_t)stream;
-    if (h->p.n_orders == 1 && h->p.irc != HEART_IRC_NONE) {
-        st = ensure_wave(h, probe_rays);
+    // the two-pass probes use the device's hit queue, held for the whole tuning
+    const bool two_pass = h->p.n_orders == 1 && h->p.irc != HEART_IRC_NONE;
+    WaveLease lease{nullptr, 0u, 0};
+    if (two_pass) {
+        st = wave_acquire(probe_rays, cs, &lease);
         if (st != HEART_OK) return st;
     }
+    struct ReleaseOnExit {
+        bool on;
+        const WaveLease &l;
+        cudaStream_t s;
+        ~ReleaseOnExit() { if (on) wave_release(l, s); }
+    } release_lease{two_pass, lease, cs};
     void *d_spec = nullptr;
     if (!spectrum.empty()) {
         cudaError_t e0 = cudaMallocAsync(&d_spec, spectrum.size(), cs);
@@ -2152,7 +2199,7 @@ extern "C" heart_status heart_autotune(heart_spectrometer *h, const heart_source
             cudaMemsetAsync(h->d_scratch, 0, kScratchWords * sizeof(unsigned long long), cs);
             cudaEventRecord(t0, cs);
             heart_status s2 = launch_fp32(h->p, P, probe_rays, 0x5eed + rep, 0, h->d_image_host_path, h->d_scratch,
-                                          cs, nullptr, persistent ? nullptr : h->d_wave, h->wave_cap);
+                                          cs, nullptr, persistent ? nullptr : lease.buf, lease.cap);
             cudaEventRecord(t1, cs);
             if (s2 != HEART_OK) return s2;
             if ((e = cudaEventSynchronize(t1)) != cudaSuccess) return cuda_fail(e, "autotune probe");

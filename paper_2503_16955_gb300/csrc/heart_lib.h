@@ -48,12 +48,24 @@ struct WaveBuf {
     void *base;
     uint32_t cap, pad;
 };
-// wave / wave_cap: the handle's queue (nullptr: the one-pass persistent kernel)
+// wave / wave_cap: a leased hit queue (nullptr: the one-pass persistent kernel)
 heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
                          void *img, unsigned long long *scratch, cudaStream_t st, const QeParams *qe = nullptr,
                          void *wave = nullptr, uint32_t wave_cap = 0);
-// make sure the handle's queue holds chunks of wave_cap_for(n) rays (grows, never shrinks)
-heart_status ensure_wave(heart_spectrometer *h, uint64_t n);
+// The hit queue of the two-pass FP32 trace: one per device, shared by every
+// spectrometer handle, grown to the largest chunk asked for (never shrunk).
+// wave_acquire locks it for the calling host thread while a trace is enqueued
+// and makes the stream wait (on the GPU) for the queue's previous user;
+// wave_release records the stream's position as the next user's start and
+// unlocks.  Traces that need the queue therefore run one after another on the
+// GPU whatever their streams; everything else stays concurrent.
+struct WaveLease {
+    void *buf;
+    uint32_t cap;
+    int device;
+};
+heart_status wave_acquire(uint64_t n, cudaStream_t st, WaveLease *out);
+void wave_release(const WaveLease &lease, cudaStream_t st);
 heart_status launch_fp32_records(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed,
                                  uint64_t offset, void *img, unsigned long long *scratch, heart_ray_record *rec,
                                  cudaStream_t st, const QeParams *qe = nullptr);
@@ -78,6 +90,4 @@ struct heart_spectrometer {
     unsigned long long *h_scratch = nullptr;   // pinned tally copy
     void *d_image_host_path = nullptr;    // image buffer of heart_trace_host
     size_t host_image_bytes = 0;
-    void *d_wave = nullptr;               // hit queue of the two-pass FP32 trace (on first use)
-    uint32_t wave_cap = 0;                // rays per chunk the queue holds
 };

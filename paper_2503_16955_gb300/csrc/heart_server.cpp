@@ -4,7 +4,9 @@
 // the memory cap; admitted jobs stay resident (tables in their spectrometer
 // handles, images and tallies here) until released.  A worker thread plans
 // rounds: every admitted, unfinished FP32 job gets a slice of its remaining
-// rays, and all slices run in one persistent batched launch.  Jobs that arrive
+// rays; the slices of jobs of 2^22 rays or more that the two-pass trace takes
+// run as single-job two-pass launches, the others together in one persistent
+// batched launch.  Jobs that arrive
 // while a round is on the GPU join the next round, which is enqueued before
 // the previous one has finished (two rounds in flight), so the device never
 // waits for the host.  Each ray keeps its counter-based stream
@@ -74,6 +76,7 @@ struct heart_server {
     std::thread worker;
     uint64_t round_rays = 64ull << 20;       // target rays per round (about 20-40 ms of GPU work)
     uint64_t min_slice = 1ull << 20;
+    uint64_t two_pass_min = 1ull << 22;      // jobs this large run their slices as two-pass launches
 };
 
 namespace heart {
@@ -198,13 +201,37 @@ void worker_main(heart_server *s) {
             }
             r.last = last;
             heart_status st = HEART_OK;
-            if (!slice_jobs.empty()) {
-                const size_t bytes = batch_bytes((int)slice_jobs.size());
+            // Slices of large jobs that the two-pass trace takes (one reflection order, a
+            // rocking curve) run as single-job two-pass launches, which are faster than the
+            // persistent batched kernel; the other slices share one batched launch.  The
+            // choice goes by the job's size, not the slice's, so a job's rays run on the
+            // same kernels however the rounds slice them.
+            std::vector<const SpecParams *> bS;
+            std::vector<SourceParams> bP;
+            std::vector<void *> bimg;
+            std::vector<unsigned long long *> btl;
+            std::vector<uint64_t> bnr, bseed, boff;
+            for (size_t i = 0; i < slice_jobs.size() && st == HEART_OK; ++i) {
+                const SpecParams &sp = *S[i];
+                if (slice_jobs[i]->n >= s->two_pass_min && sp.n_orders == 1 && sp.irc != HEART_IRC_NONE) {
+                    WaveLease lease;
+                    st = wave_acquire(nr[i], s->stream, &lease);
+                    if (st != HEART_OK) break;
+                    st = launch_fp32(sp, P[i], nr[i], seeds[i], offs[i], imgs[i], tl[i], s->stream, nullptr,
+                                     lease.buf, lease.cap);
+                    wave_release(lease, s->stream);
+                } else {
+                    bS.push_back(S[i]); bP.push_back(P[i]); bimg.push_back(imgs[i]); btl.push_back(tl[i]);
+                    bnr.push_back(nr[i]); bseed.push_back(seeds[i]); boff.push_back(offs[i]);
+                }
+            }
+            if (st == HEART_OK && !bS.empty()) {
+                const size_t bytes = batch_bytes((int)bS.size());
                 if (cudaMallocAsync(&r.dev, bytes, s->stream) != cudaSuccess) st = HEART_ENOMEM;
                 unsigned long long *unused = nullptr;
                 if (st == HEART_OK)
-                    st = launch_batch(S.data(), P.data(), nr.data(), seeds.data(), offs.data(), imgs.data(),
-                                      (int)slice_jobs.size(), r.dev, r.host, s->stream, &unused, tl.data());
+                    st = launch_batch(bS.data(), bP.data(), bnr.data(), bseed.data(), boff.data(), bimg.data(),
+                                      (int)bS.size(), r.dev, r.host, s->stream, &unused, btl.data());
             }
             for (Job *j : fp64_jobs) {
                 heart_status s2 = launch_fp64(j->spec->p, j->P, j->n, j->seed, 0, j->d_img, j->d_tally, nullptr,

@@ -173,3 +173,29 @@ def test_two_pass_trace_equals_persistent_kernel_with_invalid_energies(H):
     neg = rec["energy_keV"] < 0                          # entered, then drew a negative energy
     assert neg.sum() > 1000 and np.all(rec["outcome"][neg] == 0)
     assert t2["miss"] > int(neg.sum()) and t2["emitted"] == n
+
+
+def test_shared_hit_queue_across_handles_and_streams(H):
+    # the two-pass trace's hit queue is one per device: traces of different
+    # spectrometers enqueued on two streams at once give the images they give alone
+    import torch
+    wa, wb = W.von_hamos_hapg(), W.flat_hopg_mono()
+    sa, sb = H.heart_spectrometer_create(wa["spec"]), H.heart_spectrometer_create(wb["spec"])
+    na, nb = 3_000_000, 20_000_000
+    alone = []
+    for s, w, n in ((sa, wa, na), (sb, wb, nb)):
+        img = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+        H.heart_trace(s, w["source"], n, 31, 0, img, precision="fp32")
+        alone.append(img)
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    ia = torch.zeros(sa.shape, dtype=torch.int32, device="cuda")
+    ib = torch.zeros(sb.shape, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    H.heart_trace(sa, wa["source"], na, 31, 0, ia, precision="fp32", stream=s1, want_tally=False)
+    H.heart_trace(sb, wb["source"], nb, 31, 0, ib, precision="fp32", stream=s2, want_tally=False)
+    torch.cuda.synchronize()
+    sa.close()
+    sb.close()
+    assert torch.equal(ia, alone[0]) and torch.equal(ib, alone[1])
+    assert int(ia.sum()) > 100 and int(ib.sum()) > 100
