@@ -1966,7 +1966,7 @@ void wave_release(const WaveLease &lease, cudaStream_t st) {
 heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
                          void *img, unsigned long long *scratch, cudaStream_t st, const QeParams *qe, void *wave,
                          uint32_t wave_cap) {
-    if (!wave || n == 0 || S.n_orders > 1 || S.irc == HEART_IRC_NONE)
+    if (!wave || n == 0 || S.n_orders > 1)
         return launch_single(S, P, n, seed, offset, img, scratch, nullptr, st, qe);
     // the two-pass trace: the per-ray work in its own pass, then the walk
     Launch32 L;
@@ -1990,9 +1990,10 @@ heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n,
         if (L.geometry == HEART_FLAT) return launch_wave_t<HEART_FLAT, -1, true, true>(L, B, n, ctr, st);
         return launch_wave_t<HEART_CYL_VON_HAMOS, -1, true, true>(L, B, n, ctr, st);
     }
-    if (P.pol_on) {
+    if (P.pol_on || S.irc == HEART_IRC_NONE) {
         // polarised source: 112-byte records and the walk variant that carries p,
-        // with the rocking curve dispatched at run time (one instantiation per geometry)
+        // with the rocking curve dispatched at run time (one instantiation per
+        // geometry); the walk without rocking curve (cone candidates) runs there too
         if (L.geometry == HEART_FLAT) return launch_wave_t<HEART_FLAT, -1, true>(L, B, n, ctr, st);
         return launch_wave_t<HEART_CYL_VON_HAMOS, -1, true>(L, B, n, ctr, st);
     }
@@ -2149,7 +2150,7 @@ extern "C" heart_status heart_autotune(heart_spectrometer *h, const heart_source
     if (st != HEART_OK) return fail(st, err);
     cudaStream_t cs = (cudaStream_t)stream;
     // the two-pass probes use the device's hit queue, held for the whole tuning
-    const bool two_pass = h->p.n_orders == 1 && h->p.irc != HEART_IRC_NONE;
+    const bool two_pass = h->p.n_orders == 1;
     WaveLease lease{nullptr, 0u, 0};
     if (two_pass) {
         st = wave_acquire(probe_rays, cs, &lease);

@@ -201,8 +201,8 @@ void worker_main(heart_server *s) {
             }
             r.last = last;
             heart_status st = HEART_OK;
-            // Slices of large jobs that the two-pass trace takes (one reflection order, a
-            // rocking curve) run as single-job two-pass launches, which are faster than the
+            // Slices of large jobs that the two-pass trace takes (one reflection order)
+            // run as single-job two-pass launches, which are faster than the
             // persistent batched kernel; the other slices share one batched launch.  The
             // choice goes by the job's size, not the slice's, so a job's rays run on the
             // same kernels however the rounds slice them.
@@ -213,7 +213,7 @@ void worker_main(heart_server *s) {
             std::vector<uint64_t> bnr, bseed, boff;
             for (size_t i = 0; i < slice_jobs.size() && st == HEART_OK; ++i) {
                 const SpecParams &sp = *S[i];
-                if (slice_jobs[i]->n >= s->two_pass_min && sp.n_orders == 1 && sp.irc != HEART_IRC_NONE) {
+                if (slice_jobs[i]->n >= s->two_pass_min && sp.n_orders == 1) {
                     WaveLease lease;
                     st = wave_acquire(nr[i], s->stream, &lease);
                     if (st != HEART_OK) break;
