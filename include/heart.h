@@ -163,8 +163,8 @@ typedef struct {
      * d_spacing_A / order_m[h] with K_h = order_K_rel[h] K and a rocking curve
      * order_w_rel[h] times as wide (same shape and unit area).  A scatter
      * candidate picks its order by the order's share of the candidate rate.
-     * Precision FP32 (heart_trace, batches, FP32 server jobs) takes one order
-     * only and returns HEART_EINVAL otherwise; FP64 takes up to HEART_MAX_ORDERS. */
+     * Both precisions take up to HEART_MAX_ORDERS; FP32 traces with several
+     * orders run on the persistent batched kernel (not the two-pass trace). */
     int32_t n_orders;
     int32_t reserved2;
     int32_t order_m[4];

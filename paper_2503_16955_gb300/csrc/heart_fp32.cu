@@ -61,8 +61,6 @@ struct Launch32 {
     int32_t kind[kMaxComp];
     float e_ref[kMaxComp];                // reference energy of each component
     float width[kMaxComp], half_ln[kMaxComp], lF0[kMaxComp];
-    float sB0[kMaxComp];                  // sin(aB(e_ref) + Delta_M)
-    float A0[kMaxComp];                   // |k.N| - sB0 for k on the cone axis
     float sB_raw[kMaxComp], cB_raw[kMaxComp];   // sin / cos aB(e_ref) without the shift
     // crystal
     float half_d, half_n, thick, R, zc, sphi, cphi;
@@ -111,6 +109,15 @@ struct Launch32 {
     float irc_e[HEART_MAX_IRC_E], irc_ws[HEART_MAX_IRC_E], irc_sh[HEART_MAX_IRC_E];
     float sh_ref[kMaxComp];
     const double *ray[10];                // user arrays: ox oy oz kx ky kz E px py pz
+    // reflection orders (Sec. 2.2.3; order 0 is the one of the fields above): multiple
+    // relative to order 0's, K_h^2, 1 / width ratio, and per order and component
+    // sin(aB_h + Delta_M) at the reference energy and the cone axis's anchor;
+    // xs_on: X* scales with a width ratio or an energy table
+    int32_t n_ord, xs_on;
+    float ord_r[HEART_MAX_ORDERS], ord_k2[HEART_MAX_ORDERS], ord_iw[HEART_MAX_ORDERS];
+    float osB0[HEART_MAX_ORDERS][kMaxComp];   // sin(aB_h(e_ref) + Delta_M)
+    float oA0[HEART_MAX_ORDERS][kMaxComp];    // |k.N| - osB0 for k on the cone axis
+    double ord_rd[HEART_MAX_ORDERS];      // the multiples' ratio in FP64 (user rays)
     // tabulated spectrum: CDF thresholds on the raw word, in-interval offset and
     // slope, knots relative to the table's mean energy (its e_ref)
     int32_t n_tab, pad_tab;
@@ -269,6 +276,14 @@ struct Lane {
     float rho0, cb1, cb2, cga, ck0, ctau0;
     float p[3];                           // polarisation, crystal frame (extended kernel)
     bool pol;
+    // several reflection orders (extended kernel): the fields above hold the order
+    // of the current candidate, h; per order its anchor, sin / cos(aB_h + Delta_M),
+    // rate, inverse width scale, thinning bounds and cumulative share of the rate
+    int32_t h;
+    float oA[HEART_MAX_ORDERS], osB[HEART_MAX_ORDERS], ocB[HEART_MAX_ORDERS], oqr[HEART_MAX_ORDERS];
+    float oiw[HEART_MAX_ORDERS], ora[HEART_MAX_ORDERS], oqmin[HEART_MAX_ORDERS], opbar[HEART_MAX_ORDERS];
+    float ocum[HEART_MAX_ORDERS];
+    uint32_t ow0[HEART_MAX_ORDERS];
 };
 
 // absorption rate mu0 and scatter-candidate rate Q R_max / w of a ray of energy E
@@ -312,6 +327,41 @@ __device__ __forceinline__ void irc_energy32(const Launch32 &L, float E, float &
     const float f = (E - L.irc_e[i]) / (L.irc_e[i + 1] - L.irc_e[i]);
     ws = __fmaf_rn(f, L.irc_ws[i + 1] - L.irc_ws[i], L.irc_ws[i]);
     sh = __fmaf_rn(f, L.irc_sh[i + 1] - L.irc_sh[i], L.irc_sh[i]);
+}
+
+// an energy table's change dM of the peak shift from the reference energy's:
+// sin(a + dM) - sin(a) = c sin dM - 2 s sin^2(dM / 2), by its series
+__device__ __forceinline__ void shift_anchor(float dM, float &sB, float &A) {
+    const float dM2 = dM * dM;
+    const float cs = sqrtf(fmaxf(0.0f, __fmaf_rn(-sB, sB, 1.0f)));
+    const float inc = __fmaf_rn(cs * dM, __fmaf_rn(dM2, -0.166666667f, 1.0f), -0.5f * sB * dM2);
+    sB += inc;
+    A -= inc;
+}
+
+// Order h's anchor and sin(aB_h + Delta_M) for a sampled ray of component c,
+// from the same small quantities as order 0's: sin aB_h = r_h sin aB_0 (Eq.
+// BraggLaw on d / m_h), so the ray's sine offset ds scales by r_h; dA is the
+// entry's |k.N| offset from the cone axis, dM the energy table's change of the
+// shift.  False (sB = 1, A + sB = |k.N|) if the order has no Bragg solution.
+__device__ __forceinline__ bool order_anchor(const Launch32 &L, int c, float ds, float dA, float dM, int h,
+                                             float &A, float &sB) {
+    const float r = L.ord_r[h];
+    const float s0 = L.sB_raw[c] * r, dsh = ds * r, sraw = s0 + dsh;
+    if (!(sraw < 1.0f)) {
+        sB = 1.0f;
+        A = L.oA0[0][c] + L.osB0[0][c] + dA - 1.0f;
+        return false;
+    }
+    const float craw = sqrtf(fmaxf(0.0f, __fmaf_rn(-sraw, sraw, 1.0f)));
+    const float c0 = sqrtf(fmaxf(0.0f, __fmaf_rn(-s0, s0, 1.0f)));
+    const float den = craw + c0;
+    const float dc = den > 0.0f ? -dsh * (sraw + s0) / den : 0.0f;
+    const float dsp = __fmaf_rn(dsh, L.cos_shift[c], dc * L.sin_shift[c]);
+    sB = L.osB0[h][c] + dsp;
+    A = L.oA0[h][c] + dA - dsp;
+    if (L.n_irc_e > 0) shift_anchor(dM, sB, A);
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -384,7 +434,8 @@ __device__ __forceinline__ bool spawn_entry(const Launch32 &L, uint64_t ray, flo
 // energy is not positive and finite (the ray counts as a miss).
 __device__ __forceinline__ bool spawn_energy(const Launch32 &L, uint32_t a0, uint32_t a1, uint32_t b2, uint32_t b3,
                                              float dA, float &A, float &sB, float &mu0, float &qr, float &inv_ws,
-                                             float &E32, int &nb) {
+                                             float &E32, int &nb, float *oA = nullptr, float *osB = nullptr,
+                                             int *nbm = nullptr) {
     int c = L.n_comp - 1;
     for (int i = 0; i < L.n_comp - 1; ++i)
         if (a0 < L.comp_thr[i]) { c = i; break; }
@@ -443,41 +494,45 @@ __device__ __forceinline__ bool spawn_energy(const Launch32 &L, uint32_t a0, uin
         const float craw = sqrtf(fmaxf(0.0f, __fmaf_rn(-sraw, sraw, 1.0f)));
         const float dc = -ds * (sraw + s0) / (craw + L.cB_raw[c]);
         const float dsp = __fmaf_rn(ds, L.cos_shift[c], dc * L.sin_shift[c]);
-        sB = L.sB0[c] + dsp;
-        A = L.A0[c] + dA - dsp;
+        sB = L.osB0[0][c] + dsp;
+        A = L.oA0[0][c] + dA - dsp;
         const float lam = 12.398419843320026e-7f / E;     // mm
         Q = L.K2 * lam * lam * lam / (2.0f * sraw * craw);
     } else {
-        sB = 2.0f;
-        A = 0.0f;
+        // no Bragg solution: sin = 1 keeps A + sB = |k.N| for the segment geometry
+        sB = 1.0f;
+        A = L.oA0[0][c] + L.osB0[0][c] + dA - 1.0f;
     }
-    inv_ws = 1.0f;
+    inv_ws = L.ord_iw[0];
+    float dM = 0.0f;
     if (L.n_irc_e > 0) {
         // energy-dependent curve: width scale, and the shift's small change dM
-        // from the component's reference: sin(a + dM) - sin(a) = c sin dM - 2 s sin^2(dM / 2)
+        // from the component's reference
         float ws, sh;
         irc_energy32(L, E, ws, sh);
-        inv_ws = 1.0f / ws;
-        if (!nb) {
-            const float dM = sh - L.sh_ref[c], dM2 = dM * dM;
-            const float cs = sqrtf(fmaxf(0.0f, __fmaf_rn(-sB, sB, 1.0f)));
-            const float inc = __fmaf_rn(cs * dM, __fmaf_rn(dM2, -0.166666667f, 1.0f), -0.5f * sB * dM2);
-            sB += inc;
-            A -= inc;
-        }
+        inv_ws = L.ord_iw[0] / ws;
+        dM = sh - L.sh_ref[c];
+        if (!nb) shift_anchor(dM, sB, A);
     }
     ray_rates(L, E, Q, nb, inv_ws, sB, mu0, qr);
+    if (oA && L.n_ord > 1) {
+        // the other orders' anchors (their rates follow from E where the ray is walked)
+        int m = nb;
+        for (int h = 1; h < L.n_ord; ++h) m |= (order_anchor(L, c, ds, dA, dM, h, oA[h], osB[h]) ? 0 : 1) << h;
+        *nbm = m;
+    }
     return true;
 }
 
 // a sampled ray: spawn_entry, then spawn_energy for a hit
 template <int GEOM_T>
 __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3], float k[3], float &A,
-                                      float &sB, float &mu0, float &qr, float &inv_ws, float &E32, int &nb) {
+                                      float &sB, float &mu0, float &qr, float &inv_ws, float &E32, int &nb,
+                                      float *oA = nullptr, float *osB = nullptr, int *nbm = nullptr) {
     uint32_t a[4], b[4];
     float dA;
     if (!spawn_entry<GEOM_T>(L, ray, x, k, dA, a, b)) return false;
-    return spawn_energy(L, a[0], a[1], b[2], b[3], dA, A, sB, mu0, qr, inv_ws, E32, nb);
+    return spawn_energy(L, a[0], a[1], b[2], b[3], dA, A, sB, mu0, qr, inv_ws, E32, nb, oA, osB, nbm);
 }
 
 // user-supplied ray: read, move to the crystal frame and enter in FP64 (once
@@ -487,7 +542,7 @@ __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3
 template <int GEOM_T>
 __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float x[3], float k[3], float p[3],
                                            float &A, float &sB, float &mu0, float &qr, float &inv_ws, float &E32,
-                                           int &nb) {
+                                           int &nb, float *oA = nullptr, float *osB = nullptr, int *nbm = nullptr) {
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
     double E = L.ray[6][id], og[3], kg[3], ol[3], kl[3];
     for (int i = 0; i < 3; ++i) { og[i] = L.ray[i][id] - L.fc[i]; kg[i] = L.ray[3 + i][id]; }
@@ -540,11 +595,11 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
     nb = !(sr < 1.0);
     float Q = 0.0f;
     double cs_s = L.cs_shift, sn_s = L.sn_shift;
-    inv_ws = 1.0f;
+    inv_ws = L.ord_iw[0];
     if (L.n_irc_e > 0) {                                  // energy-dependent rocking curve
         float ws, sh;
         irc_energy32(L, (float)E, ws, sh);
-        inv_ws = 1.0f / ws;
+        inv_ws = L.ord_iw[0] / ws;
         sincos(L.shift0 + (double)sh, &sn_s, &cs_s);
     }
     if (!nb) {
@@ -555,10 +610,27 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
         const float lam = 12.398419843320026e-7f / E32;   // mm
         Q = L.K2 * lam * lam * lam / (2.0f * (float)sr * (float)cr);
     } else {
-        sB = 2.0f;
-        A = 0.0f;
+        sB = 1.0f;                                        // no Bragg solution: A + sB = |k.N|
+        A = (float)(kN - 1.0);
     }
     ray_rates(L, E32, Q, nb, inv_ws, sB, mu0, qr);
+    if (oA && L.n_ord > 1) {
+        // the other orders: sin aB_h = r_h sin aB_0, anchors in FP64 as above
+        int m = nb;
+        for (int h = 1; h < L.n_ord; ++h) {
+            const double srh = sr * L.ord_rd[h];
+            if (srh < 1.0) {
+                const double sbh = srh * cs_s + sqrt(1.0 - srh * srh) * sn_s;
+                osB[h] = (float)sbh;
+                oA[h] = (float)(kN - sbh);
+            } else {
+                osB[h] = 1.0f;
+                oA[h] = (float)(kN - 1.0);
+                m |= 1 << h;
+            }
+        }
+        *nbm = m;
+    }
     return true;
 }
 
@@ -579,7 +651,7 @@ __device__ __forceinline__ void project_pol32(const Launch32 &L, const float k[3
 __device__ __forceinline__ void bragg_window(const Launch32 &L, float sB, float cB, float inv_ws, float &e1,
                                              float &e2) {
     float sx = L.sx, hx2 = L.hx2;
-    if (L.n_irc_e > 0) {
+    if (L.xs_on) {
         const float x = L.xstar / inv_ws, x2 = x * x;     // sin x and 2 sin^2(x / 2) by their series
         sx = x * __fmaf_rn(x2, __fmaf_rn(x2, 8.33333333e-3f, -0.166666667f), 1.0f);
         hx2 = 0.5f * x2 * __fmaf_rn(x2, -0.0833333333f, 1.0f);
@@ -653,7 +725,7 @@ __device__ __forceinline__ uint32_t tilt_word32(const Launch32 &L, float qmin) {
 // more than the angular distance), keeps |Delta| >= X*.  Segments with
 // d <= X* keep the plain stream.  |k.N| is taken relative to sin(aB + dM)
 // from the small anchors.
-__device__ __forceinline__ void thin_segment(const Launch32 &L, Lane &s, float A_exit, bool flip) {
+__device__ __forceinline__ float thin_bounds(const Launch32 &L, Lane &s, float A_exit, bool flip) {
     float la = s.qr, lb = 0.0f;
     s.ra = 1.0f;
     if (L.irc_kind == HEART_IRC_NONE) {
@@ -680,7 +752,7 @@ __device__ __forceinline__ void thin_segment(const Launch32 &L, Lane &s, float A
         const float lo = flip ? -s.sB : fminf(s.A, Ae);   // relative to sB; |k.N| passes 0 on a flip
         const float hi = fmaxf(s.A, Ae);
         const float d = lo > 0.0f ? lo : (hi < 0.0f ? -hi : 0.0f);
-        float tmin = d - (L.n_irc_e > 0 ? L.xstar / s.inv_ws : L.xstar);
+        float tmin = d - (L.xs_on ? L.xstar / s.inv_ws : L.xstar);
         if (tmin > 0.0f) {
             tmin = fminf(tmin, 1.57079637f);
             // sin to float precision: a short series below 0.1 rad, the SFU above (far off Bragg)
@@ -703,12 +775,99 @@ __device__ __forceinline__ void thin_segment(const Launch32 &L, Lane &s, float A
             s.ra = la / (la + lb);
         }
     }
-    const float mu = s.mu0 + (la + lb);
+    return la + lb;
+}
+
+// the segment's majorant mu0 + lam: 1 / mu, the absorption share and its word threshold
+__device__ __forceinline__ void set_majorant(Lane &s, float lam) {
+    const float mu = s.mu0 + lam;
     s.inv_mu = 1.0f / mu;
     s.pa = s.mu0 / mu;
     s.inv_1mpa = s.pa < 1.0f ? 1.0f / (1.0f - s.pa) : 0.0f;
     // absorb iff (w + 1/2) 2^-32 < pa  <=>  w < ceil(pa 2^32 - 1/2)
     s.pa_thr = s.pa >= 1.0f ? 0xFFFFFFFFu : __float2uint_ru(fminf(s.pa * 4294967296.0f, 4294967040.0f));
+}
+
+__device__ __forceinline__ void thin_segment(const Launch32 &L, Lane &s, float A_exit, bool flip) {
+    set_majorant(s, thin_bounds(L, s, A_exit, flip));
+}
+
+// Several reflection orders (Sec. 2.2.3: the rate sums over H): every order's
+// anchor moved with the current order's (a reflection, or the walk along a
+// cylinder, changes |k.N| alike for all), each order's bounds on the segment
+// (dex: the change of the anchors to the exit), the cumulative shares of the
+// candidate rate and the majorant mu0 + sum of the orders' rates.
+__device__ __forceinline__ void thin_orders(const Launch32 &L, Lane &s, float dex, bool flip) {
+    const float dA = s.A - s.oA[s.h];
+    float lam = 0.0f;
+    for (int g = 0; g < L.n_ord; ++g) {
+        const float Ag = g == s.h ? s.A : s.oA[g] + dA;
+        s.oA[g] = Ag;
+        s.A = Ag;
+        s.sB = s.osB[g];
+        s.cB = s.ocB[g];
+        s.qr = s.oqr[g];
+        s.inv_ws = s.oiw[g];
+        lam += thin_bounds(L, s, Ag + dex, flip);
+        s.ora[g] = s.ra;
+        s.oqmin[g] = s.qmin;
+        s.opbar[g] = s.pbar;
+        s.ow0[g] = s.w0;
+        s.ocum[g] = lam;
+    }
+    for (int g = 0; g < L.n_ord; ++g) s.ocum[g] = lam > 0.0f ? s.ocum[g] / lam : 1.0f;
+    s.ocum[L.n_ord - 1] = 1.0f;
+    s.h = L.n_ord - 1;                                        // the fields hold the last order's values
+    set_majorant(s, lam);
+}
+
+// the current candidate's order (the extended kernel with several orders)
+__device__ __forceinline__ void load_order(Lane &s, int h) {
+    s.h = h;
+    s.A = s.oA[h];
+    s.sB = s.osB[h];
+    s.cB = s.ocB[h];
+    s.qr = s.oqr[h];
+    s.inv_ws = s.oiw[h];
+    s.ra = s.ora[h];
+    s.qmin = s.oqmin[h];
+    s.pbar = s.opbar[h];
+    s.w0 = s.ow0[h];
+}
+
+// A ray with several orders as a lane takes it: every order's anchor and sine
+// (oa, os), cosine, inverse width scale and rate at the ray's energy (sin aB_h
+// = r_h sin aB_0 only sets Q_h here, so FP32 rounding of E is harmless); nbm
+// marks the orders without a Bragg solution.  The fields hold order 0.
+__device__ __forceinline__ void start_orders(const Launch32 &L, Lane &s, const float oa[HEART_MAX_ORDERS],
+                                             const float os[HEART_MAX_ORDERS], int nbm) {
+    float ws = 1.0f, sh = 0.0f;
+    if (L.n_irc_e > 0) irc_energy32(L, s.E, ws, sh);
+    const float iws = 1.0f / ws;
+    const float lam = 12.398419843320026e-7f / s.E;         // mm
+    const float s1 = (float)L.hc_2d / s.E;                  // sin aB of order 0
+    float mu0;
+    for (int h = 0; h < L.n_ord; ++h) {
+        const int nb = (nbm >> h) & 1;
+        s.oA[h] = oa[h];
+        s.osB[h] = os[h];
+        s.ocB[h] = sqrtf(fmaxf(0.0f, __fmaf_rn(-os[h], os[h], 1.0f)));
+        s.oiw[h] = L.ord_iw[h] * iws;
+        float Q = 0.0f;
+        if (!nb) {
+            const float sr = fminf(s1 * L.ord_r[h], 1.0f);
+            const float cr = sqrtf(fmaxf(0.0f, __fmaf_rn(-sr, sr, 1.0f)));
+            Q = cr > 0.0f ? L.ord_k2[h] * lam * lam * lam / (2.0f * sr * cr) : 0.0f;
+        }
+        ray_rates(L, s.E, Q, nb, s.oiw[h], os[h], mu0, s.oqr[h]);
+    }
+    s.no_bragg = nbm == (1 << L.n_ord) - 1;
+    s.h = 0;
+    s.A = s.oA[0];
+    s.sB = s.osB[0];
+    s.cB = s.ocB[0];
+    s.qr = s.oqr[0];
+    s.inv_ws = s.oiw[0];
 }
 
 // start a straight segment at x0 along k; s.A, s.sgn, s.sB and (cylinder) s.rho0 are set
@@ -733,7 +892,7 @@ __device__ __forceinline__ void segment_consts(const Launch32 &L, Lane &s) {
     }
 }
 
-template <int GEOM_T>
+template <int GEOM_T, bool ORD = false>
 __device__ __forceinline__ void segment(const Launch32 &L, Lane &s) {
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
     segment_consts<GEOM_T>(L, s);
@@ -790,7 +949,8 @@ __device__ __forceinline__ void segment(const Launch32 &L, Lane &s) {
         A_exit = __fmaf_rn(s.sgn, dk, s.A);
         flip = s.sB + A_exit < 0.0f;
     }
-    thin_segment(L, s, A_exit, flip);
+    if (ORD && L.n_ord > 1) thin_orders(L, s, A_exit - s.A, flip);
+    else thin_segment(L, s, A_exit, flip);
 }
 
 __device__ __forceinline__ void to_global(const Launch32 &L, const float *p, double *g, bool point) {
@@ -906,7 +1066,7 @@ __device__ __forceinline__ void crystallite_normal(const Launch32 &L, const Lane
 // sin g = |kN|.  On the cone facing the ray (sg = sign kN) q0 comes from the
 // anchor Ac = |kN| - sin a~0 without cancellation:
 //   q0 = Ac^2 (c0 + s0 (2 s0 + Ac) / (c0 + c)) / (c0 + c).
-template <int GEOM_T, bool EXT>
+template <int GEOM_T, bool EXT, bool ORD>
 __device__ __forceinline__ int cone_step(const Launch32 &L, Lane &s, uint32_t w2, uint32_t w3, float v, float Ac,
                                          float kN, float kt2, float eps, float rho) {
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
@@ -986,11 +1146,12 @@ __device__ __forceinline__ int cone_step(const Launch32 &L, Lane &s, uint32_t w2
     } else {
         s.A = T - s0;
     }
-    segment<GEOM_T>(L, s);
+    segment<GEOM_T, ORD>(L, s);
     return -1;
 }
 
-template <int GEOM_T, int IRC, bool EXT>
+// ORD (the persistent extended kernel only): several reflection orders
+template <int GEOM_T, int IRC, bool EXT, bool ORD = false>
 __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab) {
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
     if (s.ncoll >= L.max_coll) return HEART_STUCK;
@@ -1006,6 +1167,15 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
     ++s.ncoll;
     if (w[1] < s.pa_thr) return HEART_ABSORBED;
     float v = (u01_32(w[1]) - s.pa) * s.inv_1mpa;
+    if (ORD && L.n_ord > 1) {
+        // the reflection order by its share of the candidate rate (sum over H); the
+        // conditional uniform stays the acceptance uniform
+        int h = 0;
+        while (h < L.n_ord - 1 && !(v < s.ocum[h])) ++h;
+        const float c0 = h > 0 ? s.ocum[h - 1] : 0.0f;
+        v = (v - c0) / (s.ocum[h] - c0);
+        load_order(s, h);
+    }
     // k.t2 and k.N at the collision point (cylinder: from the along-segment length)
     float dk = 0.0f, eps = 0.0f, rho = 1.0f, kt2, kN;
     if (GEOM == HEART_FLAT) {
@@ -1021,7 +1191,7 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
         kN = s.ck0 + dk;
     }
     const float Ac = __fmaf_rn(s.sgn, dk, s.A);               // anchor at the collision point
-    if ((IRC >= 0 ? IRC : L.irc_kind) == HEART_IRC_NONE) return cone_step<GEOM_T, EXT>(L, s, w[2], w[3], v, Ac, kN, kt2, eps, rho);
+    if ((IRC >= 0 ? IRC : L.irc_kind) == HEART_IRC_NONE) return cone_step<GEOM_T, EXT, ORD>(L, s, w[2], w[3], v, Ac, kN, kt2, eps, rho);
     // the candidate's stream: (a), or the plain stream, takes the table word over
     // its full range, (b) maps it onto [w0, 2^32); one table lookup for both
     // (a warp almost always holds candidates of both streams)
@@ -1126,7 +1296,7 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
         } else {
             s.A = T - s.sB;
         }
-        segment<GEOM_T>(L, s);
+        segment<GEOM_T, ORD>(L, s);
     }
     return -1;
 }
@@ -1219,14 +1389,17 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                     const unsigned long long id = base + lane;
                     float x[3], k[3], A = 0.f, sB = 0.f, mu0 = 0.f, qr = 0.f, inv_ws = 1.f, E32 = 0.f;
                     float pv[3] = {0.f, 0.f, 0.f};
-                    int nb = 0;
+                    float oA[HEART_MAX_ORDERS] = {0.f, 0.f, 0.f, 0.f}, osB[HEART_MAX_ORDERS] = {0.f, 0.f, 0.f, 0.f};
+                    int nb = 0, nbm = 0;
                     bool hit = false;
                     if (id < end) {
                         ++my_emit;
                         if (EXT && L.user) {
-                            hit = spawn_user<GEOM>(L, id, x, k, pv, A, sB, mu0, qr, inv_ws, E32, nb);
+                            hit = spawn_user<GEOM>(L, id, x, k, pv, A, sB, mu0, qr, inv_ws, E32, nb,
+                                                   EXT ? oA : nullptr, EXT ? osB : nullptr, EXT ? &nbm : nullptr);
                         } else {
-                            hit = spawn<GEOM>(L, L.offset + id, x, k, A, sB, mu0, qr, inv_ws, E32, nb);
+                            hit = spawn<GEOM>(L, L.offset + id, x, k, A, sB, mu0, qr, inv_ws, E32, nb,
+                                              EXT ? oA : nullptr, EXT ? osB : nullptr, EXT ? &nbm : nullptr);
                             if (EXT && L.pol_on) project_pol32(L, k, pv);
                         }
                         if (!hit) {
@@ -1245,7 +1418,27 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                         }
                     }
                     const unsigned hm = __ballot_sync(0xffffffffu, hit);
-                    if (hit) {
+                    if (hit && EXT && L.n_ord > 1) {
+                        // several orders: the buffer's segment fields carry the anchors and
+                        // sines of orders 1-3 and the no-Bragg mask; the walking lane
+                        // prepares the entry segment of all orders when it pops the ray
+                        const int slot = B.count + __popc(hm & lt_mask);
+                        for (int i = 0; i < 3; ++i) { B.x[i][slot] = x[i]; B.k[i][slot] = k[i]; Bp[i][slot] = pv[i]; }
+                        const uint64_t ray = L.offset + id;
+                        B.A[slot] = A;
+                        B.sB[slot] = sB;
+                        B.rl[slot] = (uint32_t)ray;
+                        B.rh[slot] = (uint32_t)(ray >> 32);
+                        B.mu0[slot] = mu0;
+                        B.E[slot] = E32;
+                        B.s_exit[slot] = oA[1];
+                        B.inv_mu[slot] = osB[1];
+                        B.pa[slot] = oA[2];
+                        B.ra[slot] = osB[2];
+                        B.qmin[slot] = oA[3];
+                        B.pbar[slot] = osB[3];
+                        B.face[slot] = nbm;
+                    } else if (hit) {
                         // the entry segment: exit face and distance, majorant and thinning bounds
                         Lane t;
                         for (int i = 0; i < 3; ++i) { t.x0[i] = x[i]; t.k[i] = k[i]; }
@@ -1321,7 +1514,14 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                         for (int i = 0; i < 3; ++i) s.p[i] = Bp[i][slot];
                         s.pol = s.p[0] != 0.0f || s.p[1] != 0.0f || s.p[2] != 0.0f;
                     }
-                    segment_consts<GEOM>(L, s);               // the rest of the entry segment was prepared
+                    if (EXT && L.n_ord > 1) {
+                        const float oa[4] = {s.A, B.s_exit[slot], B.pa[slot], B.qmin[slot]};
+                        const float os[4] = {s.sB, B.inv_mu[slot], B.ra[slot], B.pbar[slot]};
+                        start_orders(L, s, oa, os, B.face[slot]);
+                        segment<GEOM, true>(L, s);            // the entry segment of every order
+                    } else {
+                        segment_consts<GEOM>(L, s);           // the rest of the entry segment was prepared
+                    }
                     alive = true;
                 }
                 __syncwarp();
@@ -1329,7 +1529,7 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                 __syncwarp();
             }
             if (alive) {
-                const int oc = step<GEOM, IRC, EXT>(L, s, s_tab);
+                const int oc = step<GEOM, IRC, EXT, EXT>(L, s, s_tab);
                 if (oc >= 0) {
                     my_coll += (unsigned long long)s.ncoll;
                     finish<REC, EXT>(L, s, oc, bt);
@@ -1641,6 +1841,18 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
         L.irc_sh[i] = (float)S.irc_sh[i];
     }
     L.shift0 = S.irc_shift;
+    // reflection orders: order 0's multiple, K ratio and width ratio enter the
+    // single-order fields (sin aB on d / m_0, K_0, widths w_0 times the described)
+    const double m0 = (double)S.ord_m[0];
+    L.n_ord = S.n_orders;
+    L.xs_on = S.n_irc_e > 0;
+    for (int h = 0; h < S.n_orders; ++h) {
+        L.ord_r[h] = (float)(S.ord_m[h] / m0);
+        L.ord_rd[h] = S.ord_m[h] / m0;
+        L.ord_k2[h] = (float)(S.K * S.ord_k[h] * S.K * S.ord_k[h]);
+        L.ord_iw[h] = (float)(1.0 / S.ord_w[h]);
+        if (S.ord_w[h] != 1.0) L.xs_on = 1;
+    }
     L.n_comp = P.n_comp;
     for (int i = 0; i < P.n_comp; ++i) {
         // first word w with (w + 1/2) 2^-32 >= cumw
@@ -1663,7 +1875,7 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
         }
         L.e_ref[i] = (float)e_ref;
         L.lF0[i] = (float)P.lorentz_F0[i];
-        const double s0 = 12.398419843320026 / (2.0 * S.d_A * e_ref);
+        const double s0 = m0 * 12.398419843320026 / (2.0 * S.d_A * e_ref);
         L.sB_raw[i] = (float)s0;
         const double c0 = s0 < 1.0 ? std::sqrt(1.0 - s0 * s0) : 0.0;
         L.cB_raw[i] = (float)c0;
@@ -1675,11 +1887,15 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
         const double sni = S.n_irc_e > 0 ? std::sin(S.irc_shift + sh_ref) : sn;
         L.cos_shift[i] = (float)csi;
         L.sin_shift[i] = (float)sni;
-        const double sBs = s0 < 1.0 ? s0 * csi + c0 * sni : s0;    // sin(aB + Delta_M)
-        L.sB0[i] = (float)sBs;
-        // anchor of the cone-axis ray: |a_n| (flat) or the axis sine (cylinder), minus sB
+        // sin(aB + Delta_M) and the anchor of the cone-axis ray, |a_n| (flat) or the
+        // axis sine (cylinder) minus that sine, for every order (order 0 first)
         const double kref = S.geometry == HEART_FLAT ? std::fabs(a_n) : axis_sine;
-        L.A0[i] = (float)(kref - sBs);
+        for (int h = 0; h < S.n_orders; ++h) {
+            const double sh0 = s0 * (S.ord_m[h] / m0), ch0 = sh0 < 1.0 ? std::sqrt(1.0 - sh0 * sh0) : 0.0;
+            const double sBh = sh0 * csi + ch0 * sni;
+            L.osB0[h][i] = (float)sBh;
+            L.oA0[h][i] = (float)(kref - sBh);
+        }
     }
     L.half_d = (float)S.half_d;
     L.half_n = (float)S.half_n;
@@ -1712,7 +1928,7 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
     L.labs = (float)S.labs;
     L.labs_ref = (float)S.labs_ref;
     L.labs_pow = (float)S.labs_pow;
-    L.K2 = (float)(S.K * S.K);
+    L.K2 = (float)(S.K * S.ord_k[0] * S.K * S.ord_k[0]);
     L.irc_max = (float)S.irc_max;
     L.mdf = S.mdf;
     L.none_fac = (float)S.none_fac;
@@ -1773,7 +1989,7 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
         to_local(S, P.pol, pl, false);
         for (int i = 0; i < 3; ++i) L.pol[i] = (float)pl[i];
     }
-    L.hc_2d = 12.398419843320026 / (2.0 * S.d_A);
+    L.hc_2d = m0 * 12.398419843320026 / (2.0 * S.d_A);       // sin aB of order 0 times E
     L.cs_shift = cs;
     L.sn_shift = sn;
     for (int i = 0; i < 10; ++i) L.ray[i] = P.ray[i];
@@ -1862,7 +2078,6 @@ static heart_status launch_single(const SpecParams &S, const SourceParams &P, ui
                                   uint64_t offset, void *img, unsigned long long *scratch, heart_ray_record *rec,
                                   cudaStream_t st, const QeParams *qe) {
     if (n == 0) return HEART_OK;
-    if (S.n_orders > 1) return fail(HEART_EINVAL, "higher reflection orders need precision FP64");
     Launch32 L;
     make_launch32(S, P, n, seed, offset, L);
     L.img = img;
@@ -1879,7 +2094,7 @@ static heart_status launch_single(const SpecParams &S, const SourceParams &P, ui
     W.chunk_rays = chunk_for(n);
     W.n_chunks = (n + W.chunk_rays - 1) / W.chunk_rays;
     W.counter = scratch + kCounterWord;
-    const bool ext = L.pol_on || L.user;
+    const bool ext = L.pol_on || L.user || L.n_ord > 1;
     return rec ? dispatch<true>(L, W, st, false, ext) : dispatch<false>(L, W, st, false, ext);
 }
 
@@ -2049,9 +2264,8 @@ heart_status launch_batch(const SpecParams *const *S, const SourceParams *P, con
     uint64_t all_rays = 0;
     bool ext = false;
     for (int i = 0; i < n; ++i) {
-        if (S[i]->n_orders > 1) return fail(HEART_EINVAL, "higher reflection orders need precision FP64");
         all_rays += n_rays[i];
-        ext |= P[i].pol_on || P[i].user;
+        ext |= P[i].pol_on || P[i].user || S[i]->n_orders > 1;
     }
     const uint32_t chunk = chunk_for(all_rays);
     unsigned long long nch = 0;
@@ -2302,7 +2516,6 @@ extern "C" heart_status heart_trace_batch_static(heart_spectrometer *const *spec
         if (!specs[i]) return fail(HEART_EINVAL, "null spectrometer in batch");
         const size_t elt = specs[i]->p.count_type == HEART_COUNT_I64 ? 8 : 4;
         if (!d_images[i] || ((uintptr_t)d_images[i] % elt) != 0) return fail(HEART_EINVAL, "null or misaligned image in batch");
-        if (specs[i]->p.n_orders > 1) return fail(HEART_EINVAL, "higher reflection orders need precision FP64");
         heart_status st = build_source_params(srcs[i], &g_static_src[i], err, (int)sizeof err);
         if (st != HEART_OK) return fail(st, err);
     }
@@ -2315,7 +2528,7 @@ extern "C" heart_status heart_trace_batch_static(heart_spectrometer *const *spec
     unsigned long long nch = 0;
     bool ext = false;
     for (int i = 0; i < n_jobs; ++i) {
-        ext |= g_static_src[i].pol_on != 0;
+        ext |= g_static_src[i].pol_on != 0 || specs[i]->p.n_orders > 1;
         make_launch32(specs[i]->p, g_static_src[i], n_rays[i], seeds[i], 0, jobs[i]);
         jobs[i].img = d_images[i];
         jobs[i].tally = d_tallies + (size_t)i * kTallyN;

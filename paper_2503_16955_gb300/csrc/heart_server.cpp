@@ -303,8 +303,6 @@ extern "C" heart_status heart_submit(heart_server *s, heart_spectrometer *spec, 
                                      uint64_t n_rays, uint64_t seed, heart_precision precision, uint64_t *job_id) {
     if (!s || !spec || !job_id) return fail(HEART_EINVAL, "null argument");
     if (precision != HEART_FP32 && precision != HEART_FP64) return fail(HEART_EINVAL, "unknown precision");
-    if (precision == HEART_FP32 && spec->p.n_orders > 1)
-        return fail(HEART_EINVAL, "higher reflection orders need precision FP64");
     Job *j = new (std::nothrow) Job();
     if (!j) return fail(HEART_ENOMEM, "host allocation failed");
     char err[256] = {0};
