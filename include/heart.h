@@ -312,10 +312,14 @@ heart_status heart_trace_records(heart_spectrometer *spec, const heart_source_de
                                  void *d_image, heart_precision precision, void *d_records,
                                  void *stream, heart_tally *out);
 
-/* Many spectrometers of uneven ray counts in one persistent FP32 launch
- * (work items = (job, ray range) claimed by blocks).  specs[i], srcs[i],
- * n_rays[i], seeds[i], d_images[i] describe job i; out (may be NULL) receives
- * n_jobs tallies after a stream synchronisation. */
+/* Many spectrometers of uneven ray counts, FP32, on `stream`.  Jobs of fewer
+ * than 2^22 rays (and jobs of several reflection orders) share one persistent
+ * launch (work items = (job, ray range) claimed by blocks); larger jobs run as
+ * single-job two-pass traces, as heart_trace runs them, so a large job's image
+ * and tallies equal its single trace.  specs[i], srcs[i], n_rays[i], seeds[i],
+ * d_images[i] describe job i; out (may be NULL) receives n_jobs tallies after a
+ * stream synchronisation.  Allocates a small per-call work area, and the
+ * device's hit queue for the two-pass trace if it is not large enough yet. */
 heart_status heart_trace_batch(heart_spectrometer *const *specs, const heart_source_desc *const *srcs,
                                const uint64_t *n_rays, const uint64_t *seeds, void *const *d_images,
                                int32_t n_jobs, void *stream, heart_tally *out);
@@ -354,7 +358,10 @@ heart_status heart_autotune(heart_spectrometer *spec, const heart_source_desc *s
  * that the library declares at file scope, sized for HEART_STATIC_MAX_JOBS
  * jobs, and allocates nothing on the device.  The caller still passes the
  * spectrometers (created beforehand), sources and device images, exactly as
- * for heart_trace_batch, and gets the same images and tallies.
+ * for heart_trace_batch, and gets the same images and tallies for jobs below
+ * 2^22 rays.  Every job runs on the persistent kernel here (the two-pass trace
+ * needs the hit queue), which for larger jobs follows heart_trace_batch's
+ * two-pass trace up to rare rounding-level decision flips (<= 1e-4 of rays).
  *   - n_jobs > HEART_STATIC_MAX_JOBS returns HEART_EINVAL with a message.
  *   - Every GPU that loads the library holds the array until the process exits.
  *   - All calls share the array; each call rewrites it (tallies and the work

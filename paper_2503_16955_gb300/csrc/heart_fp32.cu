@@ -2325,14 +2325,66 @@ extern "C" heart_status heart_trace_batch(heart_spectrometer *const *specs, cons
         S[i] = &specs[i]->p;
     }
     cudaStream_t cs = (cudaStream_t)stream;
-    void *dev = nullptr;
-    const size_t bytes = batch_bytes(n_jobs) + spectra_bytes(spectra.data(), n_jobs);
-    cudaError_t e = cudaMallocAsync(&dev, bytes, cs);
+    // Jobs of kTwoPassMinRays rays or more that the two-pass trace takes (one
+    // reflection order) run as single-job two-pass launches, as single traces and
+    // the request loop run them; the others share one persistent launch.
+    std::vector<int> big, small;
+    for (int i = 0; i < n_jobs; ++i)
+        (n_rays[i] >= kTwoPassMinRays && S[i]->n_orders == 1 ? big : small).push_back(i);
+    // device block: [tallies x n_jobs][big jobs' spectra][the persistent launch's block]
+    const size_t tall_bytes = ((size_t)n_jobs * kTallyN * 8 + 15) & ~(size_t)15;
+    size_t big_sp = 0;
+    uint64_t big_max = 0;
+    for (int i : big) {
+        big_sp += (spectra[i].size() + 15) & ~(size_t)15;
+        big_max = n_rays[i] > big_max ? n_rays[i] : big_max;
+    }
+    const int ns = (int)small.size();
+    std::vector<const SpecParams *> sS;
+    std::vector<SourceParams> sP;
+    std::vector<std::vector<unsigned char>> sSp;
+    std::vector<uint64_t> sN, sSeed;
+    std::vector<void *> sImg;
+    for (int i : small) {
+        sS.push_back(S[i]); sP.push_back(P[i]); sSp.push_back(spectra[i]);
+        sN.push_back(n_rays[i]); sSeed.push_back(seeds[i]); sImg.push_back(d_images[i]);
+    }
+    const size_t bytes = tall_bytes + big_sp + (ns ? batch_bytes(ns) + spectra_bytes(sSp.data(), ns) : 0);
+    unsigned char *dev = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&dev, bytes, cs);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync batch");
+    unsigned long long *tall = (unsigned long long *)dev;
+    heart_status st = HEART_OK;
+    e = cudaMemsetAsync(tall, 0, tall_bytes, cs);
+    if (e != cudaSuccess) st = cuda_fail(e, "batch tallies");
+    if (st == HEART_OK && !big.empty()) {
+        WaveLease lease{nullptr, 0u, 0};
+        st = wave_acquire(big_max, cs, &lease);
+        const bool held = st == HEART_OK;
+        size_t off = tall_bytes;
+        for (size_t b = 0; st == HEART_OK && b < big.size(); ++b) {
+            const int i = big[b];
+            SourceParams Pi = P[i];
+            if (!spectra[i].empty()) {
+                // pageable source: staged before the call returns
+                e = cudaMemcpyAsync(dev + off, spectra[i].data(), spectra[i].size(), cudaMemcpyHostToDevice, cs);
+                if (e != cudaSuccess) { st = cuda_fail(e, "spectrum upload"); break; }
+                bind_spectrum(&Pi, dev + off);
+                off += (spectra[i].size() + 15) & ~(size_t)15;
+            }
+            st = launch_fp32(*S[i], Pi, n_rays[i], seeds[i], 0, d_images[i], tall + (size_t)i * kTallyN, cs, nullptr,
+                             lease.buf, lease.cap);
+        }
+        if (held) wave_release(lease, cs);
+    }
     std::vector<unsigned char> host;
-    unsigned long long *tall = nullptr;
-    heart_status st = launch_batch(S.data(), P.data(), n_rays, seeds, nullptr, d_images, n_jobs, dev, host, cs, &tall,
-                                   nullptr, spectra.data());
+    if (st == HEART_OK && ns) {
+        std::vector<unsigned long long *> tptr;
+        for (int i : small) tptr.push_back(tall + (size_t)i * kTallyN);
+        unsigned long long *unused = nullptr;
+        st = launch_batch(sS.data(), sP.data(), sN.data(), sSeed.data(), nullptr, sImg.data(), ns,
+                          dev + tall_bytes + big_sp, host, cs, &unused, tptr.data(), sSp.data());
+    }
     if (st == HEART_OK && out) {
         std::vector<unsigned long long> h((size_t)n_jobs * kTallyN);
         e = cudaMemcpyAsync(h.data(), tall, h.size() * 8, cudaMemcpyDeviceToHost, cs);

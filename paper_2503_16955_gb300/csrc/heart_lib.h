@@ -36,6 +36,9 @@ heart_status launch_fp64(const SpecParams &S, const SourceParams &P, uint64_t n,
 // polarised source), then 2 counters per chunk for kWaveGroup chunks
 constexpr uint32_t kWaveMinCap = 1u << 20, kWaveMaxCap = 1u << 24;
 constexpr int kWaveGroup = 1024;
+// jobs of at least this many rays (one reflection order) run on the two-pass
+// trace in batches and in the request loop, as single traces do
+constexpr uint64_t kTwoPassMinRays = 1ull << 22;
 constexpr int kWaveRec16 = 6;                  // 16-byte words per queued hit (a 96-byte record)
 constexpr int kWaveRecMax16 = 7;               // with the polarisation word
 inline size_t wave_bytes(uint32_t cap) { return (size_t)16 * kWaveRecMax16 * cap + (size_t)2 * 8 * kWaveGroup; }

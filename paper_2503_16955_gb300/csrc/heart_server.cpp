@@ -76,7 +76,7 @@ struct heart_server {
     std::thread worker;
     uint64_t round_rays = 64ull << 20;       // target rays per round (about 20-40 ms of GPU work)
     uint64_t min_slice = 1ull << 20;
-    uint64_t two_pass_min = 1ull << 22;      // jobs this large run their slices as two-pass launches
+    uint64_t two_pass_min = heart::kTwoPassMinRays;   // jobs this large run their slices as two-pass launches
 };
 
 namespace heart {

@@ -63,6 +63,34 @@ def test_batch_alone_equals_mixed_and_matches_single_launches(H):
         s.close()
 
 
+def test_batch_large_jobs_equal_their_single_traces(H):
+    # jobs of 2^22 rays or more run as two-pass traces inside the batch: image and
+    # tallies equal to heart_trace of the same job; the small jobs in the same call
+    # still equal the batch of themselves alone
+    import torch
+    jobs = _mix(4, 55, (1e4, 2e5))
+    jobs[1]["n_rays"] = 5_000_000
+    jobs[2]["n_rays"] = 1 << 22
+    specs = [H.heart_spectrometer_create(j["spec"]) for j in jobs]
+    imgs = [_img(H, s, torch) for s in specs]
+    tall = H.heart_trace_batch(specs, [j["source"] for j in jobs], [j["n_rays"] for j in jobs],
+                               [j["seed"] for j in jobs], imgs)
+    for i in (1, 2):
+        single = _img(H, specs[i], torch)
+        t1 = H.heart_trace(specs[i], jobs[i]["source"], jobs[i]["n_rays"], jobs[i]["seed"], 0, single)
+        assert torch.equal(single, imgs[i]), i
+        assert t1 == tall[i], i
+        assert tall[i]["emitted"] == jobs[i]["n_rays"]
+    small = [0, 3]
+    sim = [_img(H, specs[i], torch) for i in small]
+    ts = H.heart_trace_batch([specs[i] for i in small], [jobs[i]["source"] for i in small],
+                             [jobs[i]["n_rays"] for i in small], [jobs[i]["seed"] for i in small], sim)
+    for k, i in enumerate(small):
+        assert torch.equal(sim[k], imgs[i]) and ts[k] == tall[i], i
+    for s in specs:
+        s.close()
+
+
 def test_server_results_identical_alone_and_in_the_mix(H):
     import torch
     jobs = _mix(10, 44, (5e4, 2e6))
