@@ -90,6 +90,8 @@ struct Launch32 {
     int32_t n_qe, pad_qe;
     float qe_e[kMaxQe], qe_v[kMaxQe];     // detector QE knots
     double fc[3], fa[3][3];               // local -> global frame (records, user rays)
+    float faf[3][3];                      // the same rotation in FP32 (user rays' polarisation)
+    double inv_Rd;                        // 1 / R (cylinder) in FP64
     // thinned candidates: sampler, v*, X* and the window constants
     // 2 sin^2(X*/2), sin X* (the |k.n| window of |Delta| < X* from sin(aB + dM))
     int32_t sampler;
@@ -544,11 +546,18 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
                                            float &A, float &sB, float &mu0, float &qr, float &inv_ws, float &E32,
                                            int &nb, float *oA = nullptr, float *osB = nullptr, int *nbm = nullptr) {
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
+    // FP64 only where the anchor needs it (GB300's FP64 rate bounds this path):
+    // the direction, the entry point and sin(aB + Delta_M); one reciprocal square
+    // root normalises k
     double E = L.ray[6][id], og[3], kg[3], ol[3], kl[3];
     for (int i = 0; i < 3; ++i) { og[i] = L.ray[i][id] - L.fc[i]; kg[i] = L.ray[3 + i][id]; }
-    const double kk = sqrt(kg[0] * kg[0] + kg[1] * kg[1] + kg[2] * kg[2]);
-    if (kk > 0.0) for (int i = 0; i < 3; ++i) kg[i] /= kk;
-    else E = __longlong_as_double(0x7ff8000000000000LL);      // a zero direction cannot enter
+    const double kk = kg[0] * kg[0] + kg[1] * kg[1] + kg[2] * kg[2];
+    if (kk > 0.0) {
+        const double ik = rsqrt(kk);
+        for (int i = 0; i < 3; ++i) kg[i] *= ik;
+    } else {
+        E = __longlong_as_double(0x7ff8000000000000LL);      // a zero direction cannot enter
+    }
     for (int i = 0; i < 3; ++i) {
         ol[i] = og[0] * L.fa[i][0] + og[1] * L.fa[i][1] + og[2] * L.fa[i][2];
         kl[i] = kg[0] * L.fa[i][0] + kg[1] * L.fa[i][1] + kg[2] * L.fa[i][2];
@@ -557,13 +566,27 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
         p[i] = 0.0f;
     }
     if (L.pol_on) {
-        double pg[3] = {L.ray[7][id], L.ray[8][id], L.ray[9][id]};
-        const double pk = pg[0] * kg[0] + pg[1] * kg[1] + pg[2] * kg[2];
-        for (int i = 0; i < 3; ++i) pg[i] -= pk * kg[i];
-        const double pn = sqrt(pg[0] * pg[0] + pg[1] * pg[1] + pg[2] * pg[2]);
-        if (pn > 1e-12)
+        // projection perpendicular to k in FP32 (G needs ~1e-7), in FP64 when p is
+        // within 1e-3 of parallel to k; unpolarised below 1e-12 as in the FP64 kernel
+        float pf[3] = {(float)L.ray[7][id], (float)L.ray[8][id], (float)L.ray[9][id]};
+        const float kf[3] = {(float)kg[0], (float)kg[1], (float)kg[2]};
+        const float pp = __fmaf_rn(pf[0], pf[0], __fmaf_rn(pf[1], pf[1], pf[2] * pf[2]));
+        const float pk = __fmaf_rn(pf[0], kf[0], __fmaf_rn(pf[1], kf[1], pf[2] * kf[2]));
+        for (int i = 0; i < 3; ++i) pf[i] = __fmaf_rn(-pk, kf[i], pf[i]);
+        const float pn2 = __fmaf_rn(pf[0], pf[0], __fmaf_rn(pf[1], pf[1], pf[2] * pf[2]));
+        if (pn2 > 1e-6f * pp) {
+            const float ipn = rsqrtf(pn2);
             for (int i = 0; i < 3; ++i)
-                p[i] = (float)((pg[0] * L.fa[i][0] + pg[1] * L.fa[i][1] + pg[2] * L.fa[i][2]) / pn);
+                p[i] = (pf[0] * L.faf[i][0] + pf[1] * L.faf[i][1] + pf[2] * L.faf[i][2]) * ipn;
+        } else {
+            double pg[3] = {L.ray[7][id], L.ray[8][id], L.ray[9][id]};
+            const double pkd = pg[0] * kg[0] + pg[1] * kg[1] + pg[2] * kg[2];
+            for (int i = 0; i < 3; ++i) pg[i] -= pkd * kg[i];
+            const double pn = sqrt(pg[0] * pg[0] + pg[1] * pg[1] + pg[2] * pg[2]);
+            if (pn > 1e-12)
+                for (int i = 0; i < 3; ++i)
+                    p[i] = (float)((pg[0] * L.fa[i][0] + pg[1] * L.fa[i][1] + pg[2] * L.fa[i][2]) / pn);
+        }
     }
     E32 = (float)E;
     if (!(E > 0.0) || !isfinite(E)) return false;
@@ -589,7 +612,7 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
         if (fabs(xe[0] - (double)L.zc) > (double)L.half_d) return false;
         if (fabs(xe[2]) * (double)L.cphi > xe[1] * (double)L.sphi) return false;
         for (int i = 0; i < 3; ++i) x[i] = (float)xe[i];
-        kN = (kl[1] * xe[1] + kl[2] * xe[2]) / R;
+        kN = (kl[1] * xe[1] + kl[2] * xe[2]) * L.inv_Rd;
     }
     const double sr = L.hc_2d / E;                        // sin(aB), Eq. (BraggLaw)
     nb = !(sr < 1.0);
@@ -603,12 +626,13 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
         sincos(L.shift0 + (double)sh, &sn_s, &cs_s);
     }
     if (!nb) {
-        const double cr = sqrt(1.0 - sr * sr);
-        const double sb = sr * cs_s + cr * sn_s;
+        // cos aB only with a peak shift (then in FP64); Q takes it in FP32
+        const double sb = sn_s != 0.0 ? sr * cs_s + sqrt(1.0 - sr * sr) * sn_s : sr * cs_s;
         sB = (float)sb;
         A = (float)(kN - sb);
+        const float srf = (float)sr, crf = sqrtf(fmaxf(0.0f, __fmaf_rn(-srf, srf, 1.0f)));
         const float lam = 12.398419843320026e-7f / E32;   // mm
-        Q = L.K2 * lam * lam * lam / (2.0f * (float)sr * (float)cr);
+        Q = L.K2 * lam * lam * lam / (2.0f * srf * crf);
     } else {
         sB = 1.0f;                                        // no Bragg solution: A + sB = |k.N|
         A = (float)(kN - 1.0);
@@ -620,7 +644,7 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
         for (int h = 1; h < L.n_ord; ++h) {
             const double srh = sr * L.ord_rd[h];
             if (srh < 1.0) {
-                const double sbh = srh * cs_s + sqrt(1.0 - srh * srh) * sn_s;
+                const double sbh = sn_s != 0.0 ? srh * cs_s + sqrt(1.0 - srh * srh) * sn_s : srh * cs_s;
                 osB[h] = (float)sbh;
                 oA[h] = (float)(kN - sbh);
             } else {
@@ -1982,6 +2006,9 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
     const double *a1 = S.geometry == HEART_FLAT ? S.en : S.cc;
     const double *a2 = S.geometry == HEART_FLAT ? S.N : S.ww;
     for (int i = 0; i < 3; ++i) { L.fc[i] = S.c[i]; L.fa[0][i] = a0[i]; L.fa[1][i] = a1[i]; L.fa[2][i] = a2[i]; }
+    for (int r = 0; r < 3; ++r)
+        for (int i = 0; i < 3; ++i) L.faf[r][i] = (float)L.fa[r][i];
+    L.inv_Rd = L.R > 0.0f ? 1.0 / (double)L.R : 0.0;     // the radius the FP32 walk uses
     L.pol_on = P.pol_on;
     L.user = P.user;
     if (P.pol_on && !P.user) {
