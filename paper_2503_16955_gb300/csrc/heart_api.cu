@@ -310,7 +310,7 @@ static heart_status trace_impl(heart_spectrometer *h, const heart_source_desc *s
                                  cs, qe);
     } else {
         // the two-pass trace runs on the device's shared hit queue (leased while enqueued)
-        if (h->p.n_orders == 1) {
+        if (takes_two_pass(h->p, P)) {
             WaveLease lease;
             st = wave_acquire(n_rays, cs, &lease);
             if (st != HEART_OK) return st;

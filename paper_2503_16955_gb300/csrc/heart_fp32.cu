@@ -1631,11 +1631,15 @@ struct SpawnStage {
     float e[USER ? kSpawnThreads : 1];
     int32_t nb[USER ? kSpawnThreads : 1];
 };
-template <int GEOM, bool POL, bool USER>
+// ORD: several reflection orders (sampled rays): the record's segment words carry
+// orders 1-3's anchors and sines and the no-Bragg mask, and the walk prepares the
+// entry segment of every order when it takes the ray
+template <int GEOM, bool POL, bool USER, bool ORD = false>
 __global__ void __launch_bounds__(kSpawnThreads) k_spawn32(const __grid_constant__ Launch32 L,
                                                            const __grid_constant__ WaveBuf B, uint64_t first,
                                                            uint32_t count, unsigned long long *n_hits) {
     static_assert(!USER || POL, "user rays travel with their polarisation word");
+    static_assert(!ORD || (POL && !USER), "several orders: the polarised variant, sampled rays");
     __shared__ SpawnStage<POL, USER> sg;
     __shared__ unsigned int s_ofs[kSpawnWarps];
     __shared__ unsigned long long s_base;
@@ -1692,7 +1696,8 @@ __global__ void __launch_bounds__(kSpawnThreads) k_spawn32(const __grid_constant
     const unsigned j = threadIdx.x;
     if (j >= s_hits) return;
     float A = 0.f, sB = 0.f, mu0 = 0.f, qr = 0.f, inv_ws = 1.f, E32 = 0.f;
-    int nb = 0;
+    int nb = 0, nbm = 0;
+    float oA[HEART_MAX_ORDERS] = {0.f, 0.f, 0.f, 0.f}, osB[HEART_MAX_ORDERS] = {0.f, 0.f, 0.f, 0.f};
     bool ok = true;
     if (USER) {
         A = sg.dA[j];
@@ -1701,12 +1706,16 @@ __global__ void __launch_bounds__(kSpawnThreads) k_spawn32(const __grid_constant
         E32 = sg.e[USER ? j : 0];
         nb = sg.nb[USER ? j : 0];
     } else {
-        ok = spawn_energy(L, sg.a0[j], sg.a1[j], sg.b2[j], sg.b3[j], sg.dA[j], A, sB, mu0, qr, inv_ws, E32, nb);
+        ok = spawn_energy(L, sg.a0[j], sg.a1[j], sg.b2[j], sg.b3[j], sg.dA[j], A, sB, mu0, qr, inv_ws, E32, nb,
+                          ORD ? oA : nullptr, ORD ? osB : nullptr, ORD ? &nbm : nullptr);
     }
     Lane t;
     for (int m = 0; m < 3; ++m) { t.x0[m] = sg.x[m][j]; t.k[m] = sg.k[m][j]; }
     t.s_exit = 0.f; t.inv_mu = 0.f; t.pa = 0.f; t.ra = 0.f; t.qmin = 0.f; t.pbar = 0.f; t.w0 = 0u; t.face = 0;
-    if (ok) {
+    if (ORD) {
+        t.s_exit = oA[1]; t.inv_mu = osB[1]; t.pa = oA[2]; t.ra = osB[2]; t.qmin = oA[3]; t.pbar = osB[3];
+        t.face = nbm;
+    } else if (ok) {
         t.A = A;
         t.sB = sB;
         t.cB = sqrtf(fmaxf(0.0f, __fmaf_rn(-sB, sB, 1.0f)));
@@ -1730,7 +1739,7 @@ __global__ void __launch_bounds__(kSpawnThreads) k_spawn32(const __grid_constant
 
 // pass 2: a persistent grid walks the queued hits; idle lanes take the next
 // ones (warp-aggregated) once at least `refill` lanes of the warp are idle
-template <int GEOM, int IRC, int OCC, bool POL>
+template <int GEOM, int IRC, int OCC, bool POL, bool ORD = false>
 __global__ void __launch_bounds__(kBlockThreads, OCC)
     k_walk32(const __grid_constant__ Launch32 L, const __grid_constant__ WaveBuf B,
              const unsigned long long *n_hits, unsigned long long *head, uint32_t count) {
@@ -1789,13 +1798,20 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                     s.nrefl = 0;
                     s.ncoll = 0;
                     s.pol = POL && (s.p[0] != 0.0f || s.p[1] != 0.0f || s.p[2] != 0.0f);
-                    segment_consts<GEOM>(L, s);
+                    if (ORD) {
+                        // every order's rates and the entry segment of all orders
+                        const float oa[4] = {s.A, r3.x, r3.z, r4.x}, os[4] = {s.sB, r3.y, r3.w, r4.y};
+                        start_orders(L, s, oa, os, __float_as_int(r5.y));
+                        segment<GEOM, true>(L, s);
+                    } else {
+                        segment_consts<GEOM>(L, s);
+                    }
                     alive = true;
                 }
             }
         }
         if (alive) {
-            const int oc = step<GEOM, IRC, POL>(L, s, s_tab);
+            const int oc = step<GEOM, IRC, POL, ORD>(L, s, s_tab);
             if (oc >= 0) {
                 my_coll += (unsigned long long)s.ncoll;
                 finish<false, POL>(L, s, oc, bt);
@@ -2125,13 +2141,13 @@ static heart_status launch_single(const SpecParams &S, const SourceParams &P, ui
     return rec ? dispatch<true>(L, W, st, false, ext) : dispatch<false>(L, W, st, false, ext);
 }
 
-template <int GEOM, int IRC, bool POL = false, bool USER = false>
+template <int GEOM, int IRC, bool POL = false, bool USER = false, bool ORD = false>
 static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t n, unsigned long long *ctr,
                                   cudaStream_t st) {
     constexpr int OCC = POL ? 5 : 6;
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk32<GEOM, IRC, OCC, POL>, kBlockThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk32<GEOM, IRC, OCC, POL, ORD>, kBlockThreads, 0);
         if (per_sm < 1) per_sm = 1;
     }
     const int walk_blocks = per_sm * num_sms();
@@ -2146,9 +2162,9 @@ static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t 
         unsigned long long *cc = ctr + 2 * g;
         const uint64_t first = c * B.cap;
         const uint32_t count = (uint32_t)(n - first < B.cap ? n - first : B.cap);
-        k_spawn32<GEOM, POL, USER><<<(count + kSpawnThreads - 1) / kSpawnThreads, kSpawnThreads, 0, st>>>(
+        k_spawn32<GEOM, POL, USER, ORD><<<(count + kSpawnThreads - 1) / kSpawnThreads, kSpawnThreads, 0, st>>>(
             L, B, first, count, cc);
-        k_walk32<GEOM, IRC, OCC, POL><<<walk_blocks, kBlockThreads, 0, st>>>(L, B, cc, cc + 1, count);
+        k_walk32<GEOM, IRC, OCC, POL, ORD><<<walk_blocks, kBlockThreads, 0, st>>>(L, B, cc, cc + 1, count);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "FP32 two-pass launch");
@@ -2208,7 +2224,7 @@ void wave_release(const WaveLease &lease, cudaStream_t st) {
 heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
                          void *img, unsigned long long *scratch, cudaStream_t st, const QeParams *qe, void *wave,
                          uint32_t wave_cap) {
-    if (!wave || n == 0 || S.n_orders > 1)
+    if (!wave || n == 0 || !takes_two_pass(S, P))
         return launch_single(S, P, n, seed, offset, img, scratch, nullptr, st, qe);
     // the two-pass trace: the per-ray work in its own pass, then the walk
     Launch32 L;
@@ -2231,6 +2247,11 @@ heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n,
         // walked by the variant that carries p
         if (L.geometry == HEART_FLAT) return launch_wave_t<HEART_FLAT, -1, true, true>(L, B, n, ctr, st);
         return launch_wave_t<HEART_CYL_VON_HAMOS, -1, true, true>(L, B, n, ctr, st);
+    }
+    if (S.n_orders > 1) {
+        // several orders: the polarised variant (run-time rocking curve) with per-order lane state
+        if (L.geometry == HEART_FLAT) return launch_wave_t<HEART_FLAT, -1, true, false, true>(L, B, n, ctr, st);
+        return launch_wave_t<HEART_CYL_VON_HAMOS, -1, true, false, true>(L, B, n, ctr, st);
     }
     if (P.pol_on || S.irc == HEART_IRC_NONE) {
         // polarised source: 112-byte records and the walk variant that carries p,
@@ -2357,7 +2378,7 @@ extern "C" heart_status heart_trace_batch(heart_spectrometer *const *specs, cons
     // the request loop run them; the others share one persistent launch.
     std::vector<int> big, small;
     for (int i = 0; i < n_jobs; ++i)
-        (n_rays[i] >= kTwoPassMinRays && S[i]->n_orders == 1 ? big : small).push_back(i);
+        (n_rays[i] >= kTwoPassMinRays && takes_two_pass(*S[i], P[i]) ? big : small).push_back(i);
     // device block: [tallies x n_jobs][big jobs' spectra][the persistent launch's block]
     const size_t tall_bytes = ((size_t)n_jobs * kTallyN * 8 + 15) & ~(size_t)15;
     size_t big_sp = 0;
@@ -2443,7 +2464,7 @@ extern "C" heart_status heart_autotune(heart_spectrometer *h, const heart_source
     if (st != HEART_OK) return fail(st, err);
     cudaStream_t cs = (cudaStream_t)stream;
     // the two-pass probes use the device's hit queue, held for the whole tuning
-    const bool two_pass = h->p.n_orders == 1;
+    const bool two_pass = takes_two_pass(h->p, P);
     WaveLease lease{nullptr, 0u, 0};
     if (two_pass) {
         st = wave_acquire(probe_rays, cs, &lease);

@@ -39,6 +39,10 @@ constexpr int kWaveGroup = 1024;
 // jobs of at least this many rays (one reflection order) run on the two-pass
 // trace in batches and in the request loop, as single traces do
 constexpr uint64_t kTwoPassMinRays = 1ull << 22;
+
+// the two-pass trace takes every FP32 image trace but user rays with several
+// reflection orders (those run on the persistent extended kernel)
+inline bool takes_two_pass(const SpecParams &S, const SourceParams &P) { return !(P.user && S.n_orders > 1); }
 constexpr int kWaveRec16 = 6;                  // 16-byte words per queued hit (a 96-byte record)
 constexpr int kWaveRecMax16 = 7;               // with the polarisation word
 inline size_t wave_bytes(uint32_t cap) { return (size_t)16 * kWaveRecMax16 * cap + (size_t)2 * 8 * kWaveGroup; }

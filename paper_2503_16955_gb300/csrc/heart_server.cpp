@@ -213,7 +213,7 @@ void worker_main(heart_server *s) {
             std::vector<uint64_t> bnr, bseed, boff;
             for (size_t i = 0; i < slice_jobs.size() && st == HEART_OK; ++i) {
                 const SpecParams &sp = *S[i];
-                if (slice_jobs[i]->n >= s->two_pass_min && sp.n_orders == 1) {
+                if (slice_jobs[i]->n >= s->two_pass_min && takes_two_pass(sp, P[i])) {
                     WaveLease lease;
                     st = wave_acquire(nr[i], s->stream, &lease);
                     if (st != HEART_OK) break;
