@@ -37,9 +37,15 @@
  *    probability f(n) G / f(0) (f from the MDF's own formula).  The thinned
  *    sampler bounds each cone per straight segment instead: the cone facing
  *    the ray by f at the tilt 2 sin^2(d/2) (d: distance of sin a~0 from the
- *    segment's |k.N| range), the other by f at 2 sin^2(a~0/2); the cone is
- *    then drawn by its share of the bound and the candidate kept with
- *    f(n) G / (its cone's bound).
+ *    segment's |k.N| range), the other by f at 2 sin^2(a~0/2).  On the
+ *    facing cone the tilt grows with the azimuth psi measured from the side
+ *    of N, q(psi) = q0 + cos(a~0) cos(g) (1 - cos psi) (sin g = |k.N|), so
+ *    outside a window |psi| < psi* the MDF is below v* f(0) (v* the thinning
+ *    level, q_v the tilt where W / W(0) falls to v*): the facing cone splits
+ *    into the window (bound f at 2 sin^2(d/2)) and the rest (bound v* f(0)).
+ *    A candidate takes the window, the rest or the other cone by its share
+ *    of the bound, psi uniform over that part, and is kept with
+ *    f(n) G / (that part's bound).
  *  Detector (Sec. 2.3): exiting rays are propagated to the detector plane and
  *    binned into integer pixel counts.
  *
@@ -613,10 +619,24 @@ typedef struct {
     orc_mdf_table *mdf;
     /* thinned sampler: v* and the IRC half-width X* beyond which R/R_max <= v* */
     double vstar, xstar;
-    /* no rocking curve: the factor of none_factor() and W(0) */
+    /* no rocking curve: the factor of none_factor() and W(0); thinned: the tilt
+     * q_v beyond which W / W(0) <= v* (INFINITY if W never falls that low) */
     int irc_none;
-    double none_fac, W0;
+    double none_fac, W0, none_qv;
 } geom;
+
+/* q_v: a tilt with W(q) / W(0) <= v* for every q >= q_v (the MDFs decrease
+ * with the tilt), by 100 bisection steps on [0, 2] and widened by 1e-9
+ * relative; INFINITY if W(2) / W(0) > v*. */
+static double none_tilt(const orc_spec *s, double W0, double vstar) {
+    if (orc_mdf_W(s, 2.0) / W0 > vstar) return INFINITY;
+    double lo = 0.0, hi = 2.0;
+    for (int i = 0; i < 100; ++i) {
+        double m = 0.5 * (lo + hi);
+        if (orc_mdf_W(s, m) / W0 <= vstar) hi = m; else lo = m;
+    }
+    return hi * (1.0 + 1e-9);
+}
 
 /* X*: the smallest |x| such that R(x') / R_max <= v* for every |x'| >= X*.
  * Found by scanning |x| down from 1 rad on a geometric grid (ratio 1.0005),
@@ -690,6 +710,11 @@ static int geom_init(geom *g, const orc_spec *s) {
         g->none_fac = none_factor(s);
         if (!(g->W0 > 0) || !(g->none_fac > 0) || !isfinite(g->none_fac)) return fail("MDF has no mass at theta = 0");
         if (s->sampler != ORC_SAMPLER_PLAIN && s->sampler != ORC_SAMPLER_THINNED) return fail("unknown sampler");
+        if (s->sampler == ORC_SAMPLER_THINNED) {
+            g->vstar = s->thin_vstar > 0 ? s->thin_vstar : 1.0 / 64.0;
+            if (!(g->vstar < 1.0)) return fail("thin_vstar must be < 1");
+            g->none_qv = none_tilt(s, g->W0, g->vstar);
+        }
     } else if (s->sampler == ORC_SAMPLER_THINNED) {
         g->vstar = s->thin_vstar > 0 ? s->thin_vstar : 1.0 / 64.0;
         if (!(g->vstar < 1.0)) return fail("thin_vstar must be < 1");
@@ -867,8 +892,9 @@ typedef struct {
     uint64_t w0, wspan;       /* process (b): table words [w0, w0 + wspan) */
     double lam;               /* the order's candidate rate on the segment */
     /* no rocking curve, thinned: W at the smallest tilt each Bragg cone can
-     * reach on the segment, relative to W(0), and the facing cone's share */
-    double wn, wf, pnear;
+     * reach on the segment, relative to W(0); the facing cone's window |psi| <
+     * psis; the cumulative shares of the window and of the whole facing cone */
+    double wn, wf, psis, pin, pio;
 } order_bound;
 
 typedef struct {
@@ -909,7 +935,8 @@ static void bound_order(const geom *g, const orc_ray_consts *rc, int h, double l
     b->wspan = 1ull << 32;
     b->lam = rc->ord_qr[h];
     b->wn = b->wf = 1.0;
-    b->pnear = 0.5;
+    b->psis = PI;
+    b->pin = b->pio = 0.5;
     if (s->sampler == ORC_SAMPLER_THINNED && s->irc == ORC_IRC_NONE && rc->ord_qr[h] > 0) {
         /* the cone facing the ray (k.n of the sign of k.N): its crystallites are tilted
          * by at least the angle between a~0 and the grazing-angle range of the segment,
@@ -919,10 +946,20 @@ static void bound_order(const geom *g, const orc_ray_consts *rc, int h, double l
         double a0 = rc->ord_alpha[h] + rc->shift_rad, s0 = sin(a0);
         double d = s0 < lo ? lo - s0 : (s0 > hi ? s0 - hi : 0.0);
         double hn = sin(0.5 * d), hf = sin(0.5 * a0);
-        b->wn = orc_mdf_W(s, 2.0 * hn * hn) / g->W0;
+        double q0 = 2.0 * hn * hn;
+        b->wn = orc_mdf_W(s, q0) / g->W0;
         b->wf = orc_mdf_W(s, 2.0 * hf * hf) / g->W0;
-        b->lam = 0.5 * rc->ord_qr[h] * (b->wn + b->wf);
-        b->pnear = b->wn + b->wf > 0 ? b->wn / (b->wn + b->wf) : 1.0;
+        /* the window: q(psi) >= q0 + cos(a~0) cos(g_max) (1 - cos psi) >= q_v for |psi| >= psis */
+        double sh = hi < 1.0 ? hi : 1.0, cmin = cos(a0) * sqrt(1.0 - sh * sh);
+        if (q0 < g->none_qv && cmin > 0) {
+            double xq = (g->none_qv - q0) / cmin;            /* 1 - cos(psis) */
+            if (xq < 2.0) b->psis = 2.0 * asin(sqrt(0.5 * xq));
+        }
+        double fin = b->wn * (b->psis / PI), fout = b->psis < PI ? g->vstar * (1.0 - b->psis / PI) : 0.0;
+        double tot = fin + fout + b->wf;
+        b->lam = 0.5 * rc->ord_qr[h] * tot;
+        b->pin = tot > 0 ? fin / tot : 1.0;
+        b->pio = tot > 0 ? (fin + fout) / tot : 1.0;
         return;
     }
     if (s->sampler != ORC_SAMPLER_THINNED || s->irc == ORC_IRC_NONE || !(rc->ord_qr[h] > 0)) return;
@@ -1018,8 +1055,11 @@ static void cone_axes(const double k[3], const double N[3], const double t1[3], 
 
 /* a scatter candidate of order h without rocking curve: the crystallite normal
  * n = sg sin(a~0) k + cos(a~0) (cos(psi) e1 + sin(psi) e2) on the cone
- * k.n = sg sin(a~0), sg = -1 if the top bit of u2 is clear, +1 if set;
- * psi = 2 pi u3.  P = f(n) G / f(0) = W(1 - n.N) G / W(0). */
+ * k.n = sg sin(a~0).  Plain: sg = -1 if the top bit of u2 is clear, +1 if set;
+ * psi = 2 pi u3; P = f(n) G / f(0) = W(1 - n.N) G / W(0).  Thinned: by u2
+ * against the shares pin, pio the facing cone's window (psi = psis (2 u3 - 1)),
+ * the rest of the facing cone (psi = psis + 2 (pi - psis) u3) or the other cone
+ * (psi = 2 pi u3); P = W(1 - n.N) G / (W(0) x that part's bound). */
 static void cone_candidate(const geom *g, const orc_ray_consts *rc, int h, const order_bound *ob, const double x[3],
                            const double k[3], int pol, const double p[3], const uint32_t w[4], double ks[3],
                            double *P) {
@@ -1028,16 +1068,25 @@ static void cone_candidate(const geom *g, const orc_ray_consts *rc, int h, const
     cone_axes(k, N, t1, e1, e2);
     double a0 = rc->ord_alpha[h] + rc->shift_rad, s0 = sin(a0), c0 = cos(a0);
     double sg, wb = 1.0;                             /* the cone, and the bound of W / W(0) on it */
+    double psi = 2.0 * PI * U(w[3]);
     if (g->s->sampler == ORC_SAMPLER_THINNED) {
-        /* the facing cone (k.n of the sign of k.N) with probability pnear, by u2 */
-        double kN = dot3(k, N), side = kN < 0 ? -1.0 : 1.0;
-        int near_ = U(w[2]) < ob->pnear;
-        sg = near_ ? side : -side;
-        wb = near_ ? ob->wn : ob->wf;
+        /* the facing cone (k.n of the sign of k.N): its window or the rest; or the other cone */
+        double kN = dot3(k, N), side = kN < 0 ? -1.0 : 1.0, u2 = U(w[2]), u3 = U(w[3]);
+        if (u2 < ob->pin) {
+            sg = side;
+            wb = ob->wn;
+            psi = ob->psis * (2.0 * u3 - 1.0);
+        } else if (u2 < ob->pio) {
+            sg = side;
+            wb = g->vstar;
+            psi = ob->psis + 2.0 * (PI - ob->psis) * u3;
+        } else {
+            sg = -side;
+            wb = ob->wf;
+        }
     } else {
         sg = (w[2] & 0x80000000u) ? 1.0 : -1.0;
     }
-    double psi = 2.0 * PI * U(w[3]);
     for (int i = 0; i < 3; ++i) n[i] = sg * s0 * k[i] + c0 * (cos(psi) * e1[i] + sin(psi) * e2[i]);
     double q = 1.0 - dot3(n, N);                     /* 1 - cos(theta), the crystallite's tilt */
     for (int i = 0; i < 3; ++i) ks[i] = k[i] - 2.0 * (sg * s0) * n[i];   /* k.n = sg s0 */

@@ -100,6 +100,7 @@ struct Launch32 {
     // distribution's W(q) / W(0) in closed form (mdf_ratio32)
     int32_t mdf;
     float none_fac, w_a2, w_c, w_wl, w_wg, w_b, w_qmax;
+    float none_qv;                        // thinned cones: W / W(0) <= v* beyond this tilt (inf: never)
     // polarisation and user-supplied rays (the extended kernel only)
     int32_t pol_on, user;
     float pol[3];                         // source polarisation, local frame
@@ -753,9 +754,9 @@ __device__ __forceinline__ float thin_bounds(const Launch32 &L, Lane &s, float A
     float la = s.qr, lb = 0.0f;
     s.ra = 1.0f;
     if (L.irc_kind == HEART_IRC_NONE) {
-        // no rocking curve: the Bragg cones' bounds (ra: the facing cone's share of the
-        // candidates; qmin, pbar: the bounds of W / W(0) on the facing and the other cone)
-        s.ra = 0.5f; s.qmin = 1.0f; s.pbar = 1.0f;
+        // no rocking curve: the Bragg cones' bounds (qmin, pbar: the bounds of W / W(0) on
+        // the facing and the other cone; w0: the bits of the facing cone's window half-width)
+        s.ra = 0.5f; s.qmin = 1.0f; s.pbar = 1.0f; s.w0 = __float_as_uint(3.14159265f);
         if (L.sampler == HEART_SAMPLER_THINNED && s.qr > 0.0f) {
             const float Ae = flip ? -2.0f * s.sB - A_exit : A_exit;
             const float lo = flip ? -s.sB : fminf(s.A, Ae), hi = fmaxf(s.A, Ae);
@@ -763,12 +764,23 @@ __device__ __forceinline__ float thin_bounds(const Launch32 &L, Lane &s, float A
             const float h = 0.5f * d, h2 = h * h;
             const float sh = d < 0.1f ? h * __fmaf_rn(h2, __fmaf_rn(h2, 8.33333333e-3f, -0.166666667f), 1.0f)
                                       : __sinf(h);
-            const float wn = mdf_ratio32(L, 2.0f * sh * sh);
+            const float q0 = 2.0f * sh * sh;
+            const float wn = mdf_ratio32(L, q0);
             const float wf = mdf_ratio32(L, s.sB * s.sB / (1.0f + s.cB));   // 2 sin^2(a~0 / 2)
+            // the window: W <= v* W(0) where q0 + cos(a~0) cos(g_max) (1 - cos psi) >= q_v
+            float psis = 3.14159265f;
+            const float shi = fminf(s.sB + hi, 1.0f);
+            const float cmin = s.cB * sqrtf(fmaxf(0.0f, __fmaf_rn(-shi, shi, 1.0f))) * 0.999999f;
+            if (q0 < L.none_qv && cmin > 0.0f) {
+                const float xq = (L.none_qv - q0) / cmin;
+                if (xq < 2.0f) psis = 2.0f * asinf(sqrtf(0.5f * xq));
+            }
+            const float fin = wn * psis * 0.318309886f;
+            const float fout = psis < 3.14159265f ? L.vstar * __fmaf_rn(-psis, 0.318309886f, 1.0f) : 0.0f;
             s.qmin = wn;
             s.pbar = wf;
-            s.ra = wn + wf > 0.0f ? wn / (wn + wf) : 1.0f;
-            la = 0.5f * s.qr * (wn + wf);
+            s.w0 = __float_as_uint(psis);
+            la = 0.5f * s.qr * (fin + fout + wf);
         }
     } else if (L.sampler == HEART_SAMPLER_THINNED && s.qr > 0.0f) {
         // |k.N| at the exit is sB + A_exit, or -(sB + A_exit) if k.N changed sign
@@ -1082,9 +1094,12 @@ __device__ __forceinline__ void crystallite_normal(const Launch32 &L, const Lane
 
 // A scatter candidate without rocking curve (R a delta function): the
 // crystallite normal on the Bragg cone k.n = sg sin(a~0), a~0 = aB + Delta_M,
-// sg = +1 if the top bit of u2 is set, at azimuth psi = 2 pi u3 about k
-// measured from the part of N perpendicular to k; kept with probability
-// W(q) G / W(0).  In the collision's frame (t1, t2, N) with k = (k0, kt, kN)
+// at azimuth psi about k measured from the part of N perpendicular to k.
+// Plain: sg = +1 if the top bit of u2 is set, psi = 2 pi u3, kept with
+// probability W(q) G / W(0).  Thinned: u2 picks the facing cone's window
+// |psi| < psis (bound W at the segment's smallest tilt), the rest of the facing
+// cone (bound v* W(0)) or the other cone, psi uniform over the part, kept with
+// probability W(q) G / (the part's bound).  In the collision's frame (t1, t2, N) with k = (k0, kt, kN)
 // and c = sqrt(1 - kN^2): e1 = (-kN k0, -kN kt, c^2) / c, e2 = (kt, -k0, 0) / c,
 // and the tilt q = 1 - n.N = q0 + c0 c (1 - cos psi) with q0 = 1 - cos(g -+ a~0),
 // sin g = |kN|.  On the cone facing the ray (sg = sign kN) q0 comes from the
@@ -1097,13 +1112,20 @@ __device__ __forceinline__ int cone_step(const Launch32 &L, Lane &s, uint32_t w2
     const float s0 = s.sB, c0 = s.cB;
     const float sa = s0 + Ac;                                   // |k.N| at the collision
     const float cb = sqrtf(fmaxf(0.0f, __fmaf_rn(-sa, sa, 1.0f)));
-    // the cone: with the thinned sampler the one facing the ray (k.n of the sign of k.N)
-    // by its share of the segment's bound (lane fields ra, qmin, pbar), else by the top bit
-    float sg, wb = 1.0f;
+    // the cone: thinned, the facing cone's window |psi| < psis, the rest of the facing cone
+    // (k.n of the sign of k.N) or the other cone by their shares of the segment's bound
+    // (lane fields qmin, pbar: W / W(0) bounds; w0: psis); plain, the cone by the top bit.
+    // psi / (2 pi) = x0 + xs u3
+    float sg, wb = 1.0f, x0 = 0.0f, xs = 1.0f;
     if (L.sampler == HEART_SAMPLER_THINNED) {
-        const bool near_ = u01_32(w2) < s.ra;
-        sg = near_ ? s.sgn : -s.sgn;
-        wb = near_ ? s.qmin : s.pbar;
+        const float psis = __uint_as_float(s.w0);
+        const float fin = s.qmin * psis * 0.318309886f;
+        const float fout = psis < 3.14159265f ? L.vstar * __fmaf_rn(-psis, 0.318309886f, 1.0f) : 0.0f;
+        const float t2 = u01_32(w2) * (fin + fout + s.pbar);
+        const float hw = psis * 0.159154943f;                  // psis / (2 pi)
+        if (t2 < fin) { sg = s.sgn; wb = s.qmin; x0 = -hw; xs = 2.0f * hw; }
+        else if (t2 < fin + fout) { sg = s.sgn; wb = L.vstar; x0 = hw; xs = 1.0f - 2.0f * hw; }
+        else { sg = -s.sgn; wb = s.pbar; }
     } else {
         sg = (w2 & 0x80000000u) ? 1.0f : -1.0f;
     }
@@ -1115,7 +1137,7 @@ __device__ __forceinline__ int cone_step(const Launch32 &L, Lane &s, uint32_t w2
         q0 = __fmaf_rn(s0, sa, __fmaf_rn(-c0, cb, 1.0f));       // 1 - cos(g + a~0)
     }
     float sh, ch;
-    sincospif(u01_32(w3), &sh, &ch);                         // psi / 2, accurate near 0
+    sincospif(__fmaf_rn(xs, u01_32(w3), x0), &sh, &ch);      // psi / 2, accurate near 0
     const float C = c0 * cb;
     const float omc = 2.0f * sh * sh;                           // 1 - cos psi
     const float q = __fmaf_rn(C, omc, q0);
@@ -1978,6 +2000,7 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
     L.w_wg = (float)S.w_wg;
     L.w_b = (float)S.w_b;
     L.w_qmax = (float)S.w_qmax;
+    L.none_qv = (float)S.none_qv;
     L.max_refl = S.max_refl;
     L.max_coll = S.max_coll;
     double D0[3], eu[3], ev[3], nd[3];

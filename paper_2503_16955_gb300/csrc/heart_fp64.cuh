@@ -283,7 +283,9 @@ __host__ __device__ __forceinline__ void irc_energy64(const SpecParams &S, doubl
 struct Bound64 {
     double ra, vstar, qmin, pbar, S1, S2, lam;
     unsigned long long w0, wspan;
-    double wn, wf, pnear;          // no rocking curve, thinned: W / W(0) bounds of the two cones, facing share
+    // no rocking curve, thinned: W / W(0) bounds of the two cones, the facing cone's window
+    // |psi| < psis, and the cumulative shares of the window and of the whole facing cone
+    double wn, wf, psis, pin, pio;
 };
 
 struct Seg64 {
@@ -306,7 +308,7 @@ __device__ __forceinline__ void bound_order64(const SpecParams &S, const Orders6
     b.ra = 1.0; b.vstar = 1.0; b.qmin = 0.0; b.pbar = 1.0; b.S1 = 0.0; b.S2 = 0.0;
     b.w0 = 0ull; b.wspan = 1ull << 32;
     b.lam = O.qr[h];
-    b.wn = 1.0; b.wf = 1.0; b.pnear = 0.5;
+    b.wn = 1.0; b.wf = 1.0; b.psis = 3.14159265358979323846; b.pin = 0.5; b.pio = 0.5;
     if (S.sampler == HEART_SAMPLER_THINNED && S.irc == HEART_IRC_NONE && O.qr[h] > 0) {
         // no rocking curve: the facing cone's crystallites are tilted by at least d
         // (distance of sin a~0 from the segment's |k.N| range), the other cone's by at
@@ -314,10 +316,22 @@ __device__ __forceinline__ void bound_order64(const SpecParams &S, const Orders6
         const double a0 = O.alpha[h] + O.shift, s0 = sin(a0);
         const double d = s0 < lo ? lo - s0 : (s0 > hi ? s0 - hi : 0.0);
         const double hn = sin(0.5 * d), hf = sin(0.5 * a0);
-        b.wn = mdf_ratio64(S, 2.0 * hn * hn);
+        const double q0 = 2.0 * hn * hn;
+        b.wn = mdf_ratio64(S, q0);
         b.wf = mdf_ratio64(S, 2.0 * hf * hf);
-        b.lam = 0.5 * O.qr[h] * (b.wn + b.wf);
-        b.pnear = b.wn + b.wf > 0 ? b.wn / (b.wn + b.wf) : 1.0;
+        // on the facing cone q(psi) >= q0 + cos(a~0) cos(g_max) (1 - cos psi): W <= v* W(0)
+        // outside |psi| < psis
+        const double sh = fmin(hi, 1.0), cmin = cos(a0) * sqrt(1.0 - sh * sh);
+        if (q0 < S.none_qv && cmin > 0) {
+            const double xq = (S.none_qv - q0) / cmin;
+            if (xq < 2.0) b.psis = 2.0 * asin(sqrt(0.5 * xq));
+        }
+        const double pi = 3.14159265358979323846;
+        const double fin = b.wn * (b.psis / pi), fout = b.psis < pi ? S.vstar * (1.0 - b.psis / pi) : 0.0;
+        const double tot = fin + fout + b.wf;
+        b.lam = 0.5 * O.qr[h] * tot;
+        b.pin = tot > 0 ? fin / tot : 1.0;
+        b.pio = tot > 0 ? (fin + fout) / tot : 1.0;
         return;
     }
     if (S.sampler != HEART_SAMPLER_THINNED || S.irc == HEART_IRC_NONE || !(O.qr[h] > 0)) return;
@@ -543,17 +557,25 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
             // (sg by the top bit of u2) at azimuth psi = 2 pi u3 about k
             const double a0 = O.alpha[h] + O.shift, s0 = sin(a0), c0 = cos(a0);
             double sg, wb = 1.0;                                // the cone, and its bound of W / W(0)
+            double x2 = 2.0 * u01_64(wd[3]);                    // psi / pi
             if (S.sampler == HEART_SAMPLER_THINNED) {
-                // the facing cone (k.n of the sign of k.N) by its share of the bound
-                const double side = dot3d(k, N) < 0 ? -1.0 : 1.0;
-                const bool near_ = u01_64(wd[2]) < sb.o[h].pnear;
-                sg = near_ ? side : -side;
-                wb = near_ ? sb.o[h].wn : sb.o[h].wf;
+                // the facing cone (k.n of the sign of k.N): its window |psi| < psis or the
+                // rest; or the other cone; by their shares of the bound
+                const Bound64 &ob = sb.o[h];
+                const double side = dot3d(k, N) < 0 ? -1.0 : 1.0, u2 = u01_64(wd[2]), u3 = u01_64(wd[3]);
+                const double pi = 3.14159265358979323846;
+                if (u2 < ob.pin) {
+                    sg = side; wb = ob.wn; x2 = ob.psis * (2.0 * u3 - 1.0) / pi;
+                } else if (u2 < ob.pio) {
+                    sg = side; wb = S.vstar; x2 = (ob.psis + 2.0 * (pi - ob.psis) * u3) / pi;
+                } else {
+                    sg = -side; wb = ob.wf;
+                }
             } else {
                 sg = (wd[2] & 0x80000000u) ? 1.0 : -1.0;
             }
             double sp, cp, e1[3], e2[3], n[3];
-            sincospi(2.0 * u01_64(wd[3]), &sp, &cp);
+            sincospi(x2, &sp, &cp);
             cone_axes64(k, N, t1, e1, e2);
             for (int i = 0; i < 3; ++i) n[i] = sg * s0 * k[i] + c0 * (cp * e1[i] + sp * e2[i]);
             const double q = 1.0 - dot3d(n, N);                 // the crystallite's tilt, 1 - cos(theta)

@@ -313,6 +313,36 @@ void mdf_ratio_params(const heart_spectrometer_desc *d, SpecParams *p) {
     p->none_fac = (d->irc == HEART_IRC_NONE && norm > 0) ? 2.0 * W0 / norm : 0.0;
 }
 
+// W(q) / W(0) from the closed-form parameters above (as the kernels evaluate it)
+double mdf_ratio_host(const SpecParams &p, double q) {
+    switch (p.mdf) {
+    case HEART_MDF_VMF: return std::exp(-p.w_c * q);
+    case HEART_MDF_WRAPPED_LORENTZIAN: return p.w_a2 / (p.w_a2 + 2.0 * q);
+    case HEART_MDF_SPHERICAL_WRAPPED_LORENTZIAN: {
+        const double r = p.w_b / (p.w_b + q);
+        return r * r;
+    }
+    case HEART_MDF_UNIFORM: return q <= p.w_qmax ? 1.0 : 0.0;
+    default: {
+        const double th = 2.0 * std::asin(std::sqrt(0.5 * std::fmin(std::fmax(q, 0.0), 2.0)));
+        return p.w_wl * (p.w_a2 / (p.w_a2 + th * th)) + p.w_wg * std::exp(-p.w_c * th * th);
+    }
+    }
+}
+
+// the cone sampler's window tilt q_v: W(q) / W(0) <= v* for every q >= q_v (the
+// mosaic distributions decrease with the tilt); 100 bisection steps on [0, 2],
+// widened by 1e-9 relative; infinite if W(2) / W(0) > v*
+double none_window_tilt(const SpecParams &p) {
+    if (mdf_ratio_host(p, 2.0) > p.vstar) return INFINITY;
+    double lo = 0.0, hi = 2.0;
+    for (int i = 0; i < 100; ++i) {
+        const double m = 0.5 * (lo + hi);
+        if (mdf_ratio_host(p, m) <= p.vstar) hi = m; else lo = m;
+    }
+    return hi * (1.0 + 1e-9);
+}
+
 }  // namespace
 
 heart_status build_spec_params(const heart_spectrometer_desc *d, SpecParams *p, double *tab,
@@ -439,6 +469,7 @@ heart_status build_spec_params(const heart_spectrometer_desc *d, SpecParams *p, 
     case HEART_IRC_NONE: p->irc_max = 0.0; break;    // a delta function: the cone candidates take over
     }
     mdf_ratio_params(d, p);
+    p->none_qv = d->irc == HEART_IRC_NONE ? none_window_tilt(*p) : INFINITY;
 
     // physics
     p->d_A = d->d_spacing_A;

@@ -61,6 +61,8 @@ struct SpecParams {
     // exp(-w_c q); WL a2 / (a2 + 2 q); SWL w_b^2 / (w_b + q)^2; uniform q <= w_qmax
     int32_t mdf, pad_m;
     double none_fac, w_a2, w_c, w_wl, w_wg, w_b, w_qmax;
+    // no rocking curve, thinned: a tilt q_v with W(q) / W(0) <= v* for q >= q_v (infinite if none)
+    double none_qv;
     // device tables: q = 1 - cos(theta) at the body knots then the tail knots
     const double *mdf64;
     const float *mdf32;

@@ -14,8 +14,11 @@ reflect.  Pinned against what the paper and the geometry fix:
   walk) gives the same reflection probability;
 * two orthogonal polarisations reflect twice as often as unpolarised rays;
 * the thinned sampler (per straight segment, the MDF at the smallest tilt
-  each cone can reach bounds that cone) agrees with the plain one (the bound
-  f(0) for both cones) and draws far fewer candidates."""
+  each cone can reach bounds that cone, and on the facing cone a window in
+  the azimuth outside which the MDF is below v* f(0)) agrees with the plain
+  one (the bound f(0) for both cones) and draws far fewer candidates; with a
+  narrow mosaic, where the window carries nearly all of the bound, its
+  thin-slab probability still follows the cone quadrature."""
 import math
 
 import numpy as np
@@ -162,6 +165,29 @@ def test_thin_slab_reflection_probability(offset, sampler):
     got = n - t["refl_hist"][0]
     assert abs(got - n * p) < 4.5 * math.sqrt(n * p * (1 - p)), (got, n * p)
     assert got > 5000
+
+
+@pytest.mark.parametrize("mdf,W", [("gaussian", lambda t: gauss_W(t, 0.02)),
+                                   ("lorentzian", lambda t: 1.0 / (1.0 + 4.0 * t ** 2 / 0.02 ** 2))])
+@pytest.mark.parametrize("offset", [0.0, 0.004])
+def test_thin_slab_probability_narrow_mosaic_window(mdf, W, offset):
+    # a 0.02 rad mosaic: on the facing cone the MDF exceeds v* W(0) only in a window of
+    # a few hundredths of a radian of psi, so nearly all of the thinned bound sits in
+    # the window and the rest of the cone carries the v* bound; the walk's first-
+    # reflection probability must still follow the cone quadrature
+    s = flat(mdf=mdf, mdf_fwhm_rad=0.02, sampler="thinned", refl_K_per_mm2=4e9)
+    c = ob.ray_constants(s, 8.0)
+    a = c["alpha_B"] + offset
+    r = cone_rate(c["Q"], c["alpha_B"], a, W)
+    p = slab_probability(r, c["mu0"], 0.002 / math.sin(a))
+    n = 400_000
+    _, t, _ = ob.trace(s, pencil(a), n, seed=41 + int(offset * 1000))
+    got = n - t["refl_hist"][0]
+    assert abs(got - n * p) < 4.5 * math.sqrt(n * p * (1 - p)), (got, n * p)
+    assert got > 2000
+    # and it draws far fewer candidates than the plain sampler (bound 2 pi f(0) on both cones)
+    _, tp, _ = ob.trace(dict(s, sampler="plain"), pencil(a), 20_000, seed=43)
+    assert t["collisions"] / n < 0.1 * tp["collisions"] / 20_000
 
 
 def test_limit_of_narrow_box_curves():
