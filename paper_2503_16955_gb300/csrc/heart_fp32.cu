@@ -2167,7 +2167,7 @@ static heart_status launch_single(const SpecParams &S, const SourceParams &P, ui
 template <int GEOM, int IRC, bool POL = false, bool USER = false, bool ORD = false>
 static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t n, unsigned long long *ctr,
                                   cudaStream_t st) {
-    constexpr int OCC = POL ? 5 : 6;
+    constexpr int OCC = 6;                          // 79 registers or fewer in every variant, no spills
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk32<GEOM, IRC, OCC, POL, ORD>, kBlockThreads, 0);
