@@ -37,12 +37,12 @@ SM_MAX_MHZ = 2070.0
 # rays per chunk of the two-pass trace (the library's largest hit-queue chunk)
 WAVE_CHUNK = 1 << 24
 # DRAM bytes (read + write) of the two passes per traced ray, from the ncu capture in
-# profiles/k_spawn32_k_walk32_von_hamos.md (1225.8 MB for 1.6e7 rays: the hit queue written
+# profiles/k_spawn32_k_walk32_von_hamos.md (1220.0 MB for 1.6e7 rays: the hit queue written
 # and read back); valid only for the kernel sources hashed there
-TRAFFIC_BYTES_PER_RAY = 1225.829e6 / 1.6e7
+TRAFFIC_BYTES_PER_RAY = 1220.040e6 / 1.6e7
 TRAFFIC_SOURCES = ("paper_2503_16955_gb300/csrc/heart_fp32.cu", "paper_2503_16955_gb300/csrc/heart_fp64.cuh",
                    "paper_2503_16955_gb300/csrc/heart_internal.h")
-TRAFFIC_SOURCE_HASH = "fcc71d37c7a79916"
+TRAFFIC_SOURCE_HASH = "f3b266afbfb0c7d8"
 
 
 def measured_traffic(n_rays):
