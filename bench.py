@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "rays/sec to detector and fraction of FP32/SFU roofline; p50/p99 job latency"
 UNIT = "rays/s"
-# algorithmic work per unit ("Roofline"): lane-instructions
+# algorithmic work per unit, in lane-instructions (one thread executing one instruction):
 INSTR_PER_COLLISION = 110      # Philox4x32-10 (60 int) + free path, table, sin/cos, Bragg offset, IRC, accept (~50)
 INSTR_PER_RAY = 240            # two Philox blocks, source, entry, per-ray constants, detector, tallies
 INSTR_PER_SEGMENT = 120        # exit distance, grazing-angle range, tilt bound, table search, majorant
@@ -36,9 +36,9 @@ LANES_PER_SM_CLK = 128         # 4 SM sub-partitions x 32 lanes, one warp-instru
 SM_MAX_MHZ = 2070.0
 # rays per chunk of the two-pass trace (the library's largest hit-queue chunk)
 WAVE_CHUNK = 1 << 24
-# DRAM bytes (read + write) of the two passes per traced ray, from the ncu capture in
-# profiles/k_spawn32_k_walk32_von_hamos.md (1220.0 MB for 1.6e7 rays: the hit queue written
-# and read back); valid only for the kernel sources hashed there
+# DRAM bytes (read + write) of the two passes per traced ray, from one ncu capture of the
+# spawn and walk kernels on 1.6e7 rays of the von Hamos workload (1220.0 MB: the hit queue
+# written and read back); valid only for the kernel sources with the hash below
 TRAFFIC_BYTES_PER_RAY = 1220.040e6 / 1.6e7
 TRAFFIC_SOURCES = ("paper_2503_16955_gb300/csrc/heart_fp32.cu", "paper_2503_16955_gb300/csrc/heart_fp64.cuh",
                    "paper_2503_16955_gb300/csrc/heart_internal.h")
