@@ -143,13 +143,13 @@ def cpu_baseline(workload, seconds, threads=0):
 
 def batched_measurement(H, W, torch, stream):
     """64 spectrometers of uneven ray counts in one heart_trace_batch call (jobs
-    of 2^22 rays or more as two-pass traces, the rest in one persistent launch)."""
+    of 2^18 rays or more as two-pass traces, the rest in one persistent launch)."""
     jobs = W.batched_64()
     specs = [H.heart_spectrometer_create(j["spec"]) for j in jobs]
     imgs = [torch.zeros(s.shape, dtype=torch.int32, device="cuda") for s in specs]
     args = ([j["source"] for j in jobs], [j["n_rays"] for j in jobs], [j["seed"] for j in jobs])
     # warm: the same kernels (two-pass for the large jobs, the hit queue at full size)
-    small = [min(n, 1 << 24) if n >= 1 << 22 else max(1, n // 100) for n in args[1]]
+    small = [min(n, 1 << 24) if n >= 1 << 18 else max(1, n // 100) for n in args[1]]
     H.heart_trace_batch(specs, args[0], small, args[2], imgs, stream=stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -163,7 +163,7 @@ def batched_measurement(H, W, torch, stream):
         s.close()
     return {"jobs": len(jobs), "rays": total, "seconds": sec, "rays_per_s": total / sec,
             "collisions_per_ray": sum(t["collisions"] for t in tl) / total,
-            "note": "one heart_trace_batch call: jobs of >= 2^22 rays as two-pass traces, the rest in one "
+            "note": "one heart_trace_batch call: jobs of >= 2^18 rays as two-pass traces, the rest in one "
                     "persistent launch (includes tally read-back)"}
 
 

@@ -313,7 +313,7 @@ heart_status heart_trace_records(heart_spectrometer *spec, const heart_source_de
                                  void *stream, heart_tally *out);
 
 /* Many spectrometers of uneven ray counts, FP32, on `stream`.  Jobs of fewer
- * than 2^22 rays (and jobs of several reflection orders) share one persistent
+ * than 2^18 rays share one persistent
  * launch (work items = (job, ray range) claimed by blocks); larger jobs run as
  * single-job two-pass traces, as heart_trace runs them, so a large job's image
  * and tallies equal its single trace.  specs[i], srcs[i], n_rays[i], seeds[i],
@@ -359,7 +359,7 @@ heart_status heart_autotune(heart_spectrometer *spec, const heart_source_desc *s
  * jobs, and allocates nothing on the device.  The caller still passes the
  * spectrometers (created beforehand), sources and device images, exactly as
  * for heart_trace_batch, and gets the same images and tallies for jobs below
- * 2^22 rays.  Every job runs on the persistent kernel here (the two-pass trace
+ * 2^18 rays.  Every job runs on the persistent kernel here (the two-pass trace
  * needs the hit queue), which for larger jobs follows heart_trace_batch's
  * two-pass trace up to rare rounding-level decision flips (<= 1e-4 of rays).
  *   - n_jobs > HEART_STATIC_MAX_JOBS returns HEART_EINVAL with a message.

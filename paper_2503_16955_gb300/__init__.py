@@ -418,7 +418,7 @@ def heart_trace_rays(spec, rays, seed, ray_offset, d_image, precision="fp32", re
 
 
 def heart_trace_batch(specs, sources, n_rays, seeds, d_images, stream=None):
-    """Many spectrometers, FP32: jobs below 2^22 rays in one persistent launch,
+    """Many spectrometers, FP32: jobs below 2^18 rays in one persistent launch,
     larger ones as two-pass traces (each equal to its single heart_trace)."""
     n = len(specs)
     srcs = [make_source(s) for s in sources]

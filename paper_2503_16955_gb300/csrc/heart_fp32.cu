@@ -2106,9 +2106,11 @@ static int resident_blocks() {
 
 // rays per work item: about eight items per resident block, a power of two
 // between 2^12 and the tuned maximum, so the last wave of items is short
+// work items of about 1/8 of a resident block's share of the launch, a power of two from 512 rays
+// (small launches, e.g. a served job alone in its round, still spread over the SMs) up to the tuned maximum
 static uint32_t chunk_for(uint64_t total_rays) {
     const uint64_t target = total_rays / ((uint64_t)resident_blocks() * 8ull);
-    uint32_t c = 4096u;
+    uint32_t c = 512u;
     while ((uint64_t)c * 2 <= target && c * 2 <= g_tune.chunk_rays) c *= 2;
     return c;
 }
@@ -2322,15 +2324,25 @@ size_t spectra_bytes(const std::vector<unsigned char> *spectra, int n) {
 heart_status launch_batch(const SpecParams *const *S, const SourceParams *P, const uint64_t *n_rays,
                           const uint64_t *seeds, const uint64_t *offsets, void *const *imgs, int n, void *dev,
                           std::vector<unsigned char> &host, cudaStream_t st, unsigned long long **tallies_dev,
-                          unsigned long long *const *tally_ptrs, const std::vector<unsigned char> *spectra) {
+                          unsigned long long *const *tally_ptrs, const std::vector<unsigned char> *spectra,
+                          unsigned char *pinned, size_t pinned_cap) {
     const size_t base = batch_bytes(n);
     const size_t total = base + spectra_bytes(spectra, n);
-    host.assign(total, 0);
-    Launch32 *jobs = (Launch32 *)host.data();
+    // the host image of the block: in the caller's pinned buffer when it is large enough
+    // (an asynchronous upload), else in `host` (pageable: staged before the copy returns)
+    unsigned char *hb;
+    if (pinned && pinned_cap >= total) {
+        hb = pinned;
+        std::memset(hb, 0, total);
+    } else {
+        host.assign(total, 0);
+        hb = host.data();
+    }
+    Launch32 *jobs = (Launch32 *)hb;
     const size_t off_cb = ((size_t)n * sizeof(Launch32) + 15) & ~(size_t)15;
     const size_t off_t = (off_cb + (size_t)(n + 1) * 8 + 15) & ~(size_t)15;
     const size_t off_c = off_t + (size_t)n * kTallyN * 8;
-    unsigned long long *cb = (unsigned long long *)(host.data() + off_cb);
+    unsigned long long *cb = (unsigned long long *)(hb + off_cb);
     unsigned char *d = (unsigned char *)dev;
     uint64_t all_rays = 0;
     bool ext = false;
@@ -2345,7 +2357,7 @@ heart_status launch_batch(const SpecParams *const *S, const SourceParams *P, con
         SourceParams Pi = P[i];
         if (spectra && !spectra[i].empty()) {
             // the job's tabulated spectrum rides after the work plan
-            std::memcpy(host.data() + sp_off, spectra[i].data(), spectra[i].size());
+            std::memcpy(hb + sp_off, spectra[i].data(), spectra[i].size());
             bind_spectrum(&Pi, d + sp_off);
             sp_off += (spectra[i].size() + 15) & ~(size_t)15;
         }
@@ -2358,8 +2370,7 @@ heart_status launch_batch(const SpecParams *const *S, const SourceParams *P, con
     }
     cb[n] = nch;
     *tallies_dev = (unsigned long long *)(d + off_t);
-    // the host block is pageable: the copy is staged before this call returns
-    cudaError_t e = cudaMemcpyAsync(dev, host.data(), total, cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(dev, hb, total, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "batch upload");
     if (nch == 0) return HEART_OK;
     WorkPlan W;

@@ -38,7 +38,7 @@ constexpr uint32_t kWaveMinCap = 1u << 20, kWaveMaxCap = 1u << 24;
 constexpr int kWaveGroup = 1024;
 // jobs of at least this many rays (one reflection order) run on the two-pass
 // trace in batches and in the request loop, as single traces do
-constexpr uint64_t kTwoPassMinRays = 1ull << 22;
+constexpr uint64_t kTwoPassMinRays = 1ull << 18;
 
 // the two-pass trace takes every FP32 image trace but user rays with several
 // reflection orders (those run on the persistent extended kernel)
@@ -83,7 +83,8 @@ heart_status launch_batch(const SpecParams *const *S, const SourceParams *P, con
                           const uint64_t *seeds, const uint64_t *offsets, void *const *imgs, int n, void *dev,
                           std::vector<unsigned char> &host, cudaStream_t st, unsigned long long **tallies_dev,
                           unsigned long long *const *tally_ptrs,
-                          const std::vector<unsigned char> *spectra = nullptr);
+                          const std::vector<unsigned char> *spectra = nullptr, unsigned char *pinned = nullptr,
+                          size_t pinned_cap = 0);
 }  // namespace heart
 
 struct heart_spectrometer {

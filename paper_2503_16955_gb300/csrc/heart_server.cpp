@@ -4,7 +4,7 @@
 // the memory cap; admitted jobs stay resident (tables in their spectrometer
 // handles, images and tallies here) until released.  A worker thread plans
 // rounds: every admitted, unfinished FP32 job gets a slice of its remaining
-// rays; the slices of jobs of 2^22 rays or more that the two-pass trace takes
+// rays; the slices of jobs of 2^18 rays or more that the two-pass trace takes
 // run as single-job two-pass launches, the others together in one persistent
 // batched launch.  Jobs that arrive
 // while a round is on the GPU join the next round, which is enqueued before
@@ -54,7 +54,9 @@ struct Job {
 struct Round {
     cudaEvent_t done = nullptr;
     void *dev = nullptr;                     // batch work plan block
-    std::vector<unsigned char> host;
+    std::vector<unsigned char> host;         // its host image if no pinned buffer was large enough
+    unsigned char *pin = nullptr;            // pinned host image of the block (asynchronous upload)
+    size_t pin_cap = 0;
     std::vector<uint64_t> ids;               // jobs with a slice in this round
     std::vector<bool> last;                  // the slice was the job's final one
 };
@@ -77,10 +79,35 @@ struct heart_server {
     uint64_t round_rays = 64ull << 20;       // target rays per round (about 20-40 ms of GPU work)
     uint64_t min_slice = 1ull << 20;
     uint64_t two_pass_min = heart::kTwoPassMinRays;   // jobs this large run their slices as two-pass launches
+    // pinned host buffers for the rounds' work plans (reused; a round holds one until it retires)
+    std::vector<std::pair<unsigned char *, size_t>> pins;
+    unsigned long long *tally_pin = nullptr;          // pinned read-back of finished jobs' tallies
+    size_t tally_pin_n = 0;
 };
 
 namespace heart {
 namespace {
+
+// a pinned host buffer of at least `bytes` from the server's free list (worker thread only)
+void take_pin(heart_server *s, size_t bytes, unsigned char **p, size_t *cap) {
+    for (size_t i = 0; i < s->pins.size(); ++i)
+        if (s->pins[i].second >= bytes) {
+            *p = s->pins[i].first;
+            *cap = s->pins[i].second;
+            s->pins.erase(s->pins.begin() + (long)i);
+            return;
+        }
+    size_t want = 64 << 10;
+    while (want < bytes) want <<= 1;
+    void *h = nullptr;
+    if (cudaHostAlloc(&h, want, cudaHostAllocDefault) != cudaSuccess) { *p = nullptr; *cap = 0; return; }
+    *p = (unsigned char *)h;
+    *cap = want;
+}
+
+void give_pin(heart_server *s, unsigned char *p, size_t cap) {
+    if (p) s->pins.push_back({p, cap});
+}
 
 // admit queued jobs while their images fit (called with the lock held)
 void admit(heart_server *s) {
@@ -117,24 +144,52 @@ void admit(heart_server *s) {
 
 void finish_round(heart_server *s, Round &r) {
     cudaEventSynchronize(r.done);
-    std::vector<unsigned long long> h(kTallyN);
+    give_pin(s, r.pin, r.pin_cap);
+    r.pin = nullptr;
+    // the finished jobs' tallies: one asynchronous copy each into pinned memory, one wait
+    std::vector<Job *> fin;
     std::unique_lock<std::mutex> lk(s->mu);
     for (size_t i = 0; i < r.ids.size(); ++i) {
         auto it = s->jobs.find(r.ids[i]);
         if (it == s->jobs.end()) continue;
         Job *j = it->second;
         --j->pending_rounds;
-        if (r.last[i] && j->state == ADMITTED) {
-            lk.unlock();
-            cudaMemcpyAsync(h.data(), j->d_tally, kTallyN * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                            s->copy_stream);
-            cudaStreamSynchronize(s->copy_stream);
-            lk.lock();
-            std::memcpy(&j->tally, h.data(), sizeof(heart_tally));
+        if (r.last[i] && j->state == ADMITTED) fin.push_back(j);
+    }
+    lk.unlock();
+    if (!fin.empty()) {
+        if (s->tally_pin_n < fin.size()) {
+            if (s->tally_pin) cudaFreeHost(s->tally_pin);
+            s->tally_pin = nullptr;
+            s->tally_pin_n = 0;
+            size_t want = 64;
+            while (want < fin.size()) want <<= 1;
+            void *h = nullptr;
+            if (cudaHostAlloc(&h, want * kTallyN * sizeof(unsigned long long), cudaHostAllocDefault) == cudaSuccess) {
+                s->tally_pin = (unsigned long long *)h;
+                s->tally_pin_n = want;
+            }
+        }
+        std::vector<unsigned long long> pageable;
+        unsigned long long *h = s->tally_pin;
+        if (!h) {
+            pageable.resize(fin.size() * kTallyN);
+            h = pageable.data();
+        }
+        for (size_t i = 0; i < fin.size(); ++i)
+            cudaMemcpyAsync(h + i * kTallyN, fin[i]->d_tally, kTallyN * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s->copy_stream);
+        cudaStreamSynchronize(s->copy_stream);
+        lk.lock();
+        const Clock::time_point now = Clock::now();
+        for (size_t i = 0; i < fin.size(); ++i) {
+            Job *j = fin[i];
+            std::memcpy(&j->tally, h + i * kTallyN, sizeof(heart_tally));
             j->status = j->tally.stuck > 0 ? HEART_ELIMIT : HEART_OK;
             j->state = DONE;
-            j->t_done = Clock::now();
+            j->t_done = now;
         }
+        lk.unlock();
     }
     cudaFreeAsync(r.dev, s->stream);
     cudaEventDestroy(r.done);
@@ -229,9 +284,11 @@ void worker_main(heart_server *s) {
                 const size_t bytes = batch_bytes((int)bS.size());
                 if (cudaMallocAsync(&r.dev, bytes, s->stream) != cudaSuccess) st = HEART_ENOMEM;
                 unsigned long long *unused = nullptr;
+                take_pin(s, bytes, &r.pin, &r.pin_cap);
                 if (st == HEART_OK)
                     st = launch_batch(bS.data(), bP.data(), bnr.data(), bseed.data(), boff.data(), bimg.data(),
-                                      (int)bS.size(), r.dev, r.host, s->stream, &unused, btl.data());
+                                      (int)bS.size(), r.dev, r.host, s->stream, &unused, btl.data(), nullptr, r.pin,
+                                      r.pin_cap);
             }
             for (Job *j : fp64_jobs) {
                 heart_status s2 = launch_fp64(j->spec->p, j->P, j->n, j->seed, 0, j->d_img, j->d_tally, nullptr,
@@ -293,6 +350,8 @@ extern "C" heart_status heart_server_destroy(heart_server *s) {
         if (kv.second->d_block) cudaFree(kv.second->d_block);
         delete kv.second;
     }
+    for (auto &pb : s->pins) cudaFreeHost(pb.first);
+    if (s->tally_pin) cudaFreeHost(s->tally_pin);
     cudaStreamDestroy(s->stream);
     cudaStreamDestroy(s->copy_stream);
     delete s;

@@ -64,13 +64,13 @@ def test_batch_alone_equals_mixed_and_matches_single_launches(H):
 
 
 def test_batch_large_jobs_equal_their_single_traces(H):
-    # jobs of 2^22 rays or more run as two-pass traces inside the batch: image and
+    # jobs of 2^18 rays or more run as two-pass traces inside the batch: image and
     # tallies equal to heart_trace of the same job; the small jobs in the same call
     # still equal the batch of themselves alone
     import torch
     jobs = _mix(4, 55, (1e4, 2e5))
     jobs[1]["n_rays"] = 5_000_000
-    jobs[2]["n_rays"] = 1 << 22
+    jobs[2]["n_rays"] = 1 << 18
     specs = [H.heart_spectrometer_create(j["spec"]) for j in jobs]
     imgs = [_img(H, s, torch) for s in specs]
     tall = H.heart_trace_batch(specs, [j["source"] for j in jobs], [j["n_rays"] for j in jobs],

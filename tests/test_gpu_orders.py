@@ -193,7 +193,7 @@ def test_fp32_orders_user_rays(H, polarised):
 
 def test_fp32_orders_batch_and_server_equal_single(H):
     # several orders on the two-pass trace (single traces, batch and served jobs of
-    # >= 2^22 rays) and on the persistent kernel (static batch, records): the two
+    # >= 2^18 rays) and on the persistent kernel (static batch, records): the two
     # kernels trace the same rays up to rare rounding-level flips
     import torch
     w = W.von_hamos_hapg()
