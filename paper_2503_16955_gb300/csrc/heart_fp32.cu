@@ -1640,7 +1640,7 @@ __device__ __forceinline__ float4 *wave_rec(const WaveBuf &B, size_t slot) {
 // energy is not positive and finite is queued as a dead record (no_bragg = 2)
 // that the walk counts as a miss.  Emitted rays and misses are tallied by the
 // walk pass from count and the queue length.
-constexpr int kSpawnThreads = 512, kSpawnWarps = kSpawnThreads / 32;
+constexpr int kSpawnThreads = 256, kSpawnWarps = kSpawnThreads / 32;
 // staged entered rays: sampled sources keep dA and the energy words (a0 a1 b2
 // b3); user-supplied rays, set up in full by spawn_user, keep A in dA and sB,
 // mu0, qr, inv_ws in the word slots, with E and no_bragg beside them
@@ -1657,7 +1657,7 @@ struct SpawnStage {
 // orders 1-3's anchors and sines and the no-Bragg mask, and the walk prepares the
 // entry segment of every order when it takes the ray
 template <int GEOM, bool POL, bool USER, bool ORD = false>
-__global__ void __launch_bounds__(kSpawnThreads) k_spawn32(const __grid_constant__ Launch32 L,
+__global__ void __launch_bounds__(kSpawnThreads, (USER || ORD) ? 4 : 8) k_spawn32(const __grid_constant__ Launch32 L,
                                                            const __grid_constant__ WaveBuf B, uint64_t first,
                                                            uint32_t count, unsigned long long *n_hits) {
     static_assert(!USER || POL, "user rays travel with their polarisation word");
