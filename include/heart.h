@@ -269,10 +269,12 @@ heart_status heart_spectrometer_destroy(heart_spectrometer *spec);
  * aligned to its element size).  precision selects the plain FP64 kernel or
  * the FP32 kernels.  If `out` is non-NULL the call synchronises `stream` and
  * fills the tallies; returns HEART_ELIMIT (after filling) if a ray hit the
- * collision cap.  FP32 traces of one reflection order with a rocking curve run
- * in two passes through a hit queue that the library keeps per device for the
- * process (up to 1.9 GB, allocated on first use, shared by all spectrometers;
- * such traces run one after another on the GPU whatever their streams). */
+ * collision cap.  FP32 image traces (all but user rays with several reflection
+ * orders) run in two passes through a hit queue that the library keeps per
+ * device for the process (two buffers, up to 3.8 GB, allocated on first use,
+ * shared by all spectrometers; such traces run one after another on the GPU
+ * whatever their streams, each on `stream` and a side stream of the library's
+ * that `stream` waits for before the call's work ends). */
 heart_status heart_trace(heart_spectrometer *spec, const heart_source_desc *src, uint64_t n_rays,
                          uint64_t seed, uint64_t ray_offset, void *d_image,
                          heart_precision precision, void *stream, heart_tally *out);

@@ -2166,6 +2166,10 @@ static heart_status launch_single(const SpecParams &S, const SourceParams &P, ui
     return rec ? dispatch<true>(L, W, st, false, ext) : dispatch<false>(L, W, st, false, ext);
 }
 
+// the current device's side stream and fork / join events of the two-pass
+// trace (created with its hit queue; used while the queue is leased)
+static void wave_side(cudaStream_t *side, cudaEvent_t *fork, cudaEvent_t *join);
+
 template <int GEOM, int IRC, bool POL = false, bool USER = false, bool ORD = false>
 static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t n, unsigned long long *ctr,
                                   cudaStream_t st) {
@@ -2177,21 +2181,47 @@ static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t 
     }
     const int walk_blocks = per_sm * num_sms();
     const uint64_t chunks = (n + B.cap - 1) / B.cap;
+    // consecutive chunks alternate between the queue's two buffers and between the caller's
+    // stream and a side stream, so a chunk's spawn pass fills the SMs that the previous
+    // chunk's walk pass frees as it drains; each stream keeps its own chunks in order (a
+    // buffer is reused two chunks later, on the same stream)
+    WaveBuf Bs[2] = {B, B};
+    Bs[1].base = (char *)B.base + wave_buffer_bytes(B.cap);
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (chunks > 1) wave_side(&side, &fork, &join);
+    const bool two = side && fork && join;
+    cudaError_t e = cudaSuccess;
     for (uint64_t c = 0; c < chunks; ++c) {
         const uint64_t g = c % kWaveGroup;
         if (g == 0) {
+            // the counters of a group of chunks: both streams are done with the previous group
+            if (two && c > 0) {
+                if ((e = cudaEventRecord(join, side)) != cudaSuccess) return cuda_fail(e, "two-pass join");
+                if ((e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess) return cuda_fail(e, "two-pass join");
+            }
             const uint64_t left = chunks - c < (uint64_t)kWaveGroup ? chunks - c : (uint64_t)kWaveGroup;
-            cudaError_t e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long) * left, st);
+            e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long) * left, st);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync hit counters");
+            if (two) {
+                if ((e = cudaEventRecord(fork, st)) != cudaSuccess) return cuda_fail(e, "two-pass fork");
+                if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return cuda_fail(e, "two-pass fork");
+            }
         }
         unsigned long long *cc = ctr + 2 * g;
         const uint64_t first = c * B.cap;
         const uint32_t count = (uint32_t)(n - first < B.cap ? n - first : B.cap);
-        k_spawn32<GEOM, POL, USER, ORD><<<(count + kSpawnThreads - 1) / kSpawnThreads, kSpawnThreads, 0, st>>>(
-            L, B, first, count, cc);
-        k_walk32<GEOM, IRC, OCC, POL, ORD><<<walk_blocks, kBlockThreads, 0, st>>>(L, B, cc, cc + 1, count);
+        const int b = two ? (int)(c & 1) : 0;
+        cudaStream_t sc = b ? side : st;
+        k_spawn32<GEOM, POL, USER, ORD><<<(count + kSpawnThreads - 1) / kSpawnThreads, kSpawnThreads, 0, sc>>>(
+            L, Bs[b], first, count, cc);
+        k_walk32<GEOM, IRC, OCC, POL, ORD><<<walk_blocks, kBlockThreads, 0, sc>>>(L, Bs[b], cc, cc + 1, count);
     }
-    cudaError_t e = cudaGetLastError();
+    if (two) {
+        if ((e = cudaEventRecord(join, side)) != cudaSuccess) return cuda_fail(e, "two-pass join");
+        if ((e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess) return cuda_fail(e, "two-pass join");
+    }
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "FP32 two-pass launch");
     return HEART_OK;
 }
@@ -2202,10 +2232,23 @@ struct DeviceWave {
     void *buf = nullptr;
     uint32_t cap = 0;
     cudaEvent_t done = nullptr;               // recorded after the queue's last user
+    cudaStream_t side = nullptr;              // the second stream of the two-pass trace
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 constexpr int kMaxDevices = 64;
 DeviceWave g_wave[kMaxDevices];
 }  // namespace
+
+static void wave_side(cudaStream_t *side, cudaEvent_t *fork, cudaEvent_t *join) {
+    int dev = 0;
+    *side = nullptr;
+    *fork = *join = nullptr;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
+    const DeviceWave &W = g_wave[dev];
+    *side = W.side;
+    *fork = W.fork;
+    *join = W.join;
+}
 
 heart_status wave_acquire(uint64_t n, cudaStream_t st, WaveLease *out) {
     int dev = 0;
@@ -2232,6 +2275,13 @@ heart_status wave_acquire(uint64_t n, cudaStream_t st, WaveLease *out) {
             return cuda_fail(e, "cudaMalloc hit queue");
         }
         W.cap = cap;
+    }
+    if (!W.side) {
+        // the side stream and its events (a failure leaves the trace on the caller's stream alone)
+        if (cudaStreamCreateWithFlags(&W.side, cudaStreamNonBlocking) != cudaSuccess) W.side = nullptr;
+        if (cudaEventCreateWithFlags(&W.fork, cudaEventDisableTiming) != cudaSuccess) W.fork = nullptr;
+        if (cudaEventCreateWithFlags(&W.join, cudaEventDisableTiming) != cudaSuccess) W.join = nullptr;
+        cudaGetLastError();
     }
     if ((e = cudaStreamWaitEvent(st, W.done, 0)) != cudaSuccess) { W.m.unlock(); return cuda_fail(e, "hit queue"); }
     out->buf = W.buf;
@@ -2266,7 +2316,7 @@ heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n,
     B.base = wave;
     B.cap = wave_cap;
     B.pad = 0;
-    unsigned long long *ctr = (unsigned long long *)((char *)wave + (size_t)16 * kWaveRecMax16 * wave_cap);
+    unsigned long long *ctr = (unsigned long long *)((char *)wave + 2 * wave_buffer_bytes(wave_cap));
     if (P.user) {
         // user-supplied rays (polarised or not): entered in FP64 by the spawn pass,
         // walked by the variant that carries p

@@ -31,9 +31,11 @@ int num_sms();
 heart_status launch_fp64(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
                          void *img, unsigned long long *tally, heart_ray_record *rec, cudaStream_t st,
                          const QeParams *qe = nullptr);
-// queue of prepared hits for the two-pass FP32 trace: chunks of `cap` rays
-// (a power of two from 2^20 to 2^24), one record per hit (96 bytes, 112 for a
-// polarised source), then 2 counters per chunk for kWaveGroup chunks
+// queue of prepared hits for the two-pass FP32 trace: two buffers of `cap`
+// rays each (a power of two from 2^20 to 2^24; consecutive chunks alternate
+// between them so that a chunk's spawn pass can overlap the previous chunk's
+// walk), one record per hit (96 bytes, 112 for a polarised source), then 2
+// counters per chunk for kWaveGroup chunks
 constexpr uint32_t kWaveMinCap = 1u << 20, kWaveMaxCap = 1u << 24;
 constexpr int kWaveGroup = 1024;
 // jobs of at least this many rays (one reflection order) run on the two-pass
@@ -45,7 +47,8 @@ constexpr uint64_t kTwoPassMinRays = 1ull << 18;
 inline bool takes_two_pass(const SpecParams &S, const SourceParams &P) { return !(P.user && S.n_orders > 1); }
 constexpr int kWaveRec16 = 6;                  // 16-byte words per queued hit (a 96-byte record)
 constexpr int kWaveRecMax16 = 7;               // with the polarisation word
-inline size_t wave_bytes(uint32_t cap) { return (size_t)16 * kWaveRecMax16 * cap + (size_t)2 * 8 * kWaveGroup; }
+inline size_t wave_buffer_bytes(uint32_t cap) { return (size_t)16 * kWaveRecMax16 * cap; }
+inline size_t wave_bytes(uint32_t cap) { return 2 * wave_buffer_bytes(cap) + (size_t)2 * 8 * kWaveGroup; }
 inline uint32_t wave_cap_for(uint64_t n) {
     uint32_t c = kWaveMinCap;
     while (c < kWaveMaxCap && (uint64_t)c < n) c <<= 1;
