@@ -153,6 +153,32 @@ def test_fp32_int64_image_and_chunking_invariance(H):
                              ta["exit_side"] + ta["capped"] + ta["stuck"])
 
 
+def test_multi_chunk_trace_on_two_streams_equals_single_chunk_calls(H):
+    # a trace of more than one hit-queue chunk alternates between the queue's two buffers
+    # and between the caller's stream and the library's side stream; the same rays traced
+    # one chunk per call (one buffer, one stream) give the same image and tallies, on the
+    # default stream and on a stream of the caller's
+    import torch
+    w = W.von_hamos_hapg()
+    s = H.heart_spectrometer_create(w["spec"])
+    chunk = 1 << 24
+    n = 3 * chunk + 12_345
+    for stream in (None, torch.cuda.Stream()):
+        a = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+        ta = H.heart_trace(s, w["source"], n, 9, 0, a, precision="fp32", stream=stream)
+        b = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+        parts = []
+        for off in range(0, n, chunk):
+            parts.append(H.heart_trace(s, w["source"], min(chunk, n - off), 9, off, b, precision="fp32",
+                                       stream=stream))
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+        for k in ("emitted", "miss", "absorbed", "exit_front", "exit_back", "exit_side", "det_hits", "collisions"):
+            assert ta[k] == sum(p[k] for p in parts), k
+        assert ta["emitted"] == n and ta["det_hits"] == int(a.sum()) > 1000
+    s.close()
+
+
 def test_two_pass_trace_equals_persistent_kernel_with_invalid_energies(H):
     # A Gaussian line 4 keV wide about 8 keV draws E <= 0 for ~2 % of the rays: such a ray is a
     # miss.  The image trace (two passes: entry, then the energy of the rays that entered, whose
