@@ -35,7 +35,7 @@ SM_COUNT = 152
 LANES_PER_SM_CLK = 128         # 4 SM sub-partitions x 32 lanes, one warp-instruction issue each per clock
 SM_MAX_MHZ = 2070.0
 # rays per chunk of the two-pass trace (the library's largest hit-queue chunk)
-WAVE_CHUNK = 1 << 24
+WAVE_CHUNK = 1 << 25
 # DRAM bytes (read + write) of the two passes per traced ray, from one ncu capture of the
 # spawn and walk kernels on 1.6e7 rays of the von Hamos workload (1219.1 MB: the hit queue
 # written and read back); valid only for the kernel sources with the hash below
@@ -149,7 +149,7 @@ def batched_measurement(H, W, torch, stream):
     imgs = [torch.zeros(s.shape, dtype=torch.int32, device="cuda") for s in specs]
     args = ([j["source"] for j in jobs], [j["n_rays"] for j in jobs], [j["seed"] for j in jobs])
     # warm: the same kernels (two-pass for the large jobs, the hit queue at full size)
-    small = [min(n, 1 << 24) if n >= 1 << 18 else max(1, n // 100) for n in args[1]]
+    small = [min(n, 1 << 25) if n >= 1 << 18 else max(1, n // 100) for n in args[1]]
     H.heart_trace_batch(specs, args[0], small, args[2], imgs, stream=stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -324,7 +324,7 @@ def features_measurement(H, W, torch, stream):
 def large_measurement(H, W, torch, stream):
     """The large single job: von Hamos R = 100 mm, Lorentzian mosaic, elastic +
     inelastic lines, 4096^2 int64 detector, 1e10 rays in one call (streamed by
-    the library in chunks of 2^24 rays), FP32; device-timed."""
+    the library in chunks of 2^25 rays), FP32; device-timed."""
     w = W.von_hamos_large()
     s = H.heart_spectrometer_create(w["spec"])
     img = torch.zeros(s.shape, dtype=torch.int64, device="cuda")
@@ -488,7 +488,7 @@ def main():
                          "traffic_note": "ncu dram__bytes_read+write of the step's launches, per step (hit "
                                          "queue written by the spawn pass and read by the walk pass; "
                                          "captured on 1.6e7 rays, scaled by rays)",
-                         "kernel": "k_spawn32 + k_walk32 (two passes per chunk of up to 2^24 rays)",
+                         "kernel": "k_spawn32 + k_walk32 (two passes per chunk of up to 2^25 rays)",
                          "peak_basis": "152 SMs x 128 lanes x 2070 MHz (max SM clock); algorithmic "
                                        "%d instr/collision + %d instr/segment + %d instr/ray"
                                        % (INSTR_PER_COLLISION, INSTR_PER_SEGMENT, INSTR_PER_RAY)},
