@@ -122,6 +122,16 @@ class MdfTable(C.Structure):
     _fields_ = [("body", C.c_double * MDF_M), ("tail", C.c_double * (MDF_T + 1)), ("qmax", C.c_double)]
 
 
+class SegInfo(C.Structure):
+    _fields_ = [("s_exit", C.c_double), ("face", C.c_int32), ("thinned", C.c_int32),
+                ("kN0", C.c_double), ("kN1", C.c_double), ("xstar", C.c_double), ("vstar", C.c_double),
+                ("irc_max", C.c_double), ("W0", C.c_double), ("none_qv", C.c_double), ("alpha0", C.c_double),
+                ("ra", C.c_double), ("qmin", C.c_double), ("pbar", C.c_double), ("S1", C.c_double),
+                ("S2", C.c_double), ("w0", C.c_uint64), ("wspan", C.c_uint64), ("lam", C.c_double),
+                ("mu", C.c_double), ("pa", C.c_double), ("wn", C.c_double), ("wf", C.c_double),
+                ("psis", C.c_double), ("pin", C.c_double), ("pio", C.c_double)]
+
+
 _lib = None
 
 
@@ -161,6 +171,7 @@ def lib():
             "orc_sample_crystallites": (C.c_int64, [C.POINTER(Spec), C.c_double, C.c_double,
                                                     C.c_int64, C.c_uint64, dp, dp]),
             "orc_reflection_rate": (C.c_double, [C.POINTER(Spec), C.c_double, C.c_double]),
+            "orc_segment_bounds": (C.c_int, [C.POINTER(Spec), C.c_int64, dp, dp, dp, C.c_int, C.POINTER(SegInfo)]),
             "orc_last_error": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -452,6 +463,22 @@ def sample_crystallites(spec_dict, E, alpha, n, seed):
 def reflection_rate(spec_dict, E, alpha):
     s = make_spec(spec_dict)
     return lib().orc_reflection_rate(C.byref(s), E, alpha)
+
+
+def segment_bounds(spec_dict, E, pos, direction, order=0):
+    """the thinned sampler's bounds of straight segments: E (n,), pos and
+    direction (n, 3); returns a dict of arrays of the SegInfo fields"""
+    s = make_spec(spec_dict)
+    E = np.ascontiguousarray(np.atleast_1d(np.asarray(E, dtype=np.float64)))
+    x = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))
+    k = np.ascontiguousarray(np.asarray(direction, dtype=np.float64).reshape(-1, 3))
+    n = len(E)
+    out = (SegInfo * n)()
+    dp = C.POINTER(C.c_double)
+    if lib().orc_segment_bounds(C.byref(s), n, E.ctypes.data_as(dp), x.ctypes.data_as(dp),
+                                k.ctypes.data_as(dp), int(order), out):
+        raise RuntimeError(_err())
+    return {f: np.array([getattr(out[i], f) for i in range(n)]) for f, _ in SegInfo._fields_}
 
 
 def n_threads_default():

@@ -256,6 +256,30 @@ int64_t orc_sample_crystallites(const orc_spec *s, double E_keV, double alpha_ra
  * summed over the reflection orders */
 double orc_reflection_rate(const orc_spec *s, double E_keV, double alpha_rad);
 
+/* The thinned sampler's bounds of straight segments (test support): segment i
+ * is a ray of energy E[i] at x[3i..] (inside or on the crystal) along
+ * k[3i..], reflection order h; out[i] receives its bounds.  The
+ * candidates the thinned walk never draws are those with v >= v* and either a
+ * table word below w0 (tilt q below qmin), q above 2 - qmin, or an azimuth
+ * outside the arcs where |k.n| lies in (S1, S2); without a rocking curve, the
+ * facing cone's candidates outside |psi| < psis and the bounds wn, wf of
+ * W / W(0) on the two cones.  Plain sampler or a segment near the Bragg angle:
+ * ra = 1 (every candidate drawn). */
+typedef struct {
+    double s_exit;                /* distance to the first boundary crossing */
+    int32_t face, thinned;        /* exit face; 1 if the thinned bounds apply to this order */
+    double kN0, kN1;              /* k.N at the segment's start and exit */
+    double xstar, vstar;          /* the spectrometer's X* (this order's width) and v* */
+    double irc_max, W0, none_qv;  /* max R, W(0), the tilt beyond which W / W(0) <= v* */
+    double alpha0;                /* aB + Delta_M of the order */
+    double ra, qmin, pbar, S1, S2;
+    uint64_t w0, wspan;
+    double lam, mu, pa;           /* the order's candidate rate; the segment's majorant, mu0 / mu */
+    double wn, wf, psis, pin, pio;
+} orc_seg_info;
+int orc_segment_bounds(const orc_spec *s, int64_t n, const double *E_keV, const double *x, const double *k,
+                       int h, orc_seg_info *out);
+
 const char *orc_last_error(void);
 
 #ifdef __cplusplus

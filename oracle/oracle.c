@@ -1549,6 +1549,61 @@ int orc_walk_injected(const orc_spec *s, double E, const double pos[3], const do
     return orc_walk_injected_n(s, 1, &E, pos, dir, pol, words, n_words, rec);
 }
 
+/* the thinned sampler's bounds of straight segments, for tests of its exactness */
+int orc_segment_bounds(const orc_spec *s, int64_t n, const double *E, const double *xs, const double *ks, int h,
+                       orc_seg_info *outs) {
+    geom g;
+    if (geom_init(&g, s)) return -1;
+    orc_mdf_table *tab = (orc_mdf_table *)malloc(sizeof(orc_mdf_table));
+    if (!tab) return fail("out of memory");
+    if (orc_mdf_build_table(s, tab)) { free(tab); return -1; }
+    g.mdf = tab;
+    for (int64_t i = 0; i < n; ++i) {
+        const double *x = xs + 3 * i, *k = ks + 3 * i;
+        orc_seg_info *out = outs + i;
+        memset(out, 0, sizeof *out);
+        orc_ray_consts rc;
+        ray_constants(s, E[i], g.none_fac, &rc);
+        if (h < 0 || h >= rc.n_orders) { free(tab); return fail("order out of range"); }
+        int face;
+        out->s_exit = exit_distance(&g, x, k, &face);
+        out->face = face;
+        double xe[3], N0[3], N1[3], t1[3], t2[3];
+        for (int j = 0; j < 3; ++j) xe[j] = x[j] + out->s_exit * k[j];
+        local_frame(&g, x, N0, t1, t2);
+        local_frame(&g, xe, N1, t1, t2);
+        out->kN0 = dot3(k, N0);
+        out->kN1 = dot3(k, N1);
+        seg_bound sb;
+        bound_segment(&g, &rc, x, k, &sb);
+        const order_bound *b = &sb.o[h];
+        out->xstar = g.xstar * rc.ord_w[h];
+        out->vstar = g.vstar;
+        out->irc_max = g.irc_max;
+        out->W0 = g.W0;
+        out->none_qv = g.none_qv;
+        out->alpha0 = rc.ord_alpha[h] + rc.shift_rad;
+        out->thinned = b->ra < 1.0 || (g.irc_none && s->sampler == ORC_SAMPLER_THINNED && rc.ord_qr[h] > 0);
+        out->ra = b->ra;
+        out->qmin = b->qmin;
+        out->pbar = b->pbar;
+        out->S1 = b->S1;
+        out->S2 = b->S2;
+        out->w0 = b->w0;
+        out->wspan = b->wspan;
+        out->lam = b->lam;
+        out->mu = sb.mu;
+        out->pa = sb.pa;
+        out->wn = b->wn;
+        out->wf = b->wf;
+        out->psis = b->psis;
+        out->pin = b->pin;
+        out->pio = b->pio;
+    }
+    free(tab);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* accepted crystallites at fixed incidence (flat frame N = z, k in x-z) */
 /* ------------------------------------------------------------------ */

@@ -270,3 +270,49 @@ def test_appendix_bragg_angle_is_graphite_at_8_5_keV():
     # the appendix's alpha_B = 0.2192 rad is graphite (002) near 8.5 keV
     c = ob.ray_constants(_spec(), 8.5)
     assert c["alpha_B"] == pytest.approx(printed_values()["appendix_alpha_B"][0], abs=1e-4)
+
+
+# --------------------------------------------------------------------------
+# the reflectivity constant Q (Sec. 2.2.3, Eq. ZachReflXsec) from a Darwin width
+# --------------------------------------------------------------------------
+R_E_MM = 2.8179403262e-12          # classical electron radius (CODATA 2018), mm
+
+
+def test_reflectivity_constant_of_the_flat_hopg_workload():
+    """The flat HOPG workload gives its reflection strength as a Darwin FWHM of 20 urad
+    at 8 keV on graphite (002).  Two textbook relations of the kinematic/dynamical
+    theory fix Q from it, independently of how the oracle arranges them: the Darwin
+    curve's total-reflection plateau has half-width delta = r_e lambda^2 |F| / (pi V
+    sin 2 aB) (Darwin; Zachariasen; Als-Nielsen & McMorrow, ch. 6) and FWHM
+    3 delta / sqrt(2) (the curve (|y| - sqrt(y^2 - 1))^2 halves at |y| = 3 / (2 sqrt 2));
+    the mosaic cross-section constant is Q = |r_e F / V|^2 lambda^3 / sin 2 aB (Sec.
+    2.2.3, Eq. ZachReflXsec).  Hence delta = 9.43 urad and Q = 2.54e-3 / mm, the
+    value written down from these relations before the oracle existed."""
+    w = W.flat_hopg_mono()
+    c = ob.ray_constants(w["spec"], 8.0)
+    lam_mm = 12.398419843320026 / 8.0 * 1e-7
+    s2 = math.sin(2.0 * math.asin(lam_mm * 1e7 / (2.0 * 3.354)))
+    delta = 20e-6 / (3.0 / math.sqrt(2.0))
+    F_over_V = delta * math.pi * s2 / (R_E_MM * lam_mm ** 2)       # |F| / V, mm^-3
+    Q = (R_E_MM * F_over_V) ** 2 * lam_mm ** 3 / s2
+    assert delta == pytest.approx(9.43e-6, rel=1e-3)
+    assert Q == pytest.approx(2.54e-3, rel=3e-3)
+    assert c["Q"] == pytest.approx(Q, rel=1e-12)
+    # the same constant given directly as K = |r_e F / V| reproduces it
+    direct = dict(w["spec"], refl_K_per_mm2=R_E_MM * F_over_V)
+    assert ob.ray_constants(direct, 8.0)["Q"] == pytest.approx(Q, rel=1e-12)
+
+
+def test_reflectivity_constant_scales_as_lambda_cubed_over_sin_2_theta():
+    # F_H does not depend on the energy in this model, so Q(E) = K^2 lambda^3 / sin 2 aB(E)
+    s = W.flat_hopg_mono()["spec"]
+    E = [6.5, 8.0, 11.0]
+    Q = [ob.ray_constants(s, e)["Q"] for e in E]
+    for e, q in zip(E[1:], Q[1:]):
+        lam0, lam = 12.398419843320026 / E[0], 12.398419843320026 / e
+        s0 = math.sin(2.0 * math.asin(lam0 / (2.0 * 3.354)))
+        s1 = math.sin(2.0 * math.asin(lam / (2.0 * 3.354)))
+        assert q / Q[0] == pytest.approx((lam / lam0) ** 3 * s0 / s1, rel=1e-12)
+    # the majorant carries Q R_max (R of unit area peaks at its maximum)
+    c = ob.ray_constants(s, 8.0)
+    assert c["mubar"] == pytest.approx(c["mu0"] + c["Q"] * ob.irc_max(s), rel=1e-12)
