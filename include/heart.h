@@ -163,8 +163,10 @@ typedef struct {
      * d_spacing_A / order_m[h] with K_h = order_K_rel[h] K and a rocking curve
      * order_w_rel[h] times as wide (same shape and unit area).  A scatter
      * candidate picks its order by the order's share of the candidate rate.
-     * Both precisions take up to HEART_MAX_ORDERS; FP32 traces with several
-     * orders run on the persistent batched kernel (not the two-pass trace). */
+     * Both precisions take up to HEART_MAX_ORDERS.  FP32 traces of sampled
+     * sources with several orders run on the two-pass trace; user-supplied
+     * rays with several orders, and batched jobs below 2^18 rays, on the
+     * persistent kernel. */
     int32_t n_orders;
     int32_t reserved2;
     int32_t order_m[4];
@@ -292,6 +294,21 @@ heart_status heart_trace_energy(heart_spectrometer *spec, const heart_source_des
                                 const heart_qe_table *qe, heart_precision precision, void *stream,
                                 heart_tally *out);
 
+/* Calibration map of the detector (Sec. 3: the energy dispersion of a
+ * spectrometer, traced with a flat spectrum): the geometry of `src` (origin,
+ * cone, spot, polarisation; its spectral components are ignored) with one
+ * uniform component on [min_keV, max_keV], traced as heart_trace_energy with
+ * QE = 1 into d_counts (the handle's count type) and d_energy_image (uint64,
+ * 1e-6 keV units), both device, det_ny x det_nx, added to (+=); then
+ * d_mean_keV (device, double, det_ny x det_nx, overwritten) receives each
+ * pixel's mean energy, energy / counts, NaN where no photon landed.  Pass
+ * zeroed images for a map of this trace alone.  If `out` is non-NULL the call
+ * synchronises and fills the tallies. */
+heart_status heart_calibration_map(heart_spectrometer *spec, const heart_source_desc *src, double min_keV,
+                                   double max_keV, uint64_t n_rays, uint64_t seed, heart_precision precision,
+                                   void *d_counts, uint64_t *d_energy_image, double *d_mean_keV, void *stream,
+                                   heart_tally *out);
+
 /* Trace user-supplied rays (heart_ray_arrays, device memory) instead of a
  * sampled source; the walk, detector and tallies are those of heart_trace.
  * Polarised rays use G = 1 - (p . k_s)^2 (Eq. G_pol) and the polarisation
@@ -330,18 +347,18 @@ heart_status heart_trace_batch(heart_spectrometer *const *specs, const heart_sou
 typedef struct {
     int32_t blocks_per_sm;          /* persistent kernel: resident 128-thread blocks per SM, 6 (80
                                        registers) or 5 (96) */
-    int32_t refill_lanes;           /* a warp pops queued or spawned rays when this many lanes are idle */
+    int32_t refill_lanes;           /* a warp takes queued or spawned rays when this many lanes are idle */
     uint32_t max_chunk_rays;        /* largest work item (rays) a block of the persistent kernel claims */
     int32_t reserved;
     double rays_per_s;              /* this trace's rate on the probe with the chosen refill threshold */
 } heart_tune;
 
 /* Time FP32 traces of probe_rays rays of this spectrometer and source: first
- * the refill threshold (4, 8 or 16 idle lanes) on the path this trace takes
+ * the refill threshold (1, 4, 8 or 16 idle lanes) on the path this trace takes
  * (the two-pass trace for image traces it covers), then the persistent
- * kernel's blocks per SM (6 or 5), which batched and served jobs and per-ray
- * records use, on that kernel.  The fastest choices hold for all later FP32
- * launches of the process.  Call it before tracing, not concurrently with
+ * kernel's blocks per SM (6 or 5), which batched jobs below 2^18 rays and
+ * served slices use, on that kernel.  The fastest choices hold for all later
+ * FP32 launches of the process.  Call it before tracing, not concurrently with
  * traces.  Uses the handle's scratch image; `out` (may be NULL) receives the
  * choice. */
 heart_status heart_autotune(heart_spectrometer *spec, const heart_source_desc *src, uint64_t probe_rays,
@@ -359,18 +376,21 @@ heart_status heart_autotune(heart_spectrometer *spec, const heart_source_desc *s
  * counter, tallies); this variant uses a fixed work area in a device array
  * that the library declares at file scope, sized for HEART_STATIC_MAX_JOBS
  * jobs, and allocates nothing on the device.  The caller still passes the
- * spectrometers (created beforehand), sources and device images, exactly as
- * for heart_trace_batch, and gets the same images and tallies for jobs below
- * 2^18 rays.  Every job runs on the persistent kernel here (the two-pass trace
- * needs the hit queue), which for larger jobs follows heart_trace_batch's
- * two-pass trace up to rare rounding-level decision flips (<= 1e-4 of rays).
+ * spectrometers (created beforehand), sources and device images, as for
+ * heart_trace_batch, and gets the same images and tallies: every job runs on
+ * the persistent kernel here (the two-pass trace needs the hit queue), which
+ * traces each ray as the two-pass trace does.
  *   - n_jobs > HEART_STATIC_MAX_JOBS returns HEART_EINVAL with a message.
+ *   - Sources with a tabulated-spectrum component (HEART_SRC_TABLE) return
+ *     HEART_EINVAL: their table needs a device copy this call cannot make.
  *   - Every GPU that loads the library holds the array until the process exits.
  *   - All calls share the array; each call rewrites it (tallies and the work
  *     counter start at zero), so calls that overlap on the GPU race: serialise
  *     them on one stream.  Host staging is serialised by a lock.
+ *   - The work area is uploaded from pageable host memory, so the call may
+ *     wait for earlier work on `stream` before it returns.
  *   - The first call on each device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *     that device current), so it should come before any stream capture.
  * If `out` is non-NULL the call synchronises `stream` and fills n_jobs tallies. */
 heart_status heart_trace_batch_static(heart_spectrometer *const *specs, const heart_source_desc *const *srcs,
                                       const uint64_t *n_rays, const uint64_t *seeds, void *const *d_images,
@@ -393,6 +413,48 @@ heart_status heart_release(heart_server *server, uint64_t job_id);
 heart_status heart_fetch_image(heart_server *server, uint64_t job_id, void *dst, int32_t dst_is_host);
 /* Seconds from heart_submit to completion, measured by the server (finished jobs). */
 heart_status heart_job_latency(heart_server *server, uint64_t job_id, double *seconds);
+
+/* Issue rates of the SM pipes the ray path runs on (measurement support; the
+ * paper has no counterpart).  The ray kernels issue integer (Philox), FP32 and
+ * SFU instructions and are bound by those pipes, not by memory, so their
+ * roofline is the rate each pipe sustains.  heart_pipe_peaks runs one
+ * microbenchmark kernel per instruction below (eight dependent chains per
+ * thread, 32 resident warps per SM, inline PTX so the instruction is the one
+ * named) and reports, per instruction, warp instructions per second for the
+ * whole GPU (CUDA events) and per SM per clock (clock64 in every block), and
+ * the mean SM clock the runs saw.  It takes about 0.1 s, allocates a few MB
+ * of device memory for its own use and synchronises `stream`. */
+enum {
+    HEART_PIPE_FFMA = 0,       /* fma.rn.f32                       */
+    HEART_PIPE_LOP3 = 1,       /* lop3.b32 (three-input logic)     */
+    HEART_PIPE_IADD3 = 2,      /* add.u32                          */
+    HEART_PIPE_IMAD = 3,       /* mad.lo.u32                       */
+    HEART_PIPE_IMAD_HI = 4,    /* mul.hi.u32 (Philox's multiply)   */
+    HEART_PIPE_IMAD_WIDE = 5,  /* mul.wide.u32                     */
+    HEART_PIPE_MUFU_RSQ = 6,   /* rsqrt.approx.ftz.f32 (SFU)       */
+    HEART_PIPE_MUFU_EX2 = 7,   /* ex2.approx.ftz.f32 (SFU)         */
+    HEART_PIPE_MUFU_LG2 = 8,   /* lg2.approx.ftz.f32 (SFU)         */
+    HEART_PIPE_DFMA = 9,       /* fma.rn.f64                       */
+    HEART_PIPE_NOPS = 10
+};
+typedef struct {
+    double warp_inst_per_s[HEART_PIPE_NOPS];      /* whole GPU, at the clocks of the run */
+    double warp_inst_per_clk_sm[HEART_PIPE_NOPS]; /* per SM per SM clock                 */
+    double sm_clock_hz;                           /* mean SM clock during the runs        */
+    int32_t sms;
+    int32_t n_ops;
+} heart_pipe_rates;
+heart_status heart_pipe_peaks(void *stream, heart_pipe_rates *out);
+
+/* Test support (no counterpart in the paper): device functions of the FP32
+ * kernels evaluated on n values of the device arrays d_x (and d_y), results in
+ * d_out (device, n floats); asynchronous on `stream`.  which = 0: the arccos
+ * of the azimuth arcs, acos(x / y) for y > 0 (spec may be NULL); 1: the
+ * spectrometer's rocking curve divided by its maximum, R(x) / R_max at
+ * x = Delta - Delta_M; 2: the upper bound of R / R_max over |x'| >= x that the
+ * kernels' early rejection uses. */
+heart_status heart_check_functions(heart_spectrometer *spec, int32_t which, const float *d_x, const float *d_y,
+                                   float *d_out, uint64_t n, void *stream);
 
 const char *heart_last_error(void);
 

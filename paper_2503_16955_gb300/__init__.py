@@ -115,6 +115,15 @@ class heart_tune(C.Structure):
                 ("reserved", C.c_int32), ("rays_per_s", C.c_double)]
 
 
+PIPE_OPS = ["ffma", "lop3", "iadd3", "imad", "imad_hi", "imad_wide", "mufu_rsq", "mufu_ex2", "mufu_lg2", "dfma"]
+
+
+class heart_pipe_rates(C.Structure):
+    _fields_ = [("warp_inst_per_s", C.c_double * len(PIPE_OPS)),
+                ("warp_inst_per_clk_sm", C.c_double * len(PIPE_OPS)),
+                ("sm_clock_hz", C.c_double), ("sms", C.c_int32), ("n_ops", C.c_int32)]
+
+
 RECORD_DTYPE = np.dtype([
     ("ray_id", np.uint64), ("outcome", np.int32), ("nrefl", np.int32), ("ncoll", np.int64),
     ("energy_keV", np.float64), ("pos", np.float64, 3), ("dir", np.float64, 3),
@@ -126,7 +135,7 @@ EXPORTS = ["heart_spectrometer_create", "heart_spectrometer_destroy", "heart_tra
            "heart_trace_host", "heart_trace_rays",
            "heart_trace_records", "heart_trace_batch", "heart_trace_batch_static", "heart_autotune", "heart_server_create", "heart_server_destroy",
            "heart_submit", "heart_poll", "heart_release", "heart_fetch_image", "heart_job_latency",
-           "heart_last_error"]
+           "heart_pipe_peaks", "heart_calibration_map", "heart_check_functions", "heart_last_error"]
 
 
 class HeartError(RuntimeError):
@@ -172,6 +181,10 @@ def library(path=None):
     L.heart_release.argtypes = [vp, u64]
     L.heart_job_latency.argtypes = [vp, u64, C.POINTER(C.c_double)]
     L.heart_fetch_image.argtypes = [vp, u64, vp, i32]
+    L.heart_pipe_peaks.argtypes = [vp, C.POINTER(heart_pipe_rates)]
+    L.heart_check_functions.argtypes = [vp, i32, vp, vp, vp, u64, vp]
+    L.heart_calibration_map.argtypes = [vp, C.POINTER(heart_source_desc), C.c_double, C.c_double, u64, u64, i32,
+                                        vp, vp, vp, vp, C.POINTER(heart_tally)]
     L.heart_last_error.restype = C.c_char_p
     for name in EXPORTS:
         if name != "heart_last_error":
@@ -339,18 +352,29 @@ def heart_trace_energy(spec, source, n_rays, seed, ray_offset, d_image, d_energy
     return t.as_dict()
 
 
-def calibration_map(spec, source, min_keV, max_keV, n_rays, seed, precision="fp32", stream=None):
+def heart_calibration_map(spec, source, min_keV, max_keV, n_rays, seed, precision="fp32", stream=None):
     """Energy dispersion of the detector (Sec. 3): the source geometry with a
     uniform spectrum on [min_keV, max_keV]; returns (mean keV per pixel as a
-    float64 CUDA tensor, NaN where no photon landed; count image)."""
+    float64 CUDA tensor, NaN where no photon landed; count image; tallies).
+    The division runs in the library (heart_calibration_map)."""
     import torch
-    src = dict(source)
-    src["components"] = [dict(kind="uniform", lo_keV=min_keV, hi_keV=max_keV, weight=1.0)]
+    src = make_source(source)
     counts = torch.zeros(spec.shape, dtype=torch.int64 if spec.count_dtype == "int64" else torch.int32,
                          device="cuda")
     energy = torch.zeros(spec.shape, dtype=torch.int64, device="cuda")
-    heart_trace_energy(spec, src, n_rays, seed, 0, counts, energy, None, precision, stream)
-    mean = energy.to(torch.float64) * 1e-6 / counts.to(torch.float64)
+    mean = torch.empty(spec.shape, dtype=torch.float64, device="cuda")
+    t = heart_tally()
+    st = library().heart_calibration_map(spec.handle, C.byref(src), float(min_keV), float(max_keV), int(n_rays),
+                                         int(seed), PRECISION[precision], C.c_void_p(counts.data_ptr()),
+                                         C.c_void_p(energy.data_ptr()), C.c_void_p(mean.data_ptr()),
+                                         C.c_void_p(_stream_ptr(stream)), C.byref(t))
+    _check(st, allow=(0, 6))
+    return mean, counts, t.as_dict()
+
+
+def calibration_map(spec, source, min_keV, max_keV, n_rays, seed, precision="fp32", stream=None):
+    """(mean keV per pixel, count image) of heart_calibration_map"""
+    mean, counts, _ = heart_calibration_map(spec, source, min_keV, max_keV, n_rays, seed, precision, stream)
     return mean, counts
 
 
@@ -365,8 +389,11 @@ def heart_trace_host(spec, source, n_rays, seed, ray_offset, h_image, precision=
     return t.as_dict()
 
 
-def heart_trace_records(spec, source, n_rays, seed, ray_offset=0, precision="fp64", d_image=None, stream=None):
-    """Per-ray records (numpy structured array) and tallies."""
+def heart_trace_records(spec, source, n_rays, seed, ray_offset=0, precision="fp64", d_image=None, stream=None,
+                        on_device=False):
+    """Per-ray records (numpy structured array) and tallies.  on_device: return
+    the records as a CUDA uint8 tensor instead (decode slices with
+    records_from_device), for traces too large to copy whole."""
     import torch
     src = make_source(source)
     t = heart_tally()
@@ -376,8 +403,16 @@ def heart_trace_records(spec, source, n_rays, seed, ray_offset=0, precision="fp6
                                        PRECISION[precision], C.c_void_p(rec.data_ptr()),
                                        C.c_void_p(_stream_ptr(stream)), C.byref(t))
     _check(st, allow=(0, 6))
+    if on_device:
+        return rec, t.as_dict()
     out = np.frombuffer(rec.cpu().numpy().tobytes(), dtype=RECORD_DTYPE)
     return out, t.as_dict()
+
+
+def records_from_device(rec, first, count):
+    """records first .. first + count - 1 of a device record tensor (heart_trace_records(on_device=True))"""
+    b = RECORD_DTYPE.itemsize
+    return np.frombuffer(rec[first * b:(first + count) * b].cpu().numpy().tobytes(), dtype=RECORD_DTYPE)
 
 
 def heart_trace_rays(spec, rays, seed, ray_offset, d_image, precision="fp32", records=False, stream=None):
@@ -434,6 +469,36 @@ def heart_trace_batch(specs, sources, n_rays, seeds, d_images, stream=None):
 
 
 STATIC_MAX_JOBS = 64
+
+
+CHECK_FUNCTIONS = {"acos_ratio": 0, "irc_rel": 1, "irc_bound": 2}
+
+
+def heart_check_functions(spec, which, x, y=None):
+    """a device function of the FP32 kernels on float32 CUDA tensors (tests)"""
+    import torch
+    x = x.contiguous()
+    out = torch.empty_like(x)
+    st = library().heart_check_functions(spec.handle if spec is not None else None, CHECK_FUNCTIONS[which],
+                                         C.c_void_p(x.data_ptr()),
+                                         C.c_void_p(y.contiguous().data_ptr()) if y is not None else None,
+                                         C.c_void_p(out.data_ptr()), x.numel(),
+                                         C.c_void_p(_stream_ptr(None)))
+    _check(st)
+    torch.cuda.synchronize()
+    return out
+
+
+def heart_pipe_peaks(stream=None):
+    """Issue rates of the FP32, integer, SFU and FP64 pipes on this GPU (one
+    microbenchmark kernel per instruction): {op: (warp instructions per second,
+    warp instructions per SM per clock)} plus the SM clock and SM count."""
+    r = heart_pipe_rates()
+    _check(library().heart_pipe_peaks(C.c_void_p(_stream_ptr(stream)), C.byref(r)))
+    out = {op: (r.warp_inst_per_s[i], r.warp_inst_per_clk_sm[i]) for i, op in enumerate(PIPE_OPS)}
+    out["sm_clock_hz"] = r.sm_clock_hz
+    out["sms"] = r.sms
+    return out
 
 
 def heart_autotune(spec, source, probe_rays=1 << 24, stream=None):

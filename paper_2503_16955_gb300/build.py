@@ -53,8 +53,11 @@ def build(force=False, verbose=False):
         if os.path.basename(src) == "heart_fp32.cu":
             # the FP32 kernel forms only small quantities where precision matters
             # (see its header); approximate division / square root and flushing
-            # denormals do not move any decision beyond its stated tolerances
-            cmd += ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+            # denormals do not move any decision beyond its stated tolerances.
+            # No contraction of a * b + c beyond the fused multiply-adds the source
+            # writes out: every kernel that runs a device function then rounds it
+            # the same way, so the FP32 kernels trace a ray bit for bit alike.
+            cmd += ["-ftz=true", "-prec-div=false", "-prec-sqrt=false", "-fmad=false"]
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-v"] if verbose else []
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -1,6 +1,8 @@
 // heart_api.cu -- the C ABI entry points and the plain FP64 kernel.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -305,20 +307,20 @@ static heart_status trace_impl(heart_spectrometer *h, const heart_source_desc *s
     }
     if (prec == HEART_FP64) {
         st = launch_fp64(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, (heart_ray_record *)d_records, cs, qe);
+    } else if (takes_two_pass(h->p, P)) {
+        // the two-pass trace runs on the device's shared hit queue (leased while enqueued);
+        // records, when asked for, come from the same kernels
+        WaveLease lease;
+        st = wave_acquire(n_rays, cs, &lease);
+        if (st != HEART_OK) return st;
+        st = launch_fp32(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, cs, qe, lease.buf, lease.cap,
+                         (heart_ray_record *)d_records);
+        wave_release(lease, cs);
     } else if (d_records) {
         st = launch_fp32_records(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, (heart_ray_record *)d_records,
                                  cs, qe);
     } else {
-        // the two-pass trace runs on the device's shared hit queue (leased while enqueued)
-        if (takes_two_pass(h->p, P)) {
-            WaveLease lease;
-            st = wave_acquire(n_rays, cs, &lease);
-            if (st != HEART_OK) return st;
-            st = launch_fp32(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, cs, qe, lease.buf, lease.cap);
-            wave_release(lease, cs);
-        } else {
-            st = launch_fp32(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, cs, qe);
-        }
+        st = launch_fp32(h->p, P, n_rays, seed, ray_offset, img, h->d_scratch, cs, qe);
     }
     if (st != HEART_OK) return st;
     if (out || sync) {
@@ -390,6 +392,58 @@ extern "C" heart_status heart_trace_energy(heart_spectrometer *h, const heart_so
     heart_status st = build_qe_params(qe, (unsigned long long *)d_energy_image, &Q, err, (int)sizeof err);
     if (st != HEART_OK) return fail(st, err);
     return trace_impl(h, src, n_rays, seed, ray_offset, d_image, precision, nullptr, stream, out, false, &Q);
+}
+
+// mean keV per pixel of a calibration trace: energy (1e-6 keV units) / counts,
+// NaN where no photon landed
+template <typename CountT>
+__global__ void k_mean_energy(const CountT *counts, const unsigned long long *energy, double *mean, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const CountT c = counts[i];
+        mean[i] = c > 0 ? (double)energy[i] * 1e-6 / (double)c : __longlong_as_double(0x7ff8000000000000LL);
+    }
+}
+
+extern "C" heart_status heart_calibration_map(heart_spectrometer *h, const heart_source_desc *src, double min_keV,
+                                              double max_keV, uint64_t n_rays, uint64_t seed,
+                                              heart_precision precision, void *d_counts, uint64_t *d_energy_image,
+                                              double *d_mean_keV, void *stream, heart_tally *out) {
+    if (!h) return fail(HEART_EINVAL, "null spectrometer");
+    if (!src) return fail(HEART_EINVAL, "null source");
+    if (!(min_keV > 0) || !(max_keV > min_keV) || !std::isfinite(max_keV))
+        return fail(HEART_EINVAL, "calibration range needs 0 < min_keV < max_keV");
+    const size_t elt = h->p.count_type == HEART_COUNT_I64 ? 8 : 4;
+    if (!d_counts || ((uintptr_t)d_counts % elt) != 0) return fail(HEART_EINVAL, "null or misaligned count image");
+    if (!d_mean_keV || ((uintptr_t)d_mean_keV % 8) != 0) return fail(HEART_EINVAL, "null or misaligned mean image");
+    // the source's geometry with one uniform component on [min_keV, max_keV] (Sec. 3)
+    heart_source_desc cal = *src;
+    heart_spectral_component uni;
+    std::memset(&uni, 0, sizeof uni);
+    uni.kind = HEART_SRC_UNIFORM;
+    uni.lo_keV = min_keV;
+    uni.hi_keV = max_keV;
+    uni.weight = 1.0;
+    cal.components = &uni;
+    cal.n_components = 1;
+    cal.table_keV = nullptr;
+    cal.table_pdf = nullptr;
+    cal.n_table = 0;
+    heart_status st = heart_trace_energy(h, &cal, n_rays, seed, 0, d_counts, d_energy_image, nullptr, precision,
+                                         stream, out);
+    if (st != HEART_OK && st != HEART_ELIMIT) return st;
+    const size_t n = (size_t)h->p.nx * (size_t)h->p.ny;
+    const int threads = 256;
+    const int blocks = (int)std::min<size_t>((n + threads - 1) / threads, (size_t)num_sms() * 8);
+    cudaStream_t cs = (cudaStream_t)stream;
+    if (h->p.count_type == HEART_COUNT_I64)
+        k_mean_energy<long long><<<blocks, threads, 0, cs>>>((const long long *)d_counts,
+                                                             (const unsigned long long *)d_energy_image, d_mean_keV, n);
+    else
+        k_mean_energy<int><<<blocks, threads, 0, cs>>>((const int *)d_counts,
+                                                       (const unsigned long long *)d_energy_image, d_mean_keV, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "calibration map kernel");
+    return st;
 }
 
 extern "C" heart_status heart_trace_rays(heart_spectrometer *h, const heart_ray_arrays *rays, uint64_t n_rays,

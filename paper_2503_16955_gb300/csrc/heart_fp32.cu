@@ -29,6 +29,7 @@
 // `refill` of them are idle, so spawning never runs divergently.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -1012,7 +1013,52 @@ struct BlockTally {
     unsigned long long coll, emit, miss;
 };
 
-// finish a ray: detector projection + binning + tallies (+ record)
+// a ray's record (tests): written out of line, so that kernels that may write
+// records keep the registers of those that never do
+__device__ __forceinline__ void write_record(const Launch32 &L, const Lane &s, int outcome, float xe0, float xe1,
+                                          float xe2, float u, float v, int ix, int iy, int hit, bool pol) {
+    const uint64_t ray = ((uint64_t)s.rh << 32) | s.rl;
+    heart_ray_record &o = L.rec[ray - L.offset];
+    const float xe[3] = {xe0, xe1, xe2};
+    o.ray_id = ray;
+    o.outcome = outcome;
+    o.nrefl = s.nrefl;
+    o.ncoll = s.ncoll;
+    o.energy_keV = s.E;
+    to_global(L, xe, o.pos, true);
+    to_global(L, s.k, o.dir, false);
+    o.u_mm = u;
+    o.v_mm = v;
+    o.ix = ix;
+    o.iy = iy;
+    o.det_hit = hit;
+    o.no_bragg = s.no_bragg;
+    if (pol) to_global(L, s.p, o.pol, false);
+    else o.pol[0] = o.pol[1] = o.pol[2] = 0.0;
+}
+
+// the record of a ray that did not enter, or entered with an invalid energy (a miss)
+__device__ __forceinline__ void write_miss_record(const Launch32 &L, uint64_t ray, const float x[3], const float k[3],
+                                               float E, const float p[3]) {
+    heart_ray_record &o = L.rec[ray - L.offset];
+    o.ray_id = ray;
+    o.outcome = HEART_MISS;
+    o.nrefl = 0;
+    o.ncoll = 0;
+    o.energy_keV = E;
+    to_global(L, x, o.pos, true);
+    to_global(L, k, o.dir, false);
+    o.u_mm = __longlong_as_double(0x7ff8000000000000LL);
+    o.v_mm = o.u_mm;
+    o.ix = -1;
+    o.iy = -1;
+    o.det_hit = 0;
+    o.no_bragg = 0;
+    to_global(L, p, o.pol, false);
+}
+
+// finish a ray: detector projection + binning + tallies (+ record when REC and
+// the launch asks for records)
 template <bool REC, bool EXT>
 __device__ __forceinline__ void finish(const Launch32 &L, Lane &s, int outcome, BlockTally &bt) {
     int ix = -1, iy = -1, hit = 0;
@@ -1049,25 +1095,7 @@ __device__ __forceinline__ void finish(const Launch32 &L, Lane &s, int outcome, 
     atomicAdd(&bt.t[T_ABSORBED + (outcome - HEART_ABSORBED)], 1u);
     atomicAdd(&bt.t[T_HIST0 + (s.nrefl < 15 ? s.nrefl : 15)], 1u);
     if (s.no_bragg) atomicAdd(&bt.t[T_NO_BRAGG], 1u);
-    if (REC) {
-        const uint64_t ray = ((uint64_t)s.rh << 32) | s.rl;
-        heart_ray_record &o = L.rec[ray - L.offset];
-        o.ray_id = ray;
-        o.outcome = outcome;
-        o.nrefl = s.nrefl;
-        o.ncoll = s.ncoll;
-        o.energy_keV = s.E;
-        to_global(L, xe, o.pos, true);
-        to_global(L, s.k, o.dir, false);
-        o.u_mm = u;
-        o.v_mm = v;
-        o.ix = ix;
-        o.iy = iy;
-        o.det_hit = hit;
-        o.no_bragg = s.no_bragg;
-        if (EXT && s.pol) to_global(L, s.p, o.pol, false);
-        else o.pol[0] = o.pol[1] = o.pol[2] = 0.0;
-    }
+    if (REC && L.rec) write_record(L, s, outcome, xe[0], xe[1], xe[2], u, v, ix, iy, hit, EXT && s.pol);
 }
 
 // one tentative collision; returns an outcome code, or -1 while the ray lives
@@ -1450,17 +1478,7 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                         }
                         if (!hit) {
                             ++my_miss;
-                            if (REC) {
-                                heart_ray_record &o = L.rec[id];
-                                o.ray_id = L.offset + id;
-                                o.outcome = HEART_MISS;
-                                o.nrefl = 0; o.ncoll = 0; o.energy_keV = E32;
-                                to_global(L, x, o.pos, true);
-                                to_global(L, k, o.dir, false);
-                                o.u_mm = __longlong_as_double(0x7ff8000000000000LL); o.v_mm = o.u_mm;
-                                o.ix = -1; o.iy = -1; o.det_hit = 0; o.no_bragg = 0;
-                                to_global(L, pv, o.pol, false);
-                            }
+                            if (REC) write_miss_record(L, L.offset + id, x, k, E32, pv);
                         }
                     }
                     const unsigned hm = __ballot_sync(0xffffffffu, hit);
@@ -1759,9 +1777,32 @@ __global__ void __launch_bounds__(kSpawnThreads, (USER || ORD) ? 4 : 8) k_spawn3
     r[5] = make_float4(__uint_as_float(t.w0), __int_as_float(t.face), __int_as_float(ok ? nb : 2), 0.0f);
 }
 
+// Per-ray records of the rays a two-pass trace does not queue (tests): those
+// that miss the crystal or draw no valid energy.  The same source and entry
+// functions as the spawn pass, one thread per ray; the walk pass writes the
+// records of the queued rays.
+template <int GEOM, bool POL, bool USER>
+__global__ void __launch_bounds__(256) k_miss_rec32(const __grid_constant__ Launch32 L, uint64_t first,
+                                                    uint32_t count) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float x[3], k[3], pv[3] = {0.0f, 0.0f, 0.0f}, A = 0.f, sB = 0.f, mu0 = 0.f, qr = 0.f, inv_ws = 1.f, E32 = 0.f;
+    int nb = 0;
+    bool ok;
+    if (USER) {
+        ok = spawn_user<GEOM>(L, first + i, x, k, pv, A, sB, mu0, qr, inv_ws, E32, nb);
+    } else {
+        ok = spawn<GEOM>(L, L.offset + first + i, x, k, A, sB, mu0, qr, inv_ws, E32, nb);
+        if (POL) project_pol32(L, k, pv);
+    }
+    if (!ok) write_miss_record(L, L.offset + first + i, x, k, E32, pv);
+}
+
 // pass 2: a persistent grid walks the queued hits; idle lanes take the next
-// ones (warp-aggregated) once at least `refill` lanes of the warp are idle
-template <int GEOM, int IRC, int OCC, bool POL, bool ORD = false>
+// ones (warp-aggregated) once at least `refill` lanes of the warp are idle.
+// REC: also write each queued ray's record (tests; the same device functions,
+// so the same decisions as the variants without records)
+template <int GEOM, int IRC, int OCC, bool POL, bool ORD = false, bool REC = false>
 __global__ void __launch_bounds__(kBlockThreads, OCC)
     k_walk32(const __grid_constant__ Launch32 L, const __grid_constant__ WaveBuf B,
              const unsigned long long *n_hits, unsigned long long *head, uint32_t count) {
@@ -1781,8 +1822,7 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
     }
     Lane s;
     bool alive = false, more = true;
-    unsigned long long my_coll = 0;
-    unsigned my_dead = 0;
+    uint32_t my_coll = 0, my_dead = 0;         // per lane: far below 2^32 in one launch
     for (;;) {
         const unsigned idle = __ballot_sync(0xffffffffu, !alive);
         const int n_idle = __popc(idle);
@@ -1835,8 +1875,8 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
         if (alive) {
             const int oc = step<GEOM, IRC, POL, ORD>(L, s, s_tab);
             if (oc >= 0) {
-                my_coll += (unsigned long long)s.ncoll;
-                finish<false, POL>(L, s, oc, bt);
+                my_coll += (uint32_t)s.ncoll;
+                finish<REC, POL>(L, s, oc, bt);
                 alive = false;
             }
         }
@@ -1846,7 +1886,7 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
         my_dead += __shfl_down_sync(0xffffffffu, my_dead, off);
     }
     if (lane == 0) {
-        atomicAdd(&bt.coll, my_coll);
+        atomicAdd(&bt.coll, (unsigned long long)my_coll);
         if (my_dead) atomicAdd(&L.tally[T_MISS], (unsigned long long)my_dead);
     }
     __syncthreads();
@@ -1854,6 +1894,20 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
     for (int i = threadIdx.x; i < kTallyN; i += blockDim.x) {
         const unsigned long long v = i == T_COLLISIONS ? bt.coll : (unsigned long long)bt.t[i];
         if (v && i != T_EMITTED && i != T_MISS) atomicAdd(&T[i], v);
+    }
+}
+
+// Device functions of the FP32 kernels evaluated on arrays (tests):
+// 0: acos_ratio(x, y, 1 / y); 1: the rocking curve R(x) / R_max (irc_rel32);
+// 2: its upper bound over |x'| >= x used by the early rejection (irc_bound32)
+__global__ void k_check_functions(const __grid_constant__ Launch32 L, int which, const float *x, const float *y,
+                                  float *out, uint64_t n) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        float r;
+        if (which == 0) r = acos_ratio(x[i], y[i], 1.0f / y[i]);
+        else if (which == 1) r = irc_rel32<-1>(L, x[i]);
+        else r = irc_bound32<-1>(L, x[i]);
+        out[i] = r;
     }
 }
 
@@ -2170,13 +2224,14 @@ static heart_status launch_single(const SpecParams &S, const SourceParams &P, ui
 // trace (created with its hit queue; used while the queue is leased)
 static void wave_side(cudaStream_t *side, cudaEvent_t *fork, cudaEvent_t *join);
 
-template <int GEOM, int IRC, bool POL = false, bool USER = false, bool ORD = false>
+template <int GEOM, int IRC, bool POL = false, bool USER = false, bool ORD = false, bool REC = false>
 static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t n, unsigned long long *ctr,
                                   cudaStream_t st) {
-    constexpr int OCC = 6;                          // 79 registers or fewer in every variant, no spills
+    constexpr int OCC = 6;                          // 80 registers or fewer in every variant, no spills
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk32<GEOM, IRC, OCC, POL, ORD>, kBlockThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk32<GEOM, IRC, OCC, POL, ORD, REC>, kBlockThreads,
+                                                      0);
         if (per_sm < 1) per_sm = 1;
     }
     const int walk_blocks = per_sm * num_sms();
@@ -2215,7 +2270,8 @@ static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t 
         cudaStream_t sc = b ? side : st;
         k_spawn32<GEOM, POL, USER, ORD><<<(count + kSpawnThreads - 1) / kSpawnThreads, kSpawnThreads, 0, sc>>>(
             L, Bs[b], first, count, cc);
-        k_walk32<GEOM, IRC, OCC, POL, ORD><<<walk_blocks, kBlockThreads, 0, sc>>>(L, Bs[b], cc, cc + 1, count);
+        if (REC) k_miss_rec32<GEOM, POL, USER><<<(count + 255) / 256, 256, 0, sc>>>(L, first, count);
+        k_walk32<GEOM, IRC, OCC, POL, ORD, REC><<<walk_blocks, kBlockThreads, 0, sc>>>(L, Bs[b], cc, cc + 1, count);
     }
     if (two) {
         if ((e = cudaEventRecord(join, side)) != cudaSuccess) return cuda_fail(e, "two-pass join");
@@ -2298,15 +2354,15 @@ void wave_release(const WaveLease &lease, cudaStream_t st) {
 
 heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
                          void *img, unsigned long long *scratch, cudaStream_t st, const QeParams *qe, void *wave,
-                         uint32_t wave_cap) {
+                         uint32_t wave_cap, heart_ray_record *rec) {
     if (!wave || n == 0 || !takes_two_pass(S, P))
-        return launch_single(S, P, n, seed, offset, img, scratch, nullptr, st, qe);
+        return launch_single(S, P, n, seed, offset, img, scratch, rec, st, qe);
     // the two-pass trace: the per-ray work in its own pass, then the walk
     Launch32 L;
     make_launch32(S, P, n, seed, offset, L);
     L.img = img;
     L.tally = scratch;
-    L.rec = nullptr;
+    L.rec = rec;
     if (qe) {
         L.eimg = qe->eimg;
         L.n_qe = qe->n;
@@ -2317,6 +2373,18 @@ heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n,
     B.cap = wave_cap;
     B.pad = 0;
     unsigned long long *ctr = (unsigned long long *)((char *)wave + 2 * wave_buffer_bytes(wave_cap));
+    if (rec) {
+        // per-ray records (tests): the variant that carries p and dispatches the rocking
+        // curve at run time, with the record writes; it runs the same device functions
+        // as the variants below, so every ray takes the same decisions
+        const bool F = L.geometry == HEART_FLAT;
+        if (P.user) return F ? launch_wave_t<HEART_FLAT, -1, true, true, false, true>(L, B, n, ctr, st)
+                             : launch_wave_t<HEART_CYL_VON_HAMOS, -1, true, true, false, true>(L, B, n, ctr, st);
+        if (S.n_orders > 1) return F ? launch_wave_t<HEART_FLAT, -1, true, false, true, true>(L, B, n, ctr, st)
+                                     : launch_wave_t<HEART_CYL_VON_HAMOS, -1, true, false, true, true>(L, B, n, ctr, st);
+        return F ? launch_wave_t<HEART_FLAT, -1, true, false, false, true>(L, B, n, ctr, st)
+                 : launch_wave_t<HEART_CYL_VON_HAMOS, -1, true, false, false, true>(L, B, n, ctr, st);
+    }
     if (P.user) {
         // user-supplied rays (polarised or not): entered in FP64 by the spawn pass,
         // walked by the variant that carries p
@@ -2589,8 +2657,9 @@ extern "C" heart_status heart_autotune(heart_spectrometer *h, const heart_source
     cudaEventCreate(&t1);
     // Two knots, each timed on the kernel it shapes: the refill threshold on this
     // trace's own path (the two-pass trace when it applies), then the persistent
-    // kernel's blocks per SM (batched and served jobs, records) on that kernel
-    // with the chosen threshold.  A probe is timed after one warm-up run.
+    // kernel's blocks per SM (batched and served jobs, records of user rays with
+    // several orders) on that kernel with the chosen threshold.  A probe is timed
+    // after one warm-up run.
     const TuneConfig saved = g_tune;
     auto probe = [&](bool persistent, double &rate) -> heart_status {
         float ms = 0.0f;
@@ -2607,13 +2676,13 @@ extern "C" heart_status heart_autotune(heart_spectrometer *h, const heart_source
         rate = (double)probe_rays / (ms * 1e-3);
         return HEART_OK;
     };
-    const int refills[3] = {4, 8, 16};
+    const int refills[4] = {1, 4, 8, 16};
     const int occs[2] = {6, 5};
     TuneConfig best = g_tune;
     double best_rate = -1.0, rate = 0.0;
-    for (int ri = 0; ri < 3 && st == HEART_OK; ++ri) {
+    for (int ri = 0; ri < 4 && st == HEART_OK; ++ri) {
         g_tune.refill = refills[ri];
-        st = probe(false, rate);
+        st = probe(!two_pass, rate);
         if (st == HEART_OK && rate > best_rate) { best_rate = rate; best.refill = refills[ri]; }
     }
     g_tune.refill = best.refill;
@@ -2708,7 +2777,11 @@ extern "C" heart_status heart_trace_batch_static(heart_spectrometer *const *spec
     Launch32 *jobs = (Launch32 *)g_static_host;
     unsigned long long *cb = (unsigned long long *)(g_static_host + kStaticJobsBytes);
     unsigned long long *d_tallies = (unsigned long long *)(d + kStaticJobsBytes + kStaticChunkBytes);
-    const uint32_t chunk = g_tune.chunk_rays;
+    // work items sized to the whole batch, as heart_trace_batch sizes them, so that a
+    // batch of small jobs still spreads over the SMs
+    uint64_t total = 0;
+    for (int i = 0; i < n_jobs; ++i) total += n_rays[i];
+    const uint32_t chunk = chunk_for(total);
     unsigned long long nch = 0;
     bool ext = false;
     for (int i = 0; i < n_jobs; ++i) {
@@ -2751,5 +2824,42 @@ extern "C" heart_status heart_trace_batch_static(heart_spectrometer *const *spec
         }
         if (stuck) return fail(HEART_ELIMIT, "a ray reached the collision cap");
     }
+    return HEART_OK;
+}
+
+// ---------------------------------------------------------------------------
+// test support: device functions on arrays
+// ---------------------------------------------------------------------------
+extern "C" heart_status heart_check_functions(heart_spectrometer *h, int32_t which, const float *d_x,
+                                              const float *d_y, float *d_out, uint64_t n, void *stream) {
+    using namespace heart;
+    if (which < 0 || which > 2) return fail(HEART_EINVAL, "unknown function");
+    if (!d_x || !d_out || (which == 0 && !d_y)) return fail(HEART_EINVAL, "null array");
+    if (which != 0 && !h) return fail(HEART_EINVAL, "null spectrometer");
+    if (n == 0) return HEART_OK;
+    Launch32 L;
+    std::memset(&L, 0, sizeof L);
+    if (h) {
+        // the spectrometer's rocking-curve constants (a monochromatic point source fills the rest)
+        heart_spectral_component c;
+        std::memset(&c, 0, sizeof c);
+        c.kind = HEART_SRC_MONO;
+        c.e0_keV = 8.0;
+        c.weight = 1.0;
+        heart_source_desc d;
+        std::memset(&d, 0, sizeof d);
+        d.components = &c;
+        d.n_components = 1;
+        d.axis[0] = 1.0;
+        SourceParams P;
+        char err[256] = {0};
+        heart_status st = build_source_params(&d, &P, err, (int)sizeof err);
+        if (st != HEART_OK) return fail(st, err);
+        make_launch32(h->p, P, n, 1, 0, L);
+    }
+    const int blocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)num_sms() * 8);
+    k_check_functions<<<blocks, 256, 0, (cudaStream_t)stream>>>(L, which, d_x, d_y, d_out, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "check kernel");
     return HEART_OK;
 }

@@ -59,9 +59,10 @@ struct WaveBuf {
     uint32_t cap, pad;
 };
 // wave / wave_cap: a leased hit queue (nullptr: the one-pass persistent kernel)
+// rec (two-pass trace only): one heart_ray_record per ray, or nullptr
 heart_status launch_fp32(const SpecParams &S, const SourceParams &P, uint64_t n, uint64_t seed, uint64_t offset,
                          void *img, unsigned long long *scratch, cudaStream_t st, const QeParams *qe = nullptr,
-                         void *wave = nullptr, uint32_t wave_cap = 0);
+                         void *wave = nullptr, uint32_t wave_cap = 0, heart_ray_record *rec = nullptr);
 // The hit queue of the two-pass FP32 trace: one per device, shared by every
 // spectrometer handle, grown to the largest chunk asked for (never shrunk).
 // wave_acquire locks it for the calling host thread while a trace is enqueued

@@ -149,3 +149,25 @@ def test_calibration_map_follows_von_hamos_dispersion(H):
     # column means lie below x(E)
     good2, E_col2, E_pred2, _ = _column_means(H, w["spec"], w["source"], 200_000_000, 22)
     assert np.mean(E_col2[good2] - E_pred2[good2]) < -0.002
+
+
+def test_calibration_map_is_the_energy_image_over_the_count_image(H):
+    # heart_calibration_map traces the source geometry with a uniform spectrum and divides in
+    # the library: the same streams through heart_trace_energy give the same count and energy
+    # images, and the map is their ratio (NaN where no photon landed)
+    import torch
+    w = W.von_hamos_hapg()
+    s = H.heart_spectrometer_create(w["spec"])
+    mean, counts, t = H.heart_calibration_map(s, w["source"], 7.6, 8.4, 2_000_000, 41)
+    src = dict(w["source"], components=[dict(kind="uniform", lo_keV=7.6, hi_keV=8.4, weight=1.0)])
+    c2 = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    e2 = torch.zeros(s.shape, dtype=torch.int64, device="cuda")
+    t2 = H.heart_trace_energy(s, src, 2_000_000, 41, 0, c2, e2, precision="fp32")
+    s.close()
+    assert torch.equal(counts, c2) and t == t2 and t["det_hits"] > 1000
+    c = c2.cpu().numpy().astype(np.float64)
+    e = e2.cpu().numpy().astype(np.float64)
+    m = mean.cpu().numpy()
+    hit = c > 0
+    assert np.array_equal(m[hit], e[hit] * 1e-6 / c[hit])
+    assert np.all(np.isnan(m[~hit]))

@@ -63,3 +63,51 @@ def test_static_batch_rejects_more_jobs_than_its_work_area(H):
     assert e.value.status == 1 and "HEART_STATIC_MAX_JOBS" in str(e.value)
     assert int(img.sum()) == 0
     s.close()
+
+
+def test_static_batch_with_a_large_job_allocates_nothing_and_matches_the_two_pass_trace(H):
+    # heart_trace_batch runs a job of 2^19 rays as a two-pass trace (hit queue) and the small
+    # ones in one persistent launch; the static call runs all of them on the persistent kernel,
+    # which traces every ray as the two-pass trace does: the same images and tallies.  After a
+    # first call on the device (which looks up the work area's address), a call changes the
+    # device's free memory by nothing: it allocates no device memory.
+    import torch
+    jobs = W.batched_64(seed=9, n_configs=3, ray_range=(2e4, 6e4))
+    big = W.von_hamos_hapg()
+    specs = [H.heart_spectrometer_create(j["spec"]) for j in jobs] + [H.heart_spectrometer_create(big["spec"])]
+    srcs = [j["source"] for j in jobs] + [big["source"]]
+    nr = [j["n_rays"] for j in jobs] + [1 << 19]
+    seeds = [j["seed"] for j in jobs] + [33]
+    ref = [_zeros(s, torch) for s in specs]
+    t_ref = H.heart_trace_batch(specs, srcs, nr, seeds, ref)
+    for call in range(2):
+        imgs = [_zeros(s, torch) for s in specs]
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        t = H.heart_trace_batch_static(specs, srcs, nr, seeds, imgs)
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        if call == 1:
+            assert free1 == free0, (free0, free1)
+        for i in range(len(specs)):
+            assert torch.equal(imgs[i], ref[i]), (call, i)
+            assert t[i] == t_ref[i], (call, i)
+    assert t_ref[-1]["det_hits"] > 50
+    for s in specs:
+        s.close()
+
+
+def test_static_batch_rejects_a_tabulated_spectrum(H):
+    import numpy as np
+    import torch
+    w = W.flat_hopg_mono()
+    s = H.heart_spectrometer_create(w["spec"])
+    img = _zeros(s, torch)
+    src = dict(w["source"], components=[dict(kind="table", weight=1.0)],
+               table=(np.linspace(7.9, 8.1, 5), np.ones(5)))
+    with pytest.raises(H.HeartError) as e:
+        H.heart_trace_batch_static([s], [src], [1000], [1], [img])
+    assert e.value.status == 1 and "tabulated" in str(e.value)
+    torch.cuda.synchronize()
+    assert int(img.sum()) == 0
+    s.close()
