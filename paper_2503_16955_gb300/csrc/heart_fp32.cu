@@ -1820,19 +1820,50 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
         atomicAdd(&L.tally[T_EMITTED], (unsigned long long)count);
         atomicAdd(&L.tally[T_MISS], (unsigned long long)count - nh);
     }
+    // Queue slots are claimed 32 at a time, one claim ahead: lane 0 holds the current
+    // claim's first slot (cb) and the next one's (nb); a refill hands out the current
+    // claim's slots from position cpos on and, past its end, the next claim's; when the
+    // current claim is used up the next becomes current and a new claim is issued, whose
+    // atomic completes long before its slots are handed out.  (Queue indices of a chunk
+    // fit in 32 bits.)
+    constexpr uint32_t kClaim = 32;
+    unsigned int *head32 = (unsigned int *)head;      // the low word of the chunk's head counter
+    uint32_t cb = 0, nb = 0, cpos = 0;
+    if (lane == 0) {
+        cb = atomicAdd(head32, 2u * kClaim);
+        nb = cb + kClaim;
+    }
+    const uint32_t nh32 = (uint32_t)nh;
     Lane s;
-    bool alive = false, more = true;
+    bool alive = false, more = __shfl_sync(0xffffffffu, cb, 0) < nh32;
     uint32_t my_coll = 0, my_dead = 0;         // per lane: far below 2^32 in one launch
     for (;;) {
         const unsigned idle = __ballot_sync(0xffffffffu, !alive);
-        const int n_idle = __popc(idle);
+        const uint32_t n_idle = __popc(idle);
         if (!more && n_idle == 32) break;
-        if (more && (n_idle >= L.refill || n_idle == 32)) {
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(head, (unsigned long long)n_idle);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (base + n_idle >= nh) more = false;
-            const unsigned long long slot = base + __popc(idle & lt_mask);
+        if (more && (n_idle >= (uint32_t)L.refill || n_idle == 32)) {
+            const uint32_t cbu = __shfl_sync(0xffffffffu, cb, 0), nbu = __shfl_sync(0xffffffffu, nb, 0);
+            const uint32_t rank = __popc(idle & lt_mask), left = kClaim - cpos;
+            const unsigned long long slot = rank < left ? cbu + cpos + rank : nbu + (rank - left);
+            {
+                // the next claim's records into L1 ahead of their loads: one line per lane
+                // (the claim's 32 records span 24 lines, 28 with the polarisation word)
+                constexpr uint32_t kLines = (kClaim * 16u * (POL ? kWaveRec16 + 1 : kWaveRec16)) / 128u;
+                const char *q = (const char *)wave_rec<POL>(B, nbu) + 128u * lane;
+                if (lane < kLines && nbu < nh32 && q < (const char *)wave_rec<POL>(B, B.cap))
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
+            }
+            cpos += n_idle;
+            uint32_t next = cbu + cpos;
+            if (cpos >= kClaim) {
+                cpos -= kClaim;
+                next = nbu + cpos;
+                if (lane == 0) {
+                    cb = nb;
+                    nb = atomicAdd(head32, kClaim);
+                }
+            }
+            if (next >= nh32) more = false;
             if (!alive && slot < nh) {
                 const float4 *r = wave_rec<POL>(B, slot);
                 const float4 r0 = __ldcs(r), r1 = __ldcs(r + 1), r2 = __ldcs(r + 2), r3 = __ldcs(r + 3),
@@ -2227,7 +2258,9 @@ static void wave_side(cudaStream_t *side, cudaEvent_t *fork, cudaEvent_t *join);
 template <int GEOM, int IRC, bool POL = false, bool USER = false, bool ORD = false, bool REC = false>
 static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t n, unsigned long long *ctr,
                                   cudaStream_t st) {
-    constexpr int OCC = 6;                          // 80 registers or fewer in every variant, no spills
+    // 7 blocks per SM (72 registers) for the benchmark's variants; those that carry p
+    // need more registers: 6
+    constexpr int OCC = POL ? 6 : 7;
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk32<GEOM, IRC, OCC, POL, ORD, REC>, kBlockThreads,
