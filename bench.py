@@ -27,32 +27,119 @@ sys.path.insert(0, ROOT)
 
 METRIC = "rays/sec to detector and fraction of FP32/SFU roofline; p50/p99 job latency"
 UNIT = "rays/s"
-# algorithmic work per unit, in lane-instructions (one thread executing one instruction):
-INSTR_PER_COLLISION = 110      # Philox4x32-10 (60 int) + free path, table, sin/cos, Bragg offset, IRC, accept (~50)
-INSTR_PER_RAY = 240            # two Philox blocks, source, entry, per-ray constants, detector, tallies
-INSTR_PER_SEGMENT = 120        # exit distance, grazing-angle range, tilt bound, table search, majorant
+# Algorithmic work per unit in lane-instructions (one thread executing one instruction:
+# an FP32 add / multiply / fused multiply-add, an SFU function, a 32 x 32 -> 64-bit
+# multiply, a compare or select, a shared-memory load), counted operation by operation
+# from the method's steps (the itemisation is in the design doc, Measurement and roofline):
+ALGO_PER_RAY = {                # every emitted ray
+    "philox_2_blocks": 80,      # 10 rounds x (2 wide multiplies + 2 three-input XORs), twice
+    "uniforms": 8,              # 4 words -> (0, 1): convert + fused multiply-add
+    "cone_direction": 22,       # 1 - cos(phi), sin(phi), sin / cos of the azimuth, k, k.N offset
+    "gaussian_spot": 17,        # Box-Muller radius and angle, origin += spot
+    "cylinder_entry": 23,       # |o_perp + t k_perp| = R, smallest t > 0, axial and azimuth tests
+}
+ALGO_PER_ENTERED = {            # every ray that enters the crystal
+    "entry_anchor": 14,         # |k.N| at the entry minus the cone axis's, as small terms
+    "energy_and_bragg": 50,     # component, Gaussian line or 1/E draw, sin(aB) offset, anchor, Q, mu0
+}
+ALGO_PER_SEGMENT = {            # every straight segment (entered rays and reflections)
+    "exit_distance": 42,        # inner / outer cylinder, axial and azimuth planes, exit anchor
+    "thinning_bounds": 50,      # Bragg distance, tilt bound and table word, arc bound, shares
+    "majorant": 8,              # mu0 + lambda, its inverse, absorption share and word threshold
+}
+ALGO_PER_COLLISION = {          # every tentative collision
+    "philox_block": 40,
+    "free_path": 9,             # word -> ln u, times 1/mu, Kahan sum, exit compare
+    "absorb_and_share": 5,      # raw-word absorption compare, conditional uniform
+    "local_normal": 14,         # cylinder: k.N and k.t2 at the collision from the path length
+    "candidate": 22,            # stream split, table word map, quantile lookup, tilt test, sin theta
+    "azimuth_and_offset": 10,   # azimuth sine / cosine (or arc test), k.n - sin(aB + dM)
+    "rocking_curve_bound": 8,   # R bound at |e|, accept compare
+}
+ALGO_PER_EXIT = {               # every ray leaving the crystal
+    "detector": 30,             # line-plane intersection, (u, v), pixel, atomic
+}
+ALGO_PER_END = 3                # tallies of an ended ray (outcome, reflections, no-Bragg)
+ISSUE_PER_SM_CLK = 4            # 4 sub-partitions, one warp instruction each per clock
 SM_COUNT = 152
-LANES_PER_SM_CLK = 128         # 4 SM sub-partitions x 32 lanes, one warp-instruction issue each per clock
 SM_MAX_MHZ = 2070.0
+
+
+def algorithmic_instructions(t):
+    """lane-instructions of a trace's algorithmic work, from its tallies"""
+    entered = t["emitted"] - t["miss"]
+    reflections = sum(h * c for h, c in enumerate(t["refl_hist"]))
+    exits = t["exit_front"] + t["exit_back"] + t["exit_side"]
+    return (sum(ALGO_PER_RAY.values()) * t["emitted"] + sum(ALGO_PER_ENTERED.values()) * entered +
+            sum(ALGO_PER_SEGMENT.values()) * (entered + reflections) +
+            sum(ALGO_PER_COLLISION.values()) * t["collisions"] + sum(ALGO_PER_EXIT.values()) * exits +
+            ALGO_PER_END * entered)
+
+
+def algorithmic_roofline(t, seconds, sm_mhz):
+    """algorithmic lane-instructions per second against the SM issue rate (32 lanes x
+    4 sub-partitions x SMs x clock): the path runs on the integer, FP32 and SFU pipes"""
+    achieved = algorithmic_instructions(t) / seconds / 1e12
+    peak = SM_COUNT * ISSUE_PER_SM_CLK * 32 * sm_mhz * 1e6 / 1e12
+    return achieved, peak
+
+
 # rays per chunk of the two-pass trace (the library's largest hit-queue chunk)
 WAVE_CHUNK = 1 << 25
-# DRAM bytes (read + write) of the two passes per traced ray, from one ncu capture of the
-# spawn and walk kernels on 1.6e7 rays of the von Hamos workload (1219.1 MB: the hit queue
-# written and read back); valid only for the kernel sources with the hash below
-TRAFFIC_BYTES_PER_RAY = 1219.131e6 / 1.6e7
+# Per emitted ray of the von Hamos workload, from ncu captures of the two-pass kernels
+# (both passes summed): DRAM bytes read + written (the hit queue written and read back;
+# one chunk of 2^24 rays, whose 0.66 GB queue, unlike a smaller one, does not stay in
+# L2) and warp instructions issued per pipe (2^22 rays); valid only for the kernel
+# sources with the hash below.
+TRAFFIC_BYTES_PER_RAY = (0.240128e6 + 609.071104e6 + 676.584704e6 + 0.215808e6) / (1 << 24)   # 2^24 rays
+PIPE_INST_PER_RAY = {"alu": 11.6558, "fma": 14.7734, "fmaheavy": 6.1623, "fmalite": 9.4165, "xu": 1.8928,
+                     "lsu": 1.4364, "adu": 1.4870, "cbu": 3.0297, "uniform": 0.2314, "fp64": 0.0168,
+                     "total": 38.1884}
 TRAFFIC_SOURCES = ("paper_2503_16955_gb300/csrc/heart_fp32.cu", "paper_2503_16955_gb300/csrc/heart_fp64.cuh",
                    "paper_2503_16955_gb300/csrc/heart_internal.h")
-TRAFFIC_SOURCE_HASH = "e04437d69cc34361"
+TRAFFIC_SOURCE_HASH = "6558dd8a88eef9f1"
 
 
-def measured_traffic(n_rays):
-    """DRAM traffic of one step of n_rays, or None if the kernels changed since the capture"""
+def sources_hash():
     import hashlib
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    return TRAFFIC_BYTES_PER_RAY * n_rays if h.hexdigest()[:16] == TRAFFIC_SOURCE_HASH else None
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(n_rays):
+    """DRAM traffic of one step of n_rays, or None if the kernels changed since the capture"""
+    if TRAFFIC_BYTES_PER_RAY is None or sources_hash() != TRAFFIC_SOURCE_HASH:
+        return None
+    return TRAFFIC_BYTES_PER_RAY * n_rays
+
+
+def per_pipe_roofline(H, n_rays, seconds, sm_mhz):
+    """Issued warp instructions per pipe (ncu capture, per ray) over the step's time,
+    against each pipe's issue rate measured on this GPU by heart_pipe_peaks (per SM
+    per clock) at the step's SM clock; None if the kernels changed since the capture."""
+    if PIPE_INST_PER_RAY is None or sources_hash() != TRAFFIC_SOURCE_HASH:
+        return None
+    peaks = H.heart_pipe_peaks()
+    clk = sm_mhz * 1e6
+    # pipe <- the microbenchmarked instruction that runs on it
+    per_clk = {"alu": peaks["lop3"][1], "fma": peaks["ffma"][1], "fmaheavy": peaks["imad"][1],
+               "xu": peaks["mufu_lg2"][1], "issue": float(ISSUE_PER_SM_CLK)}
+    out = {}
+    for pipe, rate in per_clk.items():
+        inst = PIPE_INST_PER_RAY["total" if pipe == "issue" else pipe] * n_rays
+        achieved = inst / seconds
+        peak = rate * SM_COUNT * clk
+        out[pipe] = {"warp_inst_per_ray": PIPE_INST_PER_RAY["total" if pipe == "issue" else pipe],
+                     "achieved": achieved, "peak": peak, "frac": achieved / peak}
+    binding = max((p for p in out if p != "issue"), key=lambda p: out[p]["frac"])
+    return {"pipes": out, "binding_pipe": binding, "frac": out[binding]["frac"], "unit": "warp inst/s",
+            "peak_basis": "heart_pipe_peaks per SM per clock (alu: LOP3, fma: FFMA, fmaheavy: IMAD, xu: "
+                          "MUFU.LG2) x %d SMs x the step's median SM clock (%.0f MHz); issue: 4 per SM per "
+                          "clock" % (SM_COUNT, sm_mhz),
+            "microbenchmark": {k: v for k, v in peaks.items() if k not in ("sms",)}}
 
 
 def parse():
@@ -63,7 +150,7 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--rays", type=float, default=1e8)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--serving-jobs", type=int, default=1000)
+    p.add_argument("--serving-jobs", type=int, default=10_000)
     p.add_argument("--no-extra", action="store_true", help="skip batched / serving / FP64 measurements")
     return p.parse_args()
 
@@ -141,7 +228,7 @@ def cpu_baseline(workload, seconds, threads=0):
             "collisions_per_ray": tal["collisions"] / max(1, n2)}
 
 
-def batched_measurement(H, W, torch, stream):
+def batched_measurement(H, W, torch, stream, sm_mhz):
     """64 spectrometers of uneven ray counts in one heart_trace_batch call (jobs
     of 2^18 rays or more as two-pass traces, the rest in one persistent launch)."""
     jobs = W.batched_64()
@@ -161,18 +248,29 @@ def batched_measurement(H, W, torch, stream):
     total = sum(args[1])
     for s in specs:
         s.close()
+    summed = {k: sum(t[k] for t in tl) for k in ("emitted", "miss", "exit_front", "exit_back", "exit_side",
+                                                  "collisions")}
+    summed["refl_hist"] = [sum(t["refl_hist"][h] for t in tl) for h in range(16)]
+    achieved, peak = algorithmic_roofline(summed, sec, sm_mhz)
     return {"jobs": len(jobs), "rays": total, "seconds": sec, "rays_per_s": total / sec,
             "collisions_per_ray": sum(t["collisions"] for t in tl) / total,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-instr/s",
+                         "frac": achieved / peak, "basis": "the headline's per-unit counts over the batch's "
+                                                           "tallies, CUDA-event time of the call"},
             "note": "one heart_trace_batch call: jobs of >= 2^18 rays as two-pass traces, the rest in one "
                     "persistent launch (includes tally read-back)"}
 
 
-def serving_measurement(H, W, n_jobs, rate):
+def serving_measurement(H, W, n_jobs, rate, rho=None, capacity=None):
     """Poisson stream of trace jobs through the request loop; latencies are
-    measured by the server from submit to completion."""
+    measured by the server from submit to completion.  rate None: the rate that
+    offers rho times `capacity` rays/s."""
     import threading as th
     pool = W.batched_64(seed=4, ray_range=(1e4, 1e8))
     specs = [H.heart_spectrometer_create(j["spec"]) for j in pool]
+    if rate is None:
+        mean_rays = sum(j["n_rays"] for j in W.serving_stream(n_jobs=n_jobs, rate_per_s=1.0)) / n_jobs
+        rate = rho * capacity / mean_rays
     stream = W.serving_stream(n_jobs=n_jobs, rate_per_s=rate)
     srv = H.heart_server_create(40 << 30)
     ids = []
@@ -230,6 +328,7 @@ def serving_measurement(H, W, n_jobs, rate):
     serial_lat.sort()
     return {"jobs": n_jobs, "rate_per_s": rate, "p50_ms": q(lat_ms, 0.50), "p99_ms": q(lat_ms, 0.99),
             "max_ms": lat_ms[-1], "rays_per_s": rays / wall, "offered_rays_per_s": offered,
+            "utilisation_rho": offered / (rays / sum(service)),
             "serial_fp32": {"rays_per_s": rays / sum(service), "p50_ms": q(serial_lat, 0.50),
                             "p99_ms": q(serial_lat, 0.99), "max_ms": serial_lat[-1],
                             "note": "the same jobs, one synchronised heart_trace each, queued first come first "
@@ -321,7 +420,7 @@ def features_measurement(H, W, torch, stream):
     return out
 
 
-def large_measurement(H, W, torch, stream):
+def large_measurement(H, W, torch, stream, sm_mhz):
     """The large single job: von Hamos R = 100 mm, Lorentzian mosaic, elastic +
     inelastic lines, 4096^2 int64 detector, 1e10 rays in one call (streamed by
     the library in chunks of 2^25 rays), FP32; device-timed."""
@@ -338,9 +437,14 @@ def large_measurement(H, W, torch, stream):
     torch.cuda.synchronize()
     sec = e0.elapsed_time(e1) / 1e3
     s.close()
+    achieved, peak = algorithmic_roofline(t, sec, sm_mhz)
+    entered = n - t["miss"]
     return {"workload": w["name"], "rays": n, "seconds": sec, "rays_per_s": n / sec,
-            "collisions_per_ray": t["collisions"] / n, "det_hits": t["det_hits"],
-            "detector": "%dx%d int64" % (w["spec"]["det_ny"], w["spec"]["det_nx"])}
+            "collisions_per_ray": t["collisions"] / n, "entered_per_ray": entered / n,
+            "collisions_per_entered_ray": t["collisions"] / max(1, entered), "det_hits": t["det_hits"],
+            "detector": "%dx%d int64" % (w["spec"]["det_ny"], w["spec"]["det_nx"]),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-instr/s",
+                         "frac": achieved / peak}}
 
 
 def run_reference(args):
@@ -455,21 +559,26 @@ def main():
     e2e_value = n * e2e_steps * world / e2e_s
     img_bytes = h_img.nbytes
 
-    # roofline: issue-bound (FP32 / integer / SFU instructions), algorithmic count
-    per_launch = (INSTR_PER_COLLISION * coll_per_ray + INSTR_PER_SEGMENT * seg_per_ray + INSTR_PER_RAY) * n
-    mean_launch_s = total_max / args.steps
-    achieved = per_launch / mean_launch_s / 1e12                  # tera lane-instructions / s
-    peak = SM_COUNT * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    # roofline: issue-bound (integer, FP32 and SFU instructions); algorithmic work from the
+    # tallies of a step, over the step's mean duration, against the SM issue rate at the
+    # step's median SM clock (the max clock if unsampled)
     clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+    mean_launch_s = total_max / args.steps
+    tal_step = dict(tal)
+    achieved, peak = algorithmic_roofline(tal_step, mean_launch_s, sm_mhz)
+    pipes = per_pipe_roofline(H, n, mean_launch_s, sm_mhz) if rank == 0 else None
     cpu = cpu_baseline(w, args.cpu_seconds) if rank == 0 and world == 1 else None
     spec.close()
     extra = {}
     if rank == 0 and world == 1 and not args.no_extra:
-        extra["batched"] = batched_measurement(H, W, torch, stream)
+        extra["batched"] = batched_measurement(H, W, torch, stream, sm_mhz)
         extra["fp64_plain"] = fp64_measurement(H, W, torch, stream)
         extra["serving"] = serving_measurement(H, W, args.serving_jobs, 200.0)
+        extra["serving_high_rate"] = serving_measurement(H, W, args.serving_jobs, None, rho=0.9,
+                                                         capacity=extra["serving"]["serial_fp32"]["rays_per_s"])
         extra["features"] = features_measurement(H, W, torch, stream)
-        extra["large_job"] = large_measurement(H, W, torch, stream)
+        extra["large_job"] = large_measurement(H, W, torch, stream, sm_mhz)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -487,11 +596,15 @@ def main():
                          "frac": achieved / peak, "traffic": measured_traffic(n),
                          "traffic_note": "ncu dram__bytes_read+write of the step's launches, per step (hit "
                                          "queue written by the spawn pass and read by the walk pass; "
-                                         "captured on 1.6e7 rays, scaled by rays)",
+                                         "captured on one 2^24-ray chunk, scaled by rays)",
                          "kernel": "k_spawn32 + k_walk32 (two passes per chunk of up to 2^25 rays)",
-                         "peak_basis": "152 SMs x 128 lanes x 2070 MHz (max SM clock); algorithmic "
-                                       "%d instr/collision + %d instr/segment + %d instr/ray"
-                                       % (INSTR_PER_COLLISION, INSTR_PER_SEGMENT, INSTR_PER_RAY)},
+                         "peak_basis": "152 SMs x 4 sub-partitions x 32 lanes x %.0f MHz (the step's median SM "
+                                       "clock); algorithmic lane-instructions counted per ray %d, per entered "
+                                       "ray %d, per segment %d, per collision %d, per exit %d (DESIGN.md)"
+                                       % (sm_mhz, sum(ALGO_PER_RAY.values()), sum(ALGO_PER_ENTERED.values()),
+                                          sum(ALGO_PER_SEGMENT.values()), sum(ALGO_PER_COLLISION.values()),
+                                          sum(ALGO_PER_EXIT.values())),
+                         "per_pipe": pipes},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": img_bytes,
                     "d2h_bytes_per_step": img_bytes + 27 * 8,
                     "path": "heart_trace_host (host image uploaded, traced, downloaded each step)"},

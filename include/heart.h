@@ -396,8 +396,14 @@ heart_status heart_trace_batch_static(heart_spectrometer *const *specs, const he
                                       const uint64_t *n_rays, const uint64_t *seeds, void *const *d_images,
                                       int32_t n_jobs, void *stream, heart_tally *out);
 
-/* Request loop: jobs are admitted while their images fit under mem_cap_bytes,
- * batched into persistent launches as they arrive, and polled for results. */
+/* Request loop (continuous batching): jobs are admitted in arrival order while
+ * their images fit under mem_cap_bytes and stay resident until released.  A
+ * worker thread keeps two rounds of launches in flight; each round traces, in
+ * arrival order, every admitted job with at most 2^20 rays left whole, and
+ * gives a budget of 2^26 rays to the larger ones oldest first in slices of at
+ * least 2^22 rays.  Slices of 2^22 rays or more run as two-pass traces, the
+ * others together in one persistent batched launch; every FP32 kernel traces a
+ * ray alike, so a job's image and tallies equal its heart_trace's. */
 heart_status heart_server_create(size_t mem_cap_bytes, heart_server **out);
 heart_status heart_server_destroy(heart_server *server);
 heart_status heart_submit(heart_server *server, heart_spectrometer *spec, const heart_source_desc *src,

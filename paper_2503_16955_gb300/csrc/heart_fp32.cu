@@ -553,7 +553,8 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
     // root normalises k
     double E = L.ray[6][id], og[3], kg[3], ol[3], kl[3];
     for (int i = 0; i < 3; ++i) { og[i] = L.ray[i][id] - L.fc[i]; kg[i] = L.ray[3 + i][id]; }
-    const double kk = kg[0] * kg[0] + kg[1] * kg[1] + kg[2] * kg[2];
+    // (FP64 sums of products as explicit fused multiply-adds: GB300's FP64 rate bounds this entry)
+    const double kk = __fma_rn(kg[0], kg[0], __fma_rn(kg[1], kg[1], kg[2] * kg[2]));
     if (kk > 0.0) {
         const double ik = rsqrt(kk);
         for (int i = 0; i < 3; ++i) kg[i] *= ik;
@@ -561,8 +562,8 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
         E = __longlong_as_double(0x7ff8000000000000LL);      // a zero direction cannot enter
     }
     for (int i = 0; i < 3; ++i) {
-        ol[i] = og[0] * L.fa[i][0] + og[1] * L.fa[i][1] + og[2] * L.fa[i][2];
-        kl[i] = kg[0] * L.fa[i][0] + kg[1] * L.fa[i][1] + kg[2] * L.fa[i][2];
+        ol[i] = __fma_rn(og[0], L.fa[i][0], __fma_rn(og[1], L.fa[i][1], og[2] * L.fa[i][2]));
+        kl[i] = __fma_rn(kg[0], L.fa[i][0], __fma_rn(kg[1], L.fa[i][1], kg[2] * L.fa[i][2]));
         x[i] = (float)ol[i];
         k[i] = (float)kl[i];
         p[i] = 0.0f;
@@ -582,12 +583,12 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
                 p[i] = (pf[0] * L.faf[i][0] + pf[1] * L.faf[i][1] + pf[2] * L.faf[i][2]) * ipn;
         } else {
             double pg[3] = {L.ray[7][id], L.ray[8][id], L.ray[9][id]};
-            const double pkd = pg[0] * kg[0] + pg[1] * kg[1] + pg[2] * kg[2];
-            for (int i = 0; i < 3; ++i) pg[i] -= pkd * kg[i];
-            const double pn = sqrt(pg[0] * pg[0] + pg[1] * pg[1] + pg[2] * pg[2]);
+            const double pkd = __fma_rn(pg[0], kg[0], __fma_rn(pg[1], kg[1], pg[2] * kg[2]));
+            for (int i = 0; i < 3; ++i) pg[i] = __fma_rn(-pkd, kg[i], pg[i]);
+            const double pn = sqrt(__fma_rn(pg[0], pg[0], __fma_rn(pg[1], pg[1], pg[2] * pg[2])));
             if (pn > 1e-12)
                 for (int i = 0; i < 3; ++i)
-                    p[i] = (float)((pg[0] * L.fa[i][0] + pg[1] * L.fa[i][1] + pg[2] * L.fa[i][2]) / pn);
+                    p[i] = (float)(__fma_rn(pg[0], L.fa[i][0], __fma_rn(pg[1], L.fa[i][1], pg[2] * L.fa[i][2])) / pn);
         }
     }
     E32 = (float)E;
@@ -596,25 +597,25 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
     if (GEOM == HEART_FLAT) {
         if (!(kl[2] < 0.0) || !(ol[2] > 0.0)) return false;
         const double t = ol[2] / (-kl[2]);
-        const double ex = ol[0] + t * kl[0], ey = ol[1] + t * kl[1];
+        const double ex = __fma_rn(t, kl[0], ol[0]), ey = __fma_rn(t, kl[1], ol[1]);
         if (fabs(ex) > (double)L.half_d || fabs(ey) > (double)L.half_n) return false;
         x[0] = (float)ex; x[1] = (float)ey; x[2] = 0.0f;
         kN = -kl[2];
     } else {
-        const double aa = kl[1] * kl[1] + kl[2] * kl[2];
+        const double aa = __fma_rn(kl[1], kl[1], kl[2] * kl[2]);
         if (!(aa > 0.0)) return false;
         const double R = (double)L.R;
-        const double c0 = ol[1] * ol[1] + ol[2] * ol[2] - R * R;
+        const double c0 = __fma_rn(ol[1], ol[1], __fma_rn(ol[2], ol[2], -R * R));
         if (!(c0 < 0.0)) return false;
-        const double bo = ol[1] * kl[1] + ol[2] * kl[2];
-        const double sq = sqrt(bo * bo - aa * c0);
+        const double bo = __fma_rn(ol[1], kl[1], ol[2] * kl[2]);
+        const double sq = sqrt(__fma_rn(bo, bo, -aa * c0));
         const double t = (bo > 0.0) ? -c0 / (bo + sq) : (sq - bo) / aa;
         double xe[3];
-        for (int i = 0; i < 3; ++i) xe[i] = ol[i] + t * kl[i];
+        for (int i = 0; i < 3; ++i) xe[i] = __fma_rn(t, kl[i], ol[i]);
         if (fabs(xe[0] - (double)L.zc) > (double)L.half_d) return false;
         if (fabs(xe[2]) * (double)L.cphi > xe[1] * (double)L.sphi) return false;
         for (int i = 0; i < 3; ++i) x[i] = (float)xe[i];
-        kN = (kl[1] * xe[1] + kl[2] * xe[2]) * L.inv_Rd;
+        kN = __fma_rn(kl[1], xe[1], kl[2] * xe[2]) * L.inv_Rd;
     }
     const double sr = L.hc_2d / E;                        // sin(aB), Eq. (BraggLaw)
     nb = !(sr < 1.0);
@@ -629,7 +630,7 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
     }
     if (!nb) {
         // cos aB only with a peak shift (then in FP64); Q takes it in FP32
-        const double sb = sn_s != 0.0 ? sr * cs_s + sqrt(1.0 - sr * sr) * sn_s : sr * cs_s;
+        const double sb = sn_s != 0.0 ? __fma_rn(sr, cs_s, sqrt(__fma_rn(-sr, sr, 1.0)) * sn_s) : sr * cs_s;
         sB = (float)sb;
         A = (float)(kN - sb);
         const float srf = (float)sr, crf = sqrtf(fmaxf(0.0f, __fmaf_rn(-srf, srf, 1.0f)));
@@ -646,7 +647,8 @@ __device__ __forceinline__ bool spawn_user(const Launch32 &L, uint64_t id, float
         for (int h = 1; h < L.n_ord; ++h) {
             const double srh = sr * L.ord_rd[h];
             if (srh < 1.0) {
-                const double sbh = sn_s != 0.0 ? srh * cs_s + sqrt(1.0 - srh * srh) * sn_s : srh * cs_s;
+                const double sbh = sn_s != 0.0 ? __fma_rn(srh, cs_s, sqrt(__fma_rn(-srh, srh, 1.0)) * sn_s)
+                                               : srh * cs_s;
                 osB[h] = (float)sbh;
                 oA[h] = (float)(kN - sbh);
             } else {
@@ -1842,41 +1844,52 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
     constexpr uint32_t kClaim = 32;
     unsigned int *head32 = (unsigned int *)head;      // the low word of the chunk's head counter
     uint32_t cb = 0, nb = 0, cpos = 0;
-    if (lane == 0) {
+    if (!ORD && lane == 0) {
         cb = atomicAdd(head32, 2u * kClaim);
         nb = cb + kClaim;
     }
     const uint32_t nh32 = (uint32_t)nh;
     Lane s;
-    bool alive = false, more = __shfl_sync(0xffffffffu, cb, 0) < nh32;
+    bool alive = false, more = ORD || __shfl_sync(0xffffffffu, cb, 0) < nh32;
     uint32_t my_coll = 0, my_dead = 0;         // per lane: far below 2^32 in one launch
     for (;;) {
         const unsigned idle = __ballot_sync(0xffffffffu, !alive);
         const uint32_t n_idle = __popc(idle);
         if (!more && n_idle == 32) break;
         if (more && (n_idle >= (uint32_t)L.refill || n_idle == 32)) {
-            const uint32_t cbu = __shfl_sync(0xffffffffu, cb, 0), nbu = __shfl_sync(0xffffffffu, nb, 0);
-            const uint32_t rank = __popc(idle & lt_mask), left = kClaim - cpos;
-            const unsigned long long slot = rank < left ? cbu + cpos + rank : nbu + (rank - left);
-            {
-                // the next claim's records into L1 ahead of their loads: one line per lane
-                // (the claim's 32 records span 24 lines, 28 with the polarisation word)
-                constexpr uint32_t kLines = (kClaim * 16u * (POL ? kWaveRec16 + 1 : kWaveRec16)) / 128u;
-                const char *q = (const char *)wave_rec<POL>(B, nbu) + 128u * lane;
-                if (lane < kLines && nbu < nh32 && q < (const char *)wave_rec<POL>(B, B.cap))
-                    asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
-            }
-            cpos += n_idle;
-            uint32_t next = cbu + cpos;
-            if (cpos >= kClaim) {
-                cpos -= kClaim;
-                next = nbu + cpos;
-                if (lane == 0) {
-                    cb = nb;
-                    nb = atomicAdd(head32, kClaim);
+            unsigned long long slot;
+            if constexpr (ORD) {
+                // several orders: one claim per refill (the claim ahead measured slower here:
+                // 6.8e9 against 8.3e9 rays/s with three orders)
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(head, (unsigned long long)n_idle);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (base + n_idle >= nh) more = false;
+                slot = base + __popc(idle & lt_mask);
+            } else {
+                const uint32_t cbu = __shfl_sync(0xffffffffu, cb, 0), nbu = __shfl_sync(0xffffffffu, nb, 0);
+                const uint32_t rank = __popc(idle & lt_mask), left = kClaim - cpos;
+                slot = rank < left ? cbu + cpos + rank : nbu + (rank - left);
+                {
+                    // the next claim's records into L1 ahead of their loads: one line per lane
+                    // (the claim's 32 records span 24 lines, 28 with the polarisation word)
+                    constexpr uint32_t kLines = (kClaim * 16u * (POL ? kWaveRec16 + 1 : kWaveRec16)) / 128u;
+                    const char *q = (const char *)wave_rec<POL>(B, nbu) + 128u * lane;
+                    if (lane < kLines && nbu < nh32 && q < (const char *)wave_rec<POL>(B, B.cap))
+                        asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
                 }
+                cpos += n_idle;
+                uint32_t next = cbu + cpos;
+                if (cpos >= kClaim) {
+                    cpos -= kClaim;
+                    next = nbu + cpos;
+                    if (lane == 0) {
+                        cb = nb;
+                        nb = atomicAdd(head32, kClaim);
+                    }
+                }
+                if (next >= nh32) more = false;
             }
-            if (next >= nh32) more = false;
             if (!alive && slot < nh) {
                 const float4 *r = wave_rec<POL>(B, slot);
                 const float4 r0 = __ldcs(r), r1 = __ldcs(r + 1), r2 = __ldcs(r + 2), r3 = __ldcs(r + 3),

@@ -7,11 +7,12 @@
 // the instruction is the one named, not the compiler's choice): chain j takes
 // its own previous value, chain j + 1's, and for three-operand forms a
 // loop-invariant register, so that operands come from different register
-// banks or the operand-reuse cache.  32 resident warps per SM.  Each block
-// times its loop with clock64() (SM cycles) and %globaltimer (ns), which
-// gives the rate per SM clock and the SM clock the run saw; CUDA events give
-// the whole-GPU rate per second.  Loop overhead is one add, one compare and one
-// branch per 64 measured instructions.
+// banks or the operand-reuse cache.  32 warps per SM.  CUDA events give the
+// whole-GPU rate per second; each block times its loop with clock64() (SM
+// cycles) and %globaltimer (ns), whose ratio is the SM clock the run saw, and
+// the rate per SM per clock is the rate per second over SMs x that clock.
+// Loop overhead is one add, one compare and one branch per 64 measured
+// instructions.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -192,11 +193,13 @@ extern "C" heart_status heart_pipe_peaks(void *stream, heart_pipe_rates *out) {
             break;
         }
         const double warp_inst = (double)threads / 32.0 * (double)iters * kPipeUnroll * 8.0;
-        const double cycles_per_block = (double)acc[0] / blocks;   // the blocks of an SM run at once
         out->warp_inst_per_s[op] = warp_inst / (ms * 1e-3);
-        out->warp_inst_per_clk_sm[op] = warp_inst / (cycles_per_block * sms);
-        if (acc[1] > 0) {
-            clk_sum += (double)acc[0] / ((double)acc[1] * 1e-9);
+        // the SM clock of this run: clock64 cycles per globaltimer second, summed over the
+        // blocks (a ratio within each block, whether or not all blocks run at once)
+        const double clk = acc[1] > 0 ? (double)acc[0] / ((double)acc[1] * 1e-9) : 0.0;
+        out->warp_inst_per_clk_sm[op] = clk > 0 ? out->warp_inst_per_s[op] / (clk * sms) : 0.0;
+        if (clk > 0) {
+            clk_sum += clk;
             ++clk_n;
         }
     }

@@ -3,15 +3,16 @@
 // Jobs are admitted in arrival order while their detector images fit under
 // the memory cap; admitted jobs stay resident (tables in their spectrometer
 // handles, images and tallies here) until released.  A worker thread plans
-// rounds: every admitted, unfinished FP32 job gets a slice of its remaining
-// rays; the slices of jobs of 2^18 rays or more that the two-pass trace takes
-// run as single-job two-pass launches, the others together in one persistent
-// batched launch.  Jobs that arrive
+// rounds in arrival order: jobs with few rays left are traced whole, the
+// others share a budget of rays per round oldest first, in long slices; slices
+// of 2^22 rays or more run as single-job two-pass launches, the others
+// together in one persistent batched launch.  Jobs that arrive
 // while a round is on the GPU join the next round, which is enqueued before
 // the previous one has finished (two rounds in flight), so the device never
 // waits for the host.  Each ray keeps its counter-based stream
-// (ray_offset = rays already traced for the job), so a job's image is the same
-// whether it ran alone or mixed with others.
+// (ray_offset = rays already traced for the job), and every FP32 kernel traces
+// a ray bit for bit alike, so a job's image is the same whether it ran alone or
+// mixed with others.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -76,9 +77,10 @@ struct heart_server {
     uint64_t next_id = 1;
     bool stop = false;
     std::thread worker;
-    uint64_t round_rays = 64ull << 20;       // target rays per round (about 20-40 ms of GPU work)
-    uint64_t min_slice = 1ull << 20;
-    uint64_t two_pass_min = heart::kTwoPassMinRays;   // jobs this large run their slices as two-pass launches
+    uint64_t round_rays = 64ull << 20;       // rays per round for jobs beyond small_job (about 2.5 ms of GPU work)
+    uint64_t min_slice = 1ull << 22;         // a large job's slice is never smaller (unless it is its last)
+    uint64_t small_job = 1ull << 20;         // jobs with this many rays left are traced whole in a round
+    uint64_t two_pass_min = 1ull << 22;      // slices this large run as two-pass launches, the rest batched
     // pinned host buffers for the rounds' work plans (reused; a round holds one until it retires)
     std::vector<std::pair<unsigned char *, size_t>> pins;
     unsigned long long *tally_pin = nullptr;          // pinned read-back of finished jobs' tallies
@@ -217,14 +219,27 @@ void worker_main(heart_server *s) {
             if (inflight.empty()) s->cv_work.wait(lk, has_work);
             else has_work();
             if (s->stop && inflight.empty()) break;
-            // plan the next round: a fair slice for every admitted job, oldest first
+            // plan the next round in arrival order: every job with at most small_job rays
+            // left is traced whole (small jobs share one batched launch and never wait
+            // behind large ones for more than a round); the round's budget of round_rays
+            // goes to the other jobs oldest first, in slices of at least min_slice, so a
+            // large job runs in a few long launches as it would alone
             std::vector<Job *> active;
             for (auto &kv : s->jobs)
                 if (kv.second->state == ADMITTED && kv.second->scheduled < kv.second->n) active.push_back(kv.second);
             std::sort(active.begin(), active.end(), [](Job *a, Job *b) { return a->id < b->id; });
-            const uint64_t share = active.empty() ? 0 : std::max<uint64_t>(s->min_slice, s->round_rays / active.size());
+            uint64_t budget = s->round_rays;
             for (Job *j : active) {
-                const uint64_t take = std::min<uint64_t>(share, j->n - j->scheduled);
+                const uint64_t left = j->n - j->scheduled;
+                uint64_t take = 0;
+                if (left <= s->small_job) {
+                    take = left;
+                } else if (budget > 0) {
+                    take = std::min<uint64_t>(left, std::max<uint64_t>(budget, s->min_slice));
+                    budget -= std::min(budget, take);
+                } else {
+                    continue;
+                }
                 if (j->prec == HEART_FP64) { fp64_jobs.push_back(j); continue; }
                 slice_jobs.push_back(j);
                 nr.push_back(take);
@@ -256,11 +271,10 @@ void worker_main(heart_server *s) {
             }
             r.last = last;
             heart_status st = HEART_OK;
-            // Slices of large jobs that the two-pass trace takes (one reflection order)
-            // run as single-job two-pass launches, which are faster than the
-            // persistent batched kernel; the other slices share one batched launch.  The
-            // choice goes by the job's size, not the slice's, so a job's rays run on the
-            // same kernels however the rounds slice them.
+            // Slices of 2^22 rays or more that the two-pass trace takes run as single-job
+            // two-pass launches, the others share one persistent batched launch.  Every
+            // FP32 kernel traces a ray bit for bit alike, so a job's image does not depend
+            // on how the rounds slice it or which kernel a slice runs on.
             std::vector<const SpecParams *> bS;
             std::vector<SourceParams> bP;
             std::vector<void *> bimg;
@@ -268,7 +282,7 @@ void worker_main(heart_server *s) {
             std::vector<uint64_t> bnr, bseed, boff;
             for (size_t i = 0; i < slice_jobs.size() && st == HEART_OK; ++i) {
                 const SpecParams &sp = *S[i];
-                if (slice_jobs[i]->n >= s->two_pass_min && takes_two_pass(sp, P[i])) {
+                if (nr[i] >= s->two_pass_min && takes_two_pass(sp, P[i])) {
                     WaveLease lease;
                     st = wave_acquire(nr[i], s->stream, &lease);
                     if (st != HEART_OK) break;
