@@ -453,14 +453,18 @@ typedef struct {
 heart_status heart_pipe_peaks(void *stream, heart_pipe_rates *out);
 
 /* Test support (no counterpart in the paper): device functions of the FP32
- * kernels evaluated on n values of the device arrays d_x (and d_y), results in
- * d_out (device, n floats); asynchronous on `stream`.  which = 0: the arccos
- * of the azimuth arcs, acos(x / y) for y > 0 (spec may be NULL); 1: the
- * spectrometer's rocking curve divided by its maximum, R(x) / R_max at
- * x = Delta - Delta_M; 2: the upper bound of R / R_max over |x'| >= x that the
- * kernels' early rejection uses. */
+ * kernels evaluated on n values of the device arrays d_x (and d_y, d_z),
+ * results in d_out (device, n floats); asynchronous on `stream`.  which = 0:
+ * the arccos of the azimuth arcs, acos(x / y) for y > 0 (spec may be NULL,
+ * d_z unused); 1: the spectrometer's rocking curve divided by its maximum,
+ * R(x) / R_max at x = Delta - Delta_M; 2: the upper bound of R / R_max over
+ * |x'| >= x that the kernels' early rejection uses (1 and 2 need spec, read
+ * d_x only); 3: the upper bound the walk places on the measure, in units of
+ * pi, of the azimuth arc with cos(xi') in (x, y) / z (z > 0); 4: that measure
+ * as the thinned sampler computes it (3 and 4: spec may be NULL).  Null
+ * arrays the function reads, or which outside 0..4, give HEART_EINVAL. */
 heart_status heart_check_functions(heart_spectrometer *spec, int32_t which, const float *d_x, const float *d_y,
-                                   float *d_out, uint64_t n, void *stream);
+                                   const float *d_z, float *d_out, uint64_t n, void *stream);
 
 const char *heart_last_error(void);
 

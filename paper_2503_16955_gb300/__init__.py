@@ -182,7 +182,7 @@ def library(path=None):
     L.heart_job_latency.argtypes = [vp, u64, C.POINTER(C.c_double)]
     L.heart_fetch_image.argtypes = [vp, u64, vp, i32]
     L.heart_pipe_peaks.argtypes = [vp, C.POINTER(heart_pipe_rates)]
-    L.heart_check_functions.argtypes = [vp, i32, vp, vp, vp, u64, vp]
+    L.heart_check_functions.argtypes = [vp, i32, vp, vp, vp, vp, u64, vp]
     L.heart_calibration_map.argtypes = [vp, C.POINTER(heart_source_desc), C.c_double, C.c_double, u64, u64, i32,
                                         vp, vp, vp, vp, C.POINTER(heart_tally)]
     L.heart_last_error.restype = C.c_char_p
@@ -471,17 +471,20 @@ def heart_trace_batch(specs, sources, n_rays, seeds, d_images, stream=None):
 STATIC_MAX_JOBS = 64
 
 
-CHECK_FUNCTIONS = {"acos_ratio": 0, "irc_rel": 1, "irc_bound": 2}
+CHECK_FUNCTIONS = {"acos_ratio": 0, "irc_rel": 1, "irc_bound": 2, "arc_bound": 3, "arc_measure": 4}
 
 
-def heart_check_functions(spec, which, x, y=None):
+def heart_check_functions(spec, which, x, y=None, z=None):
     """a device function of the FP32 kernels on float32 CUDA tensors (tests)"""
     import torch
     x = x.contiguous()
+    y = y.contiguous() if y is not None else None
+    z = z.contiguous() if z is not None else None
     out = torch.empty_like(x)
     st = library().heart_check_functions(spec.handle if spec is not None else None, CHECK_FUNCTIONS[which],
                                          C.c_void_p(x.data_ptr()),
-                                         C.c_void_p(y.contiguous().data_ptr()) if y is not None else None,
+                                         C.c_void_p(y.data_ptr()) if y is not None else None,
+                                         C.c_void_p(z.data_ptr()) if z is not None else None,
                                          C.c_void_p(out.data_ptr()), x.numel(),
                                          C.c_void_p(_stream_ptr(None)))
     _check(st)

@@ -714,18 +714,22 @@ __device__ __forceinline__ float acos_ratio(float m, float b, float ib) {
 // arc measure in units of pi), then place xi' uniformly over the arcs (sign
 // from the second half of the conditional uniform).  Out of line: rarely run.
 // Returns (kept, cos xi', sin xi', sign).
+// one arc of arc_sample: xi' in [0, pi] with cos(xi') in (lo, hi) / b, as its start
+// acos(hi / b) and its length (both 0 for an empty interval)
+__device__ __forceinline__ void arc_piece(float lo, float hi, float b, float ib, float &start, float &len) {
+    start = 0.0f;
+    len = 0.0f;
+    if (lo < hi && lo < b && hi > -b) {
+        start = acos_ratio(hi, b, ib);
+        len = acos_ratio(lo, b, ib) - start;
+    }
+}
+
 __device__ __forceinline__ float4 arc_sample(float iv0, float iv1, float iv2, float iv3, float b, float ib,
                                           float t3pbar) {
-    const float iv[4] = {iv0, iv1, iv2, iv3};
     float start[2], len[2];
-    for (int j = 0; j < 2; ++j) {
-        start[j] = 0.0f;
-        len[j] = 0.0f;
-        if (iv[2 * j] < iv[2 * j + 1] && iv[2 * j] < b && iv[2 * j + 1] > -b) {
-            start[j] = acos_ratio(iv[2 * j + 1], b, ib);
-            len[j] = acos_ratio(iv[2 * j], b, ib) - start[j];
-        }
-    }
+    arc_piece(iv0, iv1, b, ib, start[0], len[0]);
+    arc_piece(iv2, iv3, b, ib, start[1], len[1]);
     const float arcs = len[0] + len[1];
     const float pxi = arcs * 0.318309886f;
     if (!(t3pbar < pxi)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -735,6 +739,25 @@ __device__ __forceinline__ float4 arc_sample(float iv0, float iv1, float iv2, fl
     float sxp, cxp;
     __sincosf(xp, &sxp, &cxp);                        // xp in [0, pi]: absolute error < 1e-6
     return make_float4(1.0f, cxp, sxp, sg);
+}
+
+// Upper bound, in units of pi, of the measure of xi' in [0, pi] with cos(xi') in
+// (lo, hi) / b (ib = 1 / b), above arc_sample's FP32 value of that measure:
+//   acos(c1) - acos(c2) <= (c2 - c1) / sqrt(1 - m^2), m = max(|c1|, |c2|) (acos' slope
+//   is largest there; 1 - m^2 = (1 - m)(1 + m) with 1 - m = (b - |.|) / b; no bound once
+//   the interval reaches +-1), and
+//   acos(c1) - acos(c2) <= min(acos(c1), pi - acos(c2)) = acos(1 - e), e the smaller of
+//   1 - c1 and 1 + c2 (formed as (b -+ .) / b, accurate at the edges), and
+//   acos(1 - e) <= (pi / 2) sqrt(2 e) for e in [0, 2];
+// 1e-4 relative and 4e-6 absolute cover FP32 rounding here and arc_sample's arccos
+// (2e-8 + 2^-20 (acos + 1) per end)
+__device__ __forceinline__ float arc_bound(float lo, float hi, float b, float ib) {
+    if (!(lo < hi && lo < b && hi > -b)) return 0.0f;     // arc_sample's empty interval
+    const float d = (hi - lo) * ib, om = (b - fmaxf(fabsf(lo), fabsf(hi))) * ib;
+    const float slope = d * rsqrtf(fmaxf(om * (2.0f - om), 1e-30f));
+    const float e = fminf(fminf((b - lo) * ib, (b + hi) * ib), 2.0f);
+    const float edge = 2.2214415f * sqrtf(e);
+    return __fmaf_rn(fminf(slope, edge), 0.318309886f * 1.0001f, 4e-6f);
 }
 
 // first table word of process (b): that of the tilt-grid point q_j = 2^(j/8 - 48) just below q_min
@@ -1314,8 +1337,11 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
             iv[0] = S1 - a; iv[1] = S2 - a; iv[2] = -S2 - a; iv[3] = -S1 - a;
         }
         const float t3pbar = u01_32(w[3]) * s.pbar;
-        // P_xi <= 2 acos(1 - w) / pi <= sqrt(2 w), w = (S2 - S1) / b: most candidates end here
+        // P_xi <= 2 acos(1 - w) / pi <= sqrt(2 w), w = (S2 - S1) / b: half of the candidates end here
         if (t3pbar * t3pbar * b >= 2.0002f * (e2 - e1)) return -1;
+        // a tighter bound before the arcs themselves (most of the rest end here); it lies
+        // above arc_sample's measure, so no candidate that arc_sample keeps ends here
+        if (t3pbar >= arc_bound(iv[0], iv[1], b, ib) + arc_bound(iv[2], iv[3], b, ib)) return -1;
         const float4 r = arc_sample(iv[0], iv[1], iv[2], iv[3], b, ib, t3pbar);
         if (r.x == 0.0f) return -1;                           // outside the arcs: cannot reflect
         const float cxp = r.y, sxp = r.z, sg = r.w;
@@ -1956,14 +1982,22 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
 
 // Device functions of the FP32 kernels evaluated on arrays (tests):
 // 0: acos_ratio(x, y, 1 / y); 1: the rocking curve R(x) / R_max (irc_rel32);
-// 2: its upper bound over |x'| >= x used by the early rejection (irc_bound32)
+// 2: its upper bound over |x'| >= x used by the early rejection (irc_bound32);
+// 3: the arc measure bound arc_bound(x, y, z, 1 / z); 4: the measure arc_sample
+// takes for that interval, its arc length over pi
 __global__ void k_check_functions(const __grid_constant__ Launch32 L, int which, const float *x, const float *y,
-                                  float *out, uint64_t n) {
+                                  const float *z, float *out, uint64_t n) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         float r;
         if (which == 0) r = acos_ratio(x[i], y[i], 1.0f / y[i]);
         else if (which == 1) r = irc_rel32<-1>(L, x[i]);
-        else r = irc_bound32<-1>(L, x[i]);
+        else if (which == 2) r = irc_bound32<-1>(L, x[i]);
+        else if (which == 3) r = arc_bound(x[i], y[i], z[i], 1.0f / z[i]);
+        else {
+            float st, len;
+            arc_piece(x[i], y[i], z[i], 1.0f / z[i], st, len);
+            r = len * 0.318309886f;
+        }
         out[i] = r;
     }
 }
@@ -2890,11 +2924,13 @@ extern "C" heart_status heart_trace_batch_static(heart_spectrometer *const *spec
 // test support: device functions on arrays
 // ---------------------------------------------------------------------------
 extern "C" heart_status heart_check_functions(heart_spectrometer *h, int32_t which, const float *d_x,
-                                              const float *d_y, float *d_out, uint64_t n, void *stream) {
+                                              const float *d_y, const float *d_z, float *d_out, uint64_t n,
+                                              void *stream) {
     using namespace heart;
-    if (which < 0 || which > 2) return fail(HEART_EINVAL, "unknown function");
-    if (!d_x || !d_out || (which == 0 && !d_y)) return fail(HEART_EINVAL, "null array");
-    if (which != 0 && !h) return fail(HEART_EINVAL, "null spectrometer");
+    if (which < 0 || which > 4) return fail(HEART_EINVAL, "unknown function");
+    if (!d_x || !d_out || ((which == 0 || which >= 3) && !d_y) || (which >= 3 && !d_z))
+        return fail(HEART_EINVAL, "null array");
+    if ((which == 1 || which == 2) && !h) return fail(HEART_EINVAL, "null spectrometer");
     if (n == 0) return HEART_OK;
     Launch32 L;
     std::memset(&L, 0, sizeof L);
@@ -2917,7 +2953,7 @@ extern "C" heart_status heart_check_functions(heart_spectrometer *h, int32_t whi
         make_launch32(h->p, P, n, 1, 0, L);
     }
     const int blocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)num_sms() * 8);
-    k_check_functions<<<blocks, 256, 0, (cudaStream_t)stream>>>(L, which, d_x, d_y, d_out, n);
+    k_check_functions<<<blocks, 256, 0, (cudaStream_t)stream>>>(L, which, d_x, d_y, d_z, d_out, n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "check kernel");
     return HEART_OK;

@@ -87,3 +87,45 @@ def test_rocking_curve_and_its_early_rejection_bound(H, irc, kw):
     tol = np.maximum(np.abs(hi - ref), np.abs(lo - ref)) + 1e-6
     bad = np.abs(rel - ref) > tol
     assert not bad.any(), (irc, float(a[bad][0]), float(rel[bad][0]), float(ref[bad][0]))
+
+
+def test_arc_bound_lies_above_the_thinned_samplers_arc_measure(H):
+    # The walk rejects a process-(b) candidate before computing its azimuth arcs when
+    # t3 pbar is at least the sum of the two arcs' bounds; the rejection changes no
+    # outcome only if each bound lies above the measure arc_sample computes for the
+    # arc (by more than the rounding of a two-term sum).  Intervals (lo, hi) / b over
+    # [-1.2, 1.2], narrow ones, ones next to +-1 and ones across it, for b over 8 decades.
+    import torch
+    rng = np.random.default_rng(11)
+    for b in (1e-7, 2e-5, 3e-3, 0.07, 0.5, 0.93, 1.0):
+        parts = []
+        c = rng.uniform(-1.2, 1.2, (2, 300_000))
+        parts.append((c.min(0), c.max(0)))
+        mid = rng.uniform(-1.0, 1.0, 200_000)
+        wid = np.geomspace(1e-7, 1e-1, 200_000)
+        parts.append((mid - wid, mid + wid))
+        e = np.geomspace(1e-8, 2.0, 700)
+        e1, e2 = np.meshgrid(e, e)
+        m = e1 > e2
+        parts.append((1.0 - e1[m], 1.0 - e2[m]))             # next to +1
+        parts.append((-1.0 + e2[m], -1.0 + e1[m]))           # next to -1
+        lo = np.concatenate([p[0] for p in parts]) * b
+        hi = np.concatenate([p[1] for p in parts]) * b
+        x = torch.from_numpy(lo.astype(np.float32)).cuda()
+        y = torch.from_numpy(hi.astype(np.float32)).cuda()
+        z = torch.full_like(x, b)
+        bound = H.heart_check_functions(None, "arc_bound", x, y, z).cpu().numpy().astype(np.float64)
+        meas = H.heart_check_functions(None, "arc_measure", x, y, z).cpu().numpy().astype(np.float64)
+        lo32, hi32 = x.cpu().numpy(), y.cpu().numpy()
+        b32 = np.float32(b)
+        empty = ~((lo32 < hi32) & (lo32 < b32) & (hi32 > -b32))   # no arc: both are 0
+        assert np.all(bound[empty] == 0.0) and np.all(meas[empty] == 0.0)
+        gap = (bound - meas)[~empty]
+        assert empty.mean() < 0.2 and np.all(gap >= 1e-6), (b, float(gap.min()))
+        # and above the exact measure of the FP32 interval
+        c1 = np.clip(lo32.astype(np.float64) / np.float64(b32), -1, 1)
+        c2 = np.clip(hi32.astype(np.float64) / np.float64(b32), -1, 1)
+        exact = np.where(c1 < c2, np.arccos(c1) - np.arccos(c2), 0.0) / math.pi
+        assert np.all(bound >= exact), (b, float((exact - bound).max()))
+        # the bound is no trivial one: within a factor 2.3 of the measure (plus its margin)
+        assert np.all(bound <= 2.3 * exact + 1e-5), (b, float((bound - 2.3 * exact).max()))
