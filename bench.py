@@ -89,15 +89,15 @@ WAVE_CHUNK = 1 << 25
 # Per emitted ray of the von Hamos workload, from ncu captures of the two-pass kernels
 # (both passes summed): DRAM bytes read + written (the hit queue written and read back;
 # one chunk of 2^24 rays, whose 0.66 GB queue, unlike a smaller one, does not stay in
-# L2) and warp instructions issued per pipe (2^22 rays); valid only for the kernel
-# sources with the hash below.
-TRAFFIC_BYTES_PER_RAY = (0.240128e6 + 609.071104e6 + 676.584704e6 + 0.215808e6) / (1 << 24)   # 2^24 rays
-PIPE_INST_PER_RAY = {"alu": 11.6558, "fma": 14.7734, "fmaheavy": 6.1623, "fmalite": 9.4165, "xu": 1.8928,
-                     "lsu": 1.4364, "adu": 1.4870, "cbu": 3.0297, "uniform": 0.2314, "fp64": 0.0168,
-                     "total": 38.1884}
+# L2) and warp instructions issued per pipe (2^22 rays), both with the library's default
+# launch shape (bench.py --no-tune); valid only for the kernel sources with the hash below.
+TRAFFIC_BYTES_PER_RAY = (0.035840e6 + 608.962304e6 + 676.955392e6 + 0.267264e6) / (1 << 24)   # 2^24 rays
+PIPE_INST_PER_RAY = {"alu": 11.3783, "fma": 14.1796, "fmaheavy": 5.8801, "fmalite": 9.0086, "xu": 1.9095,
+                     "lsu": 1.4357, "adu": 1.4858, "cbu": 2.8433, "uniform": 0.2313, "fp64": 0.0168,
+                     "total": 36.9847}
 TRAFFIC_SOURCES = ("paper_2503_16955_gb300/csrc/heart_fp32.cu", "paper_2503_16955_gb300/csrc/heart_fp64.cuh",
                    "paper_2503_16955_gb300/csrc/heart_internal.h")
-TRAFFIC_SOURCE_HASH = "6558dd8a88eef9f1"
+TRAFFIC_SOURCE_HASH = "b613ab8f24aaec1d"
 
 
 def sources_hash():
@@ -152,6 +152,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--serving-jobs", type=int, default=10_000)
     p.add_argument("--no-extra", action="store_true", help="skip batched / serving / FP64 measurements")
+    p.add_argument("--no-tune", action="store_true",
+                   help="keep the library's default launch shape instead of heart_autotune's choice (profiling: "
+                        "the tuner times its probes, and under a profiler those times say nothing)")
     return p.parse_args()
 
 
@@ -510,7 +513,8 @@ def main():
         if world > 1:
             dist.barrier()
 
-    tune = H.heart_autotune(spec, w["source"], probe_rays=min(n, 1 << 24), stream=stream)
+    tune = ("library default (refill 8 idle lanes, 6 blocks per SM)" if args.no_tune else
+            H.heart_autotune(spec, w["source"], probe_rays=min(n, 1 << 24), stream=stream))
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
             H.heart_trace(spec, w["source"], n, w["seed"], offset(1000 + i), img, precision="fp32",

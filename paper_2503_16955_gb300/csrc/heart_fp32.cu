@@ -147,18 +147,18 @@ struct WarpBuf {
 template <bool RK>
 __device__ __forceinline__ void philox_l(const Launch32 &L, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                          uint32_t out[4]) {
-    if (!RK) {
+    if constexpr (!RK) {
         philox4x32_10(c0, c1, c2, c3, L.k0, L.k1, out);
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-        const uint32_t n0 = hi1 ^ c1 ^ L.rk0[r], n2 = hi0 ^ c3 ^ L.rk1[r];
-        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        for (int r = 0; r < 10; ++r) {
+            const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+            const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+            const uint32_t n0 = hi1 ^ c1 ^ L.rk0[r], n2 = hi0 ^ c3 ^ L.rk1[r];
+            c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        }
+        out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
     }
-    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
 __device__ __forceinline__ float u01_32(uint32_t w) {
