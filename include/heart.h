@@ -390,7 +390,7 @@ heart_status heart_autotune(heart_spectrometer *spec, const heart_source_desc *s
  *   - The work area is uploaded from pageable host memory, so the call may
  *     wait for earlier work on `stream` before it returns.
  *   - The first call on each device looks up the array's device address (with
- *     that device current), so it should come before any stream capture.
+ *     that device current).
  * If `out` is non-NULL the call synchronises `stream` and fills n_jobs tallies. */
 heart_status heart_trace_batch_static(heart_spectrometer *const *specs, const heart_source_desc *const *srcs,
                                       const uint64_t *n_rays, const uint64_t *seeds, void *const *d_images,
