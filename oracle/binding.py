@@ -129,7 +129,8 @@ class SegInfo(C.Structure):
                 ("ra", C.c_double), ("qmin", C.c_double), ("pbar", C.c_double), ("S1", C.c_double),
                 ("S2", C.c_double), ("w0", C.c_uint64), ("wspan", C.c_uint64), ("lam", C.c_double),
                 ("mu", C.c_double), ("pa", C.c_double), ("wn", C.c_double), ("wf", C.c_double),
-                ("psis", C.c_double), ("pin", C.c_double), ("pio", C.c_double)]
+                ("psis", C.c_double), ("pin", C.c_double), ("pio", C.c_double), ("w1", C.c_uint64),
+                ("w2", C.c_uint64), ("pbarB", C.c_double), ("sA", C.c_double)]
 
 
 _lib = None

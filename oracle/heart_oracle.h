@@ -276,6 +276,8 @@ typedef struct {
     uint64_t w0, wspan;
     double lam, mu, pa;           /* the order's candidate rate; the segment's majorant, mu0 / mu */
     double wn, wf, psis, pin, pio;
+    uint64_t w1, w2;              /* one order: band B of process (b), table words [w1, w2) */
+    double pbarB, sA;             /* band B's arc-measure bound; band A's share of process (b) */
 } orc_seg_info;
 int orc_segment_bounds(const orc_spec *s, int64_t n, const double *E_keV, const double *x, const double *k,
                        int h, orc_seg_info *out);

@@ -884,12 +884,22 @@ static int next4(wsrc *ws, uint32_t w[4]) {
  * the table interval holding the grid point q_j = 2^(j/8 - 48) just below
  * q_min; then kept with probability P_xi(theta) / pbar (P_xi: the arc
  * measure, pbar >= P_xi on the segment), its azimuth uniform over the arcs.
- * A segment with d <= X* keeps the plain candidate stream (v* = 1). */
+ * A segment with d <= X* keeps the plain candidate stream (v* = 1).
+ * pbar is the arc measure's bound at the smallest tilt, where the window can
+ * sit at the edge of cos(xi') and the measure is largest; with one reflection
+ * order, process (b) is split further by the tilt (marking theorem again):
+ * band B, the table words [w1, w2) of the tilts from the grid point 12 steps
+ * above q_min's (a factor 2^1.5 in q) to q_J = 2^(-33/8) (0.34 rad), where the
+ * window stays away from the edge, is generated at its own bound pbarB < pbar;
+ * band A, the words [w0, w1) and [w2, 2^32), at pbar.  A (b) candidate falls in
+ * band A with probability sA = P_A pbar / (P_A pbar + P_B pbarB). */
 typedef struct {
     double ra, vstar;         /* share of process (a) among the order's scatter candidates, its v range */
     double qmin, pbar;        /* process (b): tilt bound and arc-measure bound */
     double S1, S2;            /* |k.n| window of |Delta| < X* */
     uint64_t w0, wspan;       /* process (b): table words [w0, w0 + wspan) */
+    uint64_t w1, w2;          /* band B: table words [w1, w2) (w1 = w2 = w0: no band B) */
+    double pbarB, sA;         /* band B's arc-measure bound; band A's share of process (b) */
     double lam;               /* the order's candidate rate on the segment */
     /* no rocking curve, thinned: W at the smallest tilt each Bragg cone can
      * reach on the segment, relative to W(0); the facing cone's window |psi| <
@@ -916,23 +926,60 @@ static uint64_t word_floor(const orc_mdf_table *t, double q) {
     return (uint64_t)lo << 20;
 }
 
-/* w0 for a tilt bound q_min: the grid point q_j = 2^(j/8 - 48) just below it
- * (j = floor(8 log2 q_min) + 384, at most 391), then its table interval */
-static uint64_t word_floor_grid(const orc_mdf_table *t, double qmin) {
-    if (!(qmin >= exp2(-48.0))) return 0;
+/* the grid point q_j = 2^(j/8 - 48) just below a tilt bound q_min:
+ * j = floor(8 log2 q_min) + 384, at most 391; -1 below the grid */
+static int grid_index(double qmin) {
+    if (!(qmin >= exp2(-48.0))) return -1;
     int j = (int)floor(8.0 * log2(qmin)) + 384;
-    if (j > 391) j = 391;
-    return word_floor(t, exp2(j / 8.0 - 48.0));
+    return j > 391 ? 391 : j;
+}
+
+/* w0 for a tilt bound q_min: the table interval of its grid point */
+static uint64_t word_floor_grid(const orc_mdf_table *t, double qmin) {
+    int j = grid_index(qmin);
+    return j < 0 ? 0 : word_floor(t, exp2(j / 8.0 - 48.0));
+}
+
+#define ORC_BAND_DJ 12        /* band B starts this many grid steps above q_min's grid point */
+#define ORC_BAND_J2 351       /* and ends at the grid point q_J = 2^(-33/8) */
+
+/* Band B's arc-measure bound, in units of pi: every tilt q in [q1, q2] (q2 <=
+ * 1 - cos(pi / 2)) at every point of a segment with |k.N| in [lo, hi].  With a
+ * = |k.N|, c_a = sqrt(1 - a^2) and b = c_a sin(theta), the window's two
+ * intervals of cos(xi') are (S - a (1 - q)) / b and (-S - a (1 - q)) / b for S
+ * in (S1, S2), each of width w <= (S2 - S1) / (c_a,min sin theta1).  The first
+ * stays within |y| <= M = D / (c_a,min sin theta1) + hi tan(theta2 / 2) / c_a,min
+ * (D = max |S - a| over the window and the segment; q / sin(theta) =
+ * tan(theta / 2)), where the arcsine measure of an interval is at most its
+ * width over sqrt(1 - M^2); the second lies beyond m = (S1 + lo (1 - q2)) /
+ * (c_a,max sin theta2), so its measure is at most acos(m) (0 if m >= 1); an
+ * interval of width w has measure at most acos(1 - w) wherever it lies. */
+static double band_b_bound(double lo, double hi, double S1, double S2, double q1, double q2) {
+    double h = fmin(hi, 1.0);
+    double camin = sqrt(fmax(0.0, 1.0 - h * h)), camax = sqrt(fmax(0.0, 1.0 - lo * lo));
+    double s1 = sqrt(q1 * (2.0 - q1)), s2 = sqrt(q2 * (2.0 - q2)), t2 = sqrt(q2 / (2.0 - q2));
+    if (!(camin > 0.0) || !(s1 > 0.0)) return 1.0;
+    double D = fmax(fabs(S1 - hi), fabs(S2 - lo));
+    double M = D / (camin * s1) + hi * t2 / camin;
+    double w = (S2 - S1) / (camin * s1);
+    if (!(M < 1.0)) return 1.0;
+    double edge = acos(fmax(-1.0, 1.0 - w));
+    double same = fmin(edge, w / sqrt(1.0 - M * M));
+    double m = (S1 + lo * (1.0 - q2)) / (camax * s2);
+    double mirror = m >= 1.0 ? 0.0 : fmin(edge, acos(fmax(-1.0, m)));
+    return (same + mirror) / PI;
 }
 
 /* the bound of one order h on the segment with |k.N| in [lo, hi] */
-static void bound_order(const geom *g, const orc_ray_consts *rc, int h, double lo, double hi, order_bound *b) {
+static void bound_order(const geom *g, const orc_ray_consts *rc, int h, double lo, double hi, int band,
+                        order_bound *b) {
     const orc_spec *s = g->s;
     memset(b, 0, sizeof *b);
     b->ra = 1.0;
     b->vstar = 1.0;
     b->pbar = 1.0;
     b->wspan = 1ull << 32;
+    b->sA = 1.0;
     b->lam = rc->ord_qr[h];
     b->wn = b->wf = 1.0;
     b->psis = PI;
@@ -981,9 +1028,28 @@ static void bound_order(const geom *g, const orc_ray_consts *rc, int h, double l
      * interval of that width has arcsine measure at most acos(1 - w) / pi */
     double w = (b->S2 - b->S1) / bmin;
     b->pbar = (w >= 2.0 || !(bmin > 0)) ? 1.0 : fmin(1.0, 2.0 * acos(1.0 - w) / PI);
+    b->w1 = b->w2 = b->w0;
+    b->pbarB = b->pbar;
+    int j0 = grid_index(b->qmin);
+    if (band && j0 >= 0 && j0 + ORC_BAND_DJ < ORC_BAND_J2) {
+        uint64_t w1 = word_floor(g->mdf, exp2((j0 + ORC_BAND_DJ) / 8.0 - 48.0));
+        uint64_t w2 = word_floor(g->mdf, exp2(ORC_BAND_J2 / 8.0 - 48.0));
+        if (w1 < w2) {
+            /* tilts of band B: from the table knot that starts w1's interval to q_J */
+            double pB = band_b_bound(lo, hi, b->S1, b->S2, g->mdf->body[w1 >> 20], exp2(ORC_BAND_J2 / 8.0 - 48.0));
+            if (pB < b->pbar) {
+                b->w1 = w1;
+                b->w2 = w2;
+                b->pbarB = pB;
+            }
+        }
+    }
     double QR = rc->ord_qr[h];
-    double PA = (double)b->wspan / 4294967296.0;
-    double la = QR * g->vstar, lb = QR * (1.0 - g->vstar) * PA * b->pbar;
+    double PA = (double)((b->w1 - b->w0) + ((1ull << 32) - b->w2)) / 4294967296.0;
+    double PB = (double)(b->w2 - b->w1) / 4294967296.0;
+    double lA = PA * b->pbar, lB = PB * b->pbarB;
+    b->sA = lA + lB > 0.0 ? lA / (lA + lB) : 1.0;
+    double la = QR * g->vstar, lb = QR * (1.0 - g->vstar) * (lA + lB);
     b->vstar = g->vstar;
     b->lam = la + lb;
     b->ra = la / (la + lb);
@@ -1009,7 +1075,7 @@ static void bound_segment(const geom *g, const orc_ray_consts *rc, const double 
     }
     double lam = 0.0;
     for (int h = 0; h < b->n; ++h) {
-        bound_order(g, rc, h, lo, hi, &b->o[h]);
+        bound_order(g, rc, h, lo, hi, b->n == 1, &b->o[h]);
         lam += b->o[h].lam;
     }
     double run = 0.0;
@@ -1149,18 +1215,30 @@ static void walk(const geom *g, const orc_ray_consts *rc, double x[3], double k[
             q = orc_mdf_table_lookup(g->mdf, w[2]);
             xi = 2.0 * PI * U(w[3]);
         } else {                                         /* process (b) */
-            v = ob->vstar + (1.0 - ob->vstar) * ((v - ob->ra) / (1.0 - ob->ra));
-            uint32_t wq = (uint32_t)(ob->w0 + (((uint64_t)w[2] * ob->wspan) >> 32));
-            q = orc_mdf_table_lookup(g->mdf, wq);
+            double vb = (v - ob->ra) / (1.0 - ob->ra), pb;
+            uint64_t wq;
+            if (vb < ob->sA) {                           /* band A: words [w0, w1) and [w2, 2^32) */
+                if (ob->sA < 1.0) vb /= ob->sA;
+                uint64_t span = (ob->w1 - ob->w0) + ((1ull << 32) - ob->w2);
+                wq = ob->w0 + (((uint64_t)w[2] * span) >> 32);
+                if (wq >= ob->w1) wq += ob->w2 - ob->w1;
+                pb = ob->pbar;
+            } else {                                     /* band B: words [w1, w2) */
+                vb = (vb - ob->sA) / (1.0 - ob->sA);
+                wq = ob->w1 + (((uint64_t)w[2] * (ob->w2 - ob->w1)) >> 32);
+                pb = ob->pbarB;
+            }
+            v = ob->vstar + (1.0 - ob->vstar) * vb;
+            q = orc_mdf_table_lookup(g->mdf, (uint32_t)wq);
             if (q < ob->qmin || q > 2.0 - ob->qmin) continue;  /* cannot reflect */
             double kN = dot3(k, N), sa_ = fabs(kN), ca_ = sqrt(fmax(0.0, 1.0 - kN * kN));
             double a = (kN < 0 ? -sa_ : sa_) * (1.0 - q), b = ca_ * sqrt(q * (2.0 - q));
             double arc[4];
             double Pxi = azimuth_arcs(a, b, ob->S1, ob->S2, arc);
             double t3 = U(w[3]);
-            if (!(t3 * ob->pbar < Pxi)) continue;           /* outside the arcs: cannot reflect */
+            if (!(t3 * pb < Pxi)) continue;                 /* outside the arcs: cannot reflect */
             double L = arc[1] + arc[3];
-            double pos = (t3 * ob->pbar / Pxi) * 2.0 * L, sgn = 1.0;
+            double pos = (t3 * pb / Pxi) * 2.0 * L, sgn = 1.0;
             if (pos >= L) { pos -= L; sgn = -1.0; }
             double xp = pos < arc[1] ? arc[0] + pos : arc[2] + (pos - arc[1]);
             xi = atan2(dot3(k, t2), dot3(k, t1)) + sgn * xp;
@@ -1591,6 +1669,10 @@ int orc_segment_bounds(const orc_spec *s, int64_t n, const double *E, const doub
         out->S2 = b->S2;
         out->w0 = b->w0;
         out->wspan = b->wspan;
+        out->w1 = b->w1;
+        out->w2 = b->w2;
+        out->pbarB = b->pbarB;
+        out->sA = b->sA;
         out->lam = b->lam;
         out->mu = sb.mu;
         out->pa = sb.pa;

@@ -21,6 +21,10 @@ its (separately pinned) curves R and W:
     below qmin, so no word whose tilt can reflect is left out of (b);
   * the arc bound: the measure P_xi of azimuths in the window is at most pbar
     for every tilt in [qmin, 2 - qmin] at every point of the segment;
+  * band B of stream (b) (one reflection order): its table words [w1, w2) map
+    to tilts in [qmin, q_J] beyond the band's first knot, where P_xi is at most
+    pbarB < pbar at every point of the segment; the words of band A and band B
+    together are exactly [w0, 2^32), and band A's share is its rate's share;
   * no rocking curve (candidates on the Bragg cones): W / W(0) on the cone
     facing the ray is at most wn everywhere, at most v* outside |psi| < psis,
     and at most wf on the other cone.
@@ -185,7 +189,36 @@ def check_segments(spec, E, x, k, order=0, width=1.0):
         a = kN * (1.0 - q)
         pxi = _arc_measure(a, np.maximum(b, 1e-300), S1[:, None], S2[:, None])
         assert np.all(pxi <= pbar[:, None] * (1 + 1e-9) + 1e-15), float((pxi / pbar[:, None]).max())
+    check_band_b(spec, B, act, tab, kN, kt, S1, S2)
     return int(act.sum())
+
+
+QJ = 2.0 ** (351 / 8.0 - 48.0)       # band B's largest tilt, q_J = 2^(-33/8)
+
+
+def check_band_b(spec, B, act, tab, kN, kt, S1, S2):
+    """band B of stream (b): words, tilts and the arc bound pbarB"""
+    w0, w1, w2 = B["w0"][act], B["w1"][act], B["w2"][act]
+    pbar, pbarB, sA, qmin = B["pbar"][act], B["pbarB"][act], B["sA"][act], B["qmin"][act]
+    on = w1 < w2
+    assert np.all(w0 <= w1) and np.all(w1 <= w2)
+    assert np.all(~on | (pbarB < pbar)) and np.all(on | ((w1 == w0) & (w2 == w0) & (sA == 1.0)))
+    # band A's share of stream (b) is that of its rate (words x bound)
+    spanA = (w1 - w0).astype(np.float64) + (2.0 ** 32 - w2.astype(np.float64))
+    lA, lB = spanA * pbar, (w2 - w1).astype(np.float64) * pbarB
+    assert np.allclose(sA[on], (lA / (lA + lB))[on], rtol=1e-12, atol=0)
+    for i in np.flatnonzero(on):
+        # the band's tilts: beyond qmin, from the knot that starts w1's interval, at most q_J
+        qlo, qhi = ob.mdf_table_lookup(tab, [int(w1[i]), int(w2[i]) - 1])
+        assert qlo >= qmin[i] and qhi <= QJ * (1 + 1e-12), (qlo, qhi, qmin[i])
+        # P_xi <= pbarB over the band's tilts everywhere on the segment (fine near its first tilt)
+        t_lo, t_hi = 2.0 * math.asin(math.sqrt(0.5 * qlo)), 2.0 * math.asin(math.sqrt(0.5 * QJ))
+        th = np.concatenate([t_lo * (1.0 + np.geomspace(1e-9, 0.1, 60)), np.linspace(t_lo, t_hi, 120)])
+        q = (2.0 * np.sin(0.5 * th) ** 2)[:, None]
+        b = np.sqrt(q * (2.0 - q)) * kt[i][None, :]
+        pxi = _arc_measure(kN[i][None, :] * (1.0 - q), np.maximum(b, 1e-300), S1[i], S2[i])
+        assert np.all(pxi <= pbarB[i] * (1 + 1e-9) + 1e-15), (float(pxi.max()), float(pbarB[i]))
+    return int(on.sum())
 
 
 def _spec(geometry, mdf, mdf_kw, irc, irc_kw, fwhm_deg=0.2, **extra):
