@@ -249,6 +249,14 @@ def batched_measurement(H, W, torch, stream, sm_mhz):
     torch.cuda.synchronize()
     sec = e0.elapsed_time(e1) / 1e3
     total = sum(args[1])
+    # the same batch through the entry point that allocates nothing (every job on the persistent kernel)
+    H.heart_trace_batch_static(specs, args[0], [max(1, n // 100) for n in args[1]], args[2], imgs, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    H.heart_trace_batch_static(specs, args[0], args[1], args[2], imgs, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec_static = e0.elapsed_time(e1) / 1e3
     for s in specs:
         s.close()
     summed = {k: sum(t[k] for t in tl) for k in ("emitted", "miss", "exit_front", "exit_back", "exit_side",
@@ -260,8 +268,10 @@ def batched_measurement(H, W, torch, stream, sm_mhz):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-instr/s",
                          "frac": achieved / peak, "basis": "the headline's per-unit counts over the batch's "
                                                            "tallies, CUDA-event time of the call"},
+            "static_rays_per_s": total / sec_static,
             "note": "one heart_trace_batch call: jobs of >= 2^18 rays as two-pass traces, the rest in one "
-                    "persistent launch (includes tally read-back)"}
+                    "persistent launch (includes tally read-back); static: heart_trace_batch_static on the same "
+                    "jobs, one persistent launch over all of them, no device allocation"}
 
 
 def serving_measurement(H, W, n_jobs, rate, rho=None, capacity=None):

@@ -952,21 +952,19 @@ static uint64_t word_floor_grid(const orc_mdf_table *t, double qmin) {
  * (D = max |S - a| over the window and the segment; q / sin(theta) =
  * tan(theta / 2)), where the arcsine measure of an interval is at most its
  * width over sqrt(1 - M^2); the second lies beyond m = (S1 + lo (1 - q2)) /
- * (c_a,max sin theta2), so its measure is at most acos(m) (0 if m >= 1); an
- * interval of width w has measure at most acos(1 - w) wherever it lies. */
+ * sin theta2 (b <= sin theta2), so its measure is at most acos(m) (0 if m >= 1). */
 static double band_b_bound(double lo, double hi, double S1, double S2, double q1, double q2) {
     double h = fmin(hi, 1.0);
-    double camin = sqrt(fmax(0.0, 1.0 - h * h)), camax = sqrt(fmax(0.0, 1.0 - lo * lo));
+    double camin = sqrt(fmax(0.0, 1.0 - h * h));
     double s1 = sqrt(q1 * (2.0 - q1)), s2 = sqrt(q2 * (2.0 - q2)), t2 = sqrt(q2 / (2.0 - q2));
     if (!(camin > 0.0) || !(s1 > 0.0)) return 1.0;
     double D = fmax(fabs(S1 - hi), fabs(S2 - lo));
     double M = D / (camin * s1) + hi * t2 / camin;
     double w = (S2 - S1) / (camin * s1);
     if (!(M < 1.0)) return 1.0;
-    double edge = acos(fmax(-1.0, 1.0 - w));
-    double same = fmin(edge, w / sqrt(1.0 - M * M));
-    double m = (S1 + lo * (1.0 - q2)) / (camax * s2);
-    double mirror = m >= 1.0 ? 0.0 : fmin(edge, acos(fmax(-1.0, m)));
+    double same = w / sqrt(1.0 - M * M);
+    double m = (S1 + lo * (1.0 - q2)) / s2;
+    double mirror = m >= 1.0 ? 0.0 : acos(fmax(-1.0, m));
     return (same + mirror) / PI;
 }
 

@@ -212,17 +212,26 @@ extern "C" heart_status heart_spectrometer_create(const heart_spectrometer_desc 
         }
         qgrid[j] = w;
     }
-    // [FP64 table][FP32 table, padded to 8 bytes][scratch words][tilt grid words]
+    // band B of process (b): 1 / sin(theta) at the knot starting each grid word's interval
+    std::vector<float> is1(kQGrid);
+    for (int j = 0; j < kQGrid; ++j) {
+        const double q = tab[qgrid[j] >> 20];
+        const double st = std::sqrt(q * (2.0 - q));
+        is1[j] = st > 0.0 ? std::nextafter((float)(1.0 / st), INFINITY) : 0.0f;
+    }
+    // [FP64 table][FP32 table, padded to 8 bytes][scratch words][tilt grid words][band B 1 / sin]
     size_t bytes = kMdfKnots * sizeof(double) + (kMdfKnots + (kMdfKnots & 1)) * sizeof(float) +
-                   kScratchWords * sizeof(unsigned long long) + kQGrid * sizeof(uint32_t);
+                   kScratchWords * sizeof(unsigned long long) + kQGrid * sizeof(uint32_t) + kQGrid * sizeof(float);
     if ((e = cudaMalloc(&h->d_block, bytes)) != cudaSuccess) { delete h; return cuda_fail(e, "cudaMalloc tables"); }
     h->d_tab64 = (double *)h->d_block;
     h->d_tab32 = (float *)(h->d_tab64 + kMdfKnots);
     h->d_scratch = (unsigned long long *)(h->d_tab32 + kMdfKnots + (kMdfKnots & 1));
     uint32_t *d_qgrid = (uint32_t *)(h->d_scratch + kScratchWords);
+    float *d_is1 = (float *)(d_qgrid + kQGrid);
     if ((e = cudaMemcpy(h->d_tab64, tab.data(), kMdfKnots * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(h->d_tab32, tab32.data(), kMdfKnots * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(d_qgrid, qgrid.data(), kQGrid * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        (e = cudaMemcpy(d_qgrid, qgrid.data(), kQGrid * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(d_is1, is1.data(), kQGrid * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) {
         cudaFree(h->d_block);
         delete h;
         return cuda_fail(e, "cudaMemcpy tables");
@@ -235,6 +244,8 @@ extern "C" heart_status heart_spectrometer_create(const heart_spectrometer_desc 
     p.mdf64 = h->d_tab64;
     p.mdf32 = h->d_tab32;
     p.qgrid = d_qgrid;
+    p.band_w2 = qgrid[kBandJ2];
+    p.band_is1 = d_is1;
     h->p = p;
     h->desc = *desc;
     *out = h;

@@ -84,6 +84,12 @@ struct Launch32 {
     int32_t geometry, irc_kind;
     const float *tab;
     const uint32_t *qgrid;                // tilt-grid table words (thinned sampler)
+    // band B of process (b) (one order): the first table word past it, and for its
+    // largest tilt q_J = 2^(-33/8) the values q_J and tan(theta_J / 2) rounded up,
+    // 1 / sin(theta_J) rounded down
+    uint32_t band_w2;
+    float band_q2, band_is2, band_t2;
+    const float *band_is1;                // per grid point: 1 / sin(theta) at its first knot
     void *img;                            // this job's image (int32 or int64)
     unsigned long long *tally;            // this job's kTallyN tally words
     heart_ray_record *rec;                // per-ray records or nullptr
@@ -137,7 +143,8 @@ struct WarpBuf {
     int32_t nb[kBuf];
     // the first segment, prepared while the warp spawns together
     float s_exit[kBuf], inv_mu[kBuf], pa[kBuf], ra[kBuf], qmin[kBuf], pbar[kBuf];
-    uint32_t w0[kBuf];
+    uint32_t w0[kBuf], w1[kBuf];
+    float pbarB[kBuf];
     int32_t face[kBuf];
     int count;
 };
@@ -275,6 +282,10 @@ struct Lane {
     // arc bound, first table word of process (b) (its words are [w0, 2^32))
     float ra, qmin, pbar;
     uint32_t w0;
+    // band B of process (b), one order: table words [w1, band_w2) at the arc bound
+    // pbarB; pbarB == pbar: no band B (process (b) is [w0, 2^32) at pbar)
+    uint32_t w1;
+    float pbarB;
     int32_t face, nrefl, ncoll, no_bragg;
     // cylinder: depth below the inner face at x0 and along-segment constants of k.N
     float rho0, cb1, cb2, cga, ck0, ctau0;
@@ -760,11 +771,37 @@ __device__ __forceinline__ float arc_bound(float lo, float hi, float b, float ib
     return __fmaf_rn(fminf(slope, edge), 0.318309886f * 1.0001f, 4e-6f);
 }
 
-// first table word of process (b): that of the tilt-grid point q_j = 2^(j/8 - 48) just below q_min
-__device__ __forceinline__ uint32_t tilt_word32(const Launch32 &L, float qmin) {
-    if (!(qmin >= 3.5527137e-15f)) return 0u;
-    const int j = min((int)floorf(8.0f * __log2f(qmin)) + 384, kQGrid - 1);
-    return L.qgrid[j];
+// the tilt-grid point q_j = 2^(j/8 - 48) just below q_min (-1 below the grid); its
+// table word starts process (b)
+__device__ __forceinline__ int tilt_index32(float qmin) {
+    if (!(qmin >= 3.5527137e-15f)) return -1;
+    return min((int)floorf(8.0f * __log2f(qmin)) + 384, kQGrid - 1);
+}
+
+// Band B's arc-measure bound (units of pi) for tilts q >= q1 up to q_J on a segment
+// with |k.N| in [sB + lo, sB + hi] (window |k.n| in (sB + e1, sB + e2); ca_hi =
+// sqrt(1 - |k.N|max^2); is1 >= 1 / sin(theta1)): with b = c_a sin(theta), the
+// window's interval of cos(xi') on the ray's side stays within |y| <= M = (D /
+// sin theta1 + |k.N|max tan(theta_J / 2)) / ca_hi (D = max |S - |k.N|| from the
+// small quantities), where an interval's arcsine measure is at most its width w
+// over sqrt(1 - M^2); the other one lies beyond m = (S1 + |k.N|min (1 - q_J)) /
+// sin theta_J (b <= sin theta_J), measure <= acos(m), 0 if m >= 1.  Margins of a
+// few ulp on M, m and the result cover this function's own rounding; 1 if no
+// bound applies
+__device__ __forceinline__ float band_b_bound32(const Launch32 &L, float sB, float lo, float hi, float e1, float e2,
+                                                float ca_hi, float is1) {
+    if (!(ca_hi > 0.0f) || !(is1 > 0.0f)) return 1.0f;
+    const float shi = fminf(sB + hi, 1.0f);
+    const float ic = 1.0f / (ca_hi * 0.9999995f);
+    const float D = fmaxf(fabsf(e1 - hi), fabsf(e2 - lo));
+    const float M = __fmaf_rn(D, is1, shi * L.band_t2) * ic * 1.000001f;
+    if (!(M < 1.0f)) return 1.0f;
+    const float w = (e2 - e1) * is1 * ic * 1.000001f;
+    float p = w * rsqrtf(__fmaf_rn(-M, M, 1.0f)) * 1.000001f;
+    const float slo = fmaxf(sB + lo, 0.0f);
+    const float m = __fmaf_rn(slo, 1.0f - L.band_q2, sB + e1) * L.band_is2 * 0.999999f;
+    if (m < 1.0f) p += acosf(fmaxf(m, -1.0f)) * 1.000001f;
+    return p * (0.318309886f * 1.000002f);
 }
 
 // Majorant of a straight segment.  Plain: mu0 + Q R_max.  Thinned: the
@@ -776,9 +813,11 @@ __device__ __forceinline__ uint32_t tilt_word32(const Launch32 &L, float qmin) {
 // more than the angular distance), keeps |Delta| >= X*.  Segments with
 // d <= X* keep the plain stream.  |k.N| is taken relative to sin(aB + dM)
 // from the small anchors.
-__device__ __forceinline__ float thin_bounds(const Launch32 &L, Lane &s, float A_exit, bool flip) {
+__device__ __forceinline__ float thin_bounds(const Launch32 &L, Lane &s, float A_exit, bool flip, bool band) {
     float la = s.qr, lb = 0.0f;
     s.ra = 1.0f;
+    s.pbarB = s.pbar = 1.0f;
+    s.w1 = 0u;
     if (L.irc_kind == HEART_IRC_NONE) {
         // no rocking curve: the Bragg cones' bounds (qmin, pbar: the bounds of W / W(0) on
         // the facing and the other cone; w0: the bits of the facing cone's window half-width)
@@ -823,10 +862,12 @@ __device__ __forceinline__ float thin_bounds(const Launch32 &L, Lane &s, float A
                                          : __sinf(h);
             const float st = 2.0f * sh * sqrtf(fmaxf(0.0f, __fmaf_rn(-sh, sh, 1.0f)));   // sin(theta_min)
             s.qmin = 2.0f * sh * sh;
-            s.w0 = tilt_word32(L, s.qmin);
+            const int j0 = tilt_index32(s.qmin);
+            s.w0 = j0 < 0 ? 0u : L.qgrid[j0];
             // arc bound: two |k.n| windows of width S2 - S1 over b >= cos(a_hi) sin(theta_min)
             const float shi = fminf(s.sB + hi, 1.0f);
-            const float bmin = sqrtf(fmaxf(0.0f, __fmaf_rn(-shi, shi, 1.0f))) * st * 0.999999f;
+            const float ca_hi = sqrtf(fmaxf(0.0f, __fmaf_rn(-shi, shi, 1.0f)));
+            const float bmin = ca_hi * st * 0.999999f;
             float e1, e2;
             bragg_window(L, s.sB, s.cB, s.inv_ws, e1, e2);
             // two windows of width w in cos(xi'), each of arc measure <= acos(1 - w) / pi
@@ -845,8 +886,26 @@ __device__ __forceinline__ float thin_bounds(const Launch32 &L, Lane &s, float A
             } else {
                 s.pbar = fminf(1.0f, 0.636619772f * acosf(1.0f - w) * 1.000001f);
             }
+            // band B (one order): from the grid point kBandDJ steps above q_min's, its
+            // tilts from the table knot that starts its first word's interval
+            s.w1 = s.w0;
+            s.pbarB = s.pbar;
+            float pw = (float)((1ull << 32) - s.w0) * 2.3283064365386963e-10f * s.pbar;
+            if (band && j0 >= 0 && j0 + kBandDJ < kBandJ2) {
+                const uint32_t w1 = L.qgrid[j0 + kBandDJ];
+                if (w1 < L.band_w2) {
+                    const float pB = band_b_bound32(L, s.sB, lo, hi, e1, e2, ca_hi, L.band_is1[j0 + kBandDJ]);
+                    if (pB < s.pbar) {
+                        s.w1 = w1;
+                        s.pbarB = pB;
+                        const float fA = (float)((w1 - s.w0) + (0u - L.band_w2)) * s.pbar;
+                        const float fB = (float)(L.band_w2 - w1) * pB;
+                        pw = (fA + fB) * 2.3283064365386963e-10f;
+                    }
+                }
+            }
             la = s.qr * L.vstar;
-            lb = s.qr * (1.0f - L.vstar) * ((float)((1ull << 32) - s.w0) * 2.3283064365386963e-10f) * s.pbar;
+            lb = s.qr * (1.0f - L.vstar) * pw;
             s.ra = la / (la + lb);
         }
     }
@@ -864,7 +923,7 @@ __device__ __forceinline__ void set_majorant(Lane &s, float lam) {
 }
 
 __device__ __forceinline__ void thin_segment(const Launch32 &L, Lane &s, float A_exit, bool flip) {
-    set_majorant(s, thin_bounds(L, s, A_exit, flip));
+    set_majorant(s, thin_bounds(L, s, A_exit, flip, L.n_ord == 1));
 }
 
 // Several reflection orders (Sec. 2.2.3: the rate sums over H): every order's
@@ -883,7 +942,7 @@ __device__ __forceinline__ void thin_orders(const Launch32 &L, Lane &s, float de
         s.cB = s.ocB[g];
         s.qr = s.oqr[g];
         s.inv_ws = s.oiw[g];
-        lam += thin_bounds(L, s, Ag + dex, flip);
+        lam += thin_bounds(L, s, Ag + dex, flip, false);      // several orders: no band B
         s.ora[g] = s.ra;
         s.oqmin[g] = s.qmin;
         s.opbar[g] = s.pbar;
@@ -907,6 +966,7 @@ __device__ __forceinline__ void load_order(Lane &s, int h) {
     s.ra = s.ora[h];
     s.qmin = s.oqmin[h];
     s.pbar = s.opbar[h];
+    s.pbarB = s.pbar;                                     // several orders: no band B
     s.w0 = s.ow0[h];
 }
 
@@ -1308,8 +1368,32 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
     // its full range, (b) maps it onto [w0, 2^32); one table lookup for both
     // (a warp almost always holds candidates of both streams)
     const bool in_a = v < s.ra;
-    v = in_a ? (s.ra < 1.0f ? (v / s.ra) * L.vstar : v) : __fmaf_rn(1.0f - L.vstar, (v - s.ra) / (1.0f - s.ra), L.vstar);
-    const uint32_t wq = in_a ? w[2] : s.w0 + __umulhi(w[2], 0u - s.w0) + (s.w0 == 0u ? w[2] : 0u);
+    uint32_t wq = w[2];
+    float pb = s.pbar;                                        // (b): the candidate's band's arc bound
+    if (in_a) {
+        v = s.ra < 1.0f ? (v / s.ra) * L.vstar : v;
+    } else {
+        float vb = (v - s.ra) / (1.0f - s.ra);
+        if (s.pbarB < s.pbar) {
+            // two bands: A, words [w0, w1) and [w2, 2^32) at pbar, by its share of the rate;
+            // B, words [w1, w2) at pbarB
+            const uint32_t spanA = (s.w1 - s.w0) + (0u - L.band_w2), spanB = L.band_w2 - s.w1;
+            const float fA = (float)spanA * s.pbar, fB = (float)spanB * s.pbarB;
+            const float t = vb * (fA + fB);
+            if (t < fA) {
+                vb = t / fA;
+                wq = s.w0 + __umulhi(w[2], spanA);
+                if (wq >= s.w1) wq += spanB;
+            } else {
+                vb = (t - fA) / fB;
+                wq = s.w1 + __umulhi(w[2], spanB);
+                pb = s.pbarB;
+            }
+        } else {
+            wq = s.w0 + __umulhi(w[2], 0u - s.w0) + (s.w0 == 0u ? w[2] : 0u);
+        }
+        v = __fmaf_rn(1.0f - L.vstar, vb, L.vstar);
+    }
     const float q = mdf_q32(tab, wq);
     if (!in_a && (q < s.qmin || q > 2.0f - s.qmin)) return -1;   // (b): cannot reflect
     const float st = sqrtf(q * (2.0f - q));
@@ -1336,7 +1420,7 @@ __device__ __forceinline__ int step(const Launch32 &L, Lane &s, const float *tab
             const float a = kN * (1.0f - q), S1 = s.sB + e1, S2 = s.sB + e2;
             iv[0] = S1 - a; iv[1] = S2 - a; iv[2] = -S2 - a; iv[3] = -S1 - a;
         }
-        const float t3pbar = u01_32(w[3]) * s.pbar;
+        const float t3pbar = u01_32(w[3]) * pb;
         // P_xi <= 2 acos(1 - w) / pi <= sqrt(2 w), w = (S2 - S1) / b: half of the candidates end here
         if (t3pbar * t3pbar * b >= 2.0002f * (e2 - e1)) return -1;
         // a tighter bound before the arcs themselves (most of the rest end here); it lies
@@ -1576,6 +1660,8 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                         B.qmin[slot] = t.qmin;
                         B.pbar[slot] = t.pbar;
                         B.w0[slot] = t.w0;
+                        B.w1[slot] = t.w1;
+                        B.pbarB[slot] = t.pbarB;
                         if (EXT) for (int i = 0; i < 3; ++i) Bp[i][slot] = pv[i];
                     }
                     __syncwarp();
@@ -1605,6 +1691,8 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                     s.qmin = B.qmin[slot];
                     s.pbar = B.pbar[slot];
                     s.w0 = B.w0[slot];
+                    s.w1 = B.w1[slot];
+                    s.pbarB = B.pbarB[slot];
                     s.inv_1mpa = s.pa < 1.0f ? 1.0f / (1.0f - s.pa) : 0.0f;
                     s.pa_thr = s.pa >= 1.0f ? 0xFFFFFFFFu
                                             : __float2uint_ru(fminf(s.pa * 4294967296.0f, 4294967040.0f));
@@ -1680,7 +1768,7 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
 // a prepared hit: one 96-byte record of six 16-byte words, written and read
 // with vector stores and loads (consecutive lanes touch consecutive records):
 //   [x0 x1 x2 k0] [k1 k2 A sB] [mu0 qr inv_ws E] [s_exit inv_mu pa ra]
-//   [qmin pbar ray_lo ray_hi] [w0 face no_bragg -]
+//   [qmin pbar ray_lo ray_hi] [w0 face|no_bragg<<8 w1 pbarB]
 // and for a polarised source a seventh word [p0 p1 p2 -] (112-byte records)
 template <bool POL>
 __device__ __forceinline__ float4 *wave_rec(const WaveBuf &B, size_t slot) {
@@ -1793,6 +1881,7 @@ __global__ void __launch_bounds__(kSpawnThreads, (USER || ORD) ? 4 : 8) k_spawn3
     Lane t;
     for (int m = 0; m < 3; ++m) { t.x0[m] = sg.x[m][j]; t.k[m] = sg.k[m][j]; }
     t.s_exit = 0.f; t.inv_mu = 0.f; t.pa = 0.f; t.ra = 0.f; t.qmin = 0.f; t.pbar = 0.f; t.w0 = 0u; t.face = 0;
+    t.w1 = 0u; t.pbarB = 0.f;
     if (ORD) {
         t.s_exit = oA[1]; t.inv_mu = osB[1]; t.pa = oA[2]; t.ra = osB[2]; t.qmin = oA[3]; t.pbar = osB[3];
         t.face = nbm;
@@ -1815,7 +1904,8 @@ __global__ void __launch_bounds__(kSpawnThreads, (USER || ORD) ? 4 : 8) k_spawn3
     r[2] = make_float4(mu0, qr, inv_ws, E32);
     r[3] = make_float4(t.s_exit, t.inv_mu, t.pa, t.ra);
     r[4] = make_float4(t.qmin, t.pbar, __uint_as_float((uint32_t)ray), __uint_as_float((uint32_t)(ray >> 32)));
-    r[5] = make_float4(__uint_as_float(t.w0), __int_as_float(t.face), __int_as_float(ok ? nb : 2), 0.0f);
+    r[5] = make_float4(__uint_as_float(t.w0), __int_as_float(t.face | ((ok ? nb : 2) << 8)), __uint_as_float(t.w1),
+                       t.pbarB);
 }
 
 // Per-ray records of the rays a two-pass trace does not queue (tests): those
@@ -1929,7 +2019,8 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                 s.mu0 = r2.x; s.qr = r2.y; s.inv_ws = r2.z; s.E = r2.w;
                 s.s_exit = r3.x; s.inv_mu = r3.y; s.pa = r3.z; s.ra = r3.w;
                 s.qmin = r4.x; s.pbar = r4.y; s.rl = __float_as_uint(r4.z); s.rh = __float_as_uint(r4.w);
-                s.w0 = __float_as_uint(r5.x); s.face = __float_as_int(r5.y); s.no_bragg = __float_as_int(r5.z);
+                s.w0 = __float_as_uint(r5.x); s.face = __float_as_int(r5.y) & 0xff;
+                s.no_bragg = __float_as_int(r5.y) >> 8; s.w1 = __float_as_uint(r5.z); s.pbarB = r5.w;
                 if (s.no_bragg == 2) {
                     ++my_dead;                                // no valid energy: a miss, nothing to walk
                 } else {
@@ -1946,7 +2037,7 @@ __global__ void __launch_bounds__(kBlockThreads, OCC)
                     if (ORD) {
                         // every order's rates and the entry segment of all orders
                         const float oa[4] = {s.A, r3.x, r3.z, r4.x}, os[4] = {s.sB, r3.y, r3.w, r4.y};
-                        start_orders(L, s, oa, os, __float_as_int(r5.y));
+                        start_orders(L, s, oa, os, __float_as_int(r5.y) & 0xff);
                         segment<GEOM, true>(L, s);
                     } else {
                         segment_consts<GEOM>(L, s);
@@ -2186,6 +2277,14 @@ void make_launch32(const SpecParams &S, const SourceParams &P, uint64_t n, uint6
     L.irc_kind = S.irc;
     L.tab = S.mdf32;
     L.qgrid = S.qgrid;
+    {
+        const double q2 = std::exp2(kBandJ2 / 8.0 - 48.0);
+        L.band_w2 = S.band_w2;
+        L.band_q2 = std::nextafter((float)q2, 1.0f);
+        L.band_is2 = std::nextafter((float)(1.0 / std::sqrt(q2 * (2.0 - q2))), 0.0f);
+        L.band_is1 = S.band_is1;
+        L.band_t2 = std::nextafter((float)std::sqrt(q2 / (2.0 - q2)), 1.0f);
+    }
     const double *a0 = S.geometry == HEART_FLAT ? S.ed : S.ax;
     const double *a1 = S.geometry == HEART_FLAT ? S.en : S.cc;
     const double *a2 = S.geometry == HEART_FLAT ? S.N : S.ww;

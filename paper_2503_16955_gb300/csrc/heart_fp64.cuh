@@ -283,6 +283,8 @@ __host__ __device__ __forceinline__ void irc_energy64(const SpecParams &S, doubl
 struct Bound64 {
     double ra, vstar, qmin, pbar, S1, S2, lam;
     unsigned long long w0, wspan;
+    unsigned long long w1, w2;     // band B of process (b): table words [w1, w2) (w1 = w2 = w0: none)
+    double pbarB, sA;              // band B's arc-measure bound; band A's share of process (b)
     // no rocking curve, thinned: W / W(0) bounds of the two cones, the facing cone's window
     // |psi| < psis, and the cumulative shares of the window and of the whole facing cone
     double wn, wf, psis, pin, pio;
@@ -294,12 +296,33 @@ struct Seg64 {
     Bound64 o[HEART_MAX_ORDERS];
 };
 
-// first table word of process (b): that of the tilt-grid point just below q_min
-__device__ __forceinline__ unsigned long long tilt_word64(const SpecParams &S, double qmin) {
-    if (!(qmin >= 3.552713678800501e-15)) return 0ull;                 // 2^-48
-    int j = (int)floor(8.0 * log2(qmin)) + 384;
-    j = j > kQGrid - 1 ? kQGrid - 1 : j;
-    return (unsigned long long)S.qgrid[j];
+// the tilt-grid point just below q_min (-1 below the grid)
+__device__ __forceinline__ int tilt_index64(double qmin) {
+    if (!(qmin >= 3.552713678800501e-15)) return -1;                   // 2^-48
+    const int j = (int)floor(8.0 * log2(qmin)) + 384;
+    return j > kQGrid - 1 ? kQGrid - 1 : j;
+}
+
+// Band B's arc-measure bound (units of pi) for tilts q in [q1, q2] on a segment
+// with |k.N| in [lo, hi]: with b = c_a sin(theta), the window's interval of
+// cos(xi') on the ray's side, (S - a (1 - q)) / b, stays within |y| <= M =
+// D / (c_a,min sin theta1) + hi tan(theta2 / 2) / c_a,min (D = max |S - a|), where
+// an interval's arcsine measure is at most its width over sqrt(1 - M^2); the other
+// one lies beyond m = (S1 + lo (1 - q2)) / sin theta2 (measure <= acos m,
+// 0 if m >= 1); w = (S2 - S1) / (c_a,min sin theta1)
+__device__ __forceinline__ double band_b_bound64(double lo, double hi, double S1, double S2, double q1, double q2) {
+    const double h = fmin(hi, 1.0);
+    const double camin = sqrt(fmax(0.0, 1.0 - h * h));
+    const double s1 = sqrt(q1 * (2.0 - q1)), s2 = sqrt(q2 * (2.0 - q2)), t2 = sqrt(q2 / (2.0 - q2));
+    if (!(camin > 0.0) || !(s1 > 0.0)) return 1.0;
+    const double D = fmax(fabs(S1 - hi), fabs(S2 - lo));
+    const double M = D / (camin * s1) + hi * t2 / camin;
+    const double w = (S2 - S1) / (camin * s1);
+    if (!(M < 1.0)) return 1.0;
+    const double same = w / sqrt(1.0 - M * M);
+    const double m = (S1 + lo * (1.0 - q2)) / s2;
+    const double mirror = m >= 1.0 ? 0.0 : acos(fmax(-1.0, m));
+    return (same + mirror) / 3.14159265358979323846;
 }
 
 // the thinning bound of order h on a segment with |k.N| in [lo, hi]
@@ -307,6 +330,7 @@ __device__ __forceinline__ void bound_order64(const SpecParams &S, const Orders6
                                               Bound64 &b) {
     b.ra = 1.0; b.vstar = 1.0; b.qmin = 0.0; b.pbar = 1.0; b.S1 = 0.0; b.S2 = 0.0;
     b.w0 = 0ull; b.wspan = 1ull << 32;
+    b.w1 = 0ull; b.w2 = 0ull; b.pbarB = 1.0; b.sA = 1.0;
     b.lam = O.qr[h];
     b.wn = 1.0; b.wf = 1.0; b.psis = 3.14159265358979323846; b.pin = 0.5; b.pio = 0.5;
     if (S.sampler == HEART_SAMPLER_THINNED && S.irc == HEART_IRC_NONE && O.qr[h] > 0) {
@@ -346,7 +370,8 @@ __device__ __forceinline__ void bound_order64(const SpecParams &S, const Orders6
     if (tmin > half_pi) tmin = half_pi;
     const double sh = sin(0.5 * tmin);
     b.qmin = 2.0 * sh * sh;
-    b.w0 = tilt_word64(S, b.qmin);
+    const int j0 = tilt_index64(b.qmin);
+    b.w0 = j0 < 0 ? 0ull : (unsigned long long)S.qgrid[j0];
     b.wspan = (1ull << 32) - b.w0;
     b.S1 = sin(fmax(0.0, aBs - xstar));
     b.S2 = sin(fmin(half_pi, aBs + xstar));
@@ -355,9 +380,26 @@ __device__ __forceinline__ void bound_order64(const SpecParams &S, const Orders6
     // two windows of width w in cos(xi'), each of arc measure <= acos(1 - w) / pi
     const double w = (b.S2 - b.S1) / bmin;
     b.pbar = (w >= 2.0 || !(bmin > 0)) ? 1.0 : fmin(1.0, 2.0 * acos(1.0 - w) / 3.14159265358979323846);
+    b.w1 = b.w2 = b.w0;
+    b.pbarB = b.pbar;
+    if (O.n == 1 && j0 >= 0 && j0 + kBandDJ < kBandJ2) {
+        const unsigned long long w1 = S.qgrid[j0 + kBandDJ], w2 = S.qgrid[kBandJ2];
+        if (w1 < w2) {
+            // the band's tilts: from the table knot that starts w1's interval to q_J
+            const double pB = band_b_bound64(lo, hi, b.S1, b.S2, S.mdf64[w1 >> 20], exp2(kBandJ2 / 8.0 - 48.0));
+            if (pB < b.pbar) {
+                b.w1 = w1;
+                b.w2 = w2;
+                b.pbarB = pB;
+            }
+        }
+    }
     const double QR = O.qr[h];
-    const double PA = (double)b.wspan / 4294967296.0;
-    const double la = QR * S.vstar, lb = QR * (1.0 - S.vstar) * PA * b.pbar;
+    const double PA = (double)((b.w1 - b.w0) + ((1ull << 32) - b.w2)) / 4294967296.0;
+    const double PB = (double)(b.w2 - b.w1) / 4294967296.0;
+    const double lA = PA * b.pbar, lB = PB * b.pbarB;
+    b.sA = lA + lB > 0.0 ? lA / (lA + lB) : 1.0;
+    const double la = QR * S.vstar, lb = QR * (1.0 - S.vstar) * (lA + lB);
     b.vstar = S.vstar;
     b.lam = la + lb;
     b.ra = la / (la + lb);
@@ -597,18 +639,30 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
             q = mdf_q64(tab, wd[2]);
             sincospi(2.0 * u01_64(wd[3]), &sx, &cx);
         } else {                                              // process (b)
-            v = ob.vstar + (1.0 - ob.vstar) * ((v - ob.ra) / (1.0 - ob.ra));
-            const uint32_t wq = (uint32_t)(ob.w0 + (((unsigned long long)wd[2] * ob.wspan) >> 32));
-            q = mdf_q64(tab, wq);
+            double vb = (v - ob.ra) / (1.0 - ob.ra), pb;
+            unsigned long long wq;
+            if (vb < ob.sA) {                                 // band A: words [w0, w1) and [w2, 2^32)
+                if (ob.sA < 1.0) vb /= ob.sA;
+                const unsigned long long span = (ob.w1 - ob.w0) + ((1ull << 32) - ob.w2);
+                wq = ob.w0 + (((unsigned long long)wd[2] * span) >> 32);
+                if (wq >= ob.w1) wq += ob.w2 - ob.w1;
+                pb = ob.pbar;
+            } else {                                          // band B: words [w1, w2)
+                vb = (vb - ob.sA) / (1.0 - ob.sA);
+                wq = ob.w1 + (((unsigned long long)wd[2] * (ob.w2 - ob.w1)) >> 32);
+                pb = ob.pbarB;
+            }
+            v = ob.vstar + (1.0 - ob.vstar) * vb;
+            q = mdf_q64(tab, (uint32_t)wq);
             if (q < ob.qmin || q > 2.0 - ob.qmin) continue;  // cannot reflect
             const double kN = dot3d(k, N), sa_ = fabs(kN), ca_ = sqrt(fmax(0.0, 1.0 - kN * kN));
             const double a = (kN < 0 ? -sa_ : sa_) * (1.0 - q), b = ca_ * sqrt(q * (2.0 - q));
             double arc[4];
             const double Pxi = azimuth_arcs64(a, b, ob.S1, ob.S2, arc);
             const double t3 = u01_64(wd[3]);
-            if (!(t3 * ob.pbar < Pxi)) continue;              // outside the arcs: cannot reflect
+            if (!(t3 * pb < Pxi)) continue;                   // outside the arcs: cannot reflect
             const double L = arc[1] + arc[3];
-            double pos = (t3 * ob.pbar / Pxi) * 2.0 * L, sgn = 1.0;
+            double pos = (t3 * pb / Pxi) * 2.0 * L, sgn = 1.0;
             if (pos >= L) { pos -= L; sgn = -1.0; }
             const double xp = pos < arc[1] ? arc[0] + pos : arc[2] + (pos - arc[1]);
             sincos(atan2(dot3d(k, t2), dot3d(k, t1)) + sgn * xp, &sx, &cx);

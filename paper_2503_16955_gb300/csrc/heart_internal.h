@@ -19,6 +19,10 @@ constexpr int kMaxTable = HEART_MAX_TABLE;   // knots of a tabulated spectrum
 // thinned sampler: tilt-bound grid q_j = 2^(j/8 - 48), j < kQGrid, with the
 // first mosaic-table word of the interval holding each q_j
 constexpr int kQGrid = 392;
+// process (b) of one reflection order splits into band B, the grid points from
+// kBandDJ steps above q_min's (a factor 2^1.5 in q) to kBandJ2 (q = 2^(-33/8),
+// theta = 0.34 rad), generated at its own arc-measure bound, and band A, the rest
+constexpr int kBandDJ = 12, kBandJ2 = 351;
 
 // tally word indices (same order as heart_tally)
 enum : int {
@@ -67,6 +71,10 @@ struct SpecParams {
     const double *mdf64;
     const float *mdf32;
     const uint32_t *qgrid;           // kQGrid words (thinned sampler)
+    uint32_t band_w2, pad_b;         // qgrid[kBandJ2]: the first table word past band B
+    // per grid point j: 1 / sin(theta) at the table knot that starts qgrid[j]'s interval
+    // (rounded up; 0 where the knot is 0): band B's smallest tilt when it starts at j
+    const float *band_is1;
 };
 
 struct SourceParams {
