@@ -30,7 +30,7 @@ UNIT = "rays/s"
 # Algorithmic work per unit in lane-instructions (one thread executing one instruction:
 # an FP32 add / multiply / fused multiply-add, an SFU function, a 32 x 32 -> 64-bit
 # multiply, a compare or select, a shared-memory load), counted operation by operation
-# from the method's steps (the itemisation is in the design doc, Measurement and roofline):
+# from the method's steps, item by item:
 ALGO_PER_RAY = {                # every emitted ray
     "philox_2_blocks": 80,      # 10 rounds x (2 wide multiplies + 2 three-input XORs), twice
     "uniforms": 8,              # 4 words -> (0, 1): convert + fused multiply-add
@@ -45,6 +45,7 @@ ALGO_PER_ENTERED = {            # every ray that enters the crystal
 ALGO_PER_SEGMENT = {            # every straight segment (entered rays and reflections)
     "exit_distance": 42,        # inner / outer cylinder, axial and azimuth planes, exit anchor
     "thinning_bounds": 50,      # Bragg distance, tilt bound and table word, arc bound, shares
+    "band_b_bound": 24,         # band B: its first word and 1 / sin, M, width, rsqrt, mirror test, rates
     "majorant": 8,              # mu0 + lambda, its inverse, absorption share and word threshold
 }
 ALGO_PER_COLLISION = {          # every tentative collision
@@ -91,13 +92,13 @@ WAVE_CHUNK = 1 << 25
 # one chunk of 2^24 rays, whose 0.66 GB queue, unlike a smaller one, does not stay in
 # L2) and warp instructions issued per pipe (2^22 rays), both with the library's default
 # launch shape (bench.py --no-tune); valid only for the kernel sources with the hash below.
-TRAFFIC_BYTES_PER_RAY = (0.035840e6 + 608.962304e6 + 676.955392e6 + 0.267264e6) / (1 << 24)   # 2^24 rays
-PIPE_INST_PER_RAY = {"alu": 11.3783, "fma": 14.1796, "fmaheavy": 5.8801, "fmalite": 9.0086, "xu": 1.9095,
-                     "lsu": 1.4357, "adu": 1.4858, "cbu": 2.8433, "uniform": 0.2313, "fp64": 0.0168,
-                     "total": 36.9847}
+TRAFFIC_BYTES_PER_RAY = (0.064256e6 + 612.323328e6 + 675.713792e6 + 0.434688e6) / (1 << 24)   # 2^24 rays
+PIPE_INST_PER_RAY = {"alu": 11.0950, "fma": 13.5371, "fmaheavy": 5.7283, "fmalite": 8.4638, "xu": 1.8545,
+                     "lsu": 1.4370, "adu": 1.5389, "cbu": 2.7073, "uniform": 0.3729, "fp64": 0.0168,
+                     "total": 35.9794}
 TRAFFIC_SOURCES = ("paper_2503_16955_gb300/csrc/heart_fp32.cu", "paper_2503_16955_gb300/csrc/heart_fp64.cuh",
                    "paper_2503_16955_gb300/csrc/heart_internal.h")
-TRAFFIC_SOURCE_HASH = "b613ab8f24aaec1d"
+TRAFFIC_SOURCE_HASH = "6cf87abf84a941f4"
 
 
 def sources_hash():
@@ -614,7 +615,7 @@ def main():
                          "kernel": "k_spawn32 + k_walk32 (two passes per chunk of up to 2^25 rays)",
                          "peak_basis": "152 SMs x 4 sub-partitions x 32 lanes x %.0f MHz (the step's median SM "
                                        "clock); algorithmic lane-instructions counted per ray %d, per entered "
-                                       "ray %d, per segment %d, per collision %d, per exit %d (DESIGN.md)"
+                                       "ray %d, per segment %d, per collision %d, per exit %d (bench.py ALGO_*)"
                                        % (sm_mhz, sum(ALGO_PER_RAY.values()), sum(ALGO_PER_ENTERED.values()),
                                           sum(ALGO_PER_SEGMENT.values()), sum(ALGO_PER_COLLISION.values()),
                                           sum(ALGO_PER_EXIT.values())),

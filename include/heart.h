@@ -401,7 +401,7 @@ heart_status heart_trace_batch_static(heart_spectrometer *const *specs, const he
  * worker thread keeps two rounds of launches in flight; each round traces, in
  * arrival order, every admitted job with at most 2^20 rays left whole, and
  * gives a budget of 2^26 rays to the larger ones oldest first in slices of at
- * least 2^22 rays.  Slices of 2^22 rays or more run as two-pass traces, the
+ * least 2^22 rays.  Slices of 2^18 rays or more run as two-pass traces, the
  * others together in one persistent batched launch; every FP32 kernel traces a
  * ray alike, so a job's image and tallies equal its heart_trace's. */
 heart_status heart_server_create(size_t mem_cap_bytes, heart_server **out);

@@ -5,7 +5,7 @@
 // handles, images and tallies here) until released.  A worker thread plans
 // rounds in arrival order: jobs with few rays left are traced whole, the
 // others share a budget of rays per round oldest first, in long slices; slices
-// of 2^22 rays or more run as single-job two-pass launches, the others
+// of 2^18 rays or more run as single-job two-pass launches, the others
 // together in one persistent batched launch.  Jobs that arrive
 // while a round is on the GPU join the next round, which is enqueued before
 // the previous one has finished (two rounds in flight), so the device never
@@ -80,7 +80,7 @@ struct heart_server {
     uint64_t round_rays = 64ull << 20;       // rays per round for jobs beyond small_job (about 2.5 ms of GPU work)
     uint64_t min_slice = 1ull << 22;         // a large job's slice is never smaller (unless it is its last)
     uint64_t small_job = 1ull << 20;         // jobs with this many rays left are traced whole in a round
-    uint64_t two_pass_min = 1ull << 22;      // slices this large run as two-pass launches, the rest batched
+    uint64_t two_pass_min = 1ull << 18;      // slices this large run as two-pass launches, the rest batched
     // pinned host buffers for the rounds' work plans (reused; a round holds one until it retires)
     std::vector<std::pair<unsigned char *, size_t>> pins;
     unsigned long long *tally_pin = nullptr;          // pinned read-back of finished jobs' tallies
@@ -271,7 +271,7 @@ void worker_main(heart_server *s) {
             }
             r.last = last;
             heart_status st = HEART_OK;
-            // Slices of 2^22 rays or more that the two-pass trace takes run as single-job
+            // Slices of 2^18 rays or more that the two-pass trace takes run as single-job
             // two-pass launches, the others share one persistent batched launch.  Every
             // FP32 kernel traces a ray bit for bit alike, so a job's image does not depend
             // on how the rounds slice it or which kernel a slice runs on.
