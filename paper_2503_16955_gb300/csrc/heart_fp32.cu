@@ -462,7 +462,21 @@ __device__ __forceinline__ bool spawn_energy(const Launch32 &L, uint32_t a0, uin
     case HEART_SRC_INV_E: {
         const float g = (up - 0.5f) * L.half_ln[c];       // E = e_ref exp(g)
         E = e0 * __expf(g);
-        ds = s0 * expm1f(-g);
+        // expm1(-g): for |g| <= 0.2 (a continuum up to 1.5 times its lower end) by the
+        // Taylor series to g^7, whose remainder is below 4e-10 relative
+        const float x = -g;
+        float em;
+        if (fabsf(x) <= 0.2f) {
+            float p = __fmaf_rn(x, 1.98412698e-4f, 1.38888889e-3f);
+            p = __fmaf_rn(p, x, 8.33333333e-3f);
+            p = __fmaf_rn(p, x, 4.16666667e-2f);
+            p = __fmaf_rn(p, x, 0.166666667f);
+            p = __fmaf_rn(p, x, 0.5f);
+            em = __fmaf_rn(p * x, x, x);
+        } else {
+            em = expm1f(x);
+        }
+        ds = s0 * em;
         break;
     }
     case HEART_SRC_TABLE: {
@@ -484,8 +498,7 @@ __device__ __forceinline__ bool spawn_energy(const Launch32 &L, uint32_t a0, uin
     default: {
         float dE;
         if (L.kind[c] == HEART_SRC_GAUSS) {
-            float s, co;
-            sincos_2pi(u01_32(b3), &s, &co);
+            const float co = -__cosf(6.28318530717958648f * (u01_32(b3) - 0.5f));   // cos(2 pi u), as sincos_2pi
             dE = L.width[c] * sqrtf(-2.0f * __logf(u01_32(b2))) * co;
         } else if (L.kind[c] == HEART_SRC_LORENTZ) {
             const float uu = __fmaf_rn(up, 1.0f - L.lF0[c], L.lF0[c]);
