@@ -42,8 +42,12 @@ namespace heart {
 
 constexpr int kWarpsPerBlock = 4;
 constexpr int kBlockThreads = kWarpsPerBlock * 32;
-constexpr int kBuf = 48;                 // spawned rays buffered per warp
-constexpr int kSpawnBelow = 16;          // spawn only while fewer are buffered (so <= 16 + 31 < kBuf)
+// spawned rays buffered per warp, and spawning only while fewer than kSpawnBelow are
+// buffered (so at most kSpawnBelow - 1 + 32 <= kBuf); sized so that the generic batched
+// kernel's shared memory (the mosaic table, the job and four buffers) fits 6 blocks per SM
+constexpr int kBuf = 44;
+constexpr int kSpawnBelow = 13;
+static_assert(kSpawnBelow - 1 + 32 <= kBuf, "a spawn round must fit the buffer");
 
 TuneConfig g_tune;                        // launch shape picked by the autotuner
 
