@@ -37,11 +37,22 @@ def _stale():
 
 
 def build(force=False, verbose=False):
-    """Compile every translation unit in parallel and link libheart.so."""
+    """Compile every translation unit in parallel and link libheart.so.  Processes
+    of one node that build at once (the ranks of a multi-GPU launch) take a file
+    lock: one compiles, the others find the library up to date."""
     if not force and not _stale():
         return LIB
-    nvcc = _nvcc()
+    import fcntl
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and not _stale():
+            return LIB
+        return _build_locked(verbose)
+
+
+def _build_locked(verbose):
+    nvcc = _nvcc()
     # host code: no floating-point contraction, so host-built tables (mosaic
     # quantiles, spectrum CDFs) round the same on x86-64 and aarch64
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
