@@ -92,13 +92,13 @@ WAVE_CHUNK = 1 << 25
 # one chunk of 2^24 rays, whose 0.66 GB queue, unlike a smaller one, does not stay in
 # L2) and warp instructions issued per pipe (2^22 rays), both with the library's default
 # launch shape (bench.py --no-tune); valid only for the kernel sources with the hash below.
-TRAFFIC_BYTES_PER_RAY = (0.192512e6 + 612.537344e6 + 675.728896e6 + 0.271872e6) / (1 << 24)   # 2^24 rays
-PIPE_INST_PER_RAY = {"alu": 10.9984, "fma": 13.4601, "fmaheavy": 5.6809, "fmalite": 8.4499, "xu": 1.8270,
-                     "lsu": 1.4370, "adu": 1.5392, "cbu": 2.7366, "uniform": 0.3729, "fp64": 0.0168,
-                     "total": 35.8173}
+TRAFFIC_BYTES_PER_RAY = (0.062208e6 + 612.753664e6 + 675.696896e6 + 0.505088e6) / (1 << 24)   # 2^24 rays
+PIPE_INST_PER_RAY = {"alu": 10.9907, "fma": 13.4408, "fmaheavy": 5.6724, "fmalite": 8.4381, "xu": 1.8272,
+                     "lsu": 1.4369, "adu": 1.5391, "cbu": 2.7317, "uniform": 0.3729, "fp64": 0.0168,
+                     "total": 35.8174}
 TRAFFIC_SOURCES = ("paper_2503_16955_gb300/csrc/heart_fp32.cu", "paper_2503_16955_gb300/csrc/heart_fp64.cuh",
                    "paper_2503_16955_gb300/csrc/heart_internal.h")
-TRAFFIC_SOURCE_HASH = "d151c739d3ea380b"
+TRAFFIC_SOURCE_HASH = "a27539c273d1b8ca"
 
 
 def sources_hash():
