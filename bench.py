@@ -86,7 +86,7 @@ def algorithmic_roofline(t, seconds, sm_mhz):
 
 
 # rays per chunk of the two-pass trace (the library's largest hit-queue chunk)
-WAVE_CHUNK = 1 << 25
+WAVE_CHUNK = 1 << 26
 # Per emitted ray of the von Hamos workload, from ncu captures of the two-pass kernels
 # (both passes summed): DRAM bytes read + written (the hit queue written and read back;
 # one chunk of 2^24 rays, whose 0.66 GB queue, unlike a smaller one, does not stay in
@@ -240,7 +240,7 @@ def batched_measurement(H, W, torch, stream, sm_mhz):
     imgs = [torch.zeros(s.shape, dtype=torch.int32, device="cuda") for s in specs]
     args = ([j["source"] for j in jobs], [j["n_rays"] for j in jobs], [j["seed"] for j in jobs])
     # warm: the same kernels (two-pass for the large jobs, the hit queue at full size)
-    small = [min(n, 1 << 25) if n >= 1 << 18 else max(1, n // 100) for n in args[1]]
+    small = [min(n, WAVE_CHUNK) if n >= 1 << 18 else max(1, n // 100) for n in args[1]]
     H.heart_trace_batch(specs, args[0], small, args[2], imgs, stream=stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -437,7 +437,7 @@ def features_measurement(H, W, torch, stream):
 def large_measurement(H, W, torch, stream, sm_mhz):
     """The large single job: von Hamos R = 100 mm, Lorentzian mosaic, elastic +
     inelastic lines, 4096^2 int64 detector, 1e10 rays in one call (streamed by
-    the library in chunks of 2^25 rays), FP32; device-timed."""
+    the library in chunks of 2^26 rays), FP32; device-timed."""
     w = W.von_hamos_large()
     s = H.heart_spectrometer_create(w["spec"])
     img = torch.zeros(s.shape, dtype=torch.int64, device="cuda")
@@ -612,7 +612,7 @@ def main():
                          "traffic_note": "ncu dram__bytes_read+write of the step's launches, per step (hit "
                                          "queue written by the spawn pass and read by the walk pass; "
                                          "captured on one 2^24-ray chunk, scaled by rays)",
-                         "kernel": "k_spawn32 + k_walk32 (two passes per chunk of up to 2^25 rays)",
+                         "kernel": "k_spawn32 + k_walk32 (two passes per chunk of up to 2^26 rays)",
                          "peak_basis": "152 SMs x 4 sub-partitions x 32 lanes x %.0f MHz (the step's median SM "
                                        "clock); algorithmic lane-instructions counted per ray %d, per entered "
                                        "ray %d, per segment %d, per collision %d, per exit %d (bench.py ALGO_*)"

@@ -273,7 +273,7 @@ heart_status heart_spectrometer_destroy(heart_spectrometer *spec);
  * fills the tallies; returns HEART_ELIMIT (after filling) if a ray hit the
  * collision cap.  FP32 image traces (all but user rays with several reflection
  * orders) run in two passes through a hit queue that the library keeps per
- * device for the process (two buffers, up to 7.5 GB, allocated on first use,
+ * device for the process (two buffers, up to 15 GB, allocated on first use,
  * shared by all spectrometers; such traces run one after another on the GPU
  * whatever their streams, each on `stream` and a side stream of the library's
  * that `stream` waits for before the call's work ends). */

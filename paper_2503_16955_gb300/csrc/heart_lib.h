@@ -32,11 +32,11 @@ heart_status launch_fp64(const SpecParams &S, const SourceParams &P, uint64_t n,
                          void *img, unsigned long long *tally, heart_ray_record *rec, cudaStream_t st,
                          const QeParams *qe = nullptr);
 // queue of prepared hits for the two-pass FP32 trace: two buffers of `cap`
-// rays each (a power of two from 2^20 to 2^25; consecutive chunks alternate
+// rays each (a power of two from 2^20 to 2^26; consecutive chunks alternate
 // between them so that a chunk's spawn pass can overlap the previous chunk's
 // walk), one record per hit (96 bytes, 112 for a polarised source), then 2
 // counters per chunk for kWaveGroup chunks
-constexpr uint32_t kWaveMinCap = 1u << 20, kWaveMaxCap = 1u << 25;
+constexpr uint32_t kWaveMinCap = 1u << 20, kWaveMaxCap = 1u << 26;
 constexpr int kWaveGroup = 1024;
 // jobs of at least this many rays (one reflection order) run on the two-pass
 // trace in batches and in the request loop, as single traces do

@@ -138,7 +138,7 @@ def test_multi_chunk_trace_on_two_streams_equals_single_chunk_calls(H):
     import torch
     w = W.von_hamos_hapg()
     s = H.heart_spectrometer_create(w["spec"])
-    chunk = 1 << 25
+    chunk = 1 << 26
     n = 3 * chunk + 12_345
     for stream in (None, torch.cuda.Stream()):
         a = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
