@@ -89,7 +89,9 @@ typedef enum { HEART_FP64 = 0, HEART_FP32 = 1 } heart_precision;
  * (crystallite tilts and azimuths whose |Delta| exceeds the rocking curve's
  * half-width X* at relative level v*): the same distribution of paths as
  * PLAIN, the constant-majorant walk of Sec. 2.2.3-2.2.4, with several times
- * fewer candidates off the Bragg angle. */
+ * fewer candidates off the Bragg angle.  With one reflection order the
+ * candidates that may reflect are drawn in two tilt bands, each at its own bound
+ * of the azimuth measure that reaches the Bragg window (fewer again by half). */
 typedef enum { HEART_SAMPLER_THINNED = 0, HEART_SAMPLER_PLAIN = 1 } heart_sampler;
 typedef enum { HEART_COUNT_I32 = 0, HEART_COUNT_I64 = 1 } heart_count_type;
 
