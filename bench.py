@@ -562,8 +562,10 @@ def main():
     # straight segments: one per entered ray plus one per reflection
     seg_per_ray = ((n - tal["miss"]) + sum(h * c for h, c in enumerate(tal["refl_hist"]))) / n
 
-    # end to end through the C ABI with host buffers (copies inside the call)
-    h_img = np.zeros(spec.shape, dtype=np.int32)
+    # end to end through the C ABI with host buffers (copies inside the call), the image in
+    # pinned host memory
+    h_img_t = torch.zeros(spec.shape, dtype=torch.int32, pin_memory=True)
+    h_img = h_img_t.numpy()
     e2e_steps = max(1, min(args.steps, 5))
     H.heart_trace_host(spec, w["source"], n, w["seed"], offset(2000), h_img, precision="fp32")
     torch.cuda.synchronize()
@@ -622,7 +624,7 @@ def main():
                          "per_pipe": pipes},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": img_bytes,
                     "d2h_bytes_per_step": img_bytes + 27 * 8,
-                    "path": "heart_trace_host (host image uploaded, traced, downloaded each step)"},
+                    "path": "heart_trace_host (pinned host image uploaded, traced, downloaded each step)"},
             "gpu_launches": args.steps * 2 * ((n + WAVE_CHUNK - 1) // WAVE_CHUNK),
             "clocks": clocks,
             "cpu_baseline": cpu,
