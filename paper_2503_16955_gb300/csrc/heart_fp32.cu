@@ -2434,9 +2434,9 @@ static void wave_side(cudaStream_t *side, cudaEvent_t *fork, cudaEvent_t *join);
 template <int GEOM, int IRC, bool POL = false, bool USER = false, bool ORD = false, bool REC = false>
 static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t n, unsigned long long *ctr,
                                   cudaStream_t st) {
-    // 7 blocks per SM (72 registers) for the benchmark's variants; those that carry p
-    // need more registers: 6
-    constexpr int OCC = POL ? 6 : 7;
+    // 6 blocks per SM (80 registers): with the two-band sampler the walk measured 0.6 %
+    // faster than at 7 blocks (72 registers) and 0.4 % faster than at 8 (64 registers, spills)
+    constexpr int OCC = 6;
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk32<GEOM, IRC, OCC, POL, ORD, REC>, kBlockThreads,
