@@ -92,13 +92,13 @@ WAVE_CHUNK = 1 << 26
 # one chunk of 2^24 rays, whose 0.66 GB queue, unlike a smaller one, does not stay in
 # L2) and warp instructions issued per pipe (2^22 rays), both with the library's default
 # launch shape (bench.py --no-tune); valid only for the kernel sources with the hash below.
-TRAFFIC_BYTES_PER_RAY = (0.062208e6 + 612.753664e6 + 675.696896e6 + 0.505088e6) / (1 << 24)   # 2^24 rays
-PIPE_INST_PER_RAY = {"alu": 10.9907, "fma": 13.4408, "fmaheavy": 5.6724, "fmalite": 8.4381, "xu": 1.8272,
-                     "lsu": 1.4369, "adu": 1.5391, "cbu": 2.7317, "uniform": 0.3729, "fp64": 0.0168,
-                     "total": 35.8174}
+TRAFFIC_BYTES_PER_RAY = (0.065792e6 + 612.568576e6 + 675.791872e6 + 0.443392e6) / (1 << 24)   # 2^24 rays
+PIPE_INST_PER_RAY = {"alu": 11.0880, "fma": 13.4344, "fmaheavy": 5.5239, "fmalite": 8.5550, "xu": 1.7616,
+                     "lsu": 1.4368, "adu": 1.5009, "cbu": 2.7335, "uniform": 0.6252, "fp64": 0.0168,
+                     "total": 35.9948}
 TRAFFIC_SOURCES = ("paper_2503_16955_gb300/csrc/heart_fp32.cu", "paper_2503_16955_gb300/csrc/heart_fp64.cuh",
                    "paper_2503_16955_gb300/csrc/heart_internal.h")
-TRAFFIC_SOURCE_HASH = "a27539c273d1b8ca"
+TRAFFIC_SOURCE_HASH = "e50924de66c680eb"
 
 
 def sources_hash():

@@ -2434,8 +2434,9 @@ static void wave_side(cudaStream_t *side, cudaEvent_t *fork, cudaEvent_t *join);
 template <int GEOM, int IRC, bool POL = false, bool USER = false, bool ORD = false, bool REC = false>
 static heart_status launch_wave_t(const Launch32 &L, const WaveBuf &B, uint64_t n, unsigned long long *ctr,
                                   cudaStream_t st) {
-    // 6 blocks per SM (80 registers): with the two-band sampler the walk measured 0.6 %
-    // faster than at 7 blocks (72 registers) and 0.4 % faster than at 8 (64 registers, spills)
+    // launch bound of 6 blocks per SM (up to 80 registers): the benchmark's variant then
+    // uses 72 and 7 blocks still fit (the grid follows the occupancy query); its code ran
+    // 0.6 % faster than under a bound of 7 and 0.4 % faster than under 8 (64 registers)
     constexpr int OCC = 6;
     static int per_sm = 0;
     if (per_sm == 0) {
