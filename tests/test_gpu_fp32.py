@@ -9,7 +9,8 @@ Tolerances (fixed before measuring):
   * line centroid and FWHM of the dispersive profile within 0.1 % of FP64;
   * two-sample chi-square over detector pixels (adjacent pixels of a row
     pooled until the oracle's expected count is >= 5) of the FP32 image
-    against an oracle image traced with another seed: p > 0.01;
+    against an oracle image traced with another seed, with the thinned and
+    with the plain sampler: p > 0.01;
   * two FP32 kernels on the same streams: identical images and tallies.
 """
 import math
@@ -108,6 +109,27 @@ def test_fp32_image_matches_independent_oracle(H, name, n_gpu, n_orc):
     pg, po = g.sum() / n_gpu, o.sum() / n_orc
     sd = math.sqrt(po * (1 - po) / n_orc + pg * (1 - pg) / n_gpu)
     assert abs(pg - po) <= 4.5 * sd
+
+
+@pytest.mark.parametrize("name,n_gpu,n_orc", [("flat_hopg_mono", 8_000_000, 2_000_000),
+                                              ("von_hamos_hapg", 20_000_000, 2_000_000)])
+def test_fp32_thinned_image_matches_plain_oracle(H, name, n_gpu, n_orc):
+    # The FP32 kernels' thinned sampler (process (b) in two tilt bands) against the oracle's
+    # plain constant-majorant walk, which draws every candidate and shares none of the
+    # thinning: the same image distribution (pixel chi-square) and hit fraction
+    import torch
+    w = getattr(W, name)()
+    s = H.heart_spectrometer_create(w["spec"])
+    img = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    H.heart_trace(s, w["source"], n_gpu, 3003, 0, img, precision="fp32")
+    g = img.cpu().numpy().astype(np.int64)
+    s.close()
+    o, _, _ = ob.trace(dict(w["spec"], sampler="plain"), w["source"], n_orc, 4004)
+    p, pools = pixel_chi2(g, o)
+    assert pools >= 50 and p > 0.01, (p, pools)
+    pg, po = g.sum() / n_gpu, o.sum() / n_orc
+    sd = math.sqrt(po * (1 - po) / n_orc + pg * (1 - pg) / n_gpu)
+    assert abs(pg - po) <= 4.5 * sd, (pg, po, sd)
 
 
 def test_fp32_int64_image_and_chunking_invariance(H):
