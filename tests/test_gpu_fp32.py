@@ -112,7 +112,8 @@ def test_fp32_image_matches_independent_oracle(H, name, n_gpu, n_orc):
 
 
 @pytest.mark.parametrize("name,n_gpu,n_orc", [("flat_hopg_mono", 8_000_000, 2_000_000),
-                                              ("von_hamos_hapg", 20_000_000, 2_000_000)])
+                                              ("von_hamos_hapg", 20_000_000, 2_000_000),
+                                              ("von_hamos_large", 20_000_000, 2_000_000)])
 def test_fp32_thinned_image_matches_plain_oracle(H, name, n_gpu, n_orc):
     # The FP32 kernels' thinned sampler (process (b) in two tilt bands) against the oracle's
     # plain constant-majorant walk, which draws every candidate and shares none of the
@@ -120,7 +121,7 @@ def test_fp32_thinned_image_matches_plain_oracle(H, name, n_gpu, n_orc):
     import torch
     w = getattr(W, name)()
     s = H.heart_spectrometer_create(w["spec"])
-    img = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    img = torch.zeros(s.shape, dtype=torch.int64 if s.count_dtype == "int64" else torch.int32, device="cuda")
     H.heart_trace(s, w["source"], n_gpu, 3003, 0, img, precision="fp32")
     g = img.cpu().numpy().astype(np.int64)
     s.close()
