@@ -32,13 +32,14 @@ UNIT = "rays/s"
 # multiply, a compare or select, a shared-memory load), counted operation by operation
 # from the method's steps, item by item:
 ALGO_PER_RAY = {                # every emitted ray
-    "philox_2_blocks": 80,      # 10 rounds x (2 wide multiplies + 2 three-input XORs), twice
-    "uniforms": 8,              # 4 words -> (0, 1): convert + fused multiply-add
+    "philox_block": 40,         # call 0: 10 rounds x (2 wide multiplies + 2 three-input XORs)
+    "uniforms": 8,              # its 4 words -> (0, 1): convert + fused multiply-add
     "cone_direction": 22,       # 1 - cos(phi), sin(phi), sin / cos of the azimuth, k, k.N offset
     "gaussian_spot": 17,        # Box-Muller radius and angle, origin += spot
     "cylinder_entry": 23,       # |o_perp + t k_perp| = R, smallest t > 0, axial and azimuth tests
 }
 ALGO_PER_ENTERED = {            # every ray that enters the crystal
+    "philox_block": 40,         # call 1: the energy's words, drawn for entered rays only
     "entry_anchor": 14,         # |k.N| at the entry minus the cone axis's, as small terms
     "energy_and_bragg": 50,     # component, Gaussian line or 1/E draw, sin(aB) offset, anchor, Q, mu0
 }
@@ -92,13 +93,13 @@ WAVE_CHUNK = 1 << 26
 # one chunk of 2^24 rays, whose 0.66 GB queue, unlike a smaller one, does not stay in
 # L2) and warp instructions issued per pipe (2^22 rays), both with the library's default
 # launch shape (bench.py --no-tune); valid only for the kernel sources with the hash below.
-TRAFFIC_BYTES_PER_RAY = (0.065792e6 + 612.568576e6 + 675.791872e6 + 0.443392e6) / (1 << 24)   # 2^24 rays
-PIPE_INST_PER_RAY = {"alu": 11.0880, "fma": 13.4344, "fmaheavy": 5.5239, "fmalite": 8.5550, "xu": 1.7616,
-                     "lsu": 1.4368, "adu": 1.5009, "cbu": 2.7335, "uniform": 0.6252, "fp64": 0.0168,
-                     "total": 35.9948}
+TRAFFIC_BYTES_PER_RAY = (0.165120e6 + 617.240832e6 + 676.016384e6 + 0.512512e6) / (1 << 24)   # 2^24 rays
+PIPE_INST_PER_RAY = {"alu": 10.9531, "fma": 13.2470, "fmaheavy": 5.3638, "fmalite": 8.5234, "xu": 1.7617,
+                     "lsu": 1.2817, "adu": 1.5328, "cbu": 2.7325, "uniform": 0.6104, "fp64": 0.0168,
+                     "total": 35.6005}
 TRAFFIC_SOURCES = ("paper_2503_16955_gb300/csrc/heart_fp32.cu", "paper_2503_16955_gb300/csrc/heart_fp64.cuh",
                    "paper_2503_16955_gb300/csrc/heart_internal.h")
-TRAFFIC_SOURCE_HASH = "e50924de66c680eb"
+TRAFFIC_SOURCE_HASH = "12e422257558e818"
 
 
 def sources_hash():

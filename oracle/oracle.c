@@ -1311,16 +1311,21 @@ static void source_basis(const double a[3], double b1[3], double b2[3]) {
     cross3(a, b1, b2);
 }
 
+/* Sec. 2.1 draws the source's energy, direction and spot position from
+ * independent uniforms; which Philox word feeds which draw is a convention.
+ * Here a is the ray's first block (call 0): spot radius and angle, 1 - cos(phi)
+ * and the azimuth, i.e. all that the crystal-entry test needs; b is its second
+ * block (call 1): the component, its parameter and the Gaussian line's pair. */
 static void sample_source(const orc_source *src, const double cumw[], const double *tcdf,
                           const double ax[3], const double b1[3], const double b2[3], const uint32_t a[4],
                           const uint32_t b[4], double *E, double o[3], double k[3]) {
-    /* energy: component by cumulative weight, then its parameter */
-    double uc = U(a[0]);
+    /* energy (second block): component by cumulative weight, then its parameter */
+    double uc = U(b[0]);
     int c = src->n_comp - 1;
     for (int i = 0; i < src->n_comp; ++i)
         if (uc < cumw[i]) { c = i; break; }
     const orc_component *cp = &src->comp[c];
-    double up = U(a[1]);
+    double up = U(b[1]);
     switch (cp->kind) {
     case ORC_SRC_MONO: *E = cp->e0_keV; break;
     case ORC_SRC_GAUSS: {
@@ -1346,16 +1351,16 @@ static void sample_source(const orc_source *src, const double cumw[], const doub
     }
     default: *E = NAN;
     }
-    /* direction: uniform in solid angle inside the cone */
+    /* direction (first block): uniform in solid angle inside the cone */
     double hs = sin(0.5 * src->cone_half_angle_rad);
     double w = U(a[2]) * 2.0 * hs * hs;          /* 1 - cos(phi) */
     double cphi = 1.0 - w, sphi = sqrt(w * (2.0 - w));
     double beta = 2.0 * PI * U(a[3]);
     double cb = cos(beta), sb = sin(beta);
     for (int i = 0; i < 3; ++i) k[i] = cphi * ax[i] + sphi * (cb * b1[i] + sb * b2[i]);
-    /* origin: 2-D Gaussian spot in the plane perpendicular to the cone axis */
-    double r = sqrt(-2.0 * log(U(b[0])));
-    double ang = 2.0 * PI * U(b[1]);
+    /* origin (first block): 2-D Gaussian spot in the plane perpendicular to the cone axis */
+    double r = sqrt(-2.0 * log(U(a[0])));
+    double ang = 2.0 * PI * U(a[1]);
     double z1 = r * cos(ang), z2 = r * sin(ang);
     double s1 = src->spot_fwhm_mm[0] / (2.0 * sqrt(2.0 * LN2));
     double s2 = src->spot_fwhm_mm[1] / (2.0 * sqrt(2.0 * LN2));

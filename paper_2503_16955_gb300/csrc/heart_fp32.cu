@@ -386,17 +386,16 @@ __device__ __forceinline__ bool order_anchor(const Launch32 &L, int c, float ds,
 // ---------------------------------------------------------------------------
 // spawn: source sample + entry (Sec. 2.1, Sec. 2.2) in the crystal frame
 // ---------------------------------------------------------------------------
-// The geometric part of a sampled ray: its two Philox blocks, the direction,
-// the origin and the entry.  On a hit x is the entry point and dA is |k.N|
-// there minus its value for the cone axis; a and b keep the words that the
-// energy part uses.
+// The geometric part of a sampled ray: its first Philox block (call 0: spot
+// radius and angle, 1 - cos(phi), azimuth), the direction, the origin and the
+// entry.  On a hit x is the entry point and dA is |k.N| there minus its value
+// for the cone axis.  The energy's words are the second block (call 1), drawn
+// by spawn_energy's callers for the rays that entered only.
 template <int GEOM_T>
-__device__ __forceinline__ bool spawn_entry(const Launch32 &L, uint64_t ray, float x[3], float k[3], float &dA,
-                                            uint32_t a[4], uint32_t b[4]) {
+__device__ __forceinline__ bool spawn_entry(const Launch32 &L, uint64_t ray, float x[3], float k[3], float &dA) {
     const int GEOM = GEOM_T >= 0 ? GEOM_T : L.geometry;
-    const uint32_t rl = (uint32_t)ray, rh = (uint32_t)(ray >> 32);
-    philox_l<(GEOM_T >= 0)>(L, rl, rh, 0u, 0u, a);
-    philox_l<(GEOM_T >= 0)>(L, rl, rh, 1u, 0u, b);
+    uint32_t a[4];
+    philox_l<(GEOM_T >= 0)>(L, (uint32_t)ray, (uint32_t)(ray >> 32), 0u, 0u, a);
     // direction, uniform in solid angle in the cone; dn = k.n_ref - axis.n_ref
     const float w = u01_32(a[2]) * L.omc;                 // 1 - cos(phi)
     const float sphi = sqrtf(w * (2.0f - w));
@@ -408,9 +407,9 @@ __device__ __forceinline__ bool spawn_entry(const Launch32 &L, uint64_t ray, flo
     const float dn = __fmaf_rn(p2, L.b2[ni], __fmaf_rn(p1, L.b1[ni], -w * L.ax[ni]));
     float o[3] = {L.o[0], L.o[1], L.o[2]};
     if (L.sig1 > 0.0f || L.sig2 > 0.0f) {
-        const float r = sqrtf(-2.0f * __logf(u01_32(b[0])));
+        const float r = sqrtf(-2.0f * __logf(u01_32(a[0])));
         float s, co;
-        sincos_2pi(u01_32(b[1]), &s, &co);
+        sincos_2pi(u01_32(a[1]), &s, &co);
         const float z1 = L.sig1 * r * co, z2 = L.sig2 * r * s;
         for (int i = 0; i < 3; ++i) o[i] = __fmaf_rn(z2, L.b2[i], __fmaf_rn(z1, L.b1[i], o[i]));
     }
@@ -446,19 +445,20 @@ __device__ __forceinline__ bool spawn_entry(const Launch32 &L, uint64_t ray, flo
     return true;
 }
 
-// The energy part of a ray that entered (words a0, a1 of its first Philox
-// block, b2, b3 of its second; dA from spawn_entry): spectral component and
+// The energy part of a ray that entered (the words e0 .. e3 of its second
+// Philox block: component, the component's parameter, the Gaussian line's
+// pair; dA from spawn_entry): spectral component and
 // energy, as a small offset from the component's reference energy so that
 // sin(aB) keeps ~1e-9 accuracy, the Bragg anchor and the rates.  False if the
 // energy is not positive and finite (the ray counts as a miss).
-__device__ __forceinline__ bool spawn_energy(const Launch32 &L, uint32_t a0, uint32_t a1, uint32_t b2, uint32_t b3,
+__device__ __forceinline__ bool spawn_energy(const Launch32 &L, uint32_t e0w, uint32_t e1w, uint32_t e2w, uint32_t e3w,
                                              float dA, float &A, float &sB, float &mu0, float &qr, float &inv_ws,
                                              float &E32, int &nb, float *oA = nullptr, float *osB = nullptr,
                                              int *nbm = nullptr) {
     int c = L.n_comp - 1;
     for (int i = 0; i < L.n_comp - 1; ++i)
-        if (a0 < L.comp_thr[i]) { c = i; break; }
-    const float up = u01_32(a1);
+        if (e0w < L.comp_thr[i]) { c = i; break; }
+    const float up = u01_32(e1w);
     float E, ds;                                          // ds = sin(aB(E)) - sin(aB(e_ref))
     const float e0 = L.e_ref[c], s0 = L.sB_raw[c];
     switch (L.kind[c]) {
@@ -486,7 +486,7 @@ __device__ __forceinline__ bool spawn_energy(const Launch32 &L, uint32_t a0, uin
     case HEART_SRC_TABLE: {
         // the interval with thr_i <= word < thr_i+1 (the FP64 path's decision
         // u < C_i taken exactly on the word), then linear inside it
-        const unsigned long long wv = a1;
+        const unsigned long long wv = e1w;
         int lo = 0, hi = L.n_tab - 1;
         while (hi - lo > 1) {
             const int m = (lo + hi) >> 1;
@@ -502,8 +502,8 @@ __device__ __forceinline__ bool spawn_energy(const Launch32 &L, uint32_t a0, uin
     default: {
         float dE;
         if (L.kind[c] == HEART_SRC_GAUSS) {
-            const float co = -__cosf(6.28318530717958648f * (u01_32(b3) - 0.5f));   // cos(2 pi u), as sincos_2pi
-            dE = L.width[c] * sqrtf(-2.0f * __logf(u01_32(b2))) * co;
+            const float co = -__cosf(6.28318530717958648f * (u01_32(e3w) - 0.5f));  // cos(2 pi u), as sincos_2pi
+            dE = L.width[c] * sqrtf(-2.0f * __logf(u01_32(e2w))) * co;
         } else if (L.kind[c] == HEART_SRC_LORENTZ) {
             const float uu = __fmaf_rn(up, 1.0f - L.lF0[c], L.lF0[c]);
             dE = 0.5f * L.width[c] * tanf(3.14159265f * (uu - 0.5f));
@@ -561,10 +561,11 @@ template <int GEOM_T>
 __device__ __forceinline__ bool spawn(const Launch32 &L, uint64_t ray, float x[3], float k[3], float &A,
                                       float &sB, float &mu0, float &qr, float &inv_ws, float &E32, int &nb,
                                       float *oA = nullptr, float *osB = nullptr, int *nbm = nullptr) {
-    uint32_t a[4], b[4];
     float dA;
-    if (!spawn_entry<GEOM_T>(L, ray, x, k, dA, a, b)) return false;
-    return spawn_energy(L, a[0], a[1], b[2], b[3], dA, A, sB, mu0, qr, inv_ws, E32, nb, oA, osB, nbm);
+    if (!spawn_entry<GEOM_T>(L, ray, x, k, dA)) return false;
+    uint32_t e[4];
+    philox_l<(GEOM_T >= 0)>(L, (uint32_t)ray, (uint32_t)(ray >> 32), 1u, 0u, e);
+    return spawn_energy(L, e[0], e[1], e[2], e[3], dA, A, sB, mu0, qr, inv_ws, E32, nb, oA, osB, nbm);
 }
 
 // user-supplied ray: read, move to the crystal frame and enter in FP64 (once
@@ -1805,13 +1806,13 @@ __device__ __forceinline__ float4 *wave_rec(const WaveBuf &B, size_t slot) {
 // that the walk counts as a miss.  Emitted rays and misses are tallied by the
 // walk pass from count and the queue length.
 constexpr int kSpawnThreads = 256, kSpawnWarps = kSpawnThreads / 32;
-// staged entered rays: sampled sources keep dA and the energy words (a0 a1 b2
-// b3); user-supplied rays, set up in full by spawn_user, keep A in dA and sB,
-// mu0, qr, inv_ws in the word slots, with E and no_bragg beside them
+// staged entered rays: sampled sources keep dA (the set-up draws the energy's
+// Philox block from the ray id); user-supplied rays, set up in full by
+// spawn_user, keep A in dA and sB, mu0, qr, inv_ws in u, with E and no_bragg
 template <bool POL, bool USER>
 struct SpawnStage {
     float x[3][kSpawnThreads], k[3][kSpawnThreads], dA[kSpawnThreads];
-    uint32_t a0[kSpawnThreads], a1[kSpawnThreads], b2[kSpawnThreads], b3[kSpawnThreads];
+    float u[4][USER ? kSpawnThreads : 1];
     uint32_t idx[kSpawnThreads];
     float p[3][POL ? kSpawnThreads : 1];                 // polarisation (polarised sources, user rays)
     float e[USER ? kSpawnThreads : 1];
@@ -1834,19 +1835,15 @@ __global__ void __launch_bounds__(kSpawnThreads, (USER || ORD) ? 4 : 8) k_spawn3
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     {
         float x[3], k[3], dA = 0.0f, pv[3] = {0.0f, 0.0f, 0.0f};
-        uint32_t a[4], b[4];
+        float uw[4] = {0.f, 0.f, 0.f, 1.f};
         float uE = 0.0f;
         int unb = 0;
         bool hit;
         if (USER) {
             // the ray's own origin, direction, energy and polarisation, entered in FP64
-            float A = 0.f, sB = 0.f, mu0 = 0.f, qr = 0.f, inv_ws = 1.f;
-            hit = i < count && spawn_user<GEOM>(L, first + i, x, k, pv, A, sB, mu0, qr, inv_ws, uE, unb);
-            dA = A;
-            a[0] = __float_as_uint(sB); a[1] = __float_as_uint(mu0);
-            b[2] = __float_as_uint(qr); b[3] = __float_as_uint(inv_ws);
+            hit = i < count && spawn_user<GEOM>(L, first + i, x, k, pv, dA, uw[0], uw[1], uw[2], uw[3], uE, unb);
         } else {
-            hit = i < count && spawn_entry<GEOM>(L, L.offset + first + i, x, k, dA, a, b);
+            hit = i < count && spawn_entry<GEOM>(L, L.offset + first + i, x, k, dA);
             if (POL && hit) project_pol32(L, k, pv);
         }
         const unsigned hm = __ballot_sync(0xffffffffu, hit);
@@ -1871,7 +1868,8 @@ __global__ void __launch_bounds__(kSpawnThreads, (USER || ORD) ? 4 : 8) k_spawn3
             const unsigned j = s_ofs[warp] + __popc(hm & ((1u << lane) - 1u));
             for (int m = 0; m < 3; ++m) { sg.x[m][j] = x[m]; sg.k[m][j] = k[m]; }
             sg.dA[j] = dA;
-            sg.a0[j] = a[0]; sg.a1[j] = a[1]; sg.b2[j] = b[2]; sg.b3[j] = b[3];
+            if (USER)
+                for (int m = 0; m < 4; ++m) sg.u[m][USER ? j : 0] = uw[m];
             sg.idx[j] = threadIdx.x;
             if (POL)
                 for (int m = 0; m < 3; ++m) sg.p[m][POL ? j : 0] = pv[m];
@@ -1887,12 +1885,15 @@ __global__ void __launch_bounds__(kSpawnThreads, (USER || ORD) ? 4 : 8) k_spawn3
     bool ok = true;
     if (USER) {
         A = sg.dA[j];
-        sB = __uint_as_float(sg.a0[j]); mu0 = __uint_as_float(sg.a1[j]);
-        qr = __uint_as_float(sg.b2[j]); inv_ws = __uint_as_float(sg.b3[j]);
+        sB = sg.u[0][USER ? j : 0]; mu0 = sg.u[1][USER ? j : 0];
+        qr = sg.u[2][USER ? j : 0]; inv_ws = sg.u[3][USER ? j : 0];
         E32 = sg.e[USER ? j : 0];
         nb = sg.nb[USER ? j : 0];
     } else {
-        ok = spawn_energy(L, sg.a0[j], sg.a1[j], sg.b2[j], sg.b3[j], sg.dA[j], A, sB, mu0, qr, inv_ws, E32, nb,
+        uint32_t e[4];
+        const uint64_t ray = L.offset + first + (uint64_t)blockIdx.x * blockDim.x + sg.idx[j];
+        philox_l<(GEOM >= 0)>(L, (uint32_t)ray, (uint32_t)(ray >> 32), 1u, 0u, e);
+        ok = spawn_energy(L, e[0], e[1], e[2], e[3], sg.dA[j], A, sB, mu0, qr, inv_ws, E32, nb,
                           ORD ? oA : nullptr, ORD ? osB : nullptr, ORD ? &nbm : nullptr);
     }
     Lane t;

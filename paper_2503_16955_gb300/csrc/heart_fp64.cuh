@@ -477,12 +477,14 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
     philox4x32_10(rl, rh, 0u, 0u, k0, k1, a);
     philox4x32_10(rl, rh, 1u, 0u, k0, k1, b);
 
+    // a: call 0, the spot and the direction (all the entry test needs); b: call 1,
+    // the energy's words (Sec. 2.1 draws them as independent uniforms)
     // energy (Sec. 2.1): component by cumulative weight, then its parameter
-    const double uc = u01_64(a[0]);
+    const double uc = u01_64(b[0]);
     int c = P.n_comp - 1;
     for (int i = 0; i < P.n_comp; ++i)
         if (uc < P.cumw[i]) { c = i; break; }
-    const double up = u01_64(a[1]);
+    const double up = u01_64(b[1]);
     switch (P.kind[c]) {
     case HEART_SRC_MONO: E = P.e0[c]; break;
     case HEART_SRC_GAUSS:
@@ -514,8 +516,8 @@ __device__ inline void trace_ray64(const SpecParams &S, const SourceParams &P, u
     const double cb = cos(beta), sb = sin(beta);
     for (int i = 0; i < 3; ++i) k[i] = cphi * P.ax[i] + sphi * (cb * P.b1[i] + sb * P.b2[i]);
     // Gaussian spot
-    const double rr = sqrt(-2.0 * log(u01_64(b[0])));
-    const double ang = kTwoPi * u01_64(b[1]);
+    const double rr = sqrt(-2.0 * log(u01_64(a[0])));
+    const double ang = kTwoPi * u01_64(a[1]);
     const double z1 = rr * cos(ang), z2 = rr * sin(ang);
     for (int i = 0; i < 3; ++i) o[i] = P.origin[i] + P.sig1 * z1 * P.b1[i] + P.sig2 * z2 * P.b2[i];
     if (P.pol_on) pol = project_pol64(P.pol, k, pv);
