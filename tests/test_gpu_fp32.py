@@ -4,8 +4,10 @@ against the FP64 kernel on the same Philox streams, against each other, and
 against an independent-stream oracle image.
 
 Tolerances (fixed before measuring):
-  * outcome flips (outcome or reflection count differs) <= 1e-4 of rays;
-  * for rays with the same outcome, detector hit positions within 1 um;
+  * decision flips (outcome, reflection count or tentative-collision count
+    differs: a ray that reflects at another collision took another decision
+    even when its outcome and reflection count agree) <= 1e-4 of rays;
+  * for rays with the same decisions, detector hit positions within 1 um;
   * line centroid and FWHM of the dispersive profile within 0.1 % of FP64;
   * two-sample chi-square over detector pixels (adjacent pixels of a row
     pooled until the oracle's expected count is >= 5) of the FP32 image
@@ -70,7 +72,7 @@ def test_fp32_same_stream_against_fp64(H, name, n):
     w = getattr(W, name)()
     r64, t64, r32, t32 = _pair(H, w["spec"], w["source"], n, w["seed"])
     assert np.array_equal(r64["ray_id"], r32["ray_id"])
-    flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"])
+    flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"]) | (r64["ncoll"] != r32["ncoll"])
     assert flip.mean() <= 1e-4, (int(flip.sum()), n)
     same = ~flip & (r64["det_hit"] == 1) & (r32["det_hit"] == 1)
     assert same.sum() > 100
@@ -86,8 +88,8 @@ def test_fp32_same_stream_against_fp64(H, name, n):
     assert abs(c32 - c64) <= 1e-3 * max(abs(c64), 0.5 * w["spec"]["det_nx"] * px)
     assert abs(f32 - f64) <= 1e-3 * f64 + 1e-9
     # tallies of the same streams agree up to the flipped rays
-    for k in ("emitted", "miss"):
-        assert t32[k] == t64[k]
+    assert t32["emitted"] == t64["emitted"]
+    assert abs(t32["miss"] - t64["miss"]) <= int(((r64["outcome"] == 0) != (r32["outcome"] == 0)).sum())
     assert abs(t32["det_hits"] - t64["det_hits"]) <= int(flip.sum())
     assert abs(t32["collisions"] - t64["collisions"]) <= 1e-4 * t64["collisions"] + 100 * flip.sum()
 

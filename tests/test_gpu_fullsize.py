@@ -56,7 +56,7 @@ def test_flat_hopg_full_workload_fp64_and_fp32(H):
     assert np.all(np.abs(g["u_mm"][hit] - o["u_mm"][hit]) <= 1e-9 * np.maximum(1, np.abs(o["u_mm"][hit])))
     assert gt == ot
     g32, t32 = H.heart_trace_records(s, w["source"], w["n_rays"], w["seed"], 0, precision="fp32")
-    flips = ((g32["outcome"] != o["outcome"]) | (g32["nrefl"] != o["nrefl"])).mean()
+    flips = ((g32["outcome"] != o["outcome"]) | (g32["nrefl"] != o["nrefl"]) | (g32["ncoll"] != o["ncoll"])).mean()
     assert flips <= 1e-4
     s.close()
 
@@ -91,7 +91,7 @@ def test_von_hamos_benchmark_step_full_size(H):
         _, _, o = ob.trace(w["spec"], w["source"], size, w["seed"], ray_offset=s0, records=True)
         assert np.array_equal(g["ray_id"], np.arange(s0, s0 + size, dtype=np.uint64))
         assert np.array_equal(f64["outcome"], o["outcome"]) and np.array_equal(f64["nrefl"], o["nrefl"])
-        same = (g["outcome"] == f64["outcome"]) & (g["nrefl"] == f64["nrefl"])
+        same = (g["outcome"] == f64["outcome"]) & (g["nrefl"] == f64["nrefl"]) & (g["ncoll"] == f64["ncoll"])
         flips += int((~same).sum())
         total += size
         both = same & (g["det_hit"] == 1) & (f64["det_hit"] == 1)
@@ -122,7 +122,7 @@ def test_large_job_int64_image_streamed_chunk(H):
     assert t["det_hits"] == int(img.sum())
     flips = total = 0
     for g, o in _windows(H, s, w, [3 * n, 3 * n + 500_000_000], 5_000, "fp32"):
-        flips += int(((g["outcome"] != o["outcome"]) | (g["nrefl"] != o["nrefl"])).sum())
+        flips += int(((g["outcome"] != o["outcome"]) | (g["nrefl"] != o["nrefl"]) | (g["ncoll"] != o["ncoll"])).sum())
         total += len(g)
     assert flips <= max(1, 1e-4 * total)
     s.close()

@@ -85,7 +85,7 @@ def test_fp32_energy_table_follows_fp64(H):
     r64, t64 = H.heart_trace_records(s, w["source"], n, 6, 0, precision="fp64")
     r32, t32 = H.heart_trace_records(s, w["source"], n, 6, 0, precision="fp32")
     s.close()
-    flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"])
+    flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"]) | (r64["ncoll"] != r32["ncoll"])
     assert flip.sum() <= max(2, 1e-4 * n), int(flip.sum())
     same = ~flip & (r64["det_hit"] == 1) & (r32["det_hit"] == 1)
     assert same.sum() > 100
@@ -102,7 +102,7 @@ def _fp32_vs_fp64(H, spec, src, n, seed, min_hits=100):
     r64, t64 = H.heart_trace_records(s, src, n, seed, 0, precision="fp64")
     r32, t32 = H.heart_trace_records(s, src, n, seed, 0, precision="fp32")
     s.close()
-    flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"])
+    flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"]) | (r64["ncoll"] != r32["ncoll"])
     assert flip.sum() <= max(2, 1e-4 * n), int(flip.sum())
     same = ~flip & (r64["det_hit"] == 1) & (r32["det_hit"] == 1)
     assert same.sum() >= min_hits, int(same.sum())
@@ -183,7 +183,7 @@ def test_fp32_orders_user_rays(H, polarised):
     r64, t64 = H.heart_trace_rays(s, rays, 10, 0, None, precision="fp64", records=True)
     r32, t32 = H.heart_trace_rays(s, rays, 10, 0, None, precision="fp32", records=True)
     s.close()
-    flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"])
+    flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"]) | (r64["ncoll"] != r32["ncoll"])
     assert flip.sum() <= max(2, 1e-4 * n), int(flip.sum())
     same = ~flip & (r64["det_hit"] == 1) & (r32["det_hit"] == 1)
     assert same.sum() > 5

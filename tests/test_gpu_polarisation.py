@@ -106,7 +106,7 @@ def test_fp64_polarised_source_replays_oracle(H, name):
 
 def _fp32_vs_fp64(r64, r32, n):
     assert np.array_equal(r64["ray_id"], r32["ray_id"])
-    flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"])
+    flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"]) | (r64["ncoll"] != r32["ncoll"])
     assert flip.sum() <= max(1e-4 * n, 2), (int(flip.sum()), n)
     same = ~flip & (r64["det_hit"] == 1) & (r32["det_hit"] == 1)
     assert same.sum() > 100
@@ -126,7 +126,9 @@ def test_fp32_polarised_source_follows_fp64(H, name):
     r32, t32 = H.heart_trace_records(s, src, n, 6, 0, precision="fp32")
     s.close()
     _fp32_vs_fp64(r64, r32, n)
-    assert t32["emitted"] == t64["emitted"] and t32["miss"] == t64["miss"]
+    # sampled rays enter in FP32 (an edge ray can flip): misses agree up to those flips
+    assert t32["emitted"] == t64["emitted"]
+    assert abs(t32["miss"] - t64["miss"]) <= int(((r64["outcome"] == 0) != (r32["outcome"] == 0)).sum())
 
 
 @pytest.mark.parametrize("name", ["flat_hopg_mono", "von_hamos_hapg"])

@@ -63,12 +63,14 @@ def test_fp32_table_source_follows_fp64(H):
     s.close()
     entered = r64["outcome"] != 0
     assert np.abs(r64["energy_keV"][entered] - r32["energy_keV"][entered]).max() <= 2e-6
-    flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"])
+    flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"]) | (r64["ncoll"] != r32["ncoll"])
     assert flip.sum() <= 1e-4 * n
     same = ~flip & (r64["det_hit"] == 1) & (r32["det_hit"] == 1)
     assert same.sum() > 100
     assert np.abs(r64["u_mm"][same] - r32["u_mm"][same]).max() <= 1e-3
-    assert t32["miss"] == t64["miss"]
+    # entry is decided in FP32 (a ray at the crystal's edge can flip): misses agree up
+    # to the rays whose miss status flipped, which the flip budget counts
+    assert abs(t32["miss"] - t64["miss"]) <= int(((r64["outcome"] == 0) != (r32["outcome"] == 0)).sum())
 
 
 def test_two_knot_table_equals_uniform_component_fp64(H):
