@@ -290,6 +290,48 @@ def test_conservation_and_thread_and_shard_invariance():
     assert sum(t1["refl_hist"]) == n - t1["miss"]
 
 
+def test_source_words_come_from_their_philox_blocks():
+    # Sec. 2.1 draws energy, direction and spot as independent uniforms; which Philox
+    # word feeds which draw is a convention: call 0 holds the spot's radius and angle
+    # and the direction's 1 - cos(phi) and azimuth, call 1 the component, its parameter
+    # and the Gaussian line's pair.  Checked on each ray against the published
+    # generator's words (counter = (ray, 0, call, 0), key = seed), with the crystal
+    # turned away so that every record keeps the sampled origin, direction and energy.
+    s = flat(normal=[0.0, 0.0, -1.0])
+    axis = np.array([0.3, -0.2, 0.9])
+    axis /= np.linalg.norm(axis)
+    origin = np.array([1.0, 2.0, 3.0])
+    fwhm, half = 0.8, 0.05
+    comps = [dict(kind="uniform", lo_keV=7.0, hi_keV=7.2, weight=0.3),
+             dict(kind="uniform", lo_keV=9.0, hi_keV=9.4, weight=0.7)]
+    src = dict(components=comps, origin_mm=origin.tolist(), axis=axis.tolist(),
+               cone_half_angle_rad=half, spot_fwhm_mm=(fwhm, fwhm))
+    n, seed = 3000, 0x1234_5678_9ABC
+    _, tal, rec = ob.trace(s, src, n, seed=seed, records=True)
+    assert tal["miss"] == n
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    sigma = fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    one_minus_cos = 2.0 * math.sin(0.5 * half) ** 2
+
+    def u(w):
+        return (w + 0.5) / 2.0 ** 32
+
+    for i in range(n):
+        a = ob.philox((i, 0, 0, 0), key)
+        b = ob.philox((i, 0, 1, 0), key)
+        # energy: component by word 0 of call 1 against the cumulative weight, then
+        # uniform on its range by word 1
+        lo, hi = (7.0, 7.2) if u(b[0]) < 0.3 else (9.0, 9.4)
+        assert rec["energy_keV"][i] == pytest.approx(lo + (hi - lo) * u(b[1]), rel=1e-13)
+        # direction: 1 - cos(phi) is uniform on [0, 1 - cos(half-angle)] by word 2 of call 0
+        k = rec["dir"][i]
+        assert 1.0 - float(np.dot(k, axis)) == pytest.approx(u(a[2]) * one_minus_cos, rel=1e-9, abs=1e-14)
+        # spot (circular): the offset's length is the Box-Muller radius of word 0 of call 0
+        d = rec["pos"][i] - origin
+        assert abs(float(np.dot(d, axis))) <= 1e-12
+        assert float(np.dot(d, d)) / sigma ** 2 == pytest.approx(-2.0 * math.log(u(a[0])), rel=1e-9, abs=1e-12)
+
+
 def test_source_sampling_distributions():
     # crystal turned away from the source: every ray misses and its record keeps
     # the sampled origin, direction and energy
