@@ -348,7 +348,7 @@ heart_status heart_trace_batch(heart_spectrometer *const *specs, const heart_sou
 /* Launch shape of the FP32 kernels chosen by heart_autotune. */
 typedef struct {
     int32_t blocks_per_sm;          /* persistent kernel: resident 128-thread blocks per SM, 6 (80
-                                       registers) or 5 (96) */
+                                       registers) or 5 (96; the default before any autotune) */
     int32_t refill_lanes;           /* a warp takes queued or spawned rays when this many lanes are idle */
     uint32_t max_chunk_rays;        /* largest work item (rays) a block of the persistent kernel claims */
     int32_t reserved;

@@ -18,7 +18,9 @@ constexpr int kCounterWord = 32;     // first work-counter word
 struct TuneConfig {
     int refill = 8;                    // pop new rays when this many lanes of a warp are idle
     uint32_t chunk_rays = 1u << 16;    // largest work item (rays) claimed by a block
-    int blocks_per_sm = 6;             // register budget: 6 (80 registers) or 5 (96 registers)
+    // register budget: 6 (80 registers) or 5 (96 registers); 5 is what the autotuner picked on
+    // every benchmark run (the all-persistent 64-job batch: 1.25e10 rays/s against 8.8e9 at 6)
+    int blocks_per_sm = 5;
 };
 extern TuneConfig g_tune;
 
