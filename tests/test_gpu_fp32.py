@@ -155,6 +155,34 @@ def test_fp32_int64_image_and_chunking_invariance(H):
                              ta["exit_side"] + ta["capped"] + ta["stuck"])
 
 
+def test_fp32_empty_single_ray_and_ragged_traces(H):
+    # the two-pass trace at its edges: no rays, one ray, ray counts that leave a ragged
+    # last spawn block (257, 4097: one and 16 blocks of 256 plus one ray), and a range
+    # of ray ids that crosses 2^32 (the counter's high word), ray by ray against FP64
+    import torch
+    w = W.von_hamos_hapg()
+    s = H.heart_spectrometer_create(w["spec"])
+    img = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+    t = H.heart_trace(s, w["source"], 0, 3, 0, img, precision="fp32")
+    assert t["emitted"] == 0 and t["det_hits"] == 0 and int(img.abs().sum()) == 0
+    for n, off in ((1, 0), (1, 12345), (257, 0), (4097, 0), (4097, (1 << 32) - 2000)):
+        r64, t64 = H.heart_trace_records(s, w["source"], n, 3, off, precision="fp64")
+        r32, t32 = H.heart_trace_records(s, w["source"], n, 3, off, precision="fp32")
+        assert np.array_equal(r32["ray_id"], np.arange(off, off + n, dtype=np.uint64))
+        assert t32["emitted"] == n == (t32["miss"] + t32["absorbed"] + t32["exit_front"] + t32["exit_back"] +
+                                        t32["exit_side"] + t32["capped"] + t32["stuck"])
+        flip = (r64["outcome"] != r32["outcome"]) | (r64["nrefl"] != r32["nrefl"]) | (r64["ncoll"] != r32["ncoll"])
+        assert flip.sum() <= 1, (n, off, int(flip.sum()))
+        same = ~flip & (r64["det_hit"] == 1) & (r32["det_hit"] == 1)
+        if same.any():
+            assert np.abs(r64["u_mm"][same] - r32["u_mm"][same]).max() <= 1e-3
+        # the image path of the same rays bins exactly the records' hits
+        img = torch.zeros(s.shape, dtype=torch.int32, device="cuda")
+        ti = H.heart_trace(s, w["source"], n, 3, off, img, precision="fp32")
+        assert ti == t32 and int(img.sum()) == int((r32["det_hit"] == 1).sum())
+    s.close()
+
+
 def test_multi_chunk_trace_on_two_streams_equals_single_chunk_calls(H):
     # a trace of more than one hit-queue chunk alternates between the queue's two buffers
     # and between the caller's stream and the library's side stream; the same rays traced
