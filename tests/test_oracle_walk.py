@@ -330,6 +330,15 @@ def test_source_words_come_from_their_philox_blocks():
         d = rec["pos"][i] - origin
         assert abs(float(np.dot(d, axis))) <= 1e-12
         assert float(np.dot(d, d)) / sigma ** 2 == pytest.approx(-2.0 * math.log(u(a[0])), rel=1e-9, abs=1e-12)
+    # ray ids across 2^32: the counter's first two words are the id's low and high halves
+    off = (1 << 32) - 100
+    _, _, rec = ob.trace(s, src, 200, seed=seed, ray_offset=off, records=True)
+    for i in range(200):
+        ray = off + i
+        assert int(rec["ray_id"][i]) == ray
+        b = ob.philox((ray & 0xFFFFFFFF, ray >> 32, 1, 0), key)
+        lo, hi = (7.0, 7.2) if u(b[0]) < 0.3 else (9.0, 9.4)
+        assert rec["energy_keV"][i] == pytest.approx(lo + (hi - lo) * u(b[1]), rel=1e-13)
 
 
 def test_source_sampling_distributions():
