@@ -91,6 +91,38 @@ def test_batch_large_jobs_equal_their_single_traces(H):
         s.close()
 
 
+def test_batch_with_empty_and_single_ray_jobs(H):
+    # degenerate jobs inside one batch call: jobs of no rays leave their images and
+    # tallies untouched, a one-ray job traces its one ray, and the other jobs equal
+    # the batch of themselves alone
+    import torch
+    jobs = _mix(5, 77, (1e4, 1e5))
+    jobs[0]["n_rays"] = 0
+    jobs[2]["n_rays"] = 1
+    jobs[4]["n_rays"] = 0
+    specs = [H.heart_spectrometer_create(j["spec"]) for j in jobs]
+    imgs = [_img(H, s, torch) for s in specs]
+    for i in (0, 4):
+        imgs[i].fill_(7)
+    tall = H.heart_trace_batch(specs, [j["source"] for j in jobs], [j["n_rays"] for j in jobs],
+                               [j["seed"] for j in jobs], imgs)
+    for i in (0, 4):
+        assert int((imgs[i] != 7).sum()) == 0
+        assert all(v == 0 for k, v in tall[i].items() if k != "refl_hist") and not any(tall[i]["refl_hist"])
+    t = tall[2]
+    assert t["emitted"] == 1 == (t["miss"] + t["absorbed"] + t["exit_front"] + t["exit_back"] + t["exit_side"] +
+                                 t["capped"] + t["stuck"])
+    assert int(imgs[2].sum()) == t["det_hits"] <= 1
+    rest = [1, 2, 3]
+    sim = [_img(H, specs[i], torch) for i in rest]
+    ts = H.heart_trace_batch([specs[i] for i in rest], [jobs[i]["source"] for i in rest],
+                             [jobs[i]["n_rays"] for i in rest], [jobs[i]["seed"] for i in rest], sim)
+    for k, i in enumerate(rest):
+        assert torch.equal(sim[k], imgs[i]) and ts[k] == tall[i], i
+    for s in specs:
+        s.close()
+
+
 def test_server_results_identical_alone_and_in_the_mix(H):
     import torch
     jobs = _mix(10, 44, (5e4, 2e6))
